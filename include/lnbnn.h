@@ -1,0 +1,183 @@
+/*
+ * lnbnn.h -- C ABI of the GB300 Local Naive Bayes Nearest Neighbor library.
+ *
+ * Method: McCann & Lowe, "Local Naive Bayes Nearest Neighbor for Image
+ * Classification".  Original NBNN is Alg. 1 (Section 1) with the decision
+ * rule of Eq. (eqn:nbnn) (Section 3); Local NBNN is Alg. 2 (Section 4).
+ *
+ * Conventions for every call:
+ *   - Descriptors are 128-dimensional uint8, row-major, 128 bytes per row.
+ *   - Unless a name ends in _host, every array argument is a DEVICE pointer
+ *     (cudaMalloc / PyTorch CUDA storage) owned by the caller; the library
+ *     never frees or keeps it beyond the call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device calls are asynchronous on that stream: argument
+ *     errors are returned at once; a device-side timeout is recorded in the
+ *     index and returned by lnbnn_sync().  Until it is collected, search
+ *     kernels of that index skip their work, so results of calls made between
+ *     the timeout and lnbnn_sync() are invalid.
+ *   - Distances are exact squared Euclidean distances of the raw uint8
+ *     values, as int32; totals are exact int64 sums.
+ *   - Neighbours are ordered by (distance, reference row) ascending, so equal
+ *     distances go to the lower row of the reference set given to create.
+ *   - Calls on one index share its workspace: issue them on one stream, or
+ *     serialise them; two calls on one index that overlap on the GPU race.
+ *   - No call throws; every failure is a status code.
+ */
+#ifndef LNBNN_H
+#define LNBNN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define LNBNN_API __attribute__((visibility("default")))
+#else
+#define LNBNN_API
+#endif
+
+#define LNBNN_DIM 128
+/* largest neighbourhood size k (the search keeps k + 1 neighbours) */
+#define LNBNN_MAX_K 255
+
+typedef struct lnbnn_index lnbnn_index;
+
+typedef enum lnbnn_status {
+  LNBNN_OK = 0,
+  LNBNN_ERR_INVALID_ARG = 1,  /* null pointer, negative size, bad handle */
+  LNBNN_ERR_LABEL_RANGE = 2,  /* a label outside [0, n_classes) */
+  LNBNN_ERR_EMPTY_CLASS = 3,  /* a class with no reference (NN_C undefined) */
+  LNBNN_ERR_K_RANGE = 4,      /* k < 1, k > LNBNN_MAX_K or k + 1 > n_ref */
+  LNBNN_ERR_OOM = 5,          /* device allocation failed */
+  LNBNN_ERR_CUDA = 6,         /* a CUDA runtime call or launch failed */
+  LNBNN_ERR_TIMEOUT = 7,      /* a bounded device wait expired */
+  LNBNN_ERR_UNSUPPORTED = 8,  /* device is not compute capability 10.3 (sm_103) */
+  LNBNN_ERR_OFFSETS = 9       /* offsets not 0 = o[0] <= ... <= o[n_images] = n_queries */
+} lnbnn_status;
+
+/*
+ * Build the merged reference index of Alg. 2 ("a nearest neighbor index
+ * comprising all descriptors" plus the class lookup Class(p), Section 4; the
+ * class of each descriptor stored beside it, Section 5.1).  The same index
+ * also serves original NBNN (Alg. 1), which needs NN_C for every class.
+ *
+ *   ref      device uint8 [n_ref * 128], row j = reference descriptor j
+ *   labels   device int32 [n_ref], labels[j] = class of row j, in [0, n_classes)
+ *   n_ref    >= 1;  n_classes >= 1
+ *   stream   work is issued on it; the call synchronises it before returning
+ *   out      receives the handle (set to NULL on failure)
+ *
+ * The index copies what it needs (an exact BF16 operand copy, squared norms,
+ * labels, a class-sorted copy when the labels are not already grouped), so
+ * the caller may free ref and labels afterwards.  Device memory: about
+ * 3 * 128 * n_ref bytes (plus as much again when labels are not sorted).
+ * Errors: INVALID_ARG, LABEL_RANGE, OOM, CUDA, UNSUPPORTED.  A class with no
+ * reference is accepted here; nbnn_classify then returns EMPTY_CLASS.
+ */
+LNBNN_API lnbnn_status lnbnn_index_create(const uint8_t *ref, const int32_t *labels, int64_t n_ref,
+                                int32_t n_classes, void *stream, lnbnn_index **out);
+
+/* Release the index and all device memory it owns.  NULL is accepted. */
+LNBNN_API void lnbnn_index_destroy(lnbnn_index *index);
+
+/* Sizes of an index (any output pointer may be NULL). */
+LNBNN_API lnbnn_status lnbnn_index_info(const lnbnn_index *index, int64_t *n_ref, int32_t *n_classes);
+
+/*
+ * NN(d, k) of Alg. 2 for every query descriptor: the k nearest references in
+ * the merged set, exact, ordered by (distance, reference row).
+ *
+ *   queries   device uint8 [n_queries * 128]
+ *   k         1 <= k <= LNBNN_MAX_K, k <= n_ref
+ *   idx       device int32 [n_queries * k], row-major, reference rows
+ *   dist      device int32 [n_queries * k], exact squared distances
+ * n_queries = 0 is a no-op.  Errors: INVALID_ARG, K_RANGE, OOM, CUDA, TIMEOUT.
+ */
+LNBNN_API lnbnn_status knn_search(lnbnn_index *index, const uint8_t *queries, int64_t n_queries, int32_t k,
+                        int32_t *idx, int32_t *dist, void *stream);
+
+/*
+ * LocalNBNN(Q, k), Alg. 2, for a batch of query images.  For each descriptor
+ * d of image i: {p_1..p_{k+1}} = NN(d, k+1); dist_B = ||d - p_{k+1}||^2; for
+ * each class C among p_1..p_k, dist_C = min ||d - p_j||^2 over those of class
+ * C, and totals[i][C] += dist_C - dist_B.  classes[i] = argmin_C totals[i][C]
+ * (lowest class on ties).  The background-class discount is the one Section 4
+ * describes: classes not among the k nearest are not updated.
+ *
+ *   queries   device uint8 [n_queries * 128], all images' descriptors, flattened
+ *   offsets   device int64 [n_images + 1]; image i owns rows offsets[i] ..
+ *             offsets[i+1]-1; offsets[0] = 0, nondecreasing, offsets[n_images] = n_queries
+ *   k         1 <= k <= LNBNN_MAX_K and k + 1 <= n_ref
+ *   totals    device int64 [n_images * n_classes] (overwritten; every entry <= 0)
+ *   classes   device int32 [n_images]
+ * An image with no descriptors gets all-zero totals and class 0.  Invalid
+ * offsets are detected on the device and reported as OFFSETS by lnbnn_sync.
+ * Errors: INVALID_ARG, K_RANGE, OOM, CUDA, TIMEOUT, OFFSETS.
+ */
+LNBNN_API lnbnn_status lnbnn_classify(lnbnn_index *index, const uint8_t *queries, int64_t n_queries,
+                            const int64_t *offsets, int64_t n_images, int32_t k, int64_t *totals,
+                            int32_t *classes, void *stream);
+
+/*
+ * NBNN(Q), Alg. 1: totals[i][C] = sum over descriptors d of image i of
+ * ||d - NN_C(d)||^2, classes[i] = argmin_C totals[i][C] (lowest class on
+ * ties); the rule of Eq. (eqn:nbnn).  Arguments as lnbnn_classify without k.
+ * Errors: as lnbnn_classify, plus EMPTY_CLASS when a class has no reference.
+ */
+LNBNN_API lnbnn_status nbnn_classify(lnbnn_index *index, const uint8_t *queries, int64_t n_queries,
+                           const int64_t *offsets, int64_t n_images, int64_t *totals,
+                           int32_t *classes, void *stream);
+
+/*
+ * Host-buffer forms of the two classifiers: queries, offsets, totals and
+ * classes are HOST pointers.  The call copies the inputs to the device
+ * (into the index's device staging buffer), classifies, copies the
+ * results back and synchronises `stream` before returning.  Pinned (page-locked)
+ * host buffers give the fastest copies.
+ */
+LNBNN_API lnbnn_status lnbnn_classify_host(lnbnn_index *index, const uint8_t *queries, int64_t n_queries,
+                                 const int64_t *offsets, int64_t n_images, int32_t k,
+                                 int64_t *totals, int32_t *classes, void *stream);
+LNBNN_API lnbnn_status nbnn_classify_host(lnbnn_index *index, const uint8_t *queries, int64_t n_queries,
+                                const int64_t *offsets, int64_t n_images, int64_t *totals,
+                                int32_t *classes, void *stream);
+
+/*
+ * Wait for `stream`, then report (and clear) any device-side error recorded
+ * for this index since the last report: TIMEOUT when a bounded wait inside a
+ * kernel expired, OFFSETS when a classify call got invalid offsets.
+ */
+LNBNN_API lnbnn_status lnbnn_sync(lnbnn_index *index, void *stream);
+
+/*
+ * Device-time profile of an index's calls (an aid for measurement; no part
+ * of the method).  While enabled, every classify / search call records CUDA
+ * events on its own stream around its phases: "search" is the exact search
+ * kernel (the tensor-core k+1 nearest-neighbour kernel, or the per-class
+ * NBNN kernel); "other" is everything else the call launches (query
+ * preparation, split merge, class update, argmin).  lnbnn_profile_read waits
+ * for the recorded events and returns the sums since the last enable.
+ * kernel_launches counts every kernel the library launched in those calls.
+ */
+typedef struct lnbnn_profile {
+  int64_t calls;
+  int64_t kernel_launches;
+  int64_t search_launches;
+  double search_ms;
+  double other_ms;
+} lnbnn_profile;
+
+LNBNN_API lnbnn_status lnbnn_profile_enable(lnbnn_index *index, int enable);
+LNBNN_API lnbnn_status lnbnn_profile_read(lnbnn_index *index, lnbnn_profile *out);
+
+/* Static English text for a status code. */
+LNBNN_API const char *lnbnn_status_string(lnbnn_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LNBNN_H */

@@ -1,0 +1,92 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Nothing here is part of the C ABI (see include/lnbnn.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lnbnn.h"
+
+namespace lnbnn {
+
+constexpr int kDim = LNBNN_DIM;
+// A list slot with no neighbour yet; sorts after every real (distance, row) key.
+constexpr uint64_t kEmptyKey = ~0ull;
+// Squared norm given to padding rows of the reference operand: larger than any
+// real squared distance (<= 128 * 255^2 = 8,323,200) plus its query norm, and
+// exactly representable in fp32, so a padding row never enters a top-k list
+// while real rows remain.
+constexpr float kPadNorm = 33554432.0f;  // 2^25
+// Reference rows are padded to a multiple of this (the widest reference tile).
+constexpr int kRefPad = 256;
+// Query rows are padded to a multiple of this (the query tile of every kernel).
+constexpr int kQueryPad = 128;
+
+// Bits of the per-index device error word.
+enum : uint32_t { kDevErrTimeout = 1u, kDevErrOffsets = 2u };
+
+// Neighbour key: (squared distance, reference row) packed so that one unsigned
+// compare orders by distance first, then by the lower row.
+__host__ __device__ __forceinline__ uint64_t make_key(uint32_t dist, uint32_t row) {
+  return (static_cast<uint64_t>(dist) << 32) | row;
+}
+__host__ __device__ __forceinline__ uint32_t key_dist(uint64_t k) { return static_cast<uint32_t>(k >> 32); }
+__host__ __device__ __forceinline__ uint32_t key_row(uint64_t k) { return static_cast<uint32_t>(k); }
+
+// ----------------------------------------------------------- kernels (launchers)
+// Each launcher returns cudaGetLastError() after the launch.
+
+// Reference preparation: exact BF16 copy (rows padded to n_pad with zeros) and
+// squared norms as fp32 (padding rows get kPadNorm).
+cudaError_t launch_prep_ref(const uint8_t* ref, int64_t n_ref, int64_t n_pad, __nv_bfloat16* ref_bf,
+                            float* rnorm, cudaStream_t s);
+// Query preparation: squared norms (int32) and, when qbf != nullptr, the BF16
+// operand -2q (rows padded to m_pad with zeros).
+cudaError_t launch_prep_query(const uint8_t* q, int64_t m, int64_t m_pad, int32_t* qnorm,
+                              __nv_bfloat16* qbf, cudaStream_t s);
+// Label histogram; sets *bad when a label is outside [0, C).
+cudaError_t launch_label_hist(const int32_t* labels, int64_t n, int32_t C, unsigned long long* counts,
+                              uint32_t* bad, cudaStream_t s);
+// Gather rows: dst[i] = src[perm[i]] for uint8 descriptors, bf16 operand rows, norms, labels.
+cudaError_t launch_gather_ref(const int64_t* perm, int64_t n, const uint8_t* src_u8, uint8_t* dst_u8,
+                              const __nv_bfloat16* src_bf, __nv_bfloat16* dst_bf, const float* src_norm,
+                              float* dst_norm, const int32_t* src_lab, int32_t* dst_lab, cudaStream_t s);
+
+// dst[0..n) = v
+cudaError_t launch_fill_float(float* dst, int64_t n, float v, cudaStream_t s);
+
+// Exact top-(K1) search on CUDA cores: lists[split][row][0..K1) sorted keys.
+cudaError_t launch_knn_simt(const uint8_t* q, int64_t m, const int32_t* qnorm, const uint8_t* ref,
+                            const float* rnorm, int64_t n_ref, int splits, int64_t split_len, int K1,
+                            uint64_t* lists, int64_t list_stride_rows, cudaStream_t s);
+
+// Merge `splits` sorted lists per row into one sorted list of K1 keys.
+cudaError_t launch_merge_lists(const uint64_t* lists, int splits, int64_t m, int64_t list_stride_rows,
+                               int K1, uint64_t* out, cudaStream_t s);
+// knn_search output: first k entries of each sorted list as (row, distance).
+cudaError_t launch_extract_knn(const uint64_t* lists, int64_t m, int K1, int k, int32_t* idx,
+                               int32_t* dist, cudaStream_t s);
+// Alg. 2 per-descriptor update: totals[img][C] += dist_C - dist_B.
+cudaError_t launch_lnbnn_score(const uint64_t* lists, int64_t m, int K1, int k, const int32_t* labels,
+                               const int64_t* offsets, int64_t n_img, int32_t C, int64_t* totals,
+                               uint32_t* dev_err, cudaStream_t s);
+// Offsets validation (0 = o[0] <= ... <= o[n_img] = m); flags kDevErrOffsets.
+cudaError_t launch_check_offsets(const int64_t* offsets, int64_t n_img, int64_t m, uint32_t* dev_err,
+                                 cudaStream_t s);
+// argmin over classes per image, lowest class on ties.
+cudaError_t launch_argmin(const int64_t* totals, int64_t n_img, int32_t C, int32_t* classes, cudaStream_t s);
+
+// Original NBNN on CUDA cores over the class-sorted reference copy.  Class
+// group g covers classes [group_cls[g], group_cls[g+1]).
+struct ClassGroups {
+  static constexpr int kMax = 64;
+  int32_t n;
+  int32_t cls[kMax + 1];
+};
+cudaError_t launch_nbnn_simt(const uint8_t* q, int64_t m, const int32_t* qnorm, const uint8_t* sref,
+                             const float* srnorm, const int32_t* slabels, const int64_t* class_off,
+                             const ClassGroups& groups, const int64_t* offsets, int64_t n_img, int32_t C,
+                             int64_t* totals, cudaStream_t s);
+
+}  // namespace lnbnn

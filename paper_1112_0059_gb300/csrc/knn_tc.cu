@@ -1,0 +1,302 @@
+// Exact k+1 nearest-neighbour search (the NN(d, k+1) of Alg. 2) on the sm_103a
+// tensor cores.
+//
+// For a tile of 128 query rows and 256 reference rows the MMA computes
+// acc[i][j] = sum_t (-2 q_it) r_jt in FP32; with BF16 operands holding the exact
+// integers 0..255 (and -2q), every product and partial sum is an integer of
+// magnitude below 2^24, so acc is exact.  The epilogue adds ||r_j||^2 and tests
+// acc + ||r_j||^2 < threshold - ||q_i||^2, i.e. ||q_i - r_j||^2 below the row's
+// current (k+1)-th distance; the distance matrix never leaves the SM.
+//
+// Roles (one CTA = 128 query rows x one reference split):
+//   warp 0, one thread : TMA producer (query tile once, reference K-chunks into a ring)
+//   warp 1, one thread : tcgen05.mma issuer; warp 1 also owns the TMEM allocation
+//   warps 2-5          : epilogue, one thread per query row (TMEM lane), two
+//                        256-column FP32 accumulators in flight
+// Every wait is bounded; on expiry the CTA records a timeout in the index's
+// device error word, drains what it issued and returns.
+#include <cudaTypedefs.h>
+
+#include "knn_tc.cuh"
+#include "sm103.cuh"
+#include "topk.cuh"
+
+namespace lnbnn {
+namespace {
+
+using namespace sm103;
+
+constexpr int kBM = 128;                  // query rows per CTA (MMA M)
+constexpr int kBN = kTcRefTile;           // reference rows per tile (MMA N)
+constexpr int kBK = 64;                   // K elements per 128-byte swizzle row
+constexpr int kKChunks = kDim / kBK;      // 2
+constexpr int kUmmaK = 16;                // K per tcgen05.mma (kind::f16)
+constexpr int kStages = 4;                // reference ring depth (K-chunks)
+constexpr uint32_t kAChunkBytes = kBM * kBK * 2;   // 16 KB
+constexpr uint32_t kBStageBytes = kBN * kBK * 2;   // 32 KB
+constexpr int kEpiWarps = 4;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr uint32_t kAccCols = kBN;        // FP32 columns per accumulator
+constexpr uint32_t kTmemCols = 2 * kAccCols;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
+
+constexpr uint32_t kOffA = 0;
+constexpr uint32_t kOffB = kOffA + kKChunks * kAChunkBytes;
+constexpr uint32_t kOffBar = kOffB + kStages * kBStageBytes;
+constexpr int kNumBars = 2 * kStages + 2 + 2 + 2;  // full, empty, tmem full, tmem empty, A, drain
+constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;
+constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;  // + alignment slack
+
+constexpr float kNoThreshold = 3.0e38f;
+
+struct Bars {
+  uint32_t base;
+  __device__ uint32_t full(int s) const { return base + 8 * s; }
+  __device__ uint32_t empty(int s) const { return base + 8 * (kStages + s); }
+  __device__ uint32_t tfull(int b) const { return base + 8 * (2 * kStages + b); }
+  __device__ uint32_t tempty(int b) const { return base + 8 * (2 * kStages + 2 + b); }
+  __device__ uint32_t afull() const { return base + 8 * (2 * kStages + 4); }
+  __device__ uint32_t drain() const { return base + 8 * (2 * kStages + 5); }
+};
+
+__device__ __forceinline__ void flag_timeout(volatile uint32_t* abort_flag, uint32_t* dev_err) {
+  *abort_flag = 1u;
+  atomicOr(dev_err, kDevErrTimeout);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    knn_tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_r,
+                  const int32_t* __restrict__ qnorm, const float* __restrict__ rnorm, int64_t m, int64_t n_ref,
+                  int64_t split_len, int K1, uint64_t* __restrict__ lists, int64_t stride,
+                  uint32_t* __restrict__ dev_err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = smem_u32(smem);
+  const Bars bars{sbase + kOffBar};
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffMisc);
+  volatile uint32_t* abort_flag = tmem_slot + 1;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * kBM;
+  const int64_t j_begin = (int64_t)blockIdx.y * split_len;
+  const int64_t j_end = min(j_begin + split_len, n_ref);
+  const int ntiles = (int)((j_end - j_begin + kBN - 1) / kBN);
+  // A timeout reported earlier and not yet collected by lnbnn_sync: do no work.
+  if (*reinterpret_cast<volatile uint32_t*>(dev_err) & kDevErrTimeout) return;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(bars.full(s), 1);
+      mbar_init(bars.empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bars.tfull(b), 1);
+      mbar_init(bars.tempty(b), 32 * kEpiWarps);
+    }
+    mbar_init(bars.afull(), 1);
+    mbar_init(bars.drain(), 1);
+    *abort_flag = 0u;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ producer
+      prefetch_tmap(&tmap_q);
+      prefetch_tmap(&tmap_r);
+      mbar_arrive_expect_tx(bars.afull(), kKChunks * kAChunkBytes);
+      for (int kc = 0; kc < kKChunks; ++kc)
+        tma_load_2d(sbase + kOffA + kc * kAChunkBytes, &tmap_q, kc * kBK, (int32_t)m0, bars.afull());
+      int it = 0;
+      for (int t = 0; t < ntiles && !*abort_flag; ++t) {
+        for (int kc = 0; kc < kKChunks; ++kc, ++it) {
+          const int s = it % kStages;
+          const uint32_t round = (uint32_t)(it / kStages);
+          if (!mbar_wait(bars.empty(s), (round & 1u) ^ 1u, kWaitLimitNs, abort_flag)) {
+            flag_timeout(abort_flag, dev_err);
+            break;
+          }
+          mbar_arrive_expect_tx(bars.full(s), kBStageBytes);
+          tma_load_2d(sbase + kOffB + s * kBStageBytes, &tmap_r, kc * kBK, (int32_t)(j_begin + (int64_t)t * kBN),
+                      bars.full(s));
+        }
+      }
+      // every load issued must land before the CTA may exit
+      const uint32_t never = 0;
+      mbar_wait(bars.afull(), 0, kWaitLimitNs, &never);
+      for (int s = 0; s < kStages; ++s) {
+        const int issued = it / kStages + (s < it % kStages ? 1 : 0);
+        if (issued > 0) mbar_wait(bars.full(s), (uint32_t)((issued - 1) & 1), kWaitLimitNs, &never);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------------------------------------------------- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16_f32(kBM, kBN);
+      bool ok = mbar_wait(bars.afull(), 0, kWaitLimitNs, abort_flag);
+      if (!ok) flag_timeout(abort_flag, dev_err);
+      tc_fence_after();
+      int it = 0;
+      for (int t = 0; ok && t < ntiles && !*abort_flag; ++t) {
+        const int b = t & 1;
+        const uint32_t use = (uint32_t)(t >> 1);
+        if (!mbar_wait(bars.tempty(b), (use & 1u) ^ 1u, kWaitLimitNs, abort_flag)) {
+          flag_timeout(abort_flag, dev_err);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + b * kAccCols;
+        for (int kc = 0; kc < kKChunks; ++kc, ++it) {
+          const int s = it % kStages;
+          const uint32_t round = (uint32_t)(it / kStages);
+          if (!mbar_wait(bars.full(s), round & 1u, kWaitLimitNs, abort_flag)) {
+            flag_timeout(abort_flag, dev_err);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = sbase + kOffA + kc * kAChunkBytes;
+          const uint32_t b_base = sbase + kOffB + s * kBStageBytes;
+#pragma unroll
+          for (int kk = 0; kk < kBK / kUmmaK; ++kk) {
+            mma_bf16(d_tmem, sw128_kmajor_desc(a_base + kk * 32), sw128_kmajor_desc(b_base + kk * 32), idesc,
+                     (kc | kk) != 0 ? 1u : 0u);
+          }
+          mma_commit(bars.empty(s));
+        }
+        if (ok) mma_commit(bars.tfull(b));
+      }
+      // all MMAs issued by this thread must finish before TMEM is released
+      const uint32_t never = 0;
+      mma_commit(bars.drain());
+      mbar_wait(bars.drain(), 0, kWaitLimitNs, &never);
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    const int quarter = warp & 3;  // this warp may read TMEM lanes [32*quarter, 32*quarter+32)
+    const int64_t row = m0 + quarter * 32 + lane;
+    const bool active = row < m;
+    const int32_t qn = active ? qnorm[row] : 0;
+    TopK top(lists + ((int64_t)blockIdx.y * stride + (active ? row : 0)) * K1, K1);
+    float thr = kNoThreshold;  // acc + ||r||^2 must be below this
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    for (int t = 0; t < ntiles; ++t) {
+      const int b = t & 1;
+      const uint32_t use = (uint32_t)(t >> 1);
+      if (!mbar_wait(bars.tfull(b), use & 1u, kWaitLimitNs, abort_flag)) {
+        flag_timeout(abort_flag, dev_err);
+        break;
+      }
+      tc_fence_after();
+      const int64_t jt = j_begin + (int64_t)t * kBN;
+      const float4* rn4 = reinterpret_cast<const float4*>(rnorm + jt);
+#pragma unroll 1
+      for (int c = 0; c < kBN / 32; ++c) {
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(tmem_base + lane_addr + b * kAccCols + c * 32, v);
+        float rn[32];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 r = __ldg(rn4 + c * 8 + q);
+          rn[4 * q + 0] = r.x;
+          rn[4 * q + 1] = r.y;
+          rn[4 * q + 2] = r.z;
+          rn[4 * q + 3] = r.w;
+        }
+        tmem_ld_wait();
+        float d[32];
+        bool hit = false;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          d[j] = __uint_as_float(v[j]) + rn[j];
+          hit |= d[j] < thr;
+        }
+        hit = hit && active;
+        if (__any_sync(0xffffffffu, hit)) {
+          if (hit) {
+            // rare path: a local copy keeps the hot loop's d[] in registers
+            float dl[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) dl[j] = d[j];
+#pragma unroll 1
+            for (int j = 0; j < 32; ++j) {
+              if (dl[j] < thr) {
+                const uint32_t dist = (uint32_t)((int32_t)dl[j] + qn);
+                top.push(make_key(dist, (uint32_t)(jt + c * 32 + j)));
+                if (top.size == top.cap) thr = (float)(top.threshold - qn);
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(bars.tempty(b));
+    }
+    if (active) top.finish();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// BF16 [rows, 128] row-major, boxes of 64 x box_rows with the 128-byte swizzle.
+bool encode_bf16_rows(CUtensorMap* map, const void* base, uint64_t rows, uint32_t box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t gdim[2] = {(cuuint64_t)kDim, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)kDim * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
+  cuuint32_t estride[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box, estride,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool make_tc_tensor_maps(const __nv_bfloat16* ref_bf, const __nv_bfloat16* sref_bf, int64_t n_pad, TcTensorMaps* out) {
+  return encode_bf16_rows(&out->ref, ref_bf, (uint64_t)n_pad, kBN) &&
+         encode_bf16_rows(&out->sref, sref_bf, (uint64_t)n_pad, kBN);
+}
+
+cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf, int64_t m,
+                          int64_t m_pad, const int32_t* qnorm, const float* rnorm, int64_t n_ref, int splits,
+                          int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
+                          cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  if (m_pad % kBM != 0 || split_len % kBN != 0) return cudaErrorInvalidValue;
+  CUtensorMap tq;
+  if (!encode_bf16_rows(&tq, qbf, (uint64_t)m_pad, kBM)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)(m_pad / kBM), (unsigned)splits);
+  knn_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(tq, sorted_copy ? maps.sref : maps.ref, qnorm, rnorm, m, n_ref,
+                                                   split_len, K1, lists, stride, dev_err);
+  return cudaGetLastError();
+}
+
+}  // namespace lnbnn

@@ -1,0 +1,558 @@
+// The C ABI of include/lnbnn.h: index ownership, argument checks, workspace
+// and the launch sequence of each call.  All arithmetic runs in the kernels.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+#include "knn_tc.cuh"
+
+using namespace lnbnn;
+
+struct lnbnn_index {
+  int device = 0;
+  int sm_count = 0;
+  int64_t n_ref = 0;
+  int64_t n_pad = 0;
+  int32_t n_classes = 0;
+  // merged reference set, caller's row order
+  uint8_t* ref_u8 = nullptr;
+  __nv_bfloat16* ref_bf = nullptr;  // [n_pad, 128] exact BF16 copy, zero padding rows
+  float* rnorm = nullptr;           // [n_pad] squared norms, kPadNorm on padding rows
+  int32_t* labels = nullptr;        // [n_ref]
+  // class-sorted view (aliases the above when the labels are already grouped)
+  bool sorted = true;
+  uint8_t* sref_u8 = nullptr;
+  __nv_bfloat16* sref_bf = nullptr;
+  float* srnorm = nullptr;
+  int32_t* slabels = nullptr;
+  std::vector<int64_t> class_off_h;  // [C+1]
+  int64_t* class_off_d = nullptr;
+  bool has_empty_class = false;
+  uint32_t* dev_err = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* stage = nullptr;  // device staging for the _host calls
+  size_t stage_bytes = 0;
+  TcTensorMaps tc;  // tensor maps over ref_bf / sref_bf for the tensor-core kernels
+  // optional device-time profile (lnbnn_profile_enable)
+  struct CallEvents {
+    cudaEvent_t e[4];
+  };
+  bool prof_on = false;
+  lnbnn_profile prof{};
+  std::vector<CallEvents> prof_pending, prof_free;
+};
+
+namespace {
+
+#define CK(call)                                       \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return status_of(e_);       \
+  } while (0)
+
+lnbnn_status status_of(cudaError_t e) {
+  if (e == cudaSuccess) return LNBNN_OK;
+  if (e == cudaErrorMemoryAllocation) return LNBNN_ERR_OOM;
+  (void)cudaGetLastError();
+  return LNBNN_ERR_CUDA;
+}
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+template <typename T>
+cudaError_t dmalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void free_index(lnbnn_index* ix) {
+  if (!ix) return;
+  for (auto* v : {&ix->prof_pending, &ix->prof_free})
+    for (auto& ce : *v)
+      for (cudaEvent_t e : ce.e) cudaEventDestroy(e);
+  if (!ix->sorted) {
+    cudaFree(ix->sref_u8);
+    cudaFree(ix->sref_bf);
+    cudaFree(ix->srnorm);
+    cudaFree(ix->slabels);
+  }
+  cudaFree(ix->ref_u8);
+  cudaFree(ix->ref_bf);
+  cudaFree(ix->rnorm);
+  cudaFree(ix->labels);
+  cudaFree(ix->class_off_d);
+  cudaFree(ix->dev_err);
+  cudaFree(ix->ws);
+  cudaFree(ix->stage);
+  delete ix;
+}
+
+// Carves aligned sub-buffers out of one allocation.
+struct Carve {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    const size_t at = off;
+    off += count * sizeof(T);
+    return at;
+  }
+};
+
+// Events of one call: e[0] start, e[1] before the search kernel, e[2] after
+// it, e[3] end.  Inactive unless profiling is enabled on the index.
+struct CallProfile {
+  lnbnn_index* ix;
+  cudaStream_t s;
+  lnbnn_index::CallEvents ev{};
+  bool on;
+  int marked = 0;
+  CallProfile(lnbnn_index* i, cudaStream_t st) : ix(i), s(st), on(i->prof_on) {
+    if (!on) return;
+    if (!ix->prof_free.empty()) {
+      ev = ix->prof_free.back();
+      ix->prof_free.pop_back();
+    } else {
+      for (auto& e : ev.e)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+          on = false;
+          return;
+        }
+    }
+    mark(0);
+  }
+  void mark(int i) {
+    if (on && cudaEventRecord(ev.e[i], s) == cudaSuccess) marked |= 1 << i;
+  }
+  void launched(int n, bool search = false) {
+    if (!on) return;
+    ix->prof.kernel_launches += n;
+    if (search) ix->prof.search_launches += n;
+  }
+  ~CallProfile() {
+    if (!on) return;
+    mark(3);
+    if (marked == 15) {
+      ix->prof_pending.push_back(ev);
+      ix->prof.calls += 1;
+    } else {
+      ix->prof_free.push_back(ev);
+    }
+  }
+};
+
+cudaError_t ensure(void** buf, size_t* have, size_t need) {
+  if (*have >= need) return cudaSuccess;
+  if (*buf) {
+    cudaError_t e = cudaFree(*buf);  // synchronises the device
+    *buf = nullptr;
+    *have = 0;
+    if (e != cudaSuccess) return e;
+  }
+  need = (need + (1u << 20) - 1) & ~size_t((1u << 20) - 1);
+  cudaError_t e = cudaMalloc(buf, need);
+  if (e == cudaSuccess) *have = need;
+  return e;
+}
+
+bool k_ok(const lnbnn_index* ix, int32_t k, int extra) {
+  return k >= 1 && k <= LNBNN_MAX_K && (int64_t)k + extra <= ix->n_ref;
+}
+
+// Number of reference splits so that query tiles x splits fill the GPU.
+int choose_splits(const lnbnn_index* ix, int64_t m_pad) {
+  const int64_t tiles = m_pad / kQueryPad;
+  const int64_t want = 2 * (int64_t)ix->sm_count;
+  int64_t s = tiles >= want ? 1 : (want + tiles - 1) / tiles;
+  s = std::min<int64_t>(s, std::max<int64_t>(1, ix->n_ref / 4096));
+  s = std::min<int64_t>(s, 32);
+  return (int)std::max<int64_t>(s, 1);
+}
+
+struct KnnPlan {
+  int64_t m_pad;
+  int splits;
+  int64_t split_len;
+  int K1;
+  size_t off_qnorm, off_qbf, off_lists, off_merged, bytes;
+};
+
+KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, bool tensor) {
+  KnnPlan p{};
+  p.m_pad = round_up(m, kQueryPad);
+  p.K1 = K1;
+  p.splits = choose_splits(ix, p.m_pad);
+  const int64_t tile = tensor ? kTcRefTile : kRefPad;
+  p.split_len = round_up((ix->n_ref + p.splits - 1) / p.splits, tile);
+  p.splits = (int)((ix->n_ref + p.split_len - 1) / p.split_len);
+  Carve c;
+  p.off_qnorm = c.take<int32_t>(p.m_pad);
+  p.off_qbf = tensor ? c.take<__nv_bfloat16>(p.m_pad * kDim) : 0;
+  p.off_lists = c.take<uint64_t>((size_t)p.splits * p.m_pad * K1);
+  p.off_merged = p.splits > 1 ? c.take<uint64_t>((size_t)p.m_pad * K1) : p.off_lists;
+  p.bytes = c.off;
+  return p;
+}
+
+bool use_tensor_cores() {
+  const char* v = getenv("LNBNN_KNN_KERNEL");  // development switch: "simt" selects the CUDA-core search
+  return !(v && strcmp(v, "simt") == 0);
+}
+
+// Runs the exact search; *lists receives m sorted lists of K1 keys.
+lnbnn_status run_knn(lnbnn_index* ix, const uint8_t* q, int64_t m, int K1, cudaStream_t s, const uint64_t** lists,
+                     CallProfile& prof) {
+  const bool tensor = use_tensor_cores();
+  KnnPlan p = plan_knn(ix, m, K1, tensor);
+  CK(ensure(&ix->ws, &ix->ws_bytes, p.bytes));
+  char* ws = static_cast<char*>(ix->ws);
+  int32_t* qnorm = reinterpret_cast<int32_t*>(ws + p.off_qnorm);
+  __nv_bfloat16* qbf = tensor ? reinterpret_cast<__nv_bfloat16*>(ws + p.off_qbf) : nullptr;
+  uint64_t* part = reinterpret_cast<uint64_t*>(ws + p.off_lists);
+  uint64_t* merged = reinterpret_cast<uint64_t*>(ws + p.off_merged);
+  CK(launch_prep_query(q, m, p.m_pad, qnorm, qbf, s));
+  prof.launched(1);
+  prof.mark(1);
+  if (tensor) {
+    CK(launch_knn_tc(ix->tc, /*sorted_copy=*/false, qbf, m, p.m_pad, qnorm, ix->rnorm, ix->n_ref, p.splits,
+                     p.split_len, K1, part, p.m_pad, ix->dev_err, s));
+  } else {
+    CK(launch_knn_simt(q, m, qnorm, ix->ref_u8, ix->rnorm, ix->n_ref, p.splits, p.split_len, K1, part, p.m_pad, s));
+  }
+  prof.launched(1, true);
+  prof.mark(2);
+  if (p.splits > 1) {
+    CK(launch_merge_lists(part, p.splits, m, p.m_pad, K1, merged, s));
+    prof.launched(1);
+  }
+  *lists = merged;
+  return LNBNN_OK;
+}
+
+ClassGroups make_groups(const lnbnn_index* ix, int64_t m) {
+  ClassGroups g{};
+  const int64_t tiles = round_up(m, kQueryPad) / kQueryPad;
+  const int64_t want = 2 * (int64_t)ix->sm_count;
+  int64_t G = tiles >= want ? 1 : (want + tiles - 1) / tiles;
+  G = std::min<int64_t>(G, ix->n_classes);
+  G = std::min<int64_t>(G, ClassGroups::kMax);
+  G = std::max<int64_t>(G, 1);
+  // contiguous class groups of about n_ref / G references each
+  g.cls[0] = 0;
+  int n = 0;
+  const int64_t target = (ix->n_ref + G - 1) / G;
+  int64_t acc = 0;
+  for (int32_t c = 0; c < ix->n_classes; ++c) {
+    acc += ix->class_off_h[c + 1] - ix->class_off_h[c];
+    if (acc >= target && n + 1 < G && c + 1 < ix->n_classes) {
+      g.cls[++n] = c + 1;
+      acc = 0;
+    }
+  }
+  g.cls[++n] = ix->n_classes;
+  g.n = n;
+  return g;
+}
+
+bool device_ok(int* sm_count, int* dev) {
+  if (cudaGetDevice(dev) != cudaSuccess) return false;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, *dev) != cudaSuccess) return false;
+  *sm_count = prop.multiProcessorCount;
+  return prop.major == 10 && prop.minor == 3;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lnbnn_status_string(lnbnn_status st) {
+  switch (st) {
+    case LNBNN_OK: return "ok";
+    case LNBNN_ERR_INVALID_ARG: return "invalid argument";
+    case LNBNN_ERR_LABEL_RANGE: return "label outside [0, n_classes)";
+    case LNBNN_ERR_EMPTY_CLASS: return "a class has no reference descriptor";
+    case LNBNN_ERR_K_RANGE: return "k out of range (need 1 <= k <= LNBNN_MAX_K and k + 1 <= n_ref)";
+    case LNBNN_ERR_OOM: return "device out of memory";
+    case LNBNN_ERR_CUDA: return "CUDA error";
+    case LNBNN_ERR_TIMEOUT: return "device wait timed out";
+    case LNBNN_ERR_UNSUPPORTED: return "unsupported device (needs compute capability 10.3)";
+    case LNBNN_ERR_OFFSETS: return "invalid image offsets";
+  }
+  return "unknown status";
+}
+
+lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64_t n_ref, int32_t n_classes,
+                                void* stream, lnbnn_index** out) {
+  if (!out) return LNBNN_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!ref || !labels || n_ref < 1 || n_classes < 1 || n_ref > (int64_t)INT32_MAX - kRefPad)
+    return LNBNN_ERR_INVALID_ARG;
+  int sm = 0, dev = 0;
+  if (!device_ok(&sm, &dev)) return LNBNN_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  lnbnn_index* ix = new (std::nothrow) lnbnn_index();
+  if (!ix) return LNBNN_ERR_OOM;
+  ix->device = dev;
+  ix->sm_count = sm;
+  ix->n_ref = n_ref;
+  ix->n_pad = round_up(n_ref, kRefPad);
+  ix->n_classes = n_classes;
+  lnbnn_status st = LNBNN_OK;
+  unsigned long long* counts = nullptr;
+  uint32_t* bad = nullptr;
+  int64_t* perm_d = nullptr;
+  auto fail = [&](lnbnn_status e) {
+    cudaFree(counts);
+    cudaFree(bad);
+    cudaFree(perm_d);
+    free_index(ix);
+    return e;
+  };
+#define CKF(call)                                   \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return fail(status_of(e_)); \
+  } while (0)
+  CKF(dmalloc(&ix->ref_u8, (size_t)n_ref * kDim));
+  CKF(dmalloc(&ix->ref_bf, (size_t)ix->n_pad * kDim));
+  CKF(dmalloc(&ix->rnorm, (size_t)ix->n_pad));
+  CKF(dmalloc(&ix->labels, (size_t)n_ref));
+  CKF(dmalloc(&ix->dev_err, 1));
+  CKF(dmalloc(&counts, (size_t)n_classes));
+  CKF(dmalloc(&bad, 1));
+  CKF(cudaMemsetAsync(ix->dev_err, 0, sizeof(uint32_t), s));
+  CKF(cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * n_classes, s));
+  CKF(cudaMemsetAsync(bad, 0, sizeof(uint32_t), s));
+  CKF(cudaMemcpyAsync(ix->ref_u8, ref, (size_t)n_ref * kDim, cudaMemcpyDeviceToDevice, s));
+  CKF(cudaMemcpyAsync(ix->labels, labels, sizeof(int32_t) * n_ref, cudaMemcpyDeviceToDevice, s));
+  CKF(launch_label_hist(ix->labels, n_ref, n_classes, counts, bad, s));
+  CKF(launch_prep_ref(ix->ref_u8, n_ref, ix->n_pad, ix->ref_bf, ix->rnorm, s));
+  std::vector<unsigned long long> cnt(n_classes);
+  uint32_t bad_h = 0;
+  std::vector<int32_t> lab_h(n_ref);
+  CKF(cudaMemcpyAsync(cnt.data(), counts, sizeof(unsigned long long) * n_classes, cudaMemcpyDeviceToHost, s));
+  CKF(cudaMemcpyAsync(&bad_h, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  CKF(cudaMemcpyAsync(lab_h.data(), ix->labels, sizeof(int32_t) * n_ref, cudaMemcpyDeviceToHost, s));
+  CKF(cudaStreamSynchronize(s));
+  if (bad_h) return fail(LNBNN_ERR_LABEL_RANGE);
+  ix->class_off_h.assign(n_classes + 1, 0);
+  for (int32_t c = 0; c < n_classes; ++c) {
+    ix->class_off_h[c + 1] = ix->class_off_h[c] + (int64_t)cnt[c];
+    if (cnt[c] == 0) ix->has_empty_class = true;
+  }
+  CKF(dmalloc(&ix->class_off_d, (size_t)n_classes + 1));
+  CKF(cudaMemcpyAsync(ix->class_off_d, ix->class_off_h.data(), sizeof(int64_t) * (n_classes + 1),
+                      cudaMemcpyHostToDevice, s));
+  ix->sorted = std::is_sorted(lab_h.begin(), lab_h.end());
+  if (ix->sorted) {
+    ix->sref_u8 = ix->ref_u8;
+    ix->sref_bf = ix->ref_bf;
+    ix->srnorm = ix->rnorm;
+    ix->slabels = ix->labels;
+  } else {
+    // stable counting sort by class: rows of one class keep their order
+    std::vector<int64_t> next(ix->class_off_h.begin(), ix->class_off_h.end() - 1);
+    std::vector<int64_t> perm(n_ref);
+    for (int64_t j = 0; j < n_ref; ++j) perm[next[lab_h[j]]++] = j;
+    CKF(dmalloc(&perm_d, (size_t)n_ref));
+    CKF(dmalloc(&ix->sref_u8, (size_t)n_ref * kDim));
+    CKF(dmalloc(&ix->sref_bf, (size_t)ix->n_pad * kDim));
+    CKF(dmalloc(&ix->srnorm, (size_t)ix->n_pad));
+    CKF(dmalloc(&ix->slabels, (size_t)n_ref));
+    CKF(cudaMemcpyAsync(perm_d, perm.data(), sizeof(int64_t) * n_ref, cudaMemcpyHostToDevice, s));
+    CKF(launch_gather_ref(perm_d, n_ref, ix->ref_u8, ix->sref_u8, ix->ref_bf, ix->sref_bf, ix->rnorm, ix->srnorm,
+                          ix->labels, ix->slabels, s));
+    CKF(cudaMemsetAsync(ix->sref_bf + (size_t)n_ref * kDim, 0,
+                        sizeof(__nv_bfloat16) * (size_t)(ix->n_pad - n_ref) * kDim, s));
+    CKF(launch_fill_float(ix->srnorm + n_ref, ix->n_pad - n_ref, kPadNorm, s));
+    CKF(cudaStreamSynchronize(s));  // perm (host vector) must outlive the copy
+  }
+  if (!make_tc_tensor_maps(ix->ref_bf, ix->sref_bf, ix->n_pad, &ix->tc)) return fail(LNBNN_ERR_CUDA);
+  CKF(cudaStreamSynchronize(s));
+  cudaFree(counts);
+  cudaFree(bad);
+  cudaFree(perm_d);
+  *out = ix;
+  return st;
+#undef CKF
+}
+
+void lnbnn_index_destroy(lnbnn_index* index) { free_index(index); }
+
+lnbnn_status lnbnn_index_info(const lnbnn_index* index, int64_t* n_ref, int32_t* n_classes) {
+  if (!index) return LNBNN_ERR_INVALID_ARG;
+  if (n_ref) *n_ref = index->n_ref;
+  if (n_classes) *n_classes = index->n_classes;
+  return LNBNN_OK;
+}
+
+lnbnn_status knn_search(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, int32_t k, int32_t* idx,
+                        int32_t* dist, void* stream) {
+  if (!index || n_queries < 0) return LNBNN_ERR_INVALID_ARG;
+  if (!k_ok(index, k, 0)) return LNBNN_ERR_K_RANGE;
+  if (n_queries == 0) return LNBNN_OK;
+  if (!queries || !idx || !dist) return LNBNN_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CallProfile prof(index, s);
+  const uint64_t* lists = nullptr;
+  lnbnn_status st = run_knn(index, queries, n_queries, k, s, &lists, prof);
+  if (st != LNBNN_OK) return st;
+  CK(launch_extract_knn(lists, n_queries, k, k, idx, dist, s));
+  prof.launched(1);
+  return LNBNN_OK;
+}
+
+lnbnn_status lnbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
+                            int64_t n_images, int32_t k, int64_t* totals, int32_t* classes, void* stream) {
+  if (!index || n_queries < 0 || n_images < 0) return LNBNN_ERR_INVALID_ARG;
+  if (!k_ok(index, k, 1)) return LNBNN_ERR_K_RANGE;
+  if (n_images == 0) return n_queries == 0 ? LNBNN_OK : LNBNN_ERR_OFFSETS;
+  if (!offsets || !totals || !classes || (n_queries > 0 && !queries)) return LNBNN_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CallProfile prof(index, s);
+  const int32_t C = index->n_classes;
+  CK(cudaMemsetAsync(totals, 0, sizeof(int64_t) * (size_t)n_images * C, s));
+  CK(launch_check_offsets(offsets, n_images, n_queries, index->dev_err, s));
+  prof.launched(1);
+  if (n_queries > 0) {
+    const uint64_t* lists = nullptr;
+    lnbnn_status st = run_knn(index, queries, n_queries, k + 1, s, &lists, prof);
+    if (st != LNBNN_OK) return st;
+    CK(launch_lnbnn_score(lists, n_queries, k + 1, k, index->labels, offsets, n_images, C, totals, index->dev_err, s));
+    prof.launched(1);
+  } else {
+    prof.mark(1);
+    prof.mark(2);
+  }
+  CK(launch_argmin(totals, n_images, C, classes, s));
+  prof.launched(1);
+  return LNBNN_OK;
+}
+
+lnbnn_status nbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
+                           int64_t n_images, int64_t* totals, int32_t* classes, void* stream) {
+  if (!index || n_queries < 0 || n_images < 0) return LNBNN_ERR_INVALID_ARG;
+  if (index->has_empty_class) return LNBNN_ERR_EMPTY_CLASS;
+  if (n_images == 0) return n_queries == 0 ? LNBNN_OK : LNBNN_ERR_OFFSETS;
+  if (!offsets || !totals || !classes || (n_queries > 0 && !queries)) return LNBNN_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CallProfile prof(index, s);
+  const int32_t C = index->n_classes;
+  CK(cudaMemsetAsync(totals, 0, sizeof(int64_t) * (size_t)n_images * C, s));
+  CK(launch_check_offsets(offsets, n_images, n_queries, index->dev_err, s));
+  prof.launched(1);
+  if (n_queries == 0) {
+    prof.mark(1);
+    prof.mark(2);
+  } else {
+    const int64_t m_pad = round_up(n_queries, kQueryPad);
+    Carve c;
+    const size_t off_qnorm = c.take<int32_t>(m_pad);
+    CK(ensure(&index->ws, &index->ws_bytes, c.off));
+    int32_t* qnorm = reinterpret_cast<int32_t*>(static_cast<char*>(index->ws) + off_qnorm);
+    CK(launch_prep_query(queries, n_queries, m_pad, qnorm, nullptr, s));
+    prof.launched(1);
+    prof.mark(1);
+    ClassGroups g = make_groups(index, n_queries);
+    CK(launch_nbnn_simt(queries, n_queries, qnorm, index->sref_u8, index->srnorm, index->slabels, index->class_off_d,
+                        g, offsets, n_images, C, totals, s));
+    prof.launched(1, true);
+    prof.mark(2);
+  }
+  CK(launch_argmin(totals, n_images, C, classes, s));
+  prof.launched(1);
+  return LNBNN_OK;
+}
+
+static lnbnn_status classify_host(lnbnn_index* index, bool local, const uint8_t* queries, int64_t n_queries,
+                                  const int64_t* offsets, int64_t n_images, int32_t k, int64_t* totals,
+                                  int32_t* classes, void* stream) {
+  if (!index || n_queries < 0 || n_images < 0) return LNBNN_ERR_INVALID_ARG;
+  if (n_images == 0) return n_queries == 0 ? LNBNN_OK : LNBNN_ERR_OFFSETS;
+  if (!offsets || !totals || !classes || (n_queries > 0 && !queries)) return LNBNN_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int32_t C = index->n_classes;
+  Carve c;
+  const size_t oq = c.take<uint8_t>((size_t)n_queries * kDim);
+  const size_t oo = c.take<int64_t>((size_t)n_images + 1);
+  const size_t ot = c.take<int64_t>((size_t)n_images * C);
+  const size_t oc = c.take<int32_t>((size_t)n_images);
+  CK(ensure(&index->stage, &index->stage_bytes, c.off));
+  char* b = static_cast<char*>(index->stage);
+  uint8_t* dq = reinterpret_cast<uint8_t*>(b + oq);
+  int64_t* doff = reinterpret_cast<int64_t*>(b + oo);
+  int64_t* dtot = reinterpret_cast<int64_t*>(b + ot);
+  int32_t* dcls = reinterpret_cast<int32_t*>(b + oc);
+  if (n_queries > 0) CK(cudaMemcpyAsync(dq, queries, (size_t)n_queries * kDim, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(doff, offsets, sizeof(int64_t) * (n_images + 1), cudaMemcpyHostToDevice, s));
+  lnbnn_status st = local ? lnbnn_classify(index, dq, n_queries, doff, n_images, k, dtot, dcls, stream)
+                          : nbnn_classify(index, dq, n_queries, doff, n_images, dtot, dcls, stream);
+  if (st != LNBNN_OK) return st;
+  CK(cudaMemcpyAsync(totals, dtot, sizeof(int64_t) * (size_t)n_images * C, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(classes, dcls, sizeof(int32_t) * (size_t)n_images, cudaMemcpyDeviceToHost, s));
+  return lnbnn_sync(index, stream);
+}
+
+lnbnn_status lnbnn_classify_host(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
+                                 int64_t n_images, int32_t k, int64_t* totals, int32_t* classes, void* stream) {
+  if (index && !k_ok(index, k, 1)) return LNBNN_ERR_K_RANGE;
+  return classify_host(index, true, queries, n_queries, offsets, n_images, k, totals, classes, stream);
+}
+
+lnbnn_status nbnn_classify_host(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
+                                int64_t n_images, int64_t* totals, int32_t* classes, void* stream) {
+  if (index && index->has_empty_class) return LNBNN_ERR_EMPTY_CLASS;
+  return classify_host(index, false, queries, n_queries, offsets, n_images, 0, totals, classes, stream);
+}
+
+lnbnn_status lnbnn_profile_enable(lnbnn_index* index, int enable) {
+  if (!index) return LNBNN_ERR_INVALID_ARG;
+  for (auto& ce : index->prof_pending) {
+    cudaEventSynchronize(ce.e[3]);
+    index->prof_free.push_back(ce);
+  }
+  index->prof_pending.clear();
+  index->prof = lnbnn_profile{};
+  index->prof_on = enable != 0;
+  return LNBNN_OK;
+}
+
+lnbnn_status lnbnn_profile_read(lnbnn_index* index, lnbnn_profile* out) {
+  if (!index || !out) return LNBNN_ERR_INVALID_ARG;
+  for (auto& ce : index->prof_pending) {
+    CK(cudaEventSynchronize(ce.e[3]));
+    float a = 0.f, b = 0.f, c = 0.f;
+    CK(cudaEventElapsedTime(&a, ce.e[0], ce.e[1]));
+    CK(cudaEventElapsedTime(&b, ce.e[1], ce.e[2]));
+    CK(cudaEventElapsedTime(&c, ce.e[2], ce.e[3]));
+    index->prof.other_ms += (double)a + (double)c;
+    index->prof.search_ms += (double)b;
+    index->prof_free.push_back(ce);
+  }
+  index->prof_pending.clear();
+  *out = index->prof;
+  return LNBNN_OK;
+}
+
+lnbnn_status lnbnn_sync(lnbnn_index* index, void* stream) {
+  if (!index) return LNBNN_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t err = 0;
+  CK(cudaMemcpyAsync(&err, index->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (err) {
+    CK(cudaMemsetAsync(index->dev_err, 0, sizeof(uint32_t), s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (err & kDevErrTimeout) return LNBNN_ERR_TIMEOUT;
+  if (err & kDevErrOffsets) return LNBNN_ERR_OFFSETS;
+  return LNBNN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+"""Python binding of the C ABI in include/lnbnn.h (argument marshalling only).
+
+Every step of the classifier runs in the CUDA library ``_lib/liblnbnn.so``;
+this module passes device pointers (from PyTorch CUDA tensors), sizes and the
+current CUDA stream, and turns status codes into exceptions.  There is no CPU
+fallback: without the built library every call raises.
+
+Method: McCann & Lowe, "Local Naive Bayes Nearest Neighbor for Image
+Classification" -- Alg. 1 (NBNN) and Alg. 2 (LocalNBNN).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblnbnn.so")
+
+STATUS = {
+    0: "ok",
+    1: "invalid argument",
+    2: "label out of range",
+    3: "a class has no reference descriptor",
+    4: "k out of range",
+    5: "device out of memory",
+    6: "CUDA error",
+    7: "device wait timed out",
+    8: "unsupported device",
+    9: "invalid image offsets",
+}
+MAX_K = 255
+
+EXPORTS = ["lnbnn_index_create", "lnbnn_index_destroy", "lnbnn_index_info", "knn_search", "lnbnn_classify",
+           "nbnn_classify", "lnbnn_classify_host", "nbnn_classify_host", "lnbnn_sync", "lnbnn_profile_enable",
+           "lnbnn_profile_read", "lnbnn_status_string"]
+
+
+class Profile(ctypes.Structure):
+    """Mirror of ``lnbnn_profile`` (include/lnbnn.h)."""
+    _fields_ = [("calls", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("search_launches", ctypes.c_int64), ("search_ms", ctypes.c_double), ("other_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class LnbnnError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, 'unknown status')} (status {code})")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liblnbnn.so and declare its signatures.  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None and path == LIB_PATH:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        lib.lnbnn_index_create.argtypes = [P, P, I64, I32, P, ctypes.POINTER(P)]
+        lib.lnbnn_index_destroy.argtypes = [P]
+        lib.lnbnn_index_destroy.restype = None
+        lib.lnbnn_index_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I32)]
+        lib.knn_search.argtypes = [P, P, I64, I32, P, P, P]
+        lib.lnbnn_classify.argtypes = [P, P, I64, P, I64, I32, P, P, P]
+        lib.nbnn_classify.argtypes = [P, P, I64, P, I64, P, P, P]
+        lib.lnbnn_classify_host.argtypes = [P, P, I64, P, I64, I32, P, P, P]
+        lib.nbnn_classify_host.argtypes = [P, P, I64, P, I64, P, P, P]
+        lib.lnbnn_sync.argtypes = [P, P]
+        lib.lnbnn_profile_enable.argtypes = [P, ctypes.c_int]
+        lib.lnbnn_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
+        lib.lnbnn_status_string.argtypes = [ctypes.c_int]
+        lib.lnbnn_status_string.restype = ctypes.c_char_p
+        for name in ("lnbnn_index_create", "lnbnn_index_info", "knn_search", "lnbnn_classify", "nbnn_classify",
+                     "lnbnn_classify_host", "nbnn_classify_host", "lnbnn_sync", "lnbnn_profile_enable",
+                     "lnbnn_profile_read"):
+            getattr(lib, name).restype = ctypes.c_int
+        if path == LIB_PATH:
+            _lib = lib
+        return lib
+
+
+def _check(code: int, where: str) -> None:
+    if code != 0:
+        raise LnbnnError(code, where)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Index:
+    """Merged reference index (Alg. 2's single search structure plus the class
+    lookup), also serving original NBNN.  Owns device memory until ``close()``."""
+
+    def __init__(self, ref, labels, n_classes: int, stream=None):
+        import torch
+        self._lib = load_library()
+        if ref.dim() != 2 or ref.shape[1] != 128:
+            raise ValueError("ref must be uint8 [N, 128]")
+        self.n_ref = int(ref.shape[0])
+        self.n_classes = int(n_classes)
+        h = ctypes.c_void_p()
+        _check(self._lib.lnbnn_index_create(_dev(ref, torch.uint8, "ref"), _dev(labels, torch.int32, "labels"),
+                                            self.n_ref, self.n_classes, _stream_ptr(stream), ctypes.byref(h)),
+               "lnbnn_index_create")
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.lnbnn_index_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise ValueError("index is closed")
+        return self._h
+
+    def knn_search(self, queries, k: int, stream=None):
+        """NN(d, k): ``(idx int32 [M, k], dist int32 [M, k])``, exact, by (distance, row)."""
+        import torch
+        m = int(queries.shape[0])
+        idx = torch.empty((m, k), dtype=torch.int32, device=queries.device)
+        dist = torch.empty((m, k), dtype=torch.int32, device=queries.device)
+        _check(self._lib.knn_search(self.handle, _dev(queries, torch.uint8, "queries"), m, k,
+                                    _dev(idx, torch.int32, "idx"), _dev(dist, torch.int32, "dist"),
+                                    _stream_ptr(stream)), "knn_search")
+        return idx, dist
+
+    def lnbnn_classify(self, queries, offsets, k: int, stream=None, out=None):
+        """Alg. 2: ``(totals int64 [n_img, C], classes int32 [n_img])``."""
+        import torch
+        m, n_img = int(queries.shape[0]), int(offsets.shape[0]) - 1
+        totals, classes = out if out is not None else (
+            torch.empty((n_img, self.n_classes), dtype=torch.int64, device=queries.device),
+            torch.empty((n_img,), dtype=torch.int32, device=queries.device))
+        _check(self._lib.lnbnn_classify(self.handle, _dev(queries, torch.uint8, "queries"), m,
+                                        _dev(offsets, torch.int64, "offsets"), n_img, k,
+                                        _dev(totals, torch.int64, "totals"), _dev(classes, torch.int32, "classes"),
+                                        _stream_ptr(stream)), "lnbnn_classify")
+        return totals, classes
+
+    def nbnn_classify(self, queries, offsets, stream=None, out=None):
+        """Alg. 1: ``(totals int64 [n_img, C], classes int32 [n_img])``."""
+        import torch
+        m, n_img = int(queries.shape[0]), int(offsets.shape[0]) - 1
+        totals, classes = out if out is not None else (
+            torch.empty((n_img, self.n_classes), dtype=torch.int64, device=queries.device),
+            torch.empty((n_img,), dtype=torch.int32, device=queries.device))
+        _check(self._lib.nbnn_classify(self.handle, _dev(queries, torch.uint8, "queries"), m,
+                                       _dev(offsets, torch.int64, "offsets"), n_img,
+                                       _dev(totals, torch.int64, "totals"), _dev(classes, torch.int32, "classes"),
+                                       _stream_ptr(stream)), "nbnn_classify")
+        return totals, classes
+
+    def classify_host(self, queries: np.ndarray, offsets: np.ndarray, k: int | None, totals: np.ndarray | None = None,
+                      classes: np.ndarray | None = None, stream=None):
+        """Host-buffer form (k=None -> original NBNN).  numpy in, numpy out;
+        pinned host arrays give the fastest copies."""
+        q = np.ascontiguousarray(queries, dtype=np.uint8)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        n_img = off.shape[0] - 1
+        if totals is None:
+            totals = np.empty((n_img, self.n_classes), dtype=np.int64)
+        if classes is None:
+            classes = np.empty((n_img,), dtype=np.int32)
+        p = lambda a: ctypes.c_void_p(a.ctypes.data)
+        if k is None:
+            code = self._lib.nbnn_classify_host(self.handle, p(q), q.shape[0], p(off), n_img, p(totals), p(classes),
+                                                _stream_ptr(stream))
+        else:
+            code = self._lib.lnbnn_classify_host(self.handle, p(q), q.shape[0], p(off), n_img, k, p(totals),
+                                                 p(classes), _stream_ptr(stream))
+        _check(code, "classify_host")
+        return totals, classes
+
+    def profile_enable(self, enable: bool = True) -> None:
+        """Start (and reset) or stop the per-call device-time profile."""
+        _check(self._lib.lnbnn_profile_enable(self.handle, 1 if enable else 0), "lnbnn_profile_enable")
+
+    def profile_read(self) -> dict:
+        """Sums since the last enable: calls, kernel launches, search / other device ms."""
+        p = Profile()
+        _check(self._lib.lnbnn_profile_read(self.handle, ctypes.byref(p)), "lnbnn_profile_read")
+        return p.as_dict()
+
+    def sync(self, stream=None) -> None:
+        """Wait for the stream and raise any device-side error (timeout, offsets)."""
+        _check(self._lib.lnbnn_sync(self.handle, _stream_ptr(stream)), "lnbnn_sync")
