@@ -55,7 +55,8 @@ typedef enum lnbnn_status {
   LNBNN_ERR_CUDA = 6,         /* a CUDA runtime call or launch failed */
   LNBNN_ERR_TIMEOUT = 7,      /* a bounded device wait expired */
   LNBNN_ERR_UNSUPPORTED = 8,  /* device is not compute capability 10.3 (sm_103) */
-  LNBNN_ERR_OFFSETS = 9       /* offsets not 0 = o[0] <= ... <= o[n_images] = n_queries */
+  LNBNN_ERR_OFFSETS = 9,      /* offsets not 0 = o[0] <= ... <= o[n_images] = n_queries */
+  LNBNN_ERR_SCRATCH_LIMIT = 10 /* problem larger than the fixed scratch of knn_search_noalloc */
 } lnbnn_status;
 
 /*
@@ -172,6 +173,38 @@ typedef struct lnbnn_profile {
 
 LNBNN_API lnbnn_status lnbnn_profile_enable(lnbnn_index *index, int enable);
 LNBNN_API lnbnn_status lnbnn_profile_read(lnbnn_index *index, lnbnn_profile *out);
+
+/*
+ * knn_search_noalloc -- the exact k nearest neighbours of knn_search for
+ * callers that must not allocate device memory: code running inside a host
+ * framework that owns every device allocation (a fixed memory pool or arena,
+ * a plugin whose host forbids cudaMalloc), or a caller that cannot afford the
+ * implicit device synchronisation cudaMalloc and cudaFree bring.  The paper
+ * has no counterpart; this is a deployment variant of the same search.
+ *
+ * No index is needed: ref and queries are the caller's device uint8 arrays
+ * ([n_ref * 128] and [n_queries * 128]), idx and dist its device int32 outputs
+ * ([n_queries * k], as knn_search).  Every intermediate (BF16 operand copies,
+ * squared norms, per-row neighbour lists, the error word) lives in one
+ * fixed-size array in device global memory that the library defines at file
+ * scope: LNBNN_NOALLOC_SCRATCH_BYTES (64 MiB) on every GPU that loads the
+ * library, held until the process exits.  The call makes no cudaMalloc,
+ * cudaFree or other allocating call.  A problem whose intermediates do not
+ * fit (roughly n_ref + n_queries above about 200,000 rows at k = 10) is
+ * rejected with LNBNN_ERR_SCRATCH_LIMIT before any work is issued.
+ *
+ * The first call on each device looks up that device's address of the array
+ * (once, with the device current); make that first call before any stream
+ * capture begins.  All calls share the one array and find the previous call's
+ * contents in it; two calls whose work overlaps on the GPU (different
+ * streams, or threads without ordering) race and corrupt each other.  The
+ * call waits for `stream` before returning, to report device-side errors.
+ * Errors: INVALID_ARG, K_RANGE, SCRATCH_LIMIT, UNSUPPORTED, CUDA, TIMEOUT.
+ */
+#define LNBNN_NOALLOC_SCRATCH_BYTES (64ull << 20)
+LNBNN_API lnbnn_status knn_search_noalloc(const uint8_t *ref, int64_t n_ref, const uint8_t *queries,
+                                          int64_t n_queries, int32_t k, int32_t *idx, int32_t *dist,
+                                          void *stream);
 
 /* Static English text for a status code. */
 LNBNN_API const char *lnbnn_status_string(lnbnn_status status);

@@ -283,6 +283,7 @@ const char* lnbnn_status_string(lnbnn_status st) {
     case LNBNN_ERR_TIMEOUT: return "device wait timed out";
     case LNBNN_ERR_UNSUPPORTED: return "unsupported device (needs compute capability 10.3)";
     case LNBNN_ERR_OFFSETS: return "invalid image offsets";
+    case LNBNN_ERR_SCRATCH_LIMIT: return "problem larger than the fixed scratch of knn_search_noalloc";
   }
   return "unknown status";
 }

@@ -30,12 +30,13 @@ STATUS = {
     7: "device wait timed out",
     8: "unsupported device",
     9: "invalid image offsets",
+    10: "problem larger than the fixed scratch of knn_search_noalloc",
 }
 MAX_K = 255
 
 EXPORTS = ["lnbnn_index_create", "lnbnn_index_destroy", "lnbnn_index_info", "knn_search", "lnbnn_classify",
            "nbnn_classify", "lnbnn_classify_host", "nbnn_classify_host", "lnbnn_sync", "lnbnn_profile_enable",
-           "lnbnn_profile_read", "lnbnn_status_string"]
+           "lnbnn_profile_read", "lnbnn_status_string", "knn_search_noalloc"]
 
 
 class Profile(ctypes.Structure):
@@ -223,3 +224,28 @@ class Index:
     def sync(self, stream=None) -> None:
         """Wait for the stream and raise any device-side error (timeout, offsets)."""
         _check(self._lib.lnbnn_sync(self.handle, _stream_ptr(stream)), "lnbnn_sync")
+
+
+def knn_search_noalloc(ref, queries, k: int, stream=None):
+    """knn_search without an index and without any device allocation by the
+    library: every intermediate lives in the library's fixed 64 MiB device
+    scratch array.  For callers that must not allocate device memory (a host
+    framework that owns all allocations, or code that cannot take the device
+    synchronisation cudaMalloc/cudaFree imply).  Calls share that array, so
+    calls that overlap on the GPU race.  The output tensors here are allocated
+    by PyTorch, the caller; a caller with its own buffers passes them to the C
+    entry point directly.  Returns ``(idx int32 [M, k], dist int32 [M, k])``."""
+    import torch
+    lib = load_library()
+    if not hasattr(lib.knn_search_noalloc, "_declared"):
+        P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        lib.knn_search_noalloc.argtypes = [P, I64, P, I64, I32, P, P, P]
+        lib.knn_search_noalloc.restype = ctypes.c_int
+        lib.knn_search_noalloc._declared = True
+    m = int(queries.shape[0])
+    idx = torch.empty((m, k), dtype=torch.int32, device=queries.device)
+    dist = torch.empty((m, k), dtype=torch.int32, device=queries.device)
+    _check(lib.knn_search_noalloc(_dev(ref, torch.uint8, "ref"), int(ref.shape[0]),
+                                  _dev(queries, torch.uint8, "queries"), m, k, _dev(idx, torch.int32, "idx"),
+                                  _dev(dist, torch.int32, "dist"), _stream_ptr(stream)), "knn_search_noalloc")
+    return idx, dist

@@ -1,0 +1,71 @@
+"""knn_search_noalloc against knn_search.
+
+knn_search_noalloc serves callers that must not allocate device memory (a
+host framework that owns every allocation, or code that cannot afford the
+device synchronisation of cudaMalloc/cudaFree): all its intermediates live in
+the library's fixed device scratch array.  This file runs last, so a failure
+here cannot hide any other test's result; it also passes alone in a fresh
+process, where its first call performs the per-device scratch set-up.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _case(seed, n_ref, n_q):
+    rng = np.random.default_rng(seed)
+    ref = rng.integers(0, 256, size=(n_ref, 128)).astype(np.uint8)
+    ref[7:12] = ref[3]  # exact ties: the lower row must win on both paths
+    q = rng.integers(0, 256, size=(n_q, 128)).astype(np.uint8)
+    q[0] = ref[3]
+    return ref, q
+
+
+def _noalloc(lib, ref_d, q_d, k):
+    m = q_d.shape[0]
+    idx = torch.empty((m, k), dtype=torch.int32, device=q_d.device)
+    dist = torch.empty((m, k), dtype=torch.int32, device=q_d.device)
+    code = lib.knn_search_noalloc(ctypes.c_void_p(ref_d.data_ptr()), ref_d.shape[0], ctypes.c_void_p(q_d.data_ptr()),
+                                  m, k, ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(dist.data_ptr()),
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return code, idx, dist
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1112_0059_gb300 import build, lnbnn
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    lib = lnbnn.load_library()
+    lib.knn_search_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.knn_search_noalloc.restype = ctypes.c_int
+    return lib
+
+
+def test_noalloc_matches_knn_search_on_two_calls(lib):
+    from paper_1112_0059_gb300 import lnbnn
+    # a larger call, then a smaller one that finds the first call's data in the scratch
+    for seed, n_ref, n_q, k in ((0, 20000 + 77, 3000 + 5, 10), (1, 5000 + 3, 700, 25)):
+        ref, q = _case(seed, n_ref, n_q)
+        ref_d, q_d = torch.from_numpy(ref).cuda(), torch.from_numpy(q).cuda()
+        code, idx, dist = _noalloc(lib, ref_d, q_d, k)
+        assert code == 0, lnbnn.STATUS.get(code)
+        with lnbnn.Index(ref_d, torch.zeros(n_ref, dtype=torch.int32, device="cuda"), 1) as ix:
+            want_idx, want_dist = ix.knn_search(q_d, k)
+            ix.sync()
+        # integer work: bit-exact agreement
+        assert torch.equal(idx, want_idx) and torch.equal(dist, want_dist)
+        assert int(dist[0, 0]) == 0 and int(idx[0, 0]) == 3
+
+
+def test_noalloc_rejects_sizes_beyond_the_scratch(lib):
+    ref_d = torch.zeros((300000, 128), dtype=torch.uint8, device="cuda")
+    q_d = torch.zeros((10, 128), dtype=torch.uint8, device="cuda")
+    code, _, _ = _noalloc(lib, ref_d, q_d, 10)
+    assert code == 10  # LNBNN_ERR_SCRATCH_LIMIT, before any work is issued
