@@ -23,6 +23,12 @@ constexpr int kRefPad = 256;
 // Query rows are padded to a multiple of this (the query tile of every kernel).
 constexpr int kQueryPad = 128;
 
+// Width of the K-extension that carries ||r||^2 into the tensor-core
+// contraction: a reference row gets the base-256 digits (d0, d1, d2) of its
+// squared norm, a query row the constants (1, 256, 65536), zero-padded to one
+// MMA K-step of 16 BF16 columns.  All these values are exact in BF16.
+constexpr int kExt = 16;
+
 // Bits of the per-index device error word.
 enum : uint32_t { kDevErrTimeout = 1u, kDevErrOffsets = 2u };
 
@@ -37,21 +43,25 @@ __host__ __device__ __forceinline__ uint32_t key_row(uint64_t k) { return static
 // ----------------------------------------------------------- kernels (launchers)
 // Each launcher returns cudaGetLastError() after the launch.
 
-// Reference preparation: exact BF16 copy (rows padded to n_pad with zeros) and
-// squared norms as fp32 (padding rows get kPadNorm).
+// Reference preparation: exact BF16 copy (rows padded to n_pad with zeros),
+// squared norms as fp32 (padding rows get kPadNorm) and the norm digits of the
+// K-extension [n_pad, kExt].
 cudaError_t launch_prep_ref(const uint8_t* ref, int64_t n_ref, int64_t n_pad, __nv_bfloat16* ref_bf,
-                            float* rnorm, cudaStream_t s);
+                            float* rnorm, __nv_bfloat16* ref_ext, cudaStream_t s);
 // Query preparation: squared norms (int32) and, when qbf != nullptr, the BF16
-// operand -2q (rows padded to m_pad with zeros).
+// operand -2q (rows padded to m_pad with zeros) and its K-extension
+// (1, 256, 65536, 0, ...) [m_pad, kExt].
 cudaError_t launch_prep_query(const uint8_t* q, int64_t m, int64_t m_pad, int32_t* qnorm,
-                              __nv_bfloat16* qbf, cudaStream_t s);
+                              __nv_bfloat16* qbf, __nv_bfloat16* qext, cudaStream_t s);
 // Label histogram; sets *bad when a label is outside [0, C).
 cudaError_t launch_label_hist(const int32_t* labels, int64_t n, int32_t C, unsigned long long* counts,
                               uint32_t* bad, cudaStream_t s);
-// Gather rows: dst[i] = src[perm[i]] for uint8 descriptors, bf16 operand rows, norms, labels.
+// Gather rows: dst[i] = src[perm[i]] for uint8 descriptors, bf16 operand rows,
+// norm-digit rows, norms and labels.
 cudaError_t launch_gather_ref(const int64_t* perm, int64_t n, const uint8_t* src_u8, uint8_t* dst_u8,
-                              const __nv_bfloat16* src_bf, __nv_bfloat16* dst_bf, const float* src_norm,
-                              float* dst_norm, const int32_t* src_lab, int32_t* dst_lab, cudaStream_t s);
+                              const __nv_bfloat16* src_bf, __nv_bfloat16* dst_bf, const __nv_bfloat16* src_ext,
+                              __nv_bfloat16* dst_ext, const float* src_norm, float* dst_norm,
+                              const int32_t* src_lab, int32_t* dst_lab, cudaStream_t s);
 
 // dst[0..n) = v
 cudaError_t launch_fill_float(float* dst, int64_t n, float v, cudaStream_t s);

@@ -1,16 +1,24 @@
 // Exact k+1 nearest-neighbour search (the NN(d, k+1) of Alg. 2) on the sm_103a
 // tensor cores.
 //
-// For a tile of 128 query rows and 256 reference rows the MMA computes
-// acc[i][j] = sum_t (-2 q_it) r_jt in FP32; with BF16 operands holding the exact
-// integers 0..255 (and -2q), every product and partial sum is an integer of
-// magnitude below 2^24, so acc is exact.  The epilogue adds ||r_j||^2 and tests
-// acc + ||r_j||^2 < threshold - ||q_i||^2, i.e. ||q_i - r_j||^2 below the row's
-// current (k+1)-th distance; the distance matrix never leaves the SM.
+// For a tile of 128 query rows and 256 reference rows the MMA computes, in
+// FP32 TMEM accumulators,
+//     acc[i][j] = sum_t (-2 q_it) r_jt + (1, 256, 65536) . (d0, d1, d2)_j
+//               = ||r_j||^2 - 2 q_i . r_j,
+// the last term being a 16-wide K-extension that carries each reference's
+// squared norm as base-256 digits.  BF16 holds 0..255, -2q and the digits
+// exactly; every product and partial sum is an integer below 2^24 in
+// magnitude, so acc is exact.  The epilogue keeps, per query row, the k+1
+// smallest keys (acc + ||q_i||^2, j) = (||q_i - r_j||^2, j): one compare per
+// element against the row's current (k+1)-th distance.  The distance matrix
+// never leaves the SM.
 //
 // Roles (one CTA = 128 query rows x one reference split):
-//   warp 0, one thread : TMA producer (query tile once, reference K-chunks into a ring)
-//   warp 1, one thread : tcgen05.mma issuer; warp 1 also owns the TMEM allocation
+//   warp 0, one thread : TMA producer (query tile once; reference K-chunks
+//                        into a 4-stage ring, the K-extension riding with the
+//                        second chunk of each tile)
+//   warp 1, one thread : tcgen05.mma issuer (9 MMAs of 128x256x16 per tile);
+//                        warp 1 also owns the TMEM allocation
 //   warps 2-5          : epilogue, one thread per query row (TMEM lane), two
 //                        256-column FP32 accumulators in flight
 // Every wait is bounded; on expiry the CTA records a timeout in the index's
@@ -32,20 +40,26 @@ constexpr int kBK = 64;                   // K elements per 128-byte swizzle row
 constexpr int kKChunks = kDim / kBK;      // 2
 constexpr int kUmmaK = 16;                // K per tcgen05.mma (kind::f16)
 constexpr int kStages = 4;                // reference ring depth (K-chunks)
-constexpr uint32_t kAChunkBytes = kBM * kBK * 2;   // 16 KB
-constexpr uint32_t kBStageBytes = kBN * kBK * 2;   // 32 KB
+constexpr uint32_t kAChunkBytes = kBM * kBK * 2;     // 16 KB
+constexpr uint32_t kAExtBytes = kBM * kExt * 2;      // 4 KB
+constexpr uint32_t kBChunkBytes = kBN * kBK * 2;     // 32 KB
+constexpr uint32_t kBExtBytes = kBN * kExt * 2;      // 8 KB
+constexpr uint32_t kStageBytes = kBChunkBytes + kBExtBytes;
 constexpr int kEpiWarps = 4;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kAccCols = kBN;        // FP32 columns per accumulator
 constexpr uint32_t kTmemCols = 2 * kAccCols;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
 
-constexpr uint32_t kOffA = 0;
-constexpr uint32_t kOffB = kOffA + kKChunks * kAChunkBytes;
-constexpr uint32_t kOffBar = kOffB + kStages * kBStageBytes;
+constexpr uint32_t kOffA = 0;                                   // 2 chunks, 128-byte swizzle
+constexpr uint32_t kOffAExt = kOffA + kKChunks * kAChunkBytes;  // extension, 32-byte swizzle
+constexpr uint32_t kOffB = kOffAExt + 1024 * ((kAExtBytes + 1023) / 1024);
+constexpr uint32_t kOffBar = kOffB + kStages * kStageBytes;
 constexpr int kNumBars = 2 * kStages + 2 + 2 + 2;  // full, empty, tmem full, tmem empty, A, drain
 constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;
 constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;  // + alignment slack
+static_assert(kStages % kKChunks == 0, "a tile's chunks map to fixed stage parities");
+static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
 constexpr float kNoThreshold = 3.0e38f;
 
@@ -64,11 +78,26 @@ __device__ __forceinline__ void flag_timeout(volatile uint32_t* abort_flag, uint
   atomicOr(dev_err, kDevErrTimeout);
 }
 
+// Rare path of the epilogue: offer the elements of one 32-column group that
+// pass the row's threshold to its heap.
+__device__ __forceinline__ void offer_group(TopK& top, float& thr, int32_t qn, const uint32_t (&v)[32], int64_t col0) {
+  float d[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) d[j] = __uint_as_float(v[j]);
+#pragma unroll 1
+  for (int j = 0; j < 32; ++j) {
+    if (d[j] < thr) {
+      top.push(make_key((uint32_t)((int32_t)d[j] + qn), (uint32_t)(col0 + j)));
+      if (top.size == top.cap) thr = (float)(top.threshold - qn);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
-    knn_tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_r,
-                  const int32_t* __restrict__ qnorm, const float* __restrict__ rnorm, int64_t m, int64_t n_ref,
-                  int64_t split_len, int K1, uint64_t* __restrict__ lists, int64_t stride,
-                  uint32_t* __restrict__ dev_err) {
+    knn_tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_qe,
+                  const __grid_constant__ CUtensorMap tmap_r, const __grid_constant__ CUtensorMap tmap_re,
+                  const int32_t* __restrict__ qnorm, int64_t m, int64_t n_ref, int64_t split_len, int K1,
+                  uint64_t* __restrict__ lists, int64_t stride, uint32_t* __restrict__ dev_err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
@@ -109,12 +138,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ------------------------------------------------------------ producer
       prefetch_tmap(&tmap_q);
+      prefetch_tmap(&tmap_qe);
       prefetch_tmap(&tmap_r);
-      mbar_arrive_expect_tx(bars.afull(), kKChunks * kAChunkBytes);
+      prefetch_tmap(&tmap_re);
+      mbar_arrive_expect_tx(bars.afull(), kKChunks * kAChunkBytes + kAExtBytes);
       for (int kc = 0; kc < kKChunks; ++kc)
         tma_load_2d(sbase + kOffA + kc * kAChunkBytes, &tmap_q, kc * kBK, (int32_t)m0, bars.afull());
+      tma_load_2d(sbase + kOffAExt, &tmap_qe, 0, (int32_t)m0, bars.afull());
       int it = 0;
       for (int t = 0; t < ntiles && !*abort_flag; ++t) {
+        const int32_t row = (int32_t)(j_begin + (int64_t)t * kBN);
         for (int kc = 0; kc < kKChunks; ++kc, ++it) {
           const int s = it % kStages;
           const uint32_t round = (uint32_t)(it / kStages);
@@ -122,9 +155,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             flag_timeout(abort_flag, dev_err);
             break;
           }
-          mbar_arrive_expect_tx(bars.full(s), kBStageBytes);
-          tma_load_2d(sbase + kOffB + s * kBStageBytes, &tmap_r, kc * kBK, (int32_t)(j_begin + (int64_t)t * kBN),
-                      bars.full(s));
+          const uint32_t dst = sbase + kOffB + s * kStageBytes;
+          const bool last = kc == kKChunks - 1;
+          mbar_arrive_expect_tx(bars.full(s), kBChunkBytes + (last ? kBExtBytes : 0u));
+          tma_load_2d(dst, &tmap_r, kc * kBK, row, bars.full(s));
+          if (last) tma_load_2d(dst + kBChunkBytes, &tmap_re, 0, row, bars.full(s));
         }
       }
       // every load issued must land before the CTA may exit
@@ -162,12 +197,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t a_base = sbase + kOffA + kc * kAChunkBytes;
-          const uint32_t b_base = sbase + kOffB + s * kBStageBytes;
+          const uint32_t b_base = sbase + kOffB + s * kStageBytes;
 #pragma unroll
           for (int kk = 0; kk < kBK / kUmmaK; ++kk) {
             mma_bf16(d_tmem, sw128_kmajor_desc(a_base + kk * 32), sw128_kmajor_desc(b_base + kk * 32), idesc,
                      (kc | kk) != 0 ? 1u : 0u);
           }
+          if (kc == kKChunks - 1)  // ||r||^2 through the K-extension
+            mma_bf16(d_tmem, sw32_kmajor_desc(sbase + kOffAExt), sw32_kmajor_desc(b_base + kBChunkBytes), idesc, 1u);
           mma_commit(bars.empty(s));
         }
         if (ok) mma_commit(bars.tfull(b));
@@ -184,7 +221,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool active = row < m;
     const int32_t qn = active ? qnorm[row] : 0;
     TopK top(lists + ((int64_t)blockIdx.y * stride + (active ? row : 0)) * K1, K1);
-    float thr = kNoThreshold;  // acc + ||r||^2 must be below this
+    float thr = kNoThreshold;  // acc (= ||q - r||^2 - ||q||^2) must be below this
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
@@ -195,44 +232,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_after();
       const int64_t jt = j_begin + (int64_t)t * kBN;
-      const float4* rn4 = reinterpret_cast<const float4*>(rnorm + jt);
 #pragma unroll 1
-      for (int c = 0; c < kBN / 32; ++c) {
-        uint32_t v[32];
-        tmem_ld_32x32b_x32(tmem_base + lane_addr + b * kAccCols + c * 32, v);
-        float rn[32];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 r = __ldg(rn4 + c * 8 + q);
-          rn[4 * q + 0] = r.x;
-          rn[4 * q + 1] = r.y;
-          rn[4 * q + 2] = r.z;
-          rn[4 * q + 3] = r.w;
-        }
-        tmem_ld_wait();
-        float d[32];
-        bool hit = false;
+      for (int c = 0; c < kBN / 64; ++c) {
+        uint32_t va[32], vb[32];
+        const uint32_t taddr = tmem_base + lane_addr + b * kAccCols + c * 64;
+        tmem_ld_32x32b_x32(taddr, va);
+        tmem_ld_32x32b_x32(taddr + 32, vb);
+        tmem_ld_wait(va);
+        reg_fence(vb);
+        bool hit_a = false, hit_b = false;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          d[j] = __uint_as_float(v[j]) + rn[j];
-          hit |= d[j] < thr;
+          hit_a |= __uint_as_float(va[j]) < thr;
+          hit_b |= __uint_as_float(vb[j]) < thr;
         }
-        hit = hit && active;
-        if (__any_sync(0xffffffffu, hit)) {
-          if (hit) {
-            // rare path: a local copy keeps the hot loop's d[] in registers
-            float dl[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) dl[j] = d[j];
-#pragma unroll 1
-            for (int j = 0; j < 32; ++j) {
-              if (dl[j] < thr) {
-                const uint32_t dist = (uint32_t)((int32_t)dl[j] + qn);
-                top.push(make_key(dist, (uint32_t)(jt + c * 32 + j)));
-                if (top.size == top.cap) thr = (float)(top.threshold - qn);
-              }
-            }
-          }
+        hit_a = hit_a && active;
+        hit_b = hit_b && active;
+        if (__any_sync(0xffffffffu, hit_a || hit_b)) {
+          if (hit_a) offer_group(top, thr, qn, va, jt + c * 64);
+          if (hit_b) offer_group(top, thr, qn, vb, jt + c * 64 + 32);
           __syncwarp();
         }
       }
@@ -262,39 +280,50 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// BF16 [rows, 128] row-major, boxes of 64 x box_rows with the 128-byte swizzle.
-bool encode_bf16_rows(CUtensorMap* map, const void* base, uint64_t rows, uint32_t box_rows) {
+// BF16 [rows, cols] row-major, boxes of box_cols x box_rows with the given swizzle.
+bool encode_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint32_t cols, uint32_t box_cols,
+                 uint32_t box_rows, CUtensorMapSwizzle swizzle) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t gdim[2] = {(cuuint64_t)kDim, (cuuint64_t)rows};
-  cuuint64_t gstride[1] = {(cuuint64_t)kDim * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
+  cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {box_cols, box_rows};
   cuuint32_t estride[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box, estride,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-}  // namespace
-
-bool make_tc_tensor_maps(const __nv_bfloat16* ref_bf, const __nv_bfloat16* sref_bf, int64_t n_pad, TcTensorMaps* out) {
-  return encode_bf16_rows(&out->ref, ref_bf, (uint64_t)n_pad, kBN) &&
-         encode_bf16_rows(&out->sref, sref_bf, (uint64_t)n_pad, kBN);
+// Main operand (128 K-columns, 64-column boxes, 128-byte swizzle) and its
+// 16-column K-extension (32-byte swizzle).
+bool encode_operand(CUtensorMap* main, CUtensorMap* ext, const void* bf, const void* ext_base, uint64_t rows,
+                    uint32_t box_rows) {
+  return encode_bf16(main, bf, rows, kDim, kBK, box_rows, CU_TENSOR_MAP_SWIZZLE_128B) &&
+         encode_bf16(ext, ext_base, rows, kExt, kExt, box_rows, CU_TENSOR_MAP_SWIZZLE_32B);
 }
 
-cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf, int64_t m,
-                          int64_t m_pad, const int32_t* qnorm, const float* rnorm, int64_t n_ref, int splits,
-                          int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
+}  // namespace
+
+bool make_tc_tensor_maps(const __nv_bfloat16* ref_bf, const __nv_bfloat16* sref_bf, const __nv_bfloat16* ref_ext,
+                         const __nv_bfloat16* sref_ext, int64_t n_pad, TcTensorMaps* out) {
+  return encode_operand(&out->ref, &out->ref_ext, ref_bf, ref_ext, (uint64_t)n_pad, kBN) &&
+         encode_operand(&out->sref, &out->sref_ext, sref_bf, sref_ext, (uint64_t)n_pad, kBN);
+}
+
+cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf,
+                          const __nv_bfloat16* qext, int64_t m, int64_t m_pad, const int32_t* qnorm, int64_t n_ref,
+                          int splits, int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
                           cudaStream_t s) {
   if (m == 0) return cudaSuccess;
   if (m_pad % kBM != 0 || split_len % kBN != 0) return cudaErrorInvalidValue;
-  CUtensorMap tq;
-  if (!encode_bf16_rows(&tq, qbf, (uint64_t)m_pad, kBM)) return cudaErrorInvalidValue;
+  CUtensorMap tq, tqe;
+  if (!encode_operand(&tq, &tqe, qbf, qext, (uint64_t)m_pad, kBM)) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(m_pad / kBM), (unsigned)splits);
-  knn_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(tq, sorted_copy ? maps.sref : maps.ref, qnorm, rnorm, m, n_ref,
+  knn_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(tq, tqe, sorted_copy ? maps.sref : maps.ref,
+                                                   sorted_copy ? maps.sref_ext : maps.ref_ext, qnorm, m, n_ref,
                                                    split_len, K1, lists, stride, dev_err);
   return cudaGetLastError();
 }

@@ -19,13 +19,15 @@ struct lnbnn_index {
   int32_t n_classes = 0;
   // merged reference set, caller's row order
   uint8_t* ref_u8 = nullptr;
-  __nv_bfloat16* ref_bf = nullptr;  // [n_pad, 128] exact BF16 copy, zero padding rows
-  float* rnorm = nullptr;           // [n_pad] squared norms, kPadNorm on padding rows
+  __nv_bfloat16* ref_bf = nullptr;   // [n_pad, 128] exact BF16 copy, zero padding rows
+  __nv_bfloat16* ref_ext = nullptr;  // [n_pad, 16] squared-norm digits (K-extension)
+  float* rnorm = nullptr;            // [n_pad] squared norms, kPadNorm on padding rows
   int32_t* labels = nullptr;        // [n_ref]
   // class-sorted view (aliases the above when the labels are already grouped)
   bool sorted = true;
   uint8_t* sref_u8 = nullptr;
   __nv_bfloat16* sref_bf = nullptr;
+  __nv_bfloat16* sref_ext = nullptr;
   float* srnorm = nullptr;
   int32_t* slabels = nullptr;
   std::vector<int64_t> class_off_h;  // [C+1]
@@ -78,11 +80,13 @@ void free_index(lnbnn_index* ix) {
   if (!ix->sorted) {
     cudaFree(ix->sref_u8);
     cudaFree(ix->sref_bf);
+    cudaFree(ix->sref_ext);
     cudaFree(ix->srnorm);
     cudaFree(ix->slabels);
   }
   cudaFree(ix->ref_u8);
   cudaFree(ix->ref_bf);
+  cudaFree(ix->ref_ext);
   cudaFree(ix->rnorm);
   cudaFree(ix->labels);
   cudaFree(ix->class_off_d);
@@ -179,7 +183,7 @@ struct KnnPlan {
   int splits;
   int64_t split_len;
   int K1;
-  size_t off_qnorm, off_qbf, off_lists, off_merged, bytes;
+  size_t off_qnorm, off_qbf, off_qext, off_lists, off_merged, bytes;
 };
 
 KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, bool tensor) {
@@ -193,6 +197,7 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, bool tensor) {
   Carve c;
   p.off_qnorm = c.take<int32_t>(p.m_pad);
   p.off_qbf = tensor ? c.take<__nv_bfloat16>(p.m_pad * kDim) : 0;
+  p.off_qext = tensor ? c.take<__nv_bfloat16>(p.m_pad * kExt) : 0;
   p.off_lists = c.take<uint64_t>((size_t)p.splits * p.m_pad * K1);
   p.off_merged = p.splits > 1 ? c.take<uint64_t>((size_t)p.m_pad * K1) : p.off_lists;
   p.bytes = c.off;
@@ -213,14 +218,15 @@ lnbnn_status run_knn(lnbnn_index* ix, const uint8_t* q, int64_t m, int K1, cudaS
   char* ws = static_cast<char*>(ix->ws);
   int32_t* qnorm = reinterpret_cast<int32_t*>(ws + p.off_qnorm);
   __nv_bfloat16* qbf = tensor ? reinterpret_cast<__nv_bfloat16*>(ws + p.off_qbf) : nullptr;
+  __nv_bfloat16* qext = tensor ? reinterpret_cast<__nv_bfloat16*>(ws + p.off_qext) : nullptr;
   uint64_t* part = reinterpret_cast<uint64_t*>(ws + p.off_lists);
   uint64_t* merged = reinterpret_cast<uint64_t*>(ws + p.off_merged);
-  CK(launch_prep_query(q, m, p.m_pad, qnorm, qbf, s));
+  CK(launch_prep_query(q, m, p.m_pad, qnorm, qbf, qext, s));
   prof.launched(1);
   prof.mark(1);
   if (tensor) {
-    CK(launch_knn_tc(ix->tc, /*sorted_copy=*/false, qbf, m, p.m_pad, qnorm, ix->rnorm, ix->n_ref, p.splits,
-                     p.split_len, K1, part, p.m_pad, ix->dev_err, s));
+    CK(launch_knn_tc(ix->tc, /*sorted_copy=*/false, qbf, qext, m, p.m_pad, qnorm, ix->n_ref, p.splits, p.split_len,
+                     K1, part, p.m_pad, ix->dev_err, s));
   } else {
     CK(launch_knn_simt(q, m, qnorm, ix->ref_u8, ix->rnorm, ix->n_ref, p.splits, p.split_len, K1, part, p.m_pad, s));
   }
@@ -322,6 +328,7 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
   } while (0)
   CKF(dmalloc(&ix->ref_u8, (size_t)n_ref * kDim));
   CKF(dmalloc(&ix->ref_bf, (size_t)ix->n_pad * kDim));
+  CKF(dmalloc(&ix->ref_ext, (size_t)ix->n_pad * kExt));
   CKF(dmalloc(&ix->rnorm, (size_t)ix->n_pad));
   CKF(dmalloc(&ix->labels, (size_t)n_ref));
   CKF(dmalloc(&ix->dev_err, 1));
@@ -333,7 +340,7 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
   CKF(cudaMemcpyAsync(ix->ref_u8, ref, (size_t)n_ref * kDim, cudaMemcpyDeviceToDevice, s));
   CKF(cudaMemcpyAsync(ix->labels, labels, sizeof(int32_t) * n_ref, cudaMemcpyDeviceToDevice, s));
   CKF(launch_label_hist(ix->labels, n_ref, n_classes, counts, bad, s));
-  CKF(launch_prep_ref(ix->ref_u8, n_ref, ix->n_pad, ix->ref_bf, ix->rnorm, s));
+  CKF(launch_prep_ref(ix->ref_u8, n_ref, ix->n_pad, ix->ref_bf, ix->rnorm, ix->ref_ext, s));
   std::vector<unsigned long long> cnt(n_classes);
   uint32_t bad_h = 0;
   std::vector<int32_t> lab_h(n_ref);
@@ -354,6 +361,7 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
   if (ix->sorted) {
     ix->sref_u8 = ix->ref_u8;
     ix->sref_bf = ix->ref_bf;
+    ix->sref_ext = ix->ref_ext;
     ix->srnorm = ix->rnorm;
     ix->slabels = ix->labels;
   } else {
@@ -364,17 +372,22 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
     CKF(dmalloc(&perm_d, (size_t)n_ref));
     CKF(dmalloc(&ix->sref_u8, (size_t)n_ref * kDim));
     CKF(dmalloc(&ix->sref_bf, (size_t)ix->n_pad * kDim));
+    CKF(dmalloc(&ix->sref_ext, (size_t)ix->n_pad * kExt));
     CKF(dmalloc(&ix->srnorm, (size_t)ix->n_pad));
     CKF(dmalloc(&ix->slabels, (size_t)n_ref));
     CKF(cudaMemcpyAsync(perm_d, perm.data(), sizeof(int64_t) * n_ref, cudaMemcpyHostToDevice, s));
-    CKF(launch_gather_ref(perm_d, n_ref, ix->ref_u8, ix->sref_u8, ix->ref_bf, ix->sref_bf, ix->rnorm, ix->srnorm,
-                          ix->labels, ix->slabels, s));
-    CKF(cudaMemsetAsync(ix->sref_bf + (size_t)n_ref * kDim, 0,
-                        sizeof(__nv_bfloat16) * (size_t)(ix->n_pad - n_ref) * kDim, s));
+    CKF(launch_gather_ref(perm_d, n_ref, ix->ref_u8, ix->sref_u8, ix->ref_bf, ix->sref_bf, ix->ref_ext, ix->sref_ext,
+                          ix->rnorm, ix->srnorm, ix->labels, ix->slabels, s));
+    // padding rows are the same in both orders
+    CKF(cudaMemcpyAsync(ix->sref_bf + (size_t)n_ref * kDim, ix->ref_bf + (size_t)n_ref * kDim,
+                        sizeof(__nv_bfloat16) * (size_t)(ix->n_pad - n_ref) * kDim, cudaMemcpyDeviceToDevice, s));
+    CKF(cudaMemcpyAsync(ix->sref_ext + (size_t)n_ref * kExt, ix->ref_ext + (size_t)n_ref * kExt,
+                        sizeof(__nv_bfloat16) * (size_t)(ix->n_pad - n_ref) * kExt, cudaMemcpyDeviceToDevice, s));
     CKF(launch_fill_float(ix->srnorm + n_ref, ix->n_pad - n_ref, kPadNorm, s));
     CKF(cudaStreamSynchronize(s));  // perm (host vector) must outlive the copy
   }
-  if (!make_tc_tensor_maps(ix->ref_bf, ix->sref_bf, ix->n_pad, &ix->tc)) return fail(LNBNN_ERR_CUDA);
+  if (!make_tc_tensor_maps(ix->ref_bf, ix->sref_bf, ix->ref_ext, ix->sref_ext, ix->n_pad, &ix->tc))
+    return fail(LNBNN_ERR_CUDA);
   CKF(cudaStreamSynchronize(s));
   cudaFree(counts);
   cudaFree(bad);
@@ -457,7 +470,7 @@ lnbnn_status nbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t n
     const size_t off_qnorm = c.take<int32_t>(m_pad);
     CK(ensure(&index->ws, &index->ws_bytes, c.off));
     int32_t* qnorm = reinterpret_cast<int32_t*>(static_cast<char*>(index->ws) + off_qnorm);
-    CK(launch_prep_query(queries, n_queries, m_pad, qnorm, nullptr, s));
+    CK(launch_prep_query(queries, n_queries, m_pad, qnorm, nullptr, nullptr, s));
     prof.launched(1);
     prof.mark(1);
     ClassGroups g = make_groups(index, n_queries);

@@ -95,9 +95,11 @@ extern "C" LNBNN_API lnbnn_status knn_search_noalloc(const uint8_t* ref, int64_t
   Layout L;
   const size_t o_err = L.take<uint32_t>(1);
   const size_t o_rbf = L.take<__nv_bfloat16>((size_t)n_pad * kDim);
+  const size_t o_rext = L.take<__nv_bfloat16>((size_t)n_pad * kExt);
   const size_t o_rn = L.take<float>((size_t)n_pad);
   const size_t o_qn = L.take<int32_t>((size_t)m_pad);
   const size_t o_qbf = L.take<__nv_bfloat16>((size_t)m_pad * kDim);
+  const size_t o_qext = L.take<__nv_bfloat16>((size_t)m_pad * kExt);
   const size_t o_lists = L.take<uint64_t>((size_t)splits * m_pad * k);
   const size_t o_merged = splits > 1 ? L.take<uint64_t>((size_t)m_pad * k) : o_lists;
   if (L.off > (size_t)LNBNN_NOALLOC_SCRATCH_BYTES) return LNBNN_ERR_SCRATCH_LIMIT;
@@ -105,22 +107,24 @@ extern "C" LNBNN_API lnbnn_status knn_search_noalloc(const uint8_t* ref, int64_t
   char* b = static_cast<char*>(base);
   uint32_t* err = reinterpret_cast<uint32_t*>(b + o_err);
   __nv_bfloat16* ref_bf = reinterpret_cast<__nv_bfloat16*>(b + o_rbf);
+  __nv_bfloat16* ref_ext = reinterpret_cast<__nv_bfloat16*>(b + o_rext);
   float* rnorm = reinterpret_cast<float*>(b + o_rn);
   int32_t* qnorm = reinterpret_cast<int32_t*>(b + o_qn);
   __nv_bfloat16* qbf = reinterpret_cast<__nv_bfloat16*>(b + o_qbf);
+  __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(b + o_qext);
   uint64_t* lists = reinterpret_cast<uint64_t*>(b + o_lists);
   uint64_t* merged = reinterpret_cast<uint64_t*>(b + o_merged);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   TcTensorMaps maps;
-  if (!make_tc_tensor_maps(ref_bf, ref_bf, n_pad, &maps)) return LNBNN_ERR_CUDA;
+  if (!make_tc_tensor_maps(ref_bf, ref_bf, ref_ext, ref_ext, n_pad, &maps)) return LNBNN_ERR_CUDA;
   // The array keeps the previous call's contents: the error word must start at
   // zero; every other buffer is fully written before it is read.
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
-  if (e == cudaSuccess) e = launch_prep_ref(ref, n_ref, n_pad, ref_bf, rnorm, s);
-  if (e == cudaSuccess) e = launch_prep_query(queries, n_queries, m_pad, qnorm, qbf, s);
+  if (e == cudaSuccess) e = launch_prep_ref(ref, n_ref, n_pad, ref_bf, rnorm, ref_ext, s);
+  if (e == cudaSuccess) e = launch_prep_query(queries, n_queries, m_pad, qnorm, qbf, qext, s);
   if (e == cudaSuccess)
-    e = launch_knn_tc(maps, false, qbf, n_queries, m_pad, qnorm, rnorm, n_ref, (int)splits, split_len, k, lists,
+    e = launch_knn_tc(maps, false, qbf, qext, n_queries, m_pad, qnorm, n_ref, (int)splits, split_len, k, lists,
                       m_pad, err, s);
   if (e == cudaSuccess && splits > 1) e = launch_merge_lists(lists, (int)splits, n_queries, m_pad, k, merged, s);
   if (e == cudaSuccess) e = launch_extract_knn(merged, n_queries, k, k, idx, dist, s);

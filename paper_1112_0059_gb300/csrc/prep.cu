@@ -16,8 +16,20 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+__device__ __forceinline__ uint32_t bf16_bits(float v) {
+  __nv_bfloat16 b = __float2bfloat16_rn(v);
+  return (uint32_t)*reinterpret_cast<unsigned short*>(&b);
+}
+
+// Row of the K-extension: first 8 BF16 values (a, b, c, 0, 0, 0, 0, 0); the
+// other 8 are zero.
+__device__ __forceinline__ uint4 ext_head(float a, float b, float c) {
+  return make_uint4(bf16_bits(a) | (bf16_bits(b) << 16), bf16_bits(c), 0u, 0u);
+}
+
 __global__ void prep_ref_kernel(const uint8_t* __restrict__ ref, int64_t n_ref, int64_t n_pad,
-                                __nv_bfloat16* __restrict__ ref_bf, float* __restrict__ rnorm) {
+                                __nv_bfloat16* __restrict__ ref_bf, float* __restrict__ rnorm,
+                                __nv_bfloat16* __restrict__ ref_ext) {
   const int sub = threadIdx.x % kThreadsPerRow;
   const int64_t row = (int64_t)blockIdx.x * kRowsPerBlock + threadIdx.x / kThreadsPerRow;
   if (row >= n_pad) return;
@@ -36,11 +48,18 @@ __global__ void prep_ref_kernel(const uint8_t* __restrict__ ref, int64_t n_ref, 
   *reinterpret_cast<uint4*>(ref_bf + row * kDim + sub * 8) = out;
 #pragma unroll
   for (int off = kThreadsPerRow / 2; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
-  if (sub == 0) rnorm[row] = row < n_ref ? (float)ss : kPadNorm;
+  const int32_t norm = row < n_ref ? ss : (int32_t)kPadNorm;
+  if (sub == 0) rnorm[row] = (float)norm;
+  // base-256 digits of the norm: d0 + 256 d1 + 65536 d2 (d2 <= 127 for real
+  // rows, 512 for padding rows); each digit is exact in BF16
+  uint4* ext = reinterpret_cast<uint4*>(ref_ext + row * kExt);
+  if (sub == 0) ext[0] = ext_head((float)(norm & 255), (float)((norm >> 8) & 255), (float)(norm >> 16));
+  if (sub == 1) ext[1] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 __global__ void prep_query_kernel(const uint8_t* __restrict__ q, int64_t m, int64_t m_pad,
-                                  int32_t* __restrict__ qnorm, __nv_bfloat16* __restrict__ qbf) {
+                                  int32_t* __restrict__ qnorm, __nv_bfloat16* __restrict__ qbf,
+                                  __nv_bfloat16* __restrict__ qext) {
   const int sub = threadIdx.x % kThreadsPerRow;
   const int64_t row = (int64_t)blockIdx.x * kRowsPerBlock + threadIdx.x / kThreadsPerRow;
   if (row >= m_pad) return;
@@ -57,6 +76,10 @@ __global__ void prep_query_kernel(const uint8_t* __restrict__ q, int64_t m, int6
     o[t] = pack_bf16x2(-2.0f * (float)x0, -2.0f * (float)x1);
   }
   if (qbf) *reinterpret_cast<uint4*>(qbf + row * kDim + sub * 8) = out;
+  if (qext && sub < 2) {
+    uint4* ext = reinterpret_cast<uint4*>(qext + row * kExt);
+    ext[sub] = sub == 0 ? ext_head(1.0f, 256.0f, 65536.0f) : make_uint4(0u, 0u, 0u, 0u);
+  }
 #pragma unroll
   for (int off = kThreadsPerRow / 2; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
   if (sub == 0 && row < m) qnorm[row] = ss;
@@ -76,7 +99,8 @@ __global__ void label_hist_kernel(const int32_t* __restrict__ labels, int64_t n,
 
 __global__ void gather_ref_kernel(const int64_t* __restrict__ perm, int64_t n, const uint8_t* __restrict__ src_u8,
                                   uint8_t* __restrict__ dst_u8, const __nv_bfloat16* __restrict__ src_bf,
-                                  __nv_bfloat16* __restrict__ dst_bf, const float* __restrict__ src_norm,
+                                  __nv_bfloat16* __restrict__ dst_bf, const __nv_bfloat16* __restrict__ src_ext,
+                                  __nv_bfloat16* __restrict__ dst_ext, const float* __restrict__ src_norm,
                                   float* __restrict__ dst_norm, const int32_t* __restrict__ src_lab,
                                   int32_t* __restrict__ dst_lab) {
   // one warp per row: 32 lanes x 4 bytes of uint8, 32 lanes x 8 bytes of bf16
@@ -86,6 +110,8 @@ __global__ void gather_ref_kernel(const int64_t* __restrict__ perm, int64_t n, c
   const int64_t from = perm[row];
   reinterpret_cast<uint32_t*>(dst_u8 + row * kDim)[lane] = reinterpret_cast<const uint32_t*>(src_u8 + from * kDim)[lane];
   reinterpret_cast<uint2*>(dst_bf + row * kDim)[lane] = reinterpret_cast<const uint2*>(src_bf + from * kDim)[lane];
+  if (lane < 2)
+    reinterpret_cast<uint4*>(dst_ext + row * kExt)[lane] = reinterpret_cast<const uint4*>(src_ext + from * kExt)[lane];
   if (lane == 0) {
     dst_norm[row] = src_norm[from];
     dst_lab[row] = src_lab[from];
@@ -108,17 +134,18 @@ cudaError_t launch_fill_float(float* dst, int64_t n, float v, cudaStream_t s) {
 }
 
 cudaError_t launch_prep_ref(const uint8_t* ref, int64_t n_ref, int64_t n_pad, __nv_bfloat16* ref_bf,
-                            float* rnorm, cudaStream_t s) {
+                            float* rnorm, __nv_bfloat16* ref_ext, cudaStream_t s) {
   const int64_t blocks = (n_pad + kRowsPerBlock - 1) / kRowsPerBlock;
-  prep_ref_kernel<<<(unsigned)blocks, kRowsPerBlock * kThreadsPerRow, 0, s>>>(ref, n_ref, n_pad, ref_bf, rnorm);
+  prep_ref_kernel<<<(unsigned)blocks, kRowsPerBlock * kThreadsPerRow, 0, s>>>(ref, n_ref, n_pad, ref_bf, rnorm,
+                                                                               ref_ext);
   return cudaGetLastError();
 }
 
 cudaError_t launch_prep_query(const uint8_t* q, int64_t m, int64_t m_pad, int32_t* qnorm, __nv_bfloat16* qbf,
-                              cudaStream_t s) {
+                              __nv_bfloat16* qext, cudaStream_t s) {
   if (m_pad == 0) return cudaSuccess;
   const int64_t blocks = (m_pad + kRowsPerBlock - 1) / kRowsPerBlock;
-  prep_query_kernel<<<(unsigned)blocks, kRowsPerBlock * kThreadsPerRow, 0, s>>>(q, m, m_pad, qnorm, qbf);
+  prep_query_kernel<<<(unsigned)blocks, kRowsPerBlock * kThreadsPerRow, 0, s>>>(q, m, m_pad, qnorm, qbf, qext);
   return cudaGetLastError();
 }
 
@@ -131,11 +158,12 @@ cudaError_t launch_label_hist(const int32_t* labels, int64_t n, int32_t C, unsig
 }
 
 cudaError_t launch_gather_ref(const int64_t* perm, int64_t n, const uint8_t* src_u8, uint8_t* dst_u8,
-                              const __nv_bfloat16* src_bf, __nv_bfloat16* dst_bf, const float* src_norm,
-                              float* dst_norm, const int32_t* src_lab, int32_t* dst_lab, cudaStream_t s) {
+                              const __nv_bfloat16* src_bf, __nv_bfloat16* dst_bf, const __nv_bfloat16* src_ext,
+                              __nv_bfloat16* dst_ext, const float* src_norm, float* dst_norm,
+                              const int32_t* src_lab, int32_t* dst_lab, cudaStream_t s) {
   const int64_t blocks = (n * 32 + 255) / 256;
-  gather_ref_kernel<<<(unsigned)blocks, 256, 0, s>>>(perm, n, src_u8, dst_u8, src_bf, dst_bf, src_norm, dst_norm,
-                                                     src_lab, dst_lab);
+  gather_ref_kernel<<<(unsigned)blocks, 256, 0, s>>>(perm, n, src_u8, dst_u8, src_bf, dst_bf, src_ext, dst_ext,
+                                                     src_norm, dst_norm, src_lab, dst_lab);
   return cudaGetLastError();
 }
 
