@@ -45,22 +45,29 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="caltech256-like")
     p.add_argument("--k", type=int, default=10)
+    p.add_argument("--classes", type=int, default=None, help="use the first C classes of the workload")
+    p.add_argument("--query-images", type=int, default=None, help="use the first Q query images")
+    p.add_argument("--method", choices=["local", "nbnn"], default="local",
+                   help="local: Local NBNN (Alg. 2); nbnn: original NBNN (Alg. 1)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
 
 
-def workload_config(w: synth.Workload, k: int) -> dict:
+def workload_config(w: synth.Workload, k: int, method: str = "local") -> dict:
+    local = method == "local"
+    op_gb = w.n_ref * (128 + 16) * 2 / 1e9
     return {
-        "workload": f"{w.name}: {w.notes}, k={k}",
+        "workload": f"{w.name}: {w.notes}" + (f", k={k}" if local else "")
+                    + (f"; first {w.n_classes} classes" if w.name.endswith(f"-C{w.n_classes}") else ""),
         "n_ref": w.n_ref,
         "n_classes": w.n_classes,
         "n_query_images": w.n_query_imgs,
         "query_descriptors": int(synth.query_counts(w).sum()),
-        "k": k,
-        "method": "Local NBNN (Alg. 2), exact search",
-        "l2": "inputs larger than L2 (2.95 GB BF16 reference operand re-read per query tile)",
+        "k": k if local else None,
+        "method": "Local NBNN (Alg. 2), exact search" if local else "original NBNN (Alg. 1), exact search",
+        "l2": f"inputs larger than L2 ({op_gb:.2f} GB BF16 reference operand, re-read per query tile)",
         "seed": w.seed,
     }
 
@@ -120,26 +127,34 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle timing
 
-def time_oracle(ref, labels, C, q, k, target_s: float, max_desc: int) -> dict:
-    """Local NBNN by the oracle on the first S query descriptors, S sized to
-    about target_s seconds of this host's cores."""
+def oracle_run(method, ref, labels, C, q, k, threads):
     import oracle
+    off = np.array([0, len(q)])
+    if method == "local":
+        return oracle.local_nbnn(ref, labels, C, q, off, k, threads=threads)
+    return oracle.nbnn(ref, labels, C, q, off, threads=threads)
+
+
+def time_oracle(method, ref, labels, C, q, k, target_s: float, max_desc: int) -> dict:
+    """The oracle on the first S query descriptors, S sized to about target_s
+    seconds of this host's cores."""
     threads = os.cpu_count() or 1
     s = min(max_desc, max(threads, 8))
     t0 = time.perf_counter()
-    oracle.local_nbnn(ref, labels, C, q[:s], np.array([0, s]), k, threads=threads)
+    oracle_run(method, ref, labels, C, q[:s], k, threads)
     dt = time.perf_counter() - t0
     per = dt / s
     s2 = int(min(max_desc, max(s, target_s / max(per, 1e-9))))
     s2 = max(threads, (s2 // threads) * threads) if s2 >= threads else s2
     if s2 > s:
         t0 = time.perf_counter()
-        oracle.local_nbnn(ref, labels, C, q[:s2], np.array([0, s2]), k, threads=threads)
+        oracle_run(method, ref, labels, C, q[:s2], k, threads)
         dt = time.perf_counter() - t0
         s = s2
+    name = f"Local NBNN, k={k}" if method == "local" else "original NBNN"
     return {"value": s / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"first {s} query descriptors of image 0 against all {len(ref)} references "
-                      f"(Local NBNN, k={k}), {dt:.1f} s"}
+                      f"({name}), {dt:.1f} s"}
 
 
 # ------------------------------------------------------------------ helpers
@@ -187,28 +202,28 @@ def run_reference(args, w):
         return
     ref, labels = synth.reference_set(w)
     q, off, _ = synth.query_set(w)
-    import oracle
     threads = os.cpu_count() or 1
     # per-step sample: sized from a calibration so the whole run stays within minutes
-    cal = time_oracle(ref, labels, w.n_classes, q, args.k, target_s=min(args.cpu_seconds, 8.0),
+    cal = time_oracle(args.method, ref, labels, w.n_classes, q, args.k, target_s=min(args.cpu_seconds, 8.0),
                       max_desc=int(off[1]))
     s = max(1, int(round(cal["value"] * 6.0)))  # about 6 s per step
     s = min(s, int(off[1]))
     for _ in range(args.warmup):
-        oracle.local_nbnn(ref, labels, w.n_classes, q[:s], np.array([0, s]), args.k, threads=threads)
+        oracle_run(args.method, ref, labels, w.n_classes, q[:s], args.k, threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.local_nbnn(ref, labels, w.n_classes, q[:s], np.array([0, s]), args.k, threads=threads)
+        oracle_run(args.method, ref, labels, w.n_classes, q[:s], args.k, threads)
     dt = time.perf_counter() - t0
     value = s * args.steps / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": workload_config(w, args.k),
+        "config": workload_config(w, args.k, args.method),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"each step: first {s} query descriptors of image 0 against all {len(ref)} "
-                                   f"references (Local NBNN, k={args.k}), plain C oracle"},
+                                   f"references ({'Local NBNN, k=%d' % args.k if args.method == 'local' else 'original NBNN'}),"
+                                   f" plain C oracle"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -238,9 +253,16 @@ def run_ours(args, w):
     totals = torch.empty((n_img, w.n_classes), dtype=torch.int64, device=dev)
     classes = torch.empty((n_img,), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    local = args.method == "local"
+
+    def step():
+        if local:
+            index.lnbnn_classify(q_d, off_d, k, out=(totals, classes))
+        else:
+            index.nbnn_classify(q_d, off_d, out=(totals, classes))
 
     for _ in range(args.warmup):
-        index.lnbnn_classify(q_d, off_d, k, out=(totals, classes))
+        step()
     index.sync()
 
     def barrier():
@@ -261,7 +283,7 @@ def run_ours(args, w):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        index.lnbnn_classify(q_d, off_d, k, out=(totals, classes))
+        step()
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
@@ -281,8 +303,19 @@ def run_ours(args, w):
     search_ms = prof["search_ms"] / max(prof["search_launches"], 1)
     flops = 2.0 * 128 * w.n_ref * M  # algorithmic, per launch
     achieved = flops / (search_ms / 1e3) / 1e12
-    peak = float(peaks["bf16_tflops_sustained"])
-    traffic = traffic_per_launch(M)
+    if local:
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": float(peaks["bf16_tflops_sustained"]),
+                    "unit": "TFLOP/s", "traffic": traffic_per_launch(M), "kernel": "knn_tc_kernel",
+                    "peak_source": f"bf16_tflops_sustained ({peak_src})"}
+    else:
+        # CUDA-core dp4a kernel: 4 byte-MACs (8 integer ops) per lane per cycle
+        props = torch.cuda.get_device_properties(dev)
+        peak = props.multi_processor_count * 128 * 8 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s (int8 dp4a)",
+                    "traffic": None, "kernel": "nbnn_simt_kernel",
+                    "peak_source": "SMs x 128 lanes x dp4a (8 ops) x max SM clock"}
+    roofline.update({"frac": roofline["achieved"] / roofline["peak"], "flops_per_launch": flops,
+                     "avg_launch_ms": search_ms})
 
     e2e = None
     if not args.no_e2e:
@@ -291,11 +324,12 @@ def run_ours(args, w):
         tot_h = torch.empty((n_img, w.n_classes), dtype=torch.int64).pin_memory()
         cls_h = torch.empty((n_img,), dtype=torch.int32).pin_memory()
         qn, on, tn, cn = q_h.numpy(), off_h.numpy(), tot_h.numpy(), cls_h.numpy()
-        index.classify_host(qn, on, k, tn, cn)  # warm the staging buffer
+        hk = k if local else None
+        index.classify_host(qn, on, hk, tn, cn)  # warm the staging buffer
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            index.classify_host(qn, on, k, tn, cn)
+            index.classify_host(qn, on, hk, tn, cn)
         e2e_dt = time.perf_counter() - t0
         if world > 1:
             import torch.distributed as dist
@@ -304,29 +338,29 @@ def run_ours(args, w):
             e2e_dt = float(t.item())
         e2e = {"value": M * args.steps * world / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(q.nbytes + off.nbytes),
                "d2h_bytes_per_step": int(tn.nbytes + cn.nbytes),
-               "api": "lnbnn_classify_host (pinned host buffers; copies, classify, copy-back, sync per step)"}
+               "api": ("lnbnn" if local else "nbnn") + "_classify_host (pinned host buffers; copies, classify, "
+                      "copy-back, sync per step)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = time_oracle(ref, labels, w.n_classes, q, k, args.cpu_seconds, int(off[1]))
+        cpu = time_oracle(args.method, ref, labels, w.n_classes, q, k, args.cpu_seconds, int(off[1]))
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": workload_config(w, k),
+            "config": workload_config(w, k, args.method),
             "images_per_s": n_img * args.steps * world / elapsed,
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": "knn_tc_kernel",
-                         "flops_per_launch": flops, "avg_launch_ms": search_ms,
-                         "peak_source": f"bf16_tflops_sustained ({peak_src})"},
+            "roofline": roofline,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": int(prof["kernel_launches"]),
             "clocks": clk,
             "profile": {"search_ms_total": prof["search_ms"], "other_ms_total": prof["other_ms"],
-                        "calls": prof["calls"]},
+                        "calls": prof["calls"], "search_sm_clock_ghz": prof["search_sm_clock_ghz"],
+                        "search_cycles_per_tile": prof["search_cycles_per_tile"],
+                        "mma_cycles_per_tile": 9 * 128},
         }
         print(json.dumps(line), flush=True)
     index.close()
@@ -338,6 +372,10 @@ def run_ours(args, w):
 def main():
     args = parse_args()
     w = synth.workload(args.workload)
+    if args.classes:
+        w = w.with_classes(args.classes)
+    if args.query_images:
+        w = w.with_query_imgs(args.query_images)
     if args.impl == "reference":
         run_reference(args, w)
     else:

@@ -169,6 +169,11 @@ typedef struct lnbnn_profile {
   int64_t search_launches;
   double search_ms;
   double other_ms;
+  /* tensor-core kNN search only: mean SM clock seen by its CTAs (GHz) and SM
+   * cycles per 128 x 256 tile, from clock64/globaltimer at each CTA's start
+   * and end (0 when no such launch was profiled) */
+  double search_sm_clock_ghz;
+  double search_cycles_per_tile;
 } lnbnn_profile;
 
 LNBNN_API lnbnn_status lnbnn_profile_enable(lnbnn_index *index, int enable);

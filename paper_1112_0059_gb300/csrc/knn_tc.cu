@@ -3,15 +3,15 @@
 //
 // For a tile of 128 query rows and 256 reference rows the MMA computes, in
 // FP32 TMEM accumulators,
-//     acc[i][j] = sum_t (-2 q_it) r_jt + (1, 256, 65536) . (d0, d1, d2)_j
-//               = ||r_j||^2 - 2 q_i . r_j,
-// the last term being a 16-wide K-extension that carries each reference's
-// squared norm as base-256 digits.  BF16 holds 0..255, -2q and the digits
-// exactly; every product and partial sum is an integer below 2^24 in
-// magnitude, so acc is exact.  The epilogue keeps, per query row, the k+1
-// smallest keys (acc + ||q_i||^2, j) = (||q_i - r_j||^2, j): one compare per
-// element against the row's current (k+1)-th distance.  The distance matrix
-// never leaves the SM.
+//     acc[i][j] = sum_t (-2 q_it) r_jt + (1, 256, 65536, e0, e1, e2)_i . (d0, d1, d2, 1, 256, 65536)_j
+//               = ||r_j||^2 + ||q_i||^2 - 2 q_i . r_j = ||q_i - r_j||^2,
+// the last term being a 16-wide K-extension that carries both squared norms as
+// base-256 digits.  BF16 holds 0..255, -2q and the digits exactly; every
+// product and partial sum is an integer below 2^24 in magnitude, so acc is the
+// exact squared distance.  Non-negative floats order like their bit patterns,
+// so the epilogue tests 32 columns with an integer minimum and one compare
+// against the row's current (k+1)-th distance, and keeps the k+1 smallest
+// (distance, row) pairs.  The distance matrix never leaves the SM.
 //
 // Roles (one CTA = 128 query rows x one reference split):
 //   warp 0, one thread : TMA producer (query tile once; reference K-chunks
@@ -19,7 +19,11 @@
 //                        second chunk of each tile)
 //   warp 1, one thread : tcgen05.mma issuer (9 MMAs of 128x256x16 per tile);
 //                        warp 1 also owns the TMEM allocation
-//   warps 2-5          : epilogue, one thread per query row (TMEM lane), two
+//   warps 2-9          : epilogue: two warps per TMEM lane quarter, each
+//                        taking a 128-column half of every tile with one
+//                        thread per query row (TMEM lane); each keeps its own
+//                        sorted list of the k+1 nearest (in registers for
+//                        k+1 <= 16, otherwise a heap in global memory); two
 //                        256-column FP32 accumulators in flight
 // Every wait is bounded; on expiry the CTA records a timeout in the index's
 // device error word, drains what it issued and returns.
@@ -45,8 +49,11 @@ constexpr uint32_t kAExtBytes = kBM * kExt * 2;      // 4 KB
 constexpr uint32_t kBChunkBytes = kBN * kBK * 2;     // 32 KB
 constexpr uint32_t kBExtBytes = kBN * kExt * 2;      // 8 KB
 constexpr uint32_t kStageBytes = kBChunkBytes + kBExtBytes;
-constexpr int kEpiWarps = 4;
+constexpr int kEpiPerQuarter = kTcListsPerSplit;  // epilogue warps per TMEM lane quarter
+constexpr int kEpiWarps = 4 * kEpiPerQuarter;
+constexpr int kEpiCols = kBN / kEpiPerQuarter;     // columns of a tile per epilogue warp
 constexpr int kThreads = 64 + 32 * kEpiWarps;
+static_assert(kEpiCols == 128, "each epilogue warp reads its slice as four 32-column TMEM loads");
 constexpr uint32_t kAccCols = kBN;        // FP32 columns per accumulator
 constexpr uint32_t kTmemCols = 2 * kAccCols;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
@@ -61,7 +68,6 @@ constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;  // + alignment slack
 static_assert(kStages % kKChunks == 0, "a tile's chunks map to fixed stage parities");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
-constexpr float kNoThreshold = 3.0e38f;
 
 struct Bars {
   uint32_t base;
@@ -78,26 +84,130 @@ __device__ __forceinline__ void flag_timeout(volatile uint32_t* abort_flag, uint
   atomicOr(dev_err, kDevErrTimeout);
 }
 
-// Rare path of the epilogue: offer the elements of one 32-column group that
-// pass the row's threshold to its heap.
-__device__ __forceinline__ void offer_group(TopK& top, float& thr, int32_t qn, const uint32_t (&v)[32], int64_t col0) {
-  float d[32];
+// Sorted list of the K1 smallest (distance, row) pairs seen so far, held in
+// registers: ascending in slots [KMAX-K1, KMAX); the slots below hold the
+// distance -1, which no real distance displaces, so the list always has K1
+// live entries and its largest is slot KMAX-1.  Columns arrive in increasing
+// row order, so strict comparisons keep equal distances in row order.
+template <int KMAX>
+struct RegList {
+  int32_t d[KMAX];
+  uint32_t r[KMAX];
+
+  __device__ __forceinline__ void init(int K1) {
 #pragma unroll
-  for (int j = 0; j < 32; ++j) d[j] = __uint_as_float(v[j]);
-#pragma unroll 1
-  for (int j = 0; j < 32; ++j) {
-    if (d[j] < thr) {
-      top.push(make_key((uint32_t)((int32_t)d[j] + qn), (uint32_t)(col0 + j)));
-      if (top.size == top.cap) thr = (float)(top.threshold - qn);
+    for (int i = 0; i < KMAX; ++i) {
+      d[i] = i < KMAX - K1 ? -1 : INT32_MAX;
+      r[i] = 0xFFFFFFFFu;
+    }
+  }
+  __device__ __forceinline__ int32_t worst() const { return d[KMAX - 1]; }
+  // new[i] = old[i-1] if x sorts before it, else min(x, old[i]) (x < worst()).
+  __device__ __forceinline__ void insert(int32_t x, uint32_t row) {
+#pragma unroll
+    for (int i = KMAX - 1; i > 0; --i) {
+      const bool shift = x < d[i - 1];
+      const bool place = !shift && x < d[i];
+      const int32_t nd = shift ? d[i - 1] : (place ? x : d[i]);
+      const uint32_t nr = shift ? r[i - 1] : (place ? row : r[i]);
+      d[i] = nd;
+      r[i] = nr;
+    }
+    if (x < d[0]) {
+      d[0] = x;
+      r[0] = row;
+    }
+  }
+  // Writes the K1 live entries ascending (unfilled slots as kEmptyKey).
+  __device__ __forceinline__ void store(uint64_t* out, int K1) const {
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i)
+      if (i >= KMAX - K1) out[i - (KMAX - K1)] = d[i] == INT32_MAX ? kEmptyKey : make_key((uint32_t)d[i], r[i]);
+  }
+};
+
+// Bits of a non-negative float (or -0) as int32; ordered like the float.
+__device__ __forceinline__ int32_t thr_bits(int32_t dist) { return __float_as_int((float)dist); }
+
+// v[j] for a run-time j without dynamic register indexing (no local memory):
+// a 5-level select tree on the bits of j.
+__device__ __forceinline__ int32_t select32(const uint32_t (&v)[32], int j) {
+  uint32_t t[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) t[i] = (j & 1) ? v[2 * i + 1] : v[2 * i];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) t[i] = (j & 2) ? t[2 * i + 1] : t[2 * i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) t[i] = (j & 4) ? t[2 * i + 1] : t[2 * i];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) t[i] = (j & 8) ? t[2 * i + 1] : t[2 * i];
+  return (int32_t)((j & 16) ? t[1] : t[0]);
+}
+
+// Bit j set when column j's distance is below the threshold.
+__device__ __forceinline__ uint32_t hit_mask(const uint32_t (&v)[32], int32_t thr) {
+  uint32_t mask = 0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) mask |= ((int32_t)v[j] < thr ? 1u : 0u) << j;
+  return mask;
+}
+
+// Rare path: offer the columns of one 32-column group whose distance is below
+// the list's current largest, in column order (the threshold tightens as
+// entries are inserted, so each candidate is checked again).  v holds float
+// bit patterns of exact distances.
+template <int KMAX>
+__device__ __forceinline__ void offer_group(RegList<KMAX>& L, TopK&, int32_t& thr, const uint32_t (&v)[32],
+                                            int64_t col0) {
+  for (uint32_t mask = hit_mask(v, thr); mask; mask &= mask - 1) {
+    const int j = __ffs(mask) - 1;
+    const int32_t bits = select32(v, j);
+    if (bits < thr) {
+      L.insert(__float2int_rn(__int_as_float(bits)), (uint32_t)(col0 + j));
+      thr = thr_bits(L.worst());
     }
   }
 }
 
+template <>
+struct RegList<0> {
+  __device__ __forceinline__ void init(int) {}
+};
+
+template <>
+__device__ __forceinline__ void offer_group<0>(RegList<0>&, TopK& top, int32_t& thr, const uint32_t (&v)[32],
+                                               int64_t col0) {
+  for (uint32_t mask = hit_mask(v, thr); mask; mask &= mask - 1) {
+    const int j = __ffs(mask) - 1;
+    const int32_t bits = select32(v, j);
+    if (bits < thr) {
+      top.push(make_key((uint32_t)__float2int_rn(__int_as_float(bits)), (uint32_t)(col0 + j)));
+      thr = thr_bits(top.threshold);
+    }
+  }
+}
+
+// One 32-column group: integer minimum of the bit patterns, one compare.
+template <int KMAX>
+__device__ __forceinline__ void scan_group(RegList<KMAX>& L, TopK& top, int32_t& thr, bool active,
+                                           const uint32_t (&v)[32], int64_t col0) {
+  int32_t mn = (int32_t)v[0];
+#pragma unroll
+  for (int j = 1; j < 32; ++j) mn = min(mn, (int32_t)v[j]);
+  const bool hit = active && mn < thr;
+  if (__any_sync(0xffffffffu, hit)) {
+    if (hit) offer_group<KMAX>(L, top, thr, v, col0);
+    __syncwarp();
+  }
+}
+
+// KMAX > 0: per-row lists in registers (K1 <= KMAX); KMAX = 0: heaps in global memory.
+template <int KMAX>
 __global__ void __launch_bounds__(kThreads, 1)
     knn_tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_qe,
-                  const __grid_constant__ CUtensorMap tmap_r, const __grid_constant__ CUtensorMap tmap_re,
-                  const int32_t* __restrict__ qnorm, int64_t m, int64_t n_ref, int64_t split_len, int K1,
-                  uint64_t* __restrict__ lists, int64_t stride, uint32_t* __restrict__ dev_err) {
+                  const __grid_constant__ CUtensorMap tmap_r, const __grid_constant__ CUtensorMap tmap_re, int64_t m,
+                  int64_t n_ref, int64_t split_len, int K1, uint64_t* __restrict__ lists, int64_t stride,
+                  uint32_t* __restrict__ dev_err, unsigned long long* __restrict__ stats) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
@@ -174,6 +284,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---------------------------------------------------------- MMA issuer
       constexpr uint32_t idesc = idesc_bf16_f32(kBM, kBN);
+      const long long clk0 = clock64();
+      const uint64_t ns0 = globaltimer_ns();
       bool ok = mbar_wait(bars.afull(), 0, kWaitLimitNs, abort_flag);
       if (!ok) flag_timeout(abort_flag, dev_err);
       tc_fence_after();
@@ -213,15 +325,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t never = 0;
       mma_commit(bars.drain());
       mbar_wait(bars.drain(), 0, kWaitLimitNs, &never);
+      if (stats) {
+        atomicAdd(stats + 0, (unsigned long long)(clock64() - clk0));
+        atomicAdd(stats + 1, (unsigned long long)(globaltimer_ns() - ns0));
+        atomicAdd(stats + 2, (unsigned long long)ntiles);
+        atomicAdd(stats + 3, 1ull);
+      }
     }
   } else {
     // ------------------------------------------------------------- epilogue
-    const int quarter = warp & 3;  // this warp may read TMEM lanes [32*quarter, 32*quarter+32)
+    const int quarter = warp & 3;          // this warp may read TMEM lanes [32*quarter, 32*quarter+32)
+    const int half = (warp - 2) >> 2;      // its 128-column half of every tile
     const int64_t row = m0 + quarter * 32 + lane;
     const bool active = row < m;
-    const int32_t qn = active ? qnorm[row] : 0;
-    TopK top(lists + ((int64_t)blockIdx.y * stride + (active ? row : 0)) * K1, K1);
-    float thr = kNoThreshold;  // acc (= ||q - r||^2 - ||q||^2) must be below this
+    uint64_t* out = lists + (((int64_t)blockIdx.y * kEpiPerQuarter + half) * stride + (active ? row : 0)) * K1;
+    RegList<KMAX> L;
+    L.init(K1);
+    TopK top(out, K1);
+    int32_t thr = thr_bits(INT32_MAX);  // float bits of the current largest kept distance
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
@@ -231,33 +352,38 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       tc_fence_after();
-      const int64_t jt = j_begin + (int64_t)t * kBN;
-#pragma unroll 1
-      for (int c = 0; c < kBN / 64; ++c) {
-        uint32_t va[32], vb[32];
-        const uint32_t taddr = tmem_base + lane_addr + b * kAccCols + c * 64;
-        tmem_ld_32x32b_x32(taddr, va);
-        tmem_ld_32x32b_x32(taddr + 32, vb);
-        tmem_ld_wait(va);
-        reg_fence(vb);
-        bool hit_a = false, hit_b = false;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          hit_a |= __uint_as_float(va[j]) < thr;
-          hit_b |= __uint_as_float(vb[j]) < thr;
-        }
-        hit_a = hit_a && active;
-        hit_b = hit_b && active;
-        if (__any_sync(0xffffffffu, hit_a || hit_b)) {
-          if (hit_a) offer_group(top, thr, qn, va, jt + c * 64);
-          if (hit_b) offer_group(top, thr, qn, vb, jt + c * 64 + 32);
-          __syncwarp();
-        }
+      // two rounds of 64 columns; the accumulator goes back as soon as the
+      // second round is in registers
+      const uint32_t taddr = tmem_base + lane_addr + b * kAccCols + half * kEpiCols;
+      const int64_t col0 = j_begin + (int64_t)t * kBN + half * kEpiCols;
+      {
+        uint32_t v0[32], v1[32];
+        tmem_ld_32x32b_x32(taddr, v0);
+        tmem_ld_32x32b_x32(taddr + 32, v1);
+        tmem_ld_wait(v0);
+        reg_fence(v1);
+        scan_group<KMAX>(L, top, thr, active, v0, col0);
+        scan_group<KMAX>(L, top, thr, active, v1, col0 + 32);
       }
-      tc_fence_before();
-      mbar_arrive(bars.tempty(b));
+      {
+        uint32_t v2[32], v3[32];
+        tmem_ld_32x32b_x32(taddr + 64, v2);
+        tmem_ld_32x32b_x32(taddr + 96, v3);
+        tmem_ld_wait(v2);
+        reg_fence(v3);
+        tc_fence_before();
+        mbar_arrive(bars.tempty(b));
+        scan_group<KMAX>(L, top, thr, active, v2, col0 + 64);
+        scan_group<KMAX>(L, top, thr, active, v3, col0 + 96);
+      }
     }
-    if (active) top.finish();
+    if (active) {
+      if constexpr (KMAX > 0) {
+        L.store(out, K1);
+      } else {
+        top.finish();
+      }
+    }
   }
 
   tc_fence_before();
@@ -312,19 +438,20 @@ bool make_tc_tensor_maps(const __nv_bfloat16* ref_bf, const __nv_bfloat16* sref_
 }
 
 cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf,
-                          const __nv_bfloat16* qext, int64_t m, int64_t m_pad, const int32_t* qnorm, int64_t n_ref,
-                          int splits, int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
-                          cudaStream_t s) {
+                          const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
+                          int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
+                          unsigned long long* stats, cudaStream_t s) {
   if (m == 0) return cudaSuccess;
   if (m_pad % kBM != 0 || split_len % kBN != 0) return cudaErrorInvalidValue;
   CUtensorMap tq, tqe;
   if (!encode_operand(&tq, &tqe, qbf, qext, (uint64_t)m_pad, kBM)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  auto kernel = K1 <= kTcRegListMax ? knn_tc_kernel<kTcRegListMax> : knn_tc_kernel<0>;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(m_pad / kBM), (unsigned)splits);
-  knn_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(tq, tqe, sorted_copy ? maps.sref : maps.ref,
-                                                   sorted_copy ? maps.sref_ext : maps.ref_ext, qnorm, m, n_ref,
-                                                   split_len, K1, lists, stride, dev_err);
+  kernel<<<grid, kThreads, kSmemBytes, s>>>(tq, tqe, sorted_copy ? maps.sref : maps.ref,
+                                            sorted_copy ? maps.sref_ext : maps.ref_ext, m, n_ref, split_len, K1,
+                                            lists, stride, dev_err, stats);
   return cudaGetLastError();
 }
 

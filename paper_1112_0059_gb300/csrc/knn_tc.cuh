@@ -9,6 +9,12 @@ namespace lnbnn {
 
 // References per tile of the tensor-core kernels (the MMA N extent).
 constexpr int kTcRefTile = 256;
+// Epilogue warps per TMEM lane quarter.  Each owns a column slice of every
+// tile and keeps its own top-K1 list per query row, so one reference split
+// yields this many sorted lists per row (merged afterwards).
+constexpr int kTcListsPerSplit = 2;
+// Largest K1 kept in registers; larger lists live in global memory.
+constexpr int kTcRegListMax = 16;
 
 // TMA descriptors over an index's BF16 reference operands (caller's row order
 // and class-sorted order).  Encoded once at index creation.
@@ -22,11 +28,14 @@ bool make_tc_tensor_maps(const __nv_bfloat16* ref_bf, const __nv_bfloat16* sref_
 
 // Exact top-K1 search on tensor cores.  qbf: BF16 -2q operand [m_pad, 128];
 // qext: its K-extension [m_pad, 16].  Split s scans reference rows
-// [s * split_len, min((s+1) * split_len, n_ref)); its sorted list for query row i
-// is written at lists[(s * stride + i) * K1].
+// [s * split_len, min((s+1) * split_len, n_ref)) and writes kTcListsPerSplit
+// sorted lists per query row i, list w at lists[((s * kTcListsPerSplit + w) *
+// stride + i) * K1]; the K1 smallest keys of their union are the split's answer.
 cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf,
-                          const __nv_bfloat16* qext, int64_t m, int64_t m_pad, const int32_t* qnorm, int64_t n_ref,
-                          int splits, int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
-                          cudaStream_t s);
+                          const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
+                          int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
+                          unsigned long long* stats, cudaStream_t s);
+// stats (may be null): the MMA thread of every CTA adds its SM cycles,
+// globaltimer nanoseconds and tile count to stats[0..2] and 1 to stats[3].
 
 }  // namespace lnbnn

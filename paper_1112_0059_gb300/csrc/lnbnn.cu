@@ -1,6 +1,7 @@
 // The C ABI of include/lnbnn.h: index ownership, argument checks, workspace
 // and the launch sequence of each call.  All arithmetic runs in the kernels.
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -45,6 +46,7 @@ struct lnbnn_index {
   };
   bool prof_on = false;
   lnbnn_profile prof{};
+  unsigned long long* prof_stats = nullptr;  // [4] device counters of the search kernel
   std::vector<CallEvents> prof_pending, prof_free;
 };
 
@@ -58,6 +60,7 @@ namespace {
 
 lnbnn_status status_of(cudaError_t e) {
   if (e == cudaSuccess) return LNBNN_OK;
+  if (getenv("LNBNN_DEBUG")) fprintf(stderr, "lnbnn: CUDA error: %s\n", cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return LNBNN_ERR_OOM;
   (void)cudaGetLastError();
   return LNBNN_ERR_CUDA;
@@ -91,6 +94,7 @@ void free_index(lnbnn_index* ix) {
   cudaFree(ix->labels);
   cudaFree(ix->class_off_d);
   cudaFree(ix->dev_err);
+  cudaFree(ix->prof_stats);
   cudaFree(ix->ws);
   cudaFree(ix->stage);
   delete ix;
@@ -181,6 +185,7 @@ int choose_splits(const lnbnn_index* ix, int64_t m_pad) {
 struct KnnPlan {
   int64_t m_pad;
   int splits;
+  int lists;  // sorted lists per query row the search writes (merged when > 1)
   int64_t split_len;
   int K1;
   size_t off_qnorm, off_qbf, off_qext, off_lists, off_merged, bytes;
@@ -198,8 +203,9 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, bool tensor) {
   p.off_qnorm = c.take<int32_t>(p.m_pad);
   p.off_qbf = tensor ? c.take<__nv_bfloat16>(p.m_pad * kDim) : 0;
   p.off_qext = tensor ? c.take<__nv_bfloat16>(p.m_pad * kExt) : 0;
-  p.off_lists = c.take<uint64_t>((size_t)p.splits * p.m_pad * K1);
-  p.off_merged = p.splits > 1 ? c.take<uint64_t>((size_t)p.m_pad * K1) : p.off_lists;
+  p.lists = p.splits * (tensor ? kTcListsPerSplit : 1);
+  p.off_lists = c.take<uint64_t>((size_t)p.lists * p.m_pad * K1);
+  p.off_merged = p.lists > 1 ? c.take<uint64_t>((size_t)p.m_pad * K1) : p.off_lists;
   p.bytes = c.off;
   return p;
 }
@@ -225,15 +231,15 @@ lnbnn_status run_knn(lnbnn_index* ix, const uint8_t* q, int64_t m, int K1, cudaS
   prof.launched(1);
   prof.mark(1);
   if (tensor) {
-    CK(launch_knn_tc(ix->tc, /*sorted_copy=*/false, qbf, qext, m, p.m_pad, qnorm, ix->n_ref, p.splits, p.split_len,
-                     K1, part, p.m_pad, ix->dev_err, s));
+    CK(launch_knn_tc(ix->tc, /*sorted_copy=*/false, qbf, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, K1,
+                     part, p.m_pad, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, s));
   } else {
     CK(launch_knn_simt(q, m, qnorm, ix->ref_u8, ix->rnorm, ix->n_ref, p.splits, p.split_len, K1, part, p.m_pad, s));
   }
   prof.launched(1, true);
   prof.mark(2);
-  if (p.splits > 1) {
-    CK(launch_merge_lists(part, p.splits, m, p.m_pad, K1, merged, s));
+  if (p.lists > 1) {
+    CK(launch_merge_lists(part, p.lists, m, p.m_pad, K1, merged, s));
     prof.launched(1);
   }
   *lists = merged;
@@ -534,6 +540,10 @@ lnbnn_status lnbnn_profile_enable(lnbnn_index* index, int enable) {
   index->prof_pending.clear();
   index->prof = lnbnn_profile{};
   index->prof_on = enable != 0;
+  if (index->prof_on) {
+    if (!index->prof_stats) CK(cudaMalloc(&index->prof_stats, 4 * sizeof(unsigned long long)));
+    CK(cudaMemset(index->prof_stats, 0, 4 * sizeof(unsigned long long)));
+  }
   return LNBNN_OK;
 }
 
@@ -550,6 +560,12 @@ lnbnn_status lnbnn_profile_read(lnbnn_index* index, lnbnn_profile* out) {
     index->prof_free.push_back(ce);
   }
   index->prof_pending.clear();
+  if (index->prof_stats) {
+    unsigned long long st[4] = {0, 0, 0, 0};
+    CK(cudaMemcpy(st, index->prof_stats, sizeof st, cudaMemcpyDeviceToHost));
+    index->prof.search_sm_clock_ghz = st[1] ? (double)st[0] / (double)st[1] : 0.0;
+    index->prof.search_cycles_per_tile = st[2] ? (double)st[0] / (double)st[2] : 0.0;
+  }
   *out = index->prof;
   return LNBNN_OK;
 }

@@ -100,8 +100,9 @@ extern "C" LNBNN_API lnbnn_status knn_search_noalloc(const uint8_t* ref, int64_t
   const size_t o_qn = L.take<int32_t>((size_t)m_pad);
   const size_t o_qbf = L.take<__nv_bfloat16>((size_t)m_pad * kDim);
   const size_t o_qext = L.take<__nv_bfloat16>((size_t)m_pad * kExt);
-  const size_t o_lists = L.take<uint64_t>((size_t)splits * m_pad * k);
-  const size_t o_merged = splits > 1 ? L.take<uint64_t>((size_t)m_pad * k) : o_lists;
+  const int64_t n_lists = splits * kTcListsPerSplit;
+  const size_t o_lists = L.take<uint64_t>((size_t)n_lists * m_pad * k);
+  const size_t o_merged = n_lists > 1 ? L.take<uint64_t>((size_t)m_pad * k) : o_lists;
   if (L.off > (size_t)LNBNN_NOALLOC_SCRATCH_BYTES) return LNBNN_ERR_SCRATCH_LIMIT;
 
   char* b = static_cast<char*>(base);
@@ -124,9 +125,9 @@ extern "C" LNBNN_API lnbnn_status knn_search_noalloc(const uint8_t* ref, int64_t
   if (e == cudaSuccess) e = launch_prep_ref(ref, n_ref, n_pad, ref_bf, rnorm, ref_ext, s);
   if (e == cudaSuccess) e = launch_prep_query(queries, n_queries, m_pad, qnorm, qbf, qext, s);
   if (e == cudaSuccess)
-    e = launch_knn_tc(maps, false, qbf, qext, n_queries, m_pad, qnorm, n_ref, (int)splits, split_len, k, lists,
-                      m_pad, err, s);
-  if (e == cudaSuccess && splits > 1) e = launch_merge_lists(lists, (int)splits, n_queries, m_pad, k, merged, s);
+    e = launch_knn_tc(maps, false, qbf, qext, n_queries, m_pad, n_ref, (int)splits, split_len, k, lists, m_pad, err,
+                      nullptr, s);
+  if (e == cudaSuccess && n_lists > 1) e = launch_merge_lists(lists, (int)n_lists, n_queries, m_pad, k, merged, s);
   if (e == cudaSuccess) e = launch_extract_knn(merged, n_queries, k, k, idx, dist, s);
   uint32_t herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);

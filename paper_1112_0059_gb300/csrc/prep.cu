@@ -21,10 +21,11 @@ __device__ __forceinline__ uint32_t bf16_bits(float v) {
   return (uint32_t)*reinterpret_cast<unsigned short*>(&b);
 }
 
-// Row of the K-extension: first 8 BF16 values (a, b, c, 0, 0, 0, 0, 0); the
-// other 8 are zero.
-__device__ __forceinline__ uint4 ext_head(float a, float b, float c) {
-  return make_uint4(bf16_bits(a) | (bf16_bits(b) << 16), bf16_bits(c), 0u, 0u);
+// First 8 BF16 values of a K-extension row: (a, b, c, d, e, f, 0, 0); the
+// other 8 values of the row are zero.
+__device__ __forceinline__ uint4 ext_head(float a, float b, float c, float d, float e, float f) {
+  return make_uint4(bf16_bits(a) | (bf16_bits(b) << 16), bf16_bits(c) | (bf16_bits(d) << 16),
+                    bf16_bits(e) | (bf16_bits(f) << 16), 0u);
 }
 
 __global__ void prep_ref_kernel(const uint8_t* __restrict__ ref, int64_t n_ref, int64_t n_pad,
@@ -50,10 +51,12 @@ __global__ void prep_ref_kernel(const uint8_t* __restrict__ ref, int64_t n_ref, 
   for (int off = kThreadsPerRow / 2; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
   const int32_t norm = row < n_ref ? ss : (int32_t)kPadNorm;
   if (sub == 0) rnorm[row] = (float)norm;
-  // base-256 digits of the norm: d0 + 256 d1 + 65536 d2 (d2 <= 127 for real
-  // rows, 512 for padding rows); each digit is exact in BF16
+  // K-extension (d0, d1, d2, 1, 256, 65536): base-256 digits of the norm,
+  // d0 + 256 d1 + 65536 d2 (d2 <= 127 for real rows, 512 for padding rows),
+  // then the weights that pick up the query's norm digits; all exact in BF16
   uint4* ext = reinterpret_cast<uint4*>(ref_ext + row * kExt);
-  if (sub == 0) ext[0] = ext_head((float)(norm & 255), (float)((norm >> 8) & 255), (float)(norm >> 16));
+  if (sub == 0)
+    ext[0] = ext_head((float)(norm & 255), (float)((norm >> 8) & 255), (float)(norm >> 16), 1.0f, 256.0f, 65536.0f);
   if (sub == 1) ext[1] = make_uint4(0u, 0u, 0u, 0u);
 }
 
@@ -76,13 +79,18 @@ __global__ void prep_query_kernel(const uint8_t* __restrict__ q, int64_t m, int6
     o[t] = pack_bf16x2(-2.0f * (float)x0, -2.0f * (float)x1);
   }
   if (qbf) *reinterpret_cast<uint4*>(qbf + row * kDim + sub * 8) = out;
-  if (qext && sub < 2) {
-    uint4* ext = reinterpret_cast<uint4*>(qext + row * kExt);
-    ext[sub] = sub == 0 ? ext_head(1.0f, 256.0f, 65536.0f) : make_uint4(0u, 0u, 0u, 0u);
-  }
 #pragma unroll
   for (int off = kThreadsPerRow / 2; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
   if (sub == 0 && row < m) qnorm[row] = ss;
+  if (qext && sub < 2) {
+    // K-extension (1, 256, 65536, e0, e1, e2): weights for the reference's norm
+    // digits, then the base-256 digits of this query's norm, so the MMA yields
+    // ||r||^2 + ||q||^2 - 2 q.r, the exact squared distance
+    uint4* ext = reinterpret_cast<uint4*>(qext + row * kExt);
+    ext[sub] = sub == 0 ? ext_head(1.0f, 256.0f, 65536.0f, (float)(ss & 255), (float)((ss >> 8) & 255),
+                                   (float)(ss >> 16))
+                        : make_uint4(0u, 0u, 0u, 0u);
+  }
 }
 
 __global__ void label_hist_kernel(const int32_t* __restrict__ labels, int64_t n, int32_t C,

@@ -42,7 +42,8 @@ EXPORTS = ["lnbnn_index_create", "lnbnn_index_destroy", "lnbnn_index_info", "knn
 class Profile(ctypes.Structure):
     """Mirror of ``lnbnn_profile`` (include/lnbnn.h)."""
     _fields_ = [("calls", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("search_launches", ctypes.c_int64), ("search_ms", ctypes.c_double), ("other_ms", ctypes.c_double)]
+                ("search_launches", ctypes.c_int64), ("search_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
+                ("search_sm_clock_ghz", ctypes.c_double), ("search_cycles_per_tile", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
