@@ -20,8 +20,9 @@ constexpr uint64_t kEmptyKey = ~0ull;
 constexpr float kPadNorm = 33554432.0f;  // 2^25
 // Reference rows are padded to a multiple of this (the widest reference tile).
 constexpr int kRefPad = 256;
-// Query rows are padded to a multiple of this (the query tile of every kernel).
-constexpr int kQueryPad = 128;
+// Query rows are padded to a multiple of this (two 128-row query tiles: one
+// cluster of the tensor-core search).
+constexpr int kQueryPad = 256;
 
 // Width of the K-extension that carries ||r||^2 into the tensor-core
 // contraction: a reference row gets the base-256 digits (d0, d1, d2) of its
@@ -65,11 +66,6 @@ cudaError_t launch_gather_ref(const int64_t* perm, int64_t n, const uint8_t* src
 
 // dst[0..n) = v
 cudaError_t launch_fill_float(float* dst, int64_t n, float v, cudaStream_t s);
-
-// Exact top-(K1) search on CUDA cores: lists[split][row][0..K1) sorted keys.
-cudaError_t launch_knn_simt(const uint8_t* q, int64_t m, const int32_t* qnorm, const uint8_t* ref,
-                            const float* rnorm, int64_t n_ref, int splits, int64_t split_len, int K1,
-                            uint64_t* lists, int64_t list_stride_rows, cudaStream_t s);
 
 // Merge `splits` sorted lists per row into one sorted list of K1 keys.
 cudaError_t launch_merge_lists(const uint64_t* lists, int splits, int64_t m, int64_t list_stride_rows,

@@ -1,9 +1,8 @@
-// Exact search on CUDA cores (dp4a): the k+1 nearest references of Alg. 2 and
-// the per-class nearest distance NN_C of Alg. 1.  One thread owns one query
-// row; reference tiles are staged in shared memory and read by broadcast.
-// ||q - r||^2 = ||q||^2 + ||r||^2 - 2 q.r, all exact in 32-bit integers.
+// Original NBNN on CUDA cores (dp4a): the per-class nearest distance NN_C of
+// Alg. 1.  One thread owns one query row; reference tiles are staged in
+// shared memory and read by broadcast.  ||q - r||^2 = ||q||^2 + ||r||^2 - 2 q.r,
+// all exact in 32-bit integers.
 #include "internal.cuh"
-#include "topk.cuh"
 
 namespace lnbnn {
 namespace {
@@ -44,41 +43,6 @@ __device__ __forceinline__ uint32_t dot_u8(const uint32_t (&qw)[32], const uint4
     acc = __dp4a(qw[4 * v + 3], x.w, acc);
   }
   return acc;
-}
-
-// grid: (query blocks, splits).  Split s scans reference rows
-// [s * split_len, min((s+1) * split_len, n_ref)) in increasing order, keeping the
-// K1 smallest (distance, row) keys in a max-heap at lists[(s*stride+row)*K1].
-__global__ void __launch_bounds__(kThreads) knn_simt_kernel(const uint8_t* __restrict__ q, int64_t m,
-                                                            const int32_t* __restrict__ qnorm,
-                                                            const uint8_t* __restrict__ ref,
-                                                            const float* __restrict__ rnorm, int64_t n_ref,
-                                                            int64_t split_len, int K1, uint64_t* __restrict__ lists,
-                                                            int64_t stride) {
-  __shared__ uint4 tile[kTile][8];
-  __shared__ int32_t tnorm[kTile];
-  const int64_t row = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  const bool active = row < m;
-  uint32_t qw[32];
-  load_query(q, row, active, qw);
-  const int32_t qn = active ? qnorm[row] : 0;
-  const int64_t j_begin = (int64_t)blockIdx.y * split_len;
-  const int64_t j_end = min(j_begin + split_len, n_ref);
-  uint64_t* heap = lists + ((int64_t)blockIdx.y * stride + (active ? row : 0)) * K1;
-  TopK top(heap, K1);
-  for (int64_t j0 = j_begin; j0 < j_end; j0 += kTile) {
-    __syncthreads();
-    stage_tile(ref, j0, j_end, tile);
-    if (threadIdx.x < kTile) tnorm[threadIdx.x] = j0 + threadIdx.x < j_end ? (int32_t)rnorm[j0 + threadIdx.x] : 0;
-    __syncthreads();
-    if (!active) continue;
-    const int nt = (int)min((int64_t)kTile, j_end - j0);
-    for (int r = 0; r < nt; ++r) {
-      const int32_t d = qn + tnorm[r] - 2 * (int32_t)dot_u8(qw, tile[r]);
-      if (d < top.threshold) top.push(make_key((uint32_t)d, (uint32_t)(j0 + r)));
-    }
-  }
-  if (active) top.finish();
 }
 
 // Alg. 1 per class over the class-sorted copy: block (bx, g) scans the
@@ -128,15 +92,6 @@ __global__ void __launch_bounds__(kThreads) nbnn_simt_kernel(const uint8_t* __re
 }
 
 }  // namespace
-
-cudaError_t launch_knn_simt(const uint8_t* q, int64_t m, const int32_t* qnorm, const uint8_t* ref, const float* rnorm,
-                            int64_t n_ref, int splits, int64_t split_len, int K1, uint64_t* lists, int64_t stride,
-                            cudaStream_t s) {
-  if (m == 0) return cudaSuccess;
-  dim3 grid((unsigned)((m + kThreads - 1) / kThreads), (unsigned)splits);
-  knn_simt_kernel<<<grid, kThreads, 0, s>>>(q, m, qnorm, ref, rnorm, n_ref, split_len, K1, lists, stride);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_nbnn_simt(const uint8_t* q, int64_t m, const int32_t* qnorm, const uint8_t* sref,
                              const float* srnorm, const int32_t* slabels, const int64_t* class_off,

@@ -13,6 +13,12 @@
 // against the row's current (k+1)-th distance, and keeps the k+1 smallest
 // (distance, row) pairs.  The distance matrix never leaves the SM.
 //
+// Clusters of two CTAs (two query tiles, same reference split) share every
+// reference tile: each CTA loads half of each K-chunk and multicasts it into
+// both CTAs' shared memory, and a stage is refilled only after both CTAs'
+// MMAs have consumed it.  This halves the reference traffic per SM and keeps
+// the pair in step.
+//
 // Roles (one CTA = 128 query rows x one reference split):
 //   warp 0, one thread : TMA producer (query tile once; reference K-chunks
 //                        into a 4-stage ring, the K-extension riding with the
@@ -38,7 +44,8 @@ namespace {
 
 using namespace sm103;
 
-constexpr int kBM = 128;                  // query rows per CTA (MMA M)
+constexpr int kBM = kTcQueryTile;         // query rows per CTA (MMA M)
+constexpr int kCluster = kTcCluster;      // CTAs sharing each reference tile by multicast
 constexpr int kBN = kTcRefTile;           // reference rows per tile (MMA N)
 constexpr int kBK = 64;                   // K elements per 128-byte swizzle row
 constexpr int kKChunks = kDim / kBK;      // 2
@@ -49,6 +56,9 @@ constexpr uint32_t kAExtBytes = kBM * kExt * 2;      // 4 KB
 constexpr uint32_t kBChunkBytes = kBN * kBK * 2;     // 32 KB
 constexpr uint32_t kBExtBytes = kBN * kExt * 2;      // 8 KB
 constexpr uint32_t kStageBytes = kBChunkBytes + kBExtBytes;
+constexpr int kBRowsPerCta = kBN / kCluster;                 // rows of each tile one CTA loads
+constexpr uint32_t kBChunkPart = kBChunkBytes / kCluster;   // its share of a chunk
+constexpr uint32_t kBExtPart = kBExtBytes / kCluster;       // its share of the extension
 constexpr int kEpiPerQuarter = kTcListsPerSplit;  // epilogue warps per TMEM lane quarter
 constexpr int kEpiWarps = 4 * kEpiPerQuarter;
 constexpr int kEpiCols = kBN / kEpiPerQuarter;     // columns of a tile per epilogue warp
@@ -63,7 +73,7 @@ constexpr uint32_t kOffAExt = kOffA + kKChunks * kAChunkBytes;  // extension, 32
 constexpr uint32_t kOffB = kOffAExt + 1024 * ((kAExtBytes + 1023) / 1024);
 constexpr uint32_t kOffBar = kOffB + kStages * kStageBytes;
 constexpr int kNumBars = 2 * kStages + 2 + 2 + 2;  // full, empty, tmem full, tmem empty, A, drain
-constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;
+constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;  // TMEM address, abort flag
 constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;  // + alignment slack
 static_assert(kStages % kKChunks == 0, "a tile's chunks map to fixed stage parities");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
@@ -87,8 +97,8 @@ __device__ __forceinline__ void flag_timeout(volatile uint32_t* abort_flag, uint
 // Sorted list of the K1 smallest (distance, row) pairs seen so far, held in
 // registers: ascending in slots [KMAX-K1, KMAX); the slots below hold the
 // distance -1, which no real distance displaces, so the list always has K1
-// live entries and its largest is slot KMAX-1.  Columns arrive in increasing
-// row order, so strict comparisons keep equal distances in row order.
+// live entries and its largest is slot KMAX-1.  Pairs compare by distance,
+// then row, so the result does not depend on the order columns arrive in.
 template <int KMAX>
 struct RegList {
   int32_t d[KMAX];
@@ -102,18 +112,23 @@ struct RegList {
     }
   }
   __device__ __forceinline__ int32_t worst() const { return d[KMAX - 1]; }
-  // new[i] = old[i-1] if x sorts before it, else min(x, old[i]) (x < worst()).
+  __device__ __forceinline__ bool before(int32_t x, uint32_t row, int i) const {
+    return x < d[i] || (x == d[i] && row < r[i]);
+  }
+  // Would (x, row) enter the list?
+  __device__ __forceinline__ bool admits(int32_t x, uint32_t row) const { return before(x, row, KMAX - 1); }
+  // new[i] = old[i-1] if (x, row) sorts before it, else min((x, row), old[i]).
   __device__ __forceinline__ void insert(int32_t x, uint32_t row) {
 #pragma unroll
     for (int i = KMAX - 1; i > 0; --i) {
-      const bool shift = x < d[i - 1];
-      const bool place = !shift && x < d[i];
+      const bool shift = before(x, row, i - 1);
+      const bool place = !shift && before(x, row, i);
       const int32_t nd = shift ? d[i - 1] : (place ? x : d[i]);
       const uint32_t nr = shift ? r[i - 1] : (place ? row : r[i]);
       d[i] = nd;
       r[i] = nr;
     }
-    if (x < d[0]) {
+    if (before(x, row, 0)) {
       d[0] = x;
       r[0] = row;
     }
@@ -144,27 +159,31 @@ __device__ __forceinline__ int32_t select32(const uint32_t (&v)[32], int j) {
   return (int32_t)((j & 16) ? t[1] : t[0]);
 }
 
-// Bit j set when column j's distance is below the threshold.
+// Bit j set when column j's distance is at most the threshold.
 __device__ __forceinline__ uint32_t hit_mask(const uint32_t (&v)[32], int32_t thr) {
   uint32_t mask = 0;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) mask |= ((int32_t)v[j] < thr ? 1u : 0u) << j;
+  for (int j = 0; j < 32; ++j) mask |= ((int32_t)v[j] <= thr ? 1u : 0u) << j;
   return mask;
 }
 
-// Rare path: offer the columns of one 32-column group whose distance is below
-// the list's current largest, in column order (the threshold tightens as
-// entries are inserted, so each candidate is checked again).  v holds float
-// bit patterns of exact distances.
+// Rare path: offer the columns of one 32-column group whose distance is at
+// most the list's current largest (the threshold tightens as entries are
+// inserted, so each candidate is checked again on its full (distance, row)
+// key).  v holds float bit patterns of exact distances.
 template <int KMAX>
 __device__ __forceinline__ void offer_group(RegList<KMAX>& L, TopK&, int32_t& thr, const uint32_t (&v)[32],
                                             int64_t col0) {
   for (uint32_t mask = hit_mask(v, thr); mask; mask &= mask - 1) {
     const int j = __ffs(mask) - 1;
     const int32_t bits = select32(v, j);
-    if (bits < thr) {
-      L.insert(__float2int_rn(__int_as_float(bits)), (uint32_t)(col0 + j));
-      thr = thr_bits(L.worst());
+    if (bits <= thr) {
+      const int32_t x = __float2int_rn(__int_as_float(bits));
+      const uint32_t row = (uint32_t)(col0 + j);
+      if (L.admits(x, row)) {
+        L.insert(x, row);
+        thr = thr_bits(L.worst());
+      }
     }
   }
 }
@@ -180,21 +199,22 @@ __device__ __forceinline__ void offer_group<0>(RegList<0>&, TopK& top, int32_t& 
   for (uint32_t mask = hit_mask(v, thr); mask; mask &= mask - 1) {
     const int j = __ffs(mask) - 1;
     const int32_t bits = select32(v, j);
-    if (bits < thr) {
+    if (bits <= thr) {
       top.push(make_key((uint32_t)__float2int_rn(__int_as_float(bits)), (uint32_t)(col0 + j)));
       thr = thr_bits(top.threshold);
     }
   }
 }
 
-// One 32-column group: integer minimum of the bit patterns, one compare.
+// One 32-column group: integer minimum of the bit patterns, one compare (a
+// column at exactly the threshold distance may still win on its row).
 template <int KMAX>
 __device__ __forceinline__ void scan_group(RegList<KMAX>& L, TopK& top, int32_t& thr, bool active,
                                            const uint32_t (&v)[32], int64_t col0) {
   int32_t mn = (int32_t)v[0];
 #pragma unroll
   for (int j = 1; j < 32; ++j) mn = min(mn, (int32_t)v[j]);
-  const bool hit = active && mn < thr;
+  const bool hit = active && mn <= thr;
   if (__any_sync(0xffffffffu, hit)) {
     if (hit) offer_group<KMAX>(L, top, thr, v, col0);
     __syncwarp();
@@ -203,7 +223,7 @@ __device__ __forceinline__ void scan_group(RegList<KMAX>& L, TopK& top, int32_t&
 
 // KMAX > 0: per-row lists in registers (K1 <= KMAX); KMAX = 0: heaps in global memory.
 template <int KMAX>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
     knn_tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_qe,
                   const __grid_constant__ CUtensorMap tmap_r, const __grid_constant__ CUtensorMap tmap_re, int64_t m,
                   int64_t n_ref, int64_t split_len, int K1, uint64_t* __restrict__ lists, int64_t stride,
@@ -220,14 +240,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t m0 = (int64_t)blockIdx.x * kBM;
   const int64_t j_begin = (int64_t)blockIdx.y * split_len;
   const int64_t j_end = min(j_begin + split_len, n_ref);
-  const int ntiles = (int)((j_end - j_begin + kBN - 1) / kBN);
-  // A timeout reported earlier and not yet collected by lnbnn_sync: do no work.
-  if (*reinterpret_cast<volatile uint32_t*>(dev_err) & kDevErrTimeout) return;
+  // A timeout reported earlier and not yet collected by lnbnn_sync: scan no
+  // tiles (but keep the cluster protocol, so the partner CTA is not stranded).
+  const bool stale_timeout = (*reinterpret_cast<volatile uint32_t*>(dev_err) & kDevErrTimeout) != 0;
+  const int ntiles = stale_timeout ? 0 : (int)((j_end - j_begin + kBN - 1) / kBN);
+  const uint32_t rank = cluster_ctarank();
+  constexpr uint16_t kAllCtas = (uint16_t)((1u << kCluster) - 1);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(bars.full(s), 1);
-      mbar_init(bars.empty(s), 1);
+      mbar_init(bars.empty(s), kCluster);  // one MMA completion from each CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(bars.tfull(b), 1);
@@ -240,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (warp == 1) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
   tc_fence_before();
-  __syncthreads();
+  cluster_sync();  // the partner's barriers exist before any multicast reaches them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -267,9 +290,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           const uint32_t dst = sbase + kOffB + s * kStageBytes;
           const bool last = kc == kKChunks - 1;
+          // the whole chunk lands here: this CTA's half and the partner's
           mbar_arrive_expect_tx(bars.full(s), kBChunkBytes + (last ? kBExtBytes : 0u));
-          tma_load_2d(dst, &tmap_r, kc * kBK, row, bars.full(s));
-          if (last) tma_load_2d(dst + kBChunkBytes, &tmap_re, 0, row, bars.full(s));
+          const int32_t my_row = row + (int32_t)(rank * kBRowsPerCta);
+          tma_load_2d_multicast(dst + rank * kBChunkPart, &tmap_r, kc * kBK, my_row, bars.full(s), kAllCtas);
+          if (last)
+            tma_load_2d_multicast(dst + kBChunkBytes + rank * kBExtPart, &tmap_re, 0, my_row, bars.full(s), kAllCtas);
         }
       }
       // every load issued must land before the CTA may exit
@@ -317,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           if (kc == kKChunks - 1)  // ||r||^2 through the K-extension
             mma_bf16(d_tmem, sw32_kmajor_desc(sbase + kOffAExt), sw32_kmajor_desc(b_base + kBChunkBytes), idesc, 1u);
-          mma_commit(bars.empty(s));
+          mma_commit_multicast(bars.empty(s), kAllCtas);  // both CTAs' producers refill this stage
         }
         if (ok) mma_commit(bars.tfull(b));
       }
@@ -387,7 +413,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 
   tc_fence_before();
-  __syncthreads();
+  // no CTA leaves while its partner may still signal its barriers
+  cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem_base, kTmemCols);
@@ -433,8 +460,8 @@ bool encode_operand(CUtensorMap* main, CUtensorMap* ext, const void* bf, const v
 
 bool make_tc_tensor_maps(const __nv_bfloat16* ref_bf, const __nv_bfloat16* sref_bf, const __nv_bfloat16* ref_ext,
                          const __nv_bfloat16* sref_ext, int64_t n_pad, TcTensorMaps* out) {
-  return encode_operand(&out->ref, &out->ref_ext, ref_bf, ref_ext, (uint64_t)n_pad, kBN) &&
-         encode_operand(&out->sref, &out->sref_ext, sref_bf, sref_ext, (uint64_t)n_pad, kBN);
+  return encode_operand(&out->ref, &out->ref_ext, ref_bf, ref_ext, (uint64_t)n_pad, kBRowsPerCta) &&
+         encode_operand(&out->sref, &out->sref_ext, sref_bf, sref_ext, (uint64_t)n_pad, kBRowsPerCta);
 }
 
 cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf,
@@ -442,7 +469,7 @@ cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv
                           int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
                           unsigned long long* stats, cudaStream_t s) {
   if (m == 0) return cudaSuccess;
-  if (m_pad % kBM != 0 || split_len % kBN != 0) return cudaErrorInvalidValue;
+  if (m_pad % (kBM * kCluster) != 0 || split_len % kBN != 0) return cudaErrorInvalidValue;
   CUtensorMap tq, tqe;
   if (!encode_operand(&tq, &tqe, qbf, qext, (uint64_t)m_pad, kBM)) return cudaErrorInvalidValue;
   auto kernel = K1 <= kTcRegListMax ? knn_tc_kernel<kTcRegListMax> : knn_tc_kernel<0>;

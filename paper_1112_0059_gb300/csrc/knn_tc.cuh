@@ -9,6 +9,11 @@ namespace lnbnn {
 
 // References per tile of the tensor-core kernels (the MMA N extent).
 constexpr int kTcRefTile = 256;
+// Query rows per CTA (the MMA M extent) and CTAs per cluster; the query
+// operand must be padded to kTcQueryTile * kTcCluster rows.
+constexpr int kTcQueryTile = 128;
+constexpr int kTcCluster = 2;
+static_assert(kQueryPad % (kTcQueryTile * kTcCluster) == 0, "query padding must cover whole clusters");
 // Epilogue warps per TMEM lane quarter.  Each owns a column slice of every
 // tile and keeps its own top-K1 list per query row, so one reference split
 // yields this many sorted lists per row (merged afterwards).

@@ -172,13 +172,15 @@ bool k_ok(const lnbnn_index* ix, int32_t k, int extra) {
   return k >= 1 && k <= LNBNN_MAX_K && (int64_t)k + extra <= ix->n_ref;
 }
 
+constexpr int kMaxSplits = 32;
+
 // Number of reference splits so that query tiles x splits fill the GPU.
 int choose_splits(const lnbnn_index* ix, int64_t m_pad) {
-  const int64_t tiles = m_pad / kQueryPad;
+  const int64_t tiles = m_pad / kTcQueryTile;
   const int64_t want = 2 * (int64_t)ix->sm_count;
   int64_t s = tiles >= want ? 1 : (want + tiles - 1) / tiles;
   s = std::min<int64_t>(s, std::max<int64_t>(1, ix->n_ref / 4096));
-  s = std::min<int64_t>(s, 32);
+  s = std::min<int64_t>(s, kMaxSplits);
   return (int)std::max<int64_t>(s, 1);
 }
 
@@ -191,51 +193,40 @@ struct KnnPlan {
   size_t off_qnorm, off_qbf, off_qext, off_lists, off_merged, bytes;
 };
 
-KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, bool tensor) {
+KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1) {
   KnnPlan p{};
   p.m_pad = round_up(m, kQueryPad);
   p.K1 = K1;
   p.splits = choose_splits(ix, p.m_pad);
-  const int64_t tile = tensor ? kTcRefTile : kRefPad;
-  p.split_len = round_up((ix->n_ref + p.splits - 1) / p.splits, tile);
+  p.split_len = round_up((ix->n_ref + p.splits - 1) / p.splits, kTcRefTile);
   p.splits = (int)((ix->n_ref + p.split_len - 1) / p.split_len);
   Carve c;
   p.off_qnorm = c.take<int32_t>(p.m_pad);
-  p.off_qbf = tensor ? c.take<__nv_bfloat16>(p.m_pad * kDim) : 0;
-  p.off_qext = tensor ? c.take<__nv_bfloat16>(p.m_pad * kExt) : 0;
-  p.lists = p.splits * (tensor ? kTcListsPerSplit : 1);
+  p.off_qbf = c.take<__nv_bfloat16>(p.m_pad * kDim);
+  p.off_qext = c.take<__nv_bfloat16>(p.m_pad * kExt);
+  p.lists = p.splits * kTcListsPerSplit;
   p.off_lists = c.take<uint64_t>((size_t)p.lists * p.m_pad * K1);
   p.off_merged = p.lists > 1 ? c.take<uint64_t>((size_t)p.m_pad * K1) : p.off_lists;
   p.bytes = c.off;
   return p;
 }
 
-bool use_tensor_cores() {
-  const char* v = getenv("LNBNN_KNN_KERNEL");  // development switch: "simt" selects the CUDA-core search
-  return !(v && strcmp(v, "simt") == 0);
-}
-
 // Runs the exact search; *lists receives m sorted lists of K1 keys.
 lnbnn_status run_knn(lnbnn_index* ix, const uint8_t* q, int64_t m, int K1, cudaStream_t s, const uint64_t** lists,
                      CallProfile& prof) {
-  const bool tensor = use_tensor_cores();
-  KnnPlan p = plan_knn(ix, m, K1, tensor);
+  KnnPlan p = plan_knn(ix, m, K1);
   CK(ensure(&ix->ws, &ix->ws_bytes, p.bytes));
   char* ws = static_cast<char*>(ix->ws);
   int32_t* qnorm = reinterpret_cast<int32_t*>(ws + p.off_qnorm);
-  __nv_bfloat16* qbf = tensor ? reinterpret_cast<__nv_bfloat16*>(ws + p.off_qbf) : nullptr;
-  __nv_bfloat16* qext = tensor ? reinterpret_cast<__nv_bfloat16*>(ws + p.off_qext) : nullptr;
+  __nv_bfloat16* qbf = reinterpret_cast<__nv_bfloat16*>(ws + p.off_qbf);
+  __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(ws + p.off_qext);
   uint64_t* part = reinterpret_cast<uint64_t*>(ws + p.off_lists);
   uint64_t* merged = reinterpret_cast<uint64_t*>(ws + p.off_merged);
   CK(launch_prep_query(q, m, p.m_pad, qnorm, qbf, qext, s));
   prof.launched(1);
   prof.mark(1);
-  if (tensor) {
-    CK(launch_knn_tc(ix->tc, /*sorted_copy=*/false, qbf, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, K1,
-                     part, p.m_pad, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, s));
-  } else {
-    CK(launch_knn_simt(q, m, qnorm, ix->ref_u8, ix->rnorm, ix->n_ref, p.splits, p.split_len, K1, part, p.m_pad, s));
-  }
+  CK(launch_knn_tc(ix->tc, /*sorted_copy=*/false, qbf, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, K1, part,
+                   p.m_pad, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, s));
   prof.launched(1, true);
   prof.mark(2);
   if (p.lists > 1) {
@@ -248,7 +239,7 @@ lnbnn_status run_knn(lnbnn_index* ix, const uint8_t* q, int64_t m, int K1, cudaS
 
 ClassGroups make_groups(const lnbnn_index* ix, int64_t m) {
   ClassGroups g{};
-  const int64_t tiles = round_up(m, kQueryPad) / kQueryPad;
+  const int64_t tiles = (m + 127) / 128;  // 128-row blocks of the NBNN kernel
   const int64_t want = 2 * (int64_t)ix->sm_count;
   int64_t G = tiles >= want ? 1 : (want + tiles - 1) / tiles;
   G = std::min<int64_t>(G, ix->n_classes);

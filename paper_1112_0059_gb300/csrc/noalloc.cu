@@ -85,7 +85,7 @@ extern "C" LNBNN_API lnbnn_status knn_search_noalloc(const uint8_t* ref, int64_t
   // Same plan as the index path: enough reference splits to fill the GPU.
   const int64_t n_pad = round_up(n_ref, kRefPad);
   const int64_t m_pad = round_up(n_queries, kQueryPad);
-  const int64_t tiles = m_pad / kQueryPad;
+  const int64_t tiles = m_pad / kTcQueryTile;
   const int64_t want = 2 * (int64_t)sm_count;
   int64_t splits = tiles >= want ? 1 : (want + tiles - 1) / tiles;
   splits = std::min<int64_t>(std::min<int64_t>(splits, std::max<int64_t>(1, n_ref / 4096)), 32);

@@ -13,10 +13,9 @@ struct TopK {
   uint64_t* h;
   int cap;
   int size;
-  // Distances strictly below `threshold` may enter.  Until the heap is full it
-  // is INT32_MAX; afterwards it is the distance of the current largest key.
-  // For references scanned in increasing row order this strict bound is exact:
-  // a later row at the same distance as the largest key sorts after it.
+  // Distance of the current largest key (INT32_MAX until the heap is full):
+  // a key can enter only if its distance is at most this; push() then decides
+  // on the full (distance, row) key.
   int32_t threshold;
 
   __device__ __forceinline__ TopK(uint64_t* heap, int K1) : h(heap), cap(K1), size(0), threshold(INT32_MAX) {}

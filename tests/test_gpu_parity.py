@@ -249,3 +249,18 @@ def test_caltech256_like_full_size_sampled(lnbnn):
         od, oj = oracle.knn(ref, q[rows], 11)
         assert np.array_equal(dist.cpu().numpy()[rows], od.astype(np.int32))
         assert np.array_equal(idx.cpu().numpy()[rows], oj.astype(np.int32))
+
+
+def test_repeated_searches_with_heavy_ties(lnbnn):
+    # Coordinates in {0..2} on 6 dims: most distances tie, and the lists must
+    # follow the exact (distance, row) order on every call.
+    ref, labels, q, off = random_case(12, 5000 + 11, 700, 4, hi=3, dims=6)
+    with make_index(lnbnn, ref, labels, 4) as ix:
+        od, oj = oracle.knn(ref, q, 12)
+        for _ in range(4):
+            idx, dist = ix.knn_search(dev(q), 12)
+            ix.sync()
+            assert np.array_equal(dist.cpu().numpy(), od.astype(np.int32))
+            assert np.array_equal(idx.cpu().numpy(), oj.astype(np.int32))
+        for _ in range(2):
+            check_classify(ix, ref, labels, 4, q, off, 9)
