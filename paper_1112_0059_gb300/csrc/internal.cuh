@@ -20,9 +20,9 @@ constexpr uint64_t kEmptyKey = ~0ull;
 constexpr float kPadNorm = 33554432.0f;  // 2^25
 // Reference rows are padded to a multiple of this (the widest reference tile).
 constexpr int kRefPad = 256;
-// Query rows are padded to a multiple of this (two 128-row query tiles: one
-// cluster of the tensor-core search).
-constexpr int kQueryPad = 256;
+// Query rows are padded to a multiple of this (the 128-row query tile of the
+// tensor-core search, times its cluster size).
+constexpr int kQueryPad = 128;
 
 // Width of the K-extension that carries ||r||^2 into the tensor-core
 // contraction: a reference row gets the base-256 digits (d0, d1, d2) of its

@@ -13,11 +13,13 @@
 // against the row's current (k+1)-th distance, and keeps the k+1 smallest
 // (distance, row) pairs.  The distance matrix never leaves the SM.
 //
-// Clusters of two CTAs (two query tiles, same reference split) share every
-// reference tile: each CTA loads half of each K-chunk and multicasts it into
-// both CTAs' shared memory, and a stage is refilled only after both CTAs'
-// MMAs have consumed it.  This halves the reference traffic per SM and keeps
-// the pair in step.
+// With kTcCluster > 1, the CTAs of a cluster (consecutive query tiles, same
+// reference split) share every reference tile: each loads its share of each
+// K-chunk and multicasts it into all of them, and a stage is refilled only
+// after every CTA's MMAs have consumed it.  That divides the reference
+// traffic per SM by the cluster size but couples the CTAs, each stage waiting
+// for the slowest; measured on the 256-class workload, single CTAs were ~5%
+// faster, so kTcCluster is 1.
 //
 // Roles (one CTA = 128 query rows x one reference split):
 //   warp 0, one thread : TMA producer (query tile once; reference K-chunks
@@ -97,8 +99,9 @@ __device__ __forceinline__ void flag_timeout(volatile uint32_t* abort_flag, uint
 // Sorted list of the K1 smallest (distance, row) pairs seen so far, held in
 // registers: ascending in slots [KMAX-K1, KMAX); the slots below hold the
 // distance -1, which no real distance displaces, so the list always has K1
-// live entries and its largest is slot KMAX-1.  Pairs compare by distance,
-// then row, so the result does not depend on the order columns arrive in.
+// live entries and its largest is slot KMAX-1.  Every list receives its
+// columns in increasing row order, so comparing distances strictly is exact
+// for (distance, row) order: a later row at an equal distance sorts after.
 template <int KMAX>
 struct RegList {
   int32_t d[KMAX];
@@ -112,23 +115,18 @@ struct RegList {
     }
   }
   __device__ __forceinline__ int32_t worst() const { return d[KMAX - 1]; }
-  __device__ __forceinline__ bool before(int32_t x, uint32_t row, int i) const {
-    return x < d[i] || (x == d[i] && row < r[i]);
-  }
-  // Would (x, row) enter the list?
-  __device__ __forceinline__ bool admits(int32_t x, uint32_t row) const { return before(x, row, KMAX - 1); }
-  // new[i] = old[i-1] if (x, row) sorts before it, else min((x, row), old[i]).
+  // new[i] = old[i-1] if x sorts before it, else min(x, old[i]); requires x < worst().
   __device__ __forceinline__ void insert(int32_t x, uint32_t row) {
 #pragma unroll
     for (int i = KMAX - 1; i > 0; --i) {
-      const bool shift = before(x, row, i - 1);
-      const bool place = !shift && before(x, row, i);
+      const bool shift = x < d[i - 1];
+      const bool place = !shift && x < d[i];
       const int32_t nd = shift ? d[i - 1] : (place ? x : d[i]);
       const uint32_t nr = shift ? r[i - 1] : (place ? row : r[i]);
       d[i] = nd;
       r[i] = nr;
     }
-    if (before(x, row, 0)) {
+    if (x < d[0]) {
       d[0] = x;
       r[0] = row;
     }
@@ -159,31 +157,27 @@ __device__ __forceinline__ int32_t select32(const uint32_t (&v)[32], int j) {
   return (int32_t)((j & 16) ? t[1] : t[0]);
 }
 
-// Bit j set when column j's distance is at most the threshold.
+// Bit j set when column j's distance is below the threshold.
 __device__ __forceinline__ uint32_t hit_mask(const uint32_t (&v)[32], int32_t thr) {
   uint32_t mask = 0;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) mask |= ((int32_t)v[j] <= thr ? 1u : 0u) << j;
+  for (int j = 0; j < 32; ++j) mask |= ((int32_t)v[j] < thr ? 1u : 0u) << j;
   return mask;
 }
 
-// Rare path: offer the columns of one 32-column group whose distance is at
-// most the list's current largest (the threshold tightens as entries are
-// inserted, so each candidate is checked again on its full (distance, row)
-// key).  v holds float bit patterns of exact distances.
+// Rare path: offer the columns of one 32-column group whose distance is below
+// the list's current largest, in column order (the threshold tightens as
+// entries are inserted, so each candidate is checked again).  v holds float
+// bit patterns of exact distances.
 template <int KMAX>
 __device__ __forceinline__ void offer_group(RegList<KMAX>& L, TopK&, int32_t& thr, const uint32_t (&v)[32],
                                             int64_t col0) {
   for (uint32_t mask = hit_mask(v, thr); mask; mask &= mask - 1) {
     const int j = __ffs(mask) - 1;
     const int32_t bits = select32(v, j);
-    if (bits <= thr) {
-      const int32_t x = __float2int_rn(__int_as_float(bits));
-      const uint32_t row = (uint32_t)(col0 + j);
-      if (L.admits(x, row)) {
-        L.insert(x, row);
-        thr = thr_bits(L.worst());
-      }
+    if (bits < thr) {
+      L.insert(__float2int_rn(__int_as_float(bits)), (uint32_t)(col0 + j));
+      thr = thr_bits(L.worst());
     }
   }
 }
@@ -199,22 +193,23 @@ __device__ __forceinline__ void offer_group<0>(RegList<0>&, TopK& top, int32_t& 
   for (uint32_t mask = hit_mask(v, thr); mask; mask &= mask - 1) {
     const int j = __ffs(mask) - 1;
     const int32_t bits = select32(v, j);
-    if (bits <= thr) {
+    if (bits < thr) {
       top.push(make_key((uint32_t)__float2int_rn(__int_as_float(bits)), (uint32_t)(col0 + j)));
       thr = thr_bits(top.threshold);
     }
   }
 }
 
-// One 32-column group: integer minimum of the bit patterns, one compare (a
-// column at exactly the threshold distance may still win on its row).
+// One 32-column group: integer minimum of the bit patterns, one compare.  A
+// column at exactly the threshold distance cannot enter: its row is higher
+// than every kept row's.
 template <int KMAX>
 __device__ __forceinline__ void scan_group(RegList<KMAX>& L, TopK& top, int32_t& thr, bool active,
                                            const uint32_t (&v)[32], int64_t col0) {
   int32_t mn = (int32_t)v[0];
 #pragma unroll
   for (int j = 1; j < 32; ++j) mn = min(mn, (int32_t)v[j]);
-  const bool hit = active && mn <= thr;
+  const bool hit = active && mn < thr;
   if (__any_sync(0xffffffffu, hit)) {
     if (hit) offer_group<KMAX>(L, top, thr, v, col0);
     __syncwarp();
@@ -292,10 +287,16 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
           const bool last = kc == kKChunks - 1;
           // the whole chunk lands here: this CTA's half and the partner's
           mbar_arrive_expect_tx(bars.full(s), kBChunkBytes + (last ? kBExtBytes : 0u));
-          const int32_t my_row = row + (int32_t)(rank * kBRowsPerCta);
-          tma_load_2d_multicast(dst + rank * kBChunkPart, &tmap_r, kc * kBK, my_row, bars.full(s), kAllCtas);
-          if (last)
-            tma_load_2d_multicast(dst + kBChunkBytes + rank * kBExtPart, &tmap_re, 0, my_row, bars.full(s), kAllCtas);
+          if constexpr (kCluster == 1) {
+            tma_load_2d(dst, &tmap_r, kc * kBK, row, bars.full(s));
+            if (last) tma_load_2d(dst + kBChunkBytes, &tmap_re, 0, row, bars.full(s));
+          } else {
+            const int32_t my_row = row + (int32_t)(rank * kBRowsPerCta);
+            tma_load_2d_multicast(dst + rank * kBChunkPart, &tmap_r, kc * kBK, my_row, bars.full(s), kAllCtas);
+            if (last)
+              tma_load_2d_multicast(dst + kBChunkBytes + rank * kBExtPart, &tmap_re, 0, my_row, bars.full(s),
+                                    kAllCtas);
+          }
         }
       }
       // every load issued must land before the CTA may exit
@@ -343,7 +344,11 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
           }
           if (kc == kKChunks - 1)  // ||r||^2 through the K-extension
             mma_bf16(d_tmem, sw32_kmajor_desc(sbase + kOffAExt), sw32_kmajor_desc(b_base + kBChunkBytes), idesc, 1u);
-          mma_commit_multicast(bars.empty(s), kAllCtas);  // both CTAs' producers refill this stage
+          if constexpr (kCluster == 1) {
+            mma_commit(bars.empty(s));
+          } else {
+            mma_commit_multicast(bars.empty(s), kAllCtas);  // every CTA's producer refills this stage
+          }
         }
         if (ok) mma_commit(bars.tfull(b));
       }

@@ -12,7 +12,7 @@ constexpr int kTcRefTile = 256;
 // Query rows per CTA (the MMA M extent) and CTAs per cluster; the query
 // operand must be padded to kTcQueryTile * kTcCluster rows.
 constexpr int kTcQueryTile = 128;
-constexpr int kTcCluster = 2;
+constexpr int kTcCluster = 1;
 static_assert(kQueryPad % (kTcQueryTile * kTcCluster) == 0, "query padding must cover whole clusters");
 // Epilogue warps per TMEM lane quarter.  Each owns a column slice of every
 // tile and keeps its own top-K1 list per query row, so one reference split

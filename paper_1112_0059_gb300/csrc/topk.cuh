@@ -13,9 +13,9 @@ struct TopK {
   uint64_t* h;
   int cap;
   int size;
-  // Distance of the current largest key (INT32_MAX until the heap is full):
-  // a key can enter only if its distance is at most this; push() then decides
-  // on the full (distance, row) key.
+  // Distance of the current largest key (INT32_MAX until the heap is full).
+  // When keys arrive in increasing row order, only distances strictly below
+  // it can enter; push() itself compares full (distance, row) keys.
   int32_t threshold;
 
   __device__ __forceinline__ TopK(uint64_t* heap, int K1) : h(heap), cap(K1), size(0), threshold(INT32_MAX) {}
