@@ -57,10 +57,10 @@ cudaError_t launch_prep_query(const uint8_t* q, int64_t m, int64_t m_pad, int32_
 // Label histogram; sets *bad when a label is outside [0, C).
 cudaError_t launch_label_hist(const int32_t* labels, int64_t n, int32_t C, unsigned long long* counts,
                               uint32_t* bad, cudaStream_t s);
-// Gather rows: dst[i] = src[perm[i]] for uint8 descriptors, bf16 operand rows,
-// norm-digit rows, norms and labels.
-cudaError_t launch_gather_ref(const int64_t* perm, int64_t n, const uint8_t* src_u8, uint8_t* dst_u8,
-                              const __nv_bfloat16* src_bf, __nv_bfloat16* dst_bf, const __nv_bfloat16* src_ext,
+// Gather rows: dst[i] = src[perm[i]] for bf16 operand rows, norm-digit rows,
+// norms and labels.
+cudaError_t launch_gather_ref(const int64_t* perm, int64_t n, const __nv_bfloat16* src_bf, __nv_bfloat16* dst_bf,
+                              const __nv_bfloat16* src_ext,
                               __nv_bfloat16* dst_ext, const float* src_norm, float* dst_norm,
                               const int32_t* src_lab, int32_t* dst_lab, cudaStream_t s);
 
@@ -77,22 +77,13 @@ cudaError_t launch_extract_knn(const uint64_t* lists, int64_t m, int K1, int k, 
 cudaError_t launch_lnbnn_score(const uint64_t* lists, int64_t m, int K1, int k, const int32_t* labels,
                                const int64_t* offsets, int64_t n_img, int32_t C, int64_t* totals,
                                uint32_t* dev_err, cudaStream_t s);
+// Alg. 1 sum: totals[img][c] = sum of mins[row][c] over the image's rows.
+cudaError_t launch_nbnn_sum(const int32_t* mins, int64_t m, int32_t C, const int64_t* offsets, int64_t n_img,
+                            int64_t* totals, cudaStream_t s);
 // Offsets validation (0 = o[0] <= ... <= o[n_img] = m); flags kDevErrOffsets.
 cudaError_t launch_check_offsets(const int64_t* offsets, int64_t n_img, int64_t m, uint32_t* dev_err,
                                  cudaStream_t s);
 // argmin over classes per image, lowest class on ties.
 cudaError_t launch_argmin(const int64_t* totals, int64_t n_img, int32_t C, int32_t* classes, cudaStream_t s);
-
-// Original NBNN on CUDA cores over the class-sorted reference copy.  Class
-// group g covers classes [group_cls[g], group_cls[g+1]).
-struct ClassGroups {
-  static constexpr int kMax = 64;
-  int32_t n;
-  int32_t cls[kMax + 1];
-};
-cudaError_t launch_nbnn_simt(const uint8_t* q, int64_t m, const int32_t* qnorm, const uint8_t* sref,
-                             const float* srnorm, const int32_t* slabels, const int64_t* class_off,
-                             const ClassGroups& groups, const int64_t* offsets, int64_t n_img, int32_t C,
-                             int64_t* totals, cudaStream_t s);
 
 }  // namespace lnbnn

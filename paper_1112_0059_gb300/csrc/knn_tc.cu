@@ -217,12 +217,107 @@ __device__ __forceinline__ void scan_group(RegList<KMAX>& L, TopK& top, int32_t&
 }
 
 // KMAX > 0: per-row lists in registers (K1 <= KMAX); KMAX = 0: heaps in global memory.
+// What the epilogue writes (see the two epilogues below).
+struct ScanOut {
+  uint64_t* lists;           // kNN: sorted lists, [splits * kTcListsPerSplit][stride][K1]
+  int64_t stride;
+  int K1;
+  int32_t* mins;             // NBNN: per (query row, class) minimum distance, [m_pad][C], atomicMin
+  int32_t C;
+  const int64_t* class_off;  // NBNN: class c owns sorted rows [class_off[c], class_off[c+1])
+};
+
+// kNN epilogue: the K1 smallest (distance, row) keys of the columns one
+// thread sees (Alg. 2's NN(d, k+1) restricted to a slice of the references).
 template <int KMAX>
+struct KnnEpilogue {
+  RegList<KMAX> L;
+  TopK top;
+  int32_t thr;
+  bool active;
+  int K1;
+  uint64_t* out;
+  __device__ __forceinline__ KnnEpilogue(const ScanOut& o, int list, int64_t row, bool act, int64_t)
+      : top(o.lists + ((int64_t)list * o.stride + (act ? row : 0)) * o.K1, o.K1),
+        thr(thr_bits(INT32_MAX)),
+        active(act),
+        K1(o.K1),
+        out(o.lists + ((int64_t)list * o.stride + (act ? row : 0)) * o.K1) {
+    L.init(K1);
+  }
+  __device__ __forceinline__ void group(const uint32_t (&v)[32], int64_t col0) {
+    scan_group<KMAX>(L, top, thr, active, v, col0);
+  }
+  __device__ __forceinline__ void finish() {
+    if (!active) return;
+    if constexpr (KMAX > 0) {
+      L.store(out, K1);
+    } else {
+      top.finish();
+    }
+  }
+};
+
+// NBNN epilogue (Alg. 1's NN_C for every class C): the columns are the
+// class-sorted references; each thread keeps the minimum over the current
+// class and, when the class ends, folds it into mins[row][class] with an
+// atomic minimum (other column slices and splits see other parts of the
+// class).  All lanes of a warp see the same columns, so the class bookkeeping
+// is uniform across the warp.
+struct NbnnEpilogue {
+  int32_t* dst;          // mins + row * C
+  const int64_t* class_off;
+  int64_t n_ref;
+  int32_t C;
+  int32_t cls;           // class of the current column
+  int64_t next;          // first row of the next class
+  int32_t run;           // float bits of the running minimum over cls
+  bool active;
+  __device__ __forceinline__ NbnnEpilogue(const ScanOut& o, int, int64_t row, bool act, int64_t j_begin)
+      : dst(o.mins + (act ? row : 0) * (int64_t)o.C), class_off(o.class_off), n_ref(o.class_off[o.C]), C(o.C),
+        run(INT32_MAX), active(act) {
+    // class of j_begin: the last c with class_off[c] <= j_begin
+    int32_t lo = 0, hi = C;
+    while (lo + 1 < hi) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (class_off[mid] <= j_begin) lo = mid; else hi = mid;
+    }
+    cls = lo;
+    next = class_off[cls + 1];
+  }
+  __device__ __forceinline__ void flush() {
+    if (active && run != INT32_MAX) atomicMin(dst + cls, __float2int_rn(__int_as_float(run)));
+    run = INT32_MAX;
+  }
+  __device__ __forceinline__ void group(const uint32_t (&v)[32], int64_t col0) {
+    if (col0 + 32 <= next) {  // the whole group lies in class cls
+      int32_t mn = (int32_t)v[0];
+#pragma unroll
+      for (int j = 1; j < 32; ++j) mn = min(mn, (int32_t)v[j]);
+      run = min(run, mn);
+      return;
+    }
+#pragma unroll 1
+    for (int j = 0; j < 32; ++j) {
+      const int64_t col = col0 + j;
+      if (col >= n_ref) return;  // padding rows past the last class
+      while (col >= next) {      // class boundaries (empty classes skipped)
+        flush();
+        ++cls;
+        next = class_off[cls + 1];
+      }
+      run = min(run, select32(v, j));
+    }
+  }
+  __device__ __forceinline__ void finish() { flush(); }
+};
+
+template <class Epilogue>
 __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
-    knn_tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_qe,
-                  const __grid_constant__ CUtensorMap tmap_r, const __grid_constant__ CUtensorMap tmap_re, int64_t m,
-                  int64_t n_ref, int64_t split_len, int K1, uint64_t* __restrict__ lists, int64_t stride,
-                  uint32_t* __restrict__ dev_err, unsigned long long* __restrict__ stats) {
+    tc_scan_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_qe,
+                   const __grid_constant__ CUtensorMap tmap_r, const __grid_constant__ CUtensorMap tmap_re, int64_t m,
+                   int64_t n_ref, int64_t split_len, ScanOut out, uint32_t* __restrict__ dev_err,
+                   unsigned long long* __restrict__ stats) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
@@ -369,11 +464,7 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
     const int half = (warp - 2) >> 2;      // its 128-column half of every tile
     const int64_t row = m0 + quarter * 32 + lane;
     const bool active = row < m;
-    uint64_t* out = lists + (((int64_t)blockIdx.y * kEpiPerQuarter + half) * stride + (active ? row : 0)) * K1;
-    RegList<KMAX> L;
-    L.init(K1);
-    TopK top(out, K1);
-    int32_t thr = thr_bits(INT32_MAX);  // float bits of the current largest kept distance
+    Epilogue epi(out, (int)blockIdx.y * kEpiPerQuarter + half, row, active, j_begin + half * kEpiCols);
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
@@ -393,8 +484,8 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
         tmem_ld_32x32b_x32(taddr + 32, v1);
         tmem_ld_wait(v0);
         reg_fence(v1);
-        scan_group<KMAX>(L, top, thr, active, v0, col0);
-        scan_group<KMAX>(L, top, thr, active, v1, col0 + 32);
+        epi.group(v0, col0);
+        epi.group(v1, col0 + 32);
       }
       {
         uint32_t v2[32], v3[32];
@@ -404,17 +495,11 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
         reg_fence(v3);
         tc_fence_before();
         mbar_arrive(bars.tempty(b));
-        scan_group<KMAX>(L, top, thr, active, v2, col0 + 64);
-        scan_group<KMAX>(L, top, thr, active, v3, col0 + 96);
+        epi.group(v2, col0 + 64);
+        epi.group(v3, col0 + 96);
       }
     }
-    if (active) {
-      if constexpr (KMAX > 0) {
-        L.store(out, K1);
-      } else {
-        top.finish();
-      }
-    }
+    epi.finish();
   }
 
   tc_fence_before();
@@ -469,22 +554,53 @@ bool make_tc_tensor_maps(const __nv_bfloat16* ref_bf, const __nv_bfloat16* sref_
          encode_operand(&out->sref, &out->sref_ext, sref_bf, sref_ext, (uint64_t)n_pad, kBRowsPerCta);
 }
 
-cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf,
-                          const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
-                          int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
-                          unsigned long long* stats, cudaStream_t s) {
+namespace {
+
+template <class Epilogue>
+cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const __nv_bfloat16* qbf,
+                        const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
+                        int64_t split_len, const ScanOut& out, uint32_t* dev_err, unsigned long long* stats,
+                        cudaStream_t s) {
   if (m == 0) return cudaSuccess;
   if (m_pad % (kBM * kCluster) != 0 || split_len % kBN != 0) return cudaErrorInvalidValue;
   CUtensorMap tq, tqe;
   if (!encode_operand(&tq, &tqe, qbf, qext, (uint64_t)m_pad, kBM)) return cudaErrorInvalidValue;
-  auto kernel = K1 <= kTcRegListMax ? knn_tc_kernel<kTcRegListMax> : knn_tc_kernel<0>;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  cudaError_t e =
+      cudaFuncSetAttribute(tc_scan_kernel<Epilogue>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(m_pad / kBM), (unsigned)splits);
-  kernel<<<grid, kThreads, kSmemBytes, s>>>(tq, tqe, sorted_copy ? maps.sref : maps.ref,
-                                            sorted_copy ? maps.sref_ext : maps.ref_ext, m, n_ref, split_len, K1,
-                                            lists, stride, dev_err, stats);
+  tc_scan_kernel<Epilogue><<<grid, kThreads, kSmemBytes, s>>>(tq, tqe, tr, tre, m, n_ref, split_len, out, dev_err,
+                                                              stats);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf,
+                          const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
+                          int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
+                          unsigned long long* stats, cudaStream_t s) {
+  ScanOut out{};
+  out.lists = lists;
+  out.stride = stride;
+  out.K1 = K1;
+  const CUtensorMap& tr = sorted_copy ? maps.sref : maps.ref;
+  const CUtensorMap& tre = sorted_copy ? maps.sref_ext : maps.ref_ext;
+  if (K1 <= kTcRegListMax)
+    return launch_scan<KnnEpilogue<kTcRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len, out,
+                                                   dev_err, stats, s);
+  return launch_scan<KnnEpilogue<0>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len, out, dev_err, stats, s);
+}
+
+cudaError_t launch_nbnn_tc(const TcTensorMaps& maps, const __nv_bfloat16* qbf, const __nv_bfloat16* qext, int64_t m,
+                           int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int32_t* mins, int32_t C,
+                           const int64_t* class_off, uint32_t* dev_err, unsigned long long* stats, cudaStream_t s) {
+  ScanOut out{};
+  out.mins = mins;
+  out.C = C;
+  out.class_off = class_off;
+  return launch_scan<NbnnEpilogue>(maps.sref, maps.sref_ext, qbf, qext, m, m_pad, n_ref, splits, split_len, out,
+                                   dev_err, stats, s);
 }
 
 }  // namespace lnbnn

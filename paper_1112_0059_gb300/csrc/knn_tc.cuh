@@ -40,6 +40,13 @@ cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv
                           const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
                           int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
                           unsigned long long* stats, cudaStream_t s);
+// Original NBNN on the same tensor-core scan over the class-sorted copy:
+// mins [m_pad, C] (int32, filled with INT32_MAX-like values beforehand) gets
+// atomicMin(mins[i][c], ||q_i - r||^2) over every reference r of class c that
+// split's range covers, so after all splits mins[i][c] = NN_c(q_i).
+cudaError_t launch_nbnn_tc(const TcTensorMaps& maps, const __nv_bfloat16* qbf, const __nv_bfloat16* qext, int64_t m,
+                           int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int32_t* mins, int32_t C,
+                           const int64_t* class_off, uint32_t* dev_err, unsigned long long* stats, cudaStream_t s);
 // stats (may be null): the MMA thread of every CTA adds its SM cycles,
 // globaltimer nanoseconds and tile count to stats[0..2] and 1 to stats[3].
 

@@ -19,14 +19,13 @@ struct lnbnn_index {
   int64_t n_pad = 0;
   int32_t n_classes = 0;
   // merged reference set, caller's row order
-  uint8_t* ref_u8 = nullptr;
+  uint8_t* ref_u8 = nullptr;         // [n_ref, 128] the descriptors as given
   __nv_bfloat16* ref_bf = nullptr;   // [n_pad, 128] exact BF16 copy, zero padding rows
   __nv_bfloat16* ref_ext = nullptr;  // [n_pad, 16] squared-norm digits (K-extension)
   float* rnorm = nullptr;            // [n_pad] squared norms, kPadNorm on padding rows
   int32_t* labels = nullptr;        // [n_ref]
   // class-sorted view (aliases the above when the labels are already grouped)
   bool sorted = true;
-  uint8_t* sref_u8 = nullptr;
   __nv_bfloat16* sref_bf = nullptr;
   __nv_bfloat16* sref_ext = nullptr;
   float* srnorm = nullptr;
@@ -81,7 +80,6 @@ void free_index(lnbnn_index* ix) {
     for (auto& ce : *v)
       for (cudaEvent_t e : ce.e) cudaEventDestroy(e);
   if (!ix->sorted) {
-    cudaFree(ix->sref_u8);
     cudaFree(ix->sref_bf);
     cudaFree(ix->sref_ext);
     cudaFree(ix->srnorm);
@@ -237,31 +235,6 @@ lnbnn_status run_knn(lnbnn_index* ix, const uint8_t* q, int64_t m, int K1, cudaS
   return LNBNN_OK;
 }
 
-ClassGroups make_groups(const lnbnn_index* ix, int64_t m) {
-  ClassGroups g{};
-  const int64_t tiles = (m + 127) / 128;  // 128-row blocks of the NBNN kernel
-  const int64_t want = 2 * (int64_t)ix->sm_count;
-  int64_t G = tiles >= want ? 1 : (want + tiles - 1) / tiles;
-  G = std::min<int64_t>(G, ix->n_classes);
-  G = std::min<int64_t>(G, ClassGroups::kMax);
-  G = std::max<int64_t>(G, 1);
-  // contiguous class groups of about n_ref / G references each
-  g.cls[0] = 0;
-  int n = 0;
-  const int64_t target = (ix->n_ref + G - 1) / G;
-  int64_t acc = 0;
-  for (int32_t c = 0; c < ix->n_classes; ++c) {
-    acc += ix->class_off_h[c + 1] - ix->class_off_h[c];
-    if (acc >= target && n + 1 < G && c + 1 < ix->n_classes) {
-      g.cls[++n] = c + 1;
-      acc = 0;
-    }
-  }
-  g.cls[++n] = ix->n_classes;
-  g.n = n;
-  return g;
-}
-
 bool device_ok(int* sm_count, int* dev) {
   if (cudaGetDevice(dev) != cudaSuccess) return false;
   cudaDeviceProp prop;
@@ -356,7 +329,6 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
                       cudaMemcpyHostToDevice, s));
   ix->sorted = std::is_sorted(lab_h.begin(), lab_h.end());
   if (ix->sorted) {
-    ix->sref_u8 = ix->ref_u8;
     ix->sref_bf = ix->ref_bf;
     ix->sref_ext = ix->ref_ext;
     ix->srnorm = ix->rnorm;
@@ -367,14 +339,13 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
     std::vector<int64_t> perm(n_ref);
     for (int64_t j = 0; j < n_ref; ++j) perm[next[lab_h[j]]++] = j;
     CKF(dmalloc(&perm_d, (size_t)n_ref));
-    CKF(dmalloc(&ix->sref_u8, (size_t)n_ref * kDim));
     CKF(dmalloc(&ix->sref_bf, (size_t)ix->n_pad * kDim));
     CKF(dmalloc(&ix->sref_ext, (size_t)ix->n_pad * kExt));
     CKF(dmalloc(&ix->srnorm, (size_t)ix->n_pad));
     CKF(dmalloc(&ix->slabels, (size_t)n_ref));
     CKF(cudaMemcpyAsync(perm_d, perm.data(), sizeof(int64_t) * n_ref, cudaMemcpyHostToDevice, s));
-    CKF(launch_gather_ref(perm_d, n_ref, ix->ref_u8, ix->sref_u8, ix->ref_bf, ix->sref_bf, ix->ref_ext, ix->sref_ext,
-                          ix->rnorm, ix->srnorm, ix->labels, ix->slabels, s));
+    CKF(launch_gather_ref(perm_d, n_ref, ix->ref_bf, ix->sref_bf, ix->ref_ext, ix->sref_ext, ix->rnorm, ix->srnorm,
+                          ix->labels, ix->slabels, s));
     // padding rows are the same in both orders
     CKF(cudaMemcpyAsync(ix->sref_bf + (size_t)n_ref * kDim, ix->ref_bf + (size_t)n_ref * kDim,
                         sizeof(__nv_bfloat16) * (size_t)(ix->n_pad - n_ref) * kDim, cudaMemcpyDeviceToDevice, s));
@@ -462,19 +433,30 @@ lnbnn_status nbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t n
     prof.mark(1);
     prof.mark(2);
   } else {
-    const int64_t m_pad = round_up(n_queries, kQueryPad);
+    // one query per row of a [m_pad, C] table of class minima, filled by the
+    // tensor-core scan of the class-sorted copy and summed per image
+    KnnPlan p = plan_knn(index, n_queries, 1);
     Carve c;
-    const size_t off_qnorm = c.take<int32_t>(m_pad);
+    const size_t off_qnorm = c.take<int32_t>(p.m_pad);
+    const size_t off_qbf = c.take<__nv_bfloat16>(p.m_pad * kDim);
+    const size_t off_qext = c.take<__nv_bfloat16>(p.m_pad * kExt);
+    const size_t off_mins = c.take<int32_t>((size_t)p.m_pad * C);
     CK(ensure(&index->ws, &index->ws_bytes, c.off));
-    int32_t* qnorm = reinterpret_cast<int32_t*>(static_cast<char*>(index->ws) + off_qnorm);
-    CK(launch_prep_query(queries, n_queries, m_pad, qnorm, nullptr, nullptr, s));
+    char* ws = static_cast<char*>(index->ws);
+    int32_t* qnorm = reinterpret_cast<int32_t*>(ws + off_qnorm);
+    __nv_bfloat16* qbf = reinterpret_cast<__nv_bfloat16*>(ws + off_qbf);
+    __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(ws + off_qext);
+    int32_t* mins = reinterpret_cast<int32_t*>(ws + off_mins);
+    CK(launch_prep_query(queries, n_queries, p.m_pad, qnorm, qbf, qext, s));
+    CK(cudaMemsetAsync(mins, 0x7F, sizeof(int32_t) * (size_t)p.m_pad * C, s));  // 0x7F7F7F7F > any distance
     prof.launched(1);
     prof.mark(1);
-    ClassGroups g = make_groups(index, n_queries);
-    CK(launch_nbnn_simt(queries, n_queries, qnorm, index->sref_u8, index->srnorm, index->slabels, index->class_off_d,
-                        g, offsets, n_images, C, totals, s));
+    CK(launch_nbnn_tc(index->tc, qbf, qext, n_queries, p.m_pad, index->n_ref, p.splits, p.split_len, mins, C,
+                      index->class_off_d, index->dev_err, index->prof_on ? index->prof_stats : nullptr, s));
     prof.launched(1, true);
     prof.mark(2);
+    CK(launch_nbnn_sum(mins, n_queries, C, offsets, n_images, totals, s));
+    prof.launched(1);
   }
   CK(launch_argmin(totals, n_images, C, classes, s));
   prof.launched(1);

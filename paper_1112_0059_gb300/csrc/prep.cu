@@ -105,18 +105,16 @@ __global__ void label_hist_kernel(const int32_t* __restrict__ labels, int64_t n,
   }
 }
 
-__global__ void gather_ref_kernel(const int64_t* __restrict__ perm, int64_t n, const uint8_t* __restrict__ src_u8,
-                                  uint8_t* __restrict__ dst_u8, const __nv_bfloat16* __restrict__ src_bf,
+__global__ void gather_ref_kernel(const int64_t* __restrict__ perm, int64_t n, const __nv_bfloat16* __restrict__ src_bf,
                                   __nv_bfloat16* __restrict__ dst_bf, const __nv_bfloat16* __restrict__ src_ext,
                                   __nv_bfloat16* __restrict__ dst_ext, const float* __restrict__ src_norm,
                                   float* __restrict__ dst_norm, const int32_t* __restrict__ src_lab,
                                   int32_t* __restrict__ dst_lab) {
-  // one warp per row: 32 lanes x 4 bytes of uint8, 32 lanes x 8 bytes of bf16
+  // one warp per row: 32 lanes x 8 bytes of bf16
   const int lane = threadIdx.x & 31;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (row >= n) return;
   const int64_t from = perm[row];
-  reinterpret_cast<uint32_t*>(dst_u8 + row * kDim)[lane] = reinterpret_cast<const uint32_t*>(src_u8 + from * kDim)[lane];
   reinterpret_cast<uint2*>(dst_bf + row * kDim)[lane] = reinterpret_cast<const uint2*>(src_bf + from * kDim)[lane];
   if (lane < 2)
     reinterpret_cast<uint4*>(dst_ext + row * kExt)[lane] = reinterpret_cast<const uint4*>(src_ext + from * kExt)[lane];
@@ -165,13 +163,13 @@ cudaError_t launch_label_hist(const int32_t* labels, int64_t n, int32_t C, unsig
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_ref(const int64_t* perm, int64_t n, const uint8_t* src_u8, uint8_t* dst_u8,
-                              const __nv_bfloat16* src_bf, __nv_bfloat16* dst_bf, const __nv_bfloat16* src_ext,
+cudaError_t launch_gather_ref(const int64_t* perm, int64_t n, const __nv_bfloat16* src_bf, __nv_bfloat16* dst_bf,
+                              const __nv_bfloat16* src_ext,
                               __nv_bfloat16* dst_ext, const float* src_norm, float* dst_norm,
                               const int32_t* src_lab, int32_t* dst_lab, cudaStream_t s) {
   const int64_t blocks = (n * 32 + 255) / 256;
-  gather_ref_kernel<<<(unsigned)blocks, 256, 0, s>>>(perm, n, src_u8, dst_u8, src_bf, dst_bf, src_ext, dst_ext,
-                                                     src_norm, dst_norm, src_lab, dst_lab);
+  gather_ref_kernel<<<(unsigned)blocks, 256, 0, s>>>(perm, n, src_bf, dst_bf, src_ext, dst_ext, src_norm, dst_norm,
+                                                     src_lab, dst_lab);
   return cudaGetLastError();
 }
 

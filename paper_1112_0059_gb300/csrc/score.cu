@@ -82,6 +82,20 @@ __global__ void lnbnn_score_kernel(const uint64_t* __restrict__ lists, int64_t m
   }
 }
 
+// Alg. 1's sum for image img and class c: totals[img][c] = sum over the image's
+// descriptor rows of mins[row][c] (= NN_c of that descriptor).  Rows outside
+// [0, m) are skipped (they only arise from invalid offsets, flagged elsewhere).
+__global__ void nbnn_sum_kernel(const int32_t* __restrict__ mins, int64_t m, int32_t C,
+                                const int64_t* __restrict__ offsets, int64_t* __restrict__ totals) {
+  const int64_t img = blockIdx.x;
+  const int32_t c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const int64_t r0 = max(offsets[img], (int64_t)0), r1 = min(offsets[img + 1], m);
+  int64_t acc = 0;
+  for (int64_t r = r0; r < r1; ++r) acc += mins[r * C + c];
+  totals[img * C + c] = acc;
+}
+
 __global__ void check_offsets_kernel(const int64_t* __restrict__ offsets, int64_t n_img, int64_t m,
                                      uint32_t* __restrict__ dev_err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -145,6 +159,14 @@ cudaError_t launch_lnbnn_score(const uint64_t* lists, int64_t m, int K1, int k, 
   if (m == 0 || n_img == 0) return cudaSuccess;
   lnbnn_score_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(lists, m, K1, k, labels, offsets, n_img, C, totals,
                                                                   dev_err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nbnn_sum(const int32_t* mins, int64_t m, int32_t C, const int64_t* offsets, int64_t n_img,
+                            int64_t* totals, cudaStream_t s) {
+  if (n_img == 0) return cudaSuccess;
+  dim3 grid((unsigned)n_img, (unsigned)((C + 127) / 128));
+  nbnn_sum_kernel<<<grid, 128, 0, s>>>(mins, m, C, offsets, totals);
   return cudaGetLastError();
 }
 
