@@ -71,10 +71,11 @@ typedef enum lnbnn_status {
  *   stream   work is issued on it; the call synchronises it before returning
  *   out      receives the handle (set to NULL on failure)
  *
- * The index copies what it needs (an exact BF16 operand copy, squared norms,
- * labels, a class-sorted copy when the labels are not already grouped), so
- * the caller may free ref and labels afterwards.  Device memory: about
- * 3 * 128 * n_ref bytes (plus as much again when labels are not sorted).
+ * The index copies what it needs (the descriptors, an exact BF16 operand copy
+ * with a 16-column norm extension, squared norms, labels, and a class-sorted
+ * operand copy when the labels are not already grouped by class), so the
+ * caller may free ref and labels afterwards.  Device memory: about 424 bytes
+ * per reference (plus about 296 more when the labels are not grouped).
  * Errors: INVALID_ARG, LABEL_RANGE, OOM, CUDA, UNSUPPORTED.  A class with no
  * reference is accepted here; nbnn_classify then returns EMPTY_CLASS.
  */
