@@ -20,8 +20,10 @@
  *     values, as int32; totals are exact int64 sums.
  *   - Neighbours are ordered by (distance, reference row) ascending, so equal
  *     distances go to the lower row of the reference set given to create.
- *   - Calls on one index share its workspace: issue them on one stream, or
- *     serialise them; two calls on one index that overlap on the GPU race.
+ *   - Calls without a workspace argument share the index's own workspace:
+ *     issue them on one stream, or serialise them; two such calls on one
+ *     index that overlap on the GPU race.  Calls that may overlap (several
+ *     streams) each use their own lnbnn_workspace.
  *   - No call throws; every failure is a status code.
  */
 #ifndef LNBNN_H
@@ -56,7 +58,7 @@ typedef enum lnbnn_status {
   LNBNN_ERR_TIMEOUT = 7,      /* a bounded device wait expired */
   LNBNN_ERR_UNSUPPORTED = 8,  /* device is not compute capability 10.3 (sm_103) */
   LNBNN_ERR_OFFSETS = 9,      /* offsets not 0 = o[0] <= ... <= o[n_images] = n_queries */
-  LNBNN_ERR_SCRATCH_LIMIT = 10 /* problem larger than the fixed scratch of knn_search_noalloc */
+  LNBNN_ERR_SCRATCH_LIMIT = 10 /* problem larger than a workspace or the scratch of knn_search_noalloc */
 } lnbnn_status;
 
 /*
@@ -132,6 +134,32 @@ LNBNN_API lnbnn_status lnbnn_classify(lnbnn_index *index, const uint8_t *queries
 LNBNN_API lnbnn_status nbnn_classify(lnbnn_index *index, const uint8_t *queries, int64_t n_queries,
                            const int64_t *offsets, int64_t n_images, int64_t *totals,
                            int32_t *classes, void *stream);
+
+/*
+ * Workspaces: the device scratch of one call (query operand copies, the
+ * per-row neighbour lists, the NBNN minima table), sized once for at most
+ * max_queries query descriptors and neighbourhoods up to max_k.  A call given a
+ * workspace allocates nothing, so it may be captured into a CUDA graph, and
+ * calls with distinct workspaces may run concurrently on different streams
+ * (the index itself is only read).  A workspace belongs to the index it was
+ * created for.  A call larger than its workspace returns SCRATCH_LIMIT.
+ * The profile (lnbnn_profile_*) is not for captured calls.
+ */
+typedef struct lnbnn_workspace lnbnn_workspace;
+
+LNBNN_API lnbnn_status lnbnn_workspace_create(lnbnn_index *index, int64_t max_queries, int32_t max_k,
+                                              lnbnn_workspace **out);
+LNBNN_API void lnbnn_workspace_destroy(lnbnn_workspace *workspace);
+
+/* knn_search, lnbnn_classify and nbnn_classify with an explicit workspace. */
+LNBNN_API lnbnn_status knn_search_ws(lnbnn_index *index, lnbnn_workspace *workspace, const uint8_t *queries,
+                                     int64_t n_queries, int32_t k, int32_t *idx, int32_t *dist, void *stream);
+LNBNN_API lnbnn_status lnbnn_classify_ws(lnbnn_index *index, lnbnn_workspace *workspace, const uint8_t *queries,
+                                         int64_t n_queries, const int64_t *offsets, int64_t n_images, int32_t k,
+                                         int64_t *totals, int32_t *classes, void *stream);
+LNBNN_API lnbnn_status nbnn_classify_ws(lnbnn_index *index, lnbnn_workspace *workspace, const uint8_t *queries,
+                                        int64_t n_queries, const int64_t *offsets, int64_t n_images,
+                                        int64_t *totals, int32_t *classes, void *stream);
 
 /*
  * Host-buffer forms of the two classifiers: queries, offsets, totals and

@@ -565,9 +565,6 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const __n
   if (m_pad % (kBM * kCluster) != 0 || split_len % kBN != 0) return cudaErrorInvalidValue;
   CUtensorMap tq, tqe;
   if (!encode_operand(&tq, &tqe, qbf, qext, (uint64_t)m_pad, kBM)) return cudaErrorInvalidValue;
-  cudaError_t e =
-      cudaFuncSetAttribute(tc_scan_kernel<Epilogue>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(m_pad / kBM), (unsigned)splits);
   tc_scan_kernel<Epilogue><<<grid, kThreads, kSmemBytes, s>>>(tq, tqe, tr, tre, m, n_ref, split_len, out, dev_err,
                                                               stats);
@@ -575,6 +572,18 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const __n
 }
 
 }  // namespace
+
+cudaError_t prepare_tc_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(tc_scan_kernel<KnnEpilogue<kTcRegListMax>>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_scan_kernel<KnnEpilogue<0>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_scan_kernel<NbnnEpilogue>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes);
+  return e;
+}
 
 cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf,
                           const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,

@@ -28,6 +28,10 @@ struct TcTensorMaps {
   CUtensorMap sref, sref_ext;  // the same over the class-sorted copy
 };
 
+// Sets the kernels' shared-memory size on the current device; call once per
+// device before launching (and before any stream capture).
+cudaError_t prepare_tc_kernels();
+
 bool make_tc_tensor_maps(const __nv_bfloat16* ref_bf, const __nv_bfloat16* sref_bf, const __nv_bfloat16* ref_ext,
                          const __nv_bfloat16* sref_ext, int64_t n_pad, TcTensorMaps* out);
 

@@ -49,6 +49,12 @@ struct lnbnn_index {
   std::vector<CallEvents> prof_pending, prof_free;
 };
 
+struct lnbnn_workspace {
+  const lnbnn_index* index = nullptr;
+  void* base = nullptr;
+  size_t bytes = 0;
+};
+
 namespace {
 
 #define CK(call)                                       \
@@ -209,12 +215,57 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1) {
   return p;
 }
 
+// Device scratch of one call: the caller's workspace (fixed size, nothing is
+// allocated) or else the index's grow-only workspace.
+struct Scratch {
+  lnbnn_index* ix;
+  lnbnn_workspace* w;
+  lnbnn_status get(size_t need, char** out) {
+    if (w) {
+      if (need > w->bytes) return LNBNN_ERR_SCRATCH_LIMIT;
+      *out = static_cast<char*>(w->base);
+      return LNBNN_OK;
+    }
+    CK(ensure(&ix->ws, &ix->ws_bytes, need));
+    *out = static_cast<char*>(ix->ws);
+    return LNBNN_OK;
+  }
+};
+
+struct NbnnPlan {
+  KnnPlan k;
+  size_t off_qnorm, off_qbf, off_qext, off_mins, bytes;
+};
+
+NbnnPlan plan_nbnn(const lnbnn_index* ix, int64_t m) {
+  NbnnPlan p{};
+  p.k = plan_knn(ix, m, 1);
+  Carve c;
+  p.off_qnorm = c.take<int32_t>(p.k.m_pad);
+  p.off_qbf = c.take<__nv_bfloat16>(p.k.m_pad * kDim);
+  p.off_qext = c.take<__nv_bfloat16>(p.k.m_pad * kExt);
+  p.off_mins = c.take<int32_t>((size_t)p.k.m_pad * ix->n_classes);
+  p.bytes = c.off;
+  return p;
+}
+
+// Largest scratch any call with at most max_q queries and lists of K1 needs.
+size_t scratch_bound(const lnbnn_index* ix, int64_t max_q, int K1) {
+  size_t b = 0;
+  for (int64_t m = kQueryPad; m < max_q + kQueryPad; m += kQueryPad) {
+    b = std::max(b, plan_knn(ix, std::min(m, max_q), K1).bytes);
+    b = std::max(b, plan_nbnn(ix, std::min(m, max_q)).bytes);
+  }
+  return b;
+}
+
 // Runs the exact search; *lists receives m sorted lists of K1 keys.
-lnbnn_status run_knn(lnbnn_index* ix, const uint8_t* q, int64_t m, int K1, cudaStream_t s, const uint64_t** lists,
-                     CallProfile& prof) {
+lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_t m, int K1, cudaStream_t s,
+                     const uint64_t** lists, CallProfile& prof) {
   KnnPlan p = plan_knn(ix, m, K1);
-  CK(ensure(&ix->ws, &ix->ws_bytes, p.bytes));
-  char* ws = static_cast<char*>(ix->ws);
+  char* ws = nullptr;
+  lnbnn_status st = scratch.get(p.bytes, &ws);
+  if (st != LNBNN_OK) return st;
   int32_t* qnorm = reinterpret_cast<int32_t*>(ws + p.off_qnorm);
   __nv_bfloat16* qbf = reinterpret_cast<__nv_bfloat16*>(ws + p.off_qbf);
   __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(ws + p.off_qext);
@@ -259,7 +310,7 @@ const char* lnbnn_status_string(lnbnn_status st) {
     case LNBNN_ERR_TIMEOUT: return "device wait timed out";
     case LNBNN_ERR_UNSUPPORTED: return "unsupported device (needs compute capability 10.3)";
     case LNBNN_ERR_OFFSETS: return "invalid image offsets";
-    case LNBNN_ERR_SCRATCH_LIMIT: return "problem larger than the fixed scratch of knn_search_noalloc";
+    case LNBNN_ERR_SCRATCH_LIMIT: return "problem larger than the fixed scratch (workspace or knn_search_noalloc)";
   }
   return "unknown status";
 }
@@ -356,6 +407,7 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
   }
   if (!make_tc_tensor_maps(ix->ref_bf, ix->sref_bf, ix->ref_ext, ix->sref_ext, ix->n_pad, &ix->tc))
     return fail(LNBNN_ERR_CUDA);
+  CKF(prepare_tc_kernels());
   CKF(cudaStreamSynchronize(s));
   cudaFree(counts);
   cudaFree(bad);
@@ -374,24 +426,26 @@ lnbnn_status lnbnn_index_info(const lnbnn_index* index, int64_t* n_ref, int32_t*
   return LNBNN_OK;
 }
 
-lnbnn_status knn_search(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, int32_t k, int32_t* idx,
-                        int32_t* dist, void* stream) {
+static lnbnn_status do_knn_search(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries, int64_t n_queries,
+                                  int32_t k, int32_t* idx, int32_t* dist, void* stream) {
   if (!index || n_queries < 0) return LNBNN_ERR_INVALID_ARG;
   if (!k_ok(index, k, 0)) return LNBNN_ERR_K_RANGE;
   if (n_queries == 0) return LNBNN_OK;
   if (!queries || !idx || !dist) return LNBNN_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CallProfile prof(index, s);
+  Scratch scratch{index, w};
   const uint64_t* lists = nullptr;
-  lnbnn_status st = run_knn(index, queries, n_queries, k, s, &lists, prof);
+  lnbnn_status st = run_knn(index, scratch, queries, n_queries, k, s, &lists, prof);
   if (st != LNBNN_OK) return st;
   CK(launch_extract_knn(lists, n_queries, k, k, idx, dist, s));
   prof.launched(1);
   return LNBNN_OK;
 }
 
-lnbnn_status lnbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
-                            int64_t n_images, int32_t k, int64_t* totals, int32_t* classes, void* stream) {
+static lnbnn_status do_lnbnn_classify(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries,
+                                      int64_t n_queries, const int64_t* offsets, int64_t n_images, int32_t k,
+                                      int64_t* totals, int32_t* classes, void* stream) {
   if (!index || n_queries < 0 || n_images < 0) return LNBNN_ERR_INVALID_ARG;
   if (!k_ok(index, k, 1)) return LNBNN_ERR_K_RANGE;
   if (n_images == 0) return n_queries == 0 ? LNBNN_OK : LNBNN_ERR_OFFSETS;
@@ -403,8 +457,9 @@ lnbnn_status lnbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t 
   CK(launch_check_offsets(offsets, n_images, n_queries, index->dev_err, s));
   prof.launched(1);
   if (n_queries > 0) {
+    Scratch scratch{index, w};
     const uint64_t* lists = nullptr;
-    lnbnn_status st = run_knn(index, queries, n_queries, k + 1, s, &lists, prof);
+    lnbnn_status st = run_knn(index, scratch, queries, n_queries, k + 1, s, &lists, prof);
     if (st != LNBNN_OK) return st;
     CK(launch_lnbnn_score(lists, n_queries, k + 1, k, index->labels, offsets, n_images, C, totals, index->dev_err, s));
     prof.launched(1);
@@ -417,8 +472,9 @@ lnbnn_status lnbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t 
   return LNBNN_OK;
 }
 
-lnbnn_status nbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
-                           int64_t n_images, int64_t* totals, int32_t* classes, void* stream) {
+static lnbnn_status do_nbnn_classify(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries,
+                                     int64_t n_queries, const int64_t* offsets, int64_t n_images, int64_t* totals,
+                                     int32_t* classes, void* stream) {
   if (!index || n_queries < 0 || n_images < 0) return LNBNN_ERR_INVALID_ARG;
   if (index->has_empty_class) return LNBNN_ERR_EMPTY_CLASS;
   if (n_images == 0) return n_queries == 0 ? LNBNN_OK : LNBNN_ERR_OFFSETS;
@@ -435,18 +491,16 @@ lnbnn_status nbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t n
   } else {
     // one query per row of a [m_pad, C] table of class minima, filled by the
     // tensor-core scan of the class-sorted copy and summed per image
-    KnnPlan p = plan_knn(index, n_queries, 1);
-    Carve c;
-    const size_t off_qnorm = c.take<int32_t>(p.m_pad);
-    const size_t off_qbf = c.take<__nv_bfloat16>(p.m_pad * kDim);
-    const size_t off_qext = c.take<__nv_bfloat16>(p.m_pad * kExt);
-    const size_t off_mins = c.take<int32_t>((size_t)p.m_pad * C);
-    CK(ensure(&index->ws, &index->ws_bytes, c.off));
-    char* ws = static_cast<char*>(index->ws);
-    int32_t* qnorm = reinterpret_cast<int32_t*>(ws + off_qnorm);
-    __nv_bfloat16* qbf = reinterpret_cast<__nv_bfloat16*>(ws + off_qbf);
-    __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(ws + off_qext);
-    int32_t* mins = reinterpret_cast<int32_t*>(ws + off_mins);
+    const NbnnPlan np = plan_nbnn(index, n_queries);
+    const KnnPlan& p = np.k;
+    Scratch scratch{index, w};
+    char* ws = nullptr;
+    lnbnn_status st = scratch.get(np.bytes, &ws);
+    if (st != LNBNN_OK) return st;
+    int32_t* qnorm = reinterpret_cast<int32_t*>(ws + np.off_qnorm);
+    __nv_bfloat16* qbf = reinterpret_cast<__nv_bfloat16*>(ws + np.off_qbf);
+    __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(ws + np.off_qext);
+    int32_t* mins = reinterpret_cast<int32_t*>(ws + np.off_mins);
     CK(launch_prep_query(queries, n_queries, p.m_pad, qnorm, qbf, qext, s));
     CK(cudaMemsetAsync(mins, 0x7F, sizeof(int32_t) * (size_t)p.m_pad * C, s));  // 0x7F7F7F7F > any distance
     prof.launched(1);
@@ -461,6 +515,65 @@ lnbnn_status nbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t n
   CK(launch_argmin(totals, n_images, C, classes, s));
   prof.launched(1);
   return LNBNN_OK;
+}
+
+lnbnn_status knn_search(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, int32_t k, int32_t* idx,
+                        int32_t* dist, void* stream) {
+  return do_knn_search(index, nullptr, queries, n_queries, k, idx, dist, stream);
+}
+
+lnbnn_status lnbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
+                            int64_t n_images, int32_t k, int64_t* totals, int32_t* classes, void* stream) {
+  return do_lnbnn_classify(index, nullptr, queries, n_queries, offsets, n_images, k, totals, classes, stream);
+}
+
+lnbnn_status nbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
+                           int64_t n_images, int64_t* totals, int32_t* classes, void* stream) {
+  return do_nbnn_classify(index, nullptr, queries, n_queries, offsets, n_images, totals, classes, stream);
+}
+
+lnbnn_status lnbnn_workspace_create(lnbnn_index* index, int64_t max_queries, int32_t max_k, lnbnn_workspace** out) {
+  if (!out) return LNBNN_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!index || max_queries < 1) return LNBNN_ERR_INVALID_ARG;
+  if (!k_ok(index, max_k, 0)) return LNBNN_ERR_K_RANGE;
+  lnbnn_workspace* w = new (std::nothrow) lnbnn_workspace();
+  if (!w) return LNBNN_ERR_OOM;
+  w->index = index;
+  w->bytes = scratch_bound(index, max_queries, std::min<int>(max_k + 1, LNBNN_MAX_K + 1));
+  cudaError_t e = cudaMalloc(&w->base, w->bytes);
+  if (e != cudaSuccess) {
+    delete w;
+    return status_of(e);
+  }
+  *out = w;
+  return LNBNN_OK;
+}
+
+void lnbnn_workspace_destroy(lnbnn_workspace* w) {
+  if (!w) return;
+  cudaFree(w->base);
+  delete w;
+}
+
+lnbnn_status knn_search_ws(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries, int64_t n_queries,
+                           int32_t k, int32_t* idx, int32_t* dist, void* stream) {
+  if (!w || w->index != index) return LNBNN_ERR_INVALID_ARG;
+  return do_knn_search(index, w, queries, n_queries, k, idx, dist, stream);
+}
+
+lnbnn_status lnbnn_classify_ws(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries, int64_t n_queries,
+                               const int64_t* offsets, int64_t n_images, int32_t k, int64_t* totals, int32_t* classes,
+                               void* stream) {
+  if (!w || w->index != index) return LNBNN_ERR_INVALID_ARG;
+  return do_lnbnn_classify(index, w, queries, n_queries, offsets, n_images, k, totals, classes, stream);
+}
+
+lnbnn_status nbnn_classify_ws(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries, int64_t n_queries,
+                              const int64_t* offsets, int64_t n_images, int64_t* totals, int32_t* classes,
+                              void* stream) {
+  if (!w || w->index != index) return LNBNN_ERR_INVALID_ARG;
+  return do_nbnn_classify(index, w, queries, n_queries, offsets, n_images, totals, classes, stream);
 }
 
 static lnbnn_status classify_host(lnbnn_index* index, bool local, const uint8_t* queries, int64_t n_queries,

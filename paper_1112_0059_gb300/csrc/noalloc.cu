@@ -42,6 +42,10 @@ lnbnn_status scratch_on_current_device(void** addr, int* sm_count) {
       return LNBNN_ERR_CUDA;
     }
     if (prop.major != 10 || prop.minor != 3) return LNBNN_ERR_UNSUPPORTED;
+    if (prepare_tc_kernels() != cudaSuccess) {
+      cudaGetLastError();
+      return LNBNN_ERR_CUDA;
+    }
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
       cudaGetLastError();

@@ -30,13 +30,14 @@ STATUS = {
     7: "device wait timed out",
     8: "unsupported device",
     9: "invalid image offsets",
-    10: "problem larger than the fixed scratch of knn_search_noalloc",
+    10: "problem larger than a workspace or the scratch of knn_search_noalloc",
 }
 MAX_K = 255
 
 EXPORTS = ["lnbnn_index_create", "lnbnn_index_destroy", "lnbnn_index_info", "knn_search", "lnbnn_classify",
            "nbnn_classify", "lnbnn_classify_host", "nbnn_classify_host", "lnbnn_sync", "lnbnn_profile_enable",
-           "lnbnn_profile_read", "lnbnn_status_string", "knn_search_noalloc"]
+           "lnbnn_profile_read", "lnbnn_status_string", "knn_search_noalloc", "lnbnn_workspace_create",
+           "lnbnn_workspace_destroy", "knn_search_ws", "lnbnn_classify_ws", "nbnn_classify_ws"]
 
 
 class Profile(ctypes.Structure):
@@ -81,11 +82,18 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.lnbnn_sync.argtypes = [P, P]
         lib.lnbnn_profile_enable.argtypes = [P, ctypes.c_int]
         lib.lnbnn_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
+        lib.lnbnn_workspace_create.argtypes = [P, I64, I32, ctypes.POINTER(P)]
+        lib.lnbnn_workspace_destroy.argtypes = [P]
+        lib.lnbnn_workspace_destroy.restype = None
+        lib.knn_search_ws.argtypes = [P, P, P, I64, I32, P, P, P]
+        lib.lnbnn_classify_ws.argtypes = [P, P, P, I64, P, I64, I32, P, P, P]
+        lib.nbnn_classify_ws.argtypes = [P, P, P, I64, P, I64, P, P, P]
         lib.lnbnn_status_string.argtypes = [ctypes.c_int]
         lib.lnbnn_status_string.restype = ctypes.c_char_p
         for name in ("lnbnn_index_create", "lnbnn_index_info", "knn_search", "lnbnn_classify", "nbnn_classify",
                      "lnbnn_classify_host", "nbnn_classify_host", "lnbnn_sync", "lnbnn_profile_enable",
-                     "lnbnn_profile_read"):
+                     "lnbnn_profile_read", "lnbnn_workspace_create", "knn_search_ws", "lnbnn_classify_ws",
+                     "nbnn_classify_ws"):
             getattr(lib, name).restype = ctypes.c_int
         if path == LIB_PATH:
             _lib = lib
@@ -154,41 +162,54 @@ class Index:
             raise ValueError("index is closed")
         return self._h
 
-    def knn_search(self, queries, k: int, stream=None):
+    def workspace(self, max_queries: int, max_k: int) -> "Workspace":
+        """Device scratch for calls of at most max_queries descriptors and k <= max_k
+        (no allocation inside those calls; one per concurrent stream)."""
+        return Workspace(self, max_queries, max_k)
+
+    def knn_search(self, queries, k: int, stream=None, workspace=None, out=None):
         """NN(d, k): ``(idx int32 [M, k], dist int32 [M, k])``, exact, by (distance, row)."""
         import torch
         m = int(queries.shape[0])
-        idx = torch.empty((m, k), dtype=torch.int32, device=queries.device)
-        dist = torch.empty((m, k), dtype=torch.int32, device=queries.device)
-        _check(self._lib.knn_search(self.handle, _dev(queries, torch.uint8, "queries"), m, k,
-                                    _dev(idx, torch.int32, "idx"), _dev(dist, torch.int32, "dist"),
-                                    _stream_ptr(stream)), "knn_search")
+        idx, dist = out if out is not None else (
+            torch.empty((m, k), dtype=torch.int32, device=queries.device),
+            torch.empty((m, k), dtype=torch.int32, device=queries.device))
+        args = (_dev(queries, torch.uint8, "queries"), m, k, _dev(idx, torch.int32, "idx"),
+                _dev(dist, torch.int32, "dist"), _stream_ptr(stream))
+        if workspace is None:
+            _check(self._lib.knn_search(self.handle, *args), "knn_search")
+        else:
+            _check(self._lib.knn_search_ws(self.handle, workspace.handle, *args), "knn_search_ws")
         return idx, dist
 
-    def lnbnn_classify(self, queries, offsets, k: int, stream=None, out=None):
+    def lnbnn_classify(self, queries, offsets, k: int, stream=None, out=None, workspace=None):
         """Alg. 2: ``(totals int64 [n_img, C], classes int32 [n_img])``."""
         import torch
         m, n_img = int(queries.shape[0]), int(offsets.shape[0]) - 1
         totals, classes = out if out is not None else (
             torch.empty((n_img, self.n_classes), dtype=torch.int64, device=queries.device),
             torch.empty((n_img,), dtype=torch.int32, device=queries.device))
-        _check(self._lib.lnbnn_classify(self.handle, _dev(queries, torch.uint8, "queries"), m,
-                                        _dev(offsets, torch.int64, "offsets"), n_img, k,
-                                        _dev(totals, torch.int64, "totals"), _dev(classes, torch.int32, "classes"),
-                                        _stream_ptr(stream)), "lnbnn_classify")
+        args = (_dev(queries, torch.uint8, "queries"), m, _dev(offsets, torch.int64, "offsets"), n_img, k,
+                _dev(totals, torch.int64, "totals"), _dev(classes, torch.int32, "classes"), _stream_ptr(stream))
+        if workspace is None:
+            _check(self._lib.lnbnn_classify(self.handle, *args), "lnbnn_classify")
+        else:
+            _check(self._lib.lnbnn_classify_ws(self.handle, workspace.handle, *args), "lnbnn_classify_ws")
         return totals, classes
 
-    def nbnn_classify(self, queries, offsets, stream=None, out=None):
+    def nbnn_classify(self, queries, offsets, stream=None, out=None, workspace=None):
         """Alg. 1: ``(totals int64 [n_img, C], classes int32 [n_img])``."""
         import torch
         m, n_img = int(queries.shape[0]), int(offsets.shape[0]) - 1
         totals, classes = out if out is not None else (
             torch.empty((n_img, self.n_classes), dtype=torch.int64, device=queries.device),
             torch.empty((n_img,), dtype=torch.int32, device=queries.device))
-        _check(self._lib.nbnn_classify(self.handle, _dev(queries, torch.uint8, "queries"), m,
-                                       _dev(offsets, torch.int64, "offsets"), n_img,
-                                       _dev(totals, torch.int64, "totals"), _dev(classes, torch.int32, "classes"),
-                                       _stream_ptr(stream)), "nbnn_classify")
+        args = (_dev(queries, torch.uint8, "queries"), m, _dev(offsets, torch.int64, "offsets"), n_img,
+                _dev(totals, torch.int64, "totals"), _dev(classes, torch.int32, "classes"), _stream_ptr(stream))
+        if workspace is None:
+            _check(self._lib.nbnn_classify(self.handle, *args), "nbnn_classify")
+        else:
+            _check(self._lib.nbnn_classify_ws(self.handle, workspace.handle, *args), "nbnn_classify_ws")
         return totals, classes
 
     def classify_host(self, queries: np.ndarray, offsets: np.ndarray, k: int | None, totals: np.ndarray | None = None,
@@ -225,6 +246,42 @@ class Index:
     def sync(self, stream=None) -> None:
         """Wait for the stream and raise any device-side error (timeout, offsets)."""
         _check(self._lib.lnbnn_sync(self.handle, _stream_ptr(stream)), "lnbnn_sync")
+
+
+class Workspace:
+    """Device scratch of one in-flight call (see ``lnbnn_workspace_create``)."""
+
+    def __init__(self, index: Index, max_queries: int, max_k: int):
+        self._lib = index._lib
+        self.index = index
+        self.max_queries, self.max_k = int(max_queries), int(max_k)
+        h = ctypes.c_void_p()
+        _check(self._lib.lnbnn_workspace_create(index.handle, self.max_queries, self.max_k, ctypes.byref(h)),
+               "lnbnn_workspace_create")
+        self._h = h
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise ValueError("workspace is closed")
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.lnbnn_workspace_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def knn_search_noalloc(ref, queries, k: int, stream=None):
