@@ -52,6 +52,9 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--serve-rates", default="100,300,1000",
+                   help="Poisson arrival rates (images/s) of the serving runs; empty to skip them")
+    p.add_argument("--serve-seconds", type=float, default=2.5, help="arrival window of each serving run")
     return p.parse_args()
 
 
@@ -336,6 +339,11 @@ def run_ours(args, w):
                "api": ("lnbnn" if local else "nbnn") + "_classify_host (pinned host buffers; copies, classify, "
                       "copy-back, sync per step)"}
 
+    serve_block = None
+    rates = [float(r) for r in args.serve_rates.split(",") if r.strip()]
+    if rates and args.method == "local" and w.n_classes == synth.workload("serving").n_classes:
+        serve_block = run_serving(index, rates, args.serve_seconds, k)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(args.method, ref, labels, w.n_classes, q, k, args.cpu_seconds, int(off[1]))
@@ -350,6 +358,7 @@ def run_ours(args, w):
             "roofline": roofline,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "serve": serve_block,
             "gpu_launches": int(prof["kernel_launches"]),
             "clocks": clk,
             "profile": {"search_ms_total": prof["search_ms"], "other_ms_total": prof["other_ms"],
@@ -362,6 +371,28 @@ def run_ours(args, w):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_serving(index, rates, seconds, k) -> dict:
+    """The continuous-batching server over the resident index: Poisson
+    arrivals of query images with log-uniform [100, 4000] descriptors."""
+    from paper_1112_0059_gb300 import serve
+    w = synth.workload("serving")
+    cfg = {"slots": 3, "max_batch_queries": 16384, "max_batch_images": 256, "graphs": True, "graph_granule": 2048}
+    runs, first = [], 0
+    with serve.Server(index, k=k, method="local", **cfg) as srv:
+        srv.run(serve.poisson_requests(w, 1000.0, 8, seed=99, first_image=100000))  # warm-up
+        for rate in rates:
+            n = max(8, int(rate * seconds))
+            reqs = serve.poisson_requests(w, rate, n, seed=0, first_image=first)
+            first += n
+            srv.log = []
+            done = srv.run(reqs)
+            st = serve.latency_stats(done, srv.log)
+            st["rate_offered"] = rate
+            runs.append(st)
+    return {"form": "exact", "k": k, "workload": "256-class index; Poisson arrivals; log-uniform [100, 4000] "
+            "descriptors per image; latency = arrival to totals and class on the host", **cfg, "runs": runs}
 
 
 def main():
