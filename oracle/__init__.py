@@ -15,6 +15,13 @@ Functions (paper: McCann & Lowe, "Local Naive Bayes Nearest Neighbor"):
   local_nbnn     -- Alg. 2 (LocalNBNN), per-image int64 totals + argmin
   local_nbnn_closed_form -- the same totals by sum_i min(0, NN_C - dist_B)
   nbnn           -- Alg. 1 (original NBNN), per-image int64 totals + argmin
+
+Coarse-shortlist form (this project's approximate search, in the place of the
+approximate kd-tree search of Section 5; exact neighbours on the shortlist):
+  e4m3_round     -- nearest FP8 E4M3 value of integers, ties to even mantissa
+  coarse_matrix  -- ||q'||^2 + ||r'||^2 - 2 q~.r~ with x' = x - 64, x~ = E4M3(x')
+  knn_coarse     -- the m smallest coarse values, reranked by exact distance
+  local_nbnn_coarse -- Alg. 2 on the reranked neighbours
 """
 from __future__ import annotations
 
@@ -73,8 +80,13 @@ class Oracle:
         for f in (lib.oracle_lnbnn, lib.oracle_lnbnn_closed_form):
             f.argtypes = [P, P, I64, I32, P, P, I64, I32, P, P, INT]
         lib.oracle_nbnn.argtypes = [P, P, I64, I32, P, P, I64, P, P, INT]
+        lib.oracle_e4m3_round.argtypes = [P, I64, P]
+        lib.oracle_coarse_matrix.argtypes = [P, I64, P, I64, P]
+        lib.oracle_knn_coarse.argtypes = [P, I64, P, I64, I32, I32, P, P, INT]
+        lib.oracle_lnbnn_coarse.argtypes = [P, P, I64, I32, P, P, I64, I32, I32, P, P, INT]
         for f in (lib.oracle_sqdist_matrix, lib.oracle_knn, lib.oracle_class_min,
-                  lib.oracle_lnbnn, lib.oracle_lnbnn_closed_form, lib.oracle_nbnn):
+                  lib.oracle_lnbnn, lib.oracle_lnbnn_closed_form, lib.oracle_nbnn, lib.oracle_e4m3_round,
+                  lib.oracle_coarse_matrix, lib.oracle_knn_coarse, lib.oracle_lnbnn_coarse):
             f.restype = ctypes.c_int
         self.lib = lib
 
@@ -134,6 +146,44 @@ class Oracle:
         """Alg. 1: ``(totals int64 [n_img, C], classes int32 [n_img])``."""
         return self._classify(self.lib.oracle_nbnn, ref, labels, n_classes, q, offsets, None,
                               threads)
+
+
+    def e4m3_round(self, x) -> np.ndarray:
+        """Nearest FP8 E4M3 value of each integer (|x| <= 448), ties to even mantissa."""
+        x = np.ascontiguousarray(x, dtype=np.int32)
+        out = np.empty_like(x)
+        _check(self.lib.oracle_e4m3_round(_p(x), x.size, _p(out)))
+        return out
+
+    def coarse_matrix(self, ref, q) -> np.ndarray:
+        """int64 [M, N]: coarse(q_i, r_j) = ||q'||^2 + ||r'||^2 - 2 q~.r~."""
+        ref, q = _u8(ref), _u8(q)
+        out = np.empty((q.shape[0], ref.shape[0]), dtype=np.int64)
+        _check(self.lib.oracle_coarse_matrix(_p(ref), ref.shape[0], _p(q), q.shape[0], _p(out)))
+        return out
+
+    def knn_coarse(self, ref, q, kk: int, m: int, threads: int = 0) -> tuple[np.ndarray, np.ndarray]:
+        """``(dist, idx)`` int64 [M, kk]: exact rerank of the coarse shortlist of m."""
+        ref, q = _u8(ref), _u8(q)
+        dist = np.empty((q.shape[0], kk), dtype=np.int64)
+        idx = np.empty((q.shape[0], kk), dtype=np.int64)
+        _check(self.lib.oracle_knn_coarse(_p(ref), ref.shape[0], _p(q), q.shape[0], kk, m, _p(dist), _p(idx),
+                                          threads))
+        return dist, idx
+
+    def local_nbnn_coarse(self, ref, labels, n_classes, q, offsets, k, m, threads: int = 0):
+        """Alg. 2 on the neighbours of the coarse shortlist of m (m >= k + 1)."""
+        ref, q = _u8(ref), _u8(q)
+        labels = np.ascontiguousarray(labels, dtype=np.int32)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        n_img = offsets.shape[0] - 1
+        if n_img < 0 or offsets[-1] != q.shape[0]:
+            raise OracleError(-5)
+        totals = np.empty((n_img, n_classes), dtype=np.int64)
+        classes = np.empty(n_img, dtype=np.int32)
+        _check(self.lib.oracle_lnbnn_coarse(_p(ref), _p(labels), ref.shape[0], n_classes, _p(q), _p(offsets),
+                                            n_img, k, m, _p(totals), _p(classes), threads))
+        return totals, classes
 
 
 def _u8(a) -> np.ndarray:
@@ -197,6 +247,22 @@ def local_nbnn_closed_form(ref, labels, n_classes, q, offsets, k, threads=0):
 
 def nbnn(ref, labels, n_classes, q, offsets, threads=0):
     return default().nbnn(ref, labels, n_classes, q, offsets, threads)
+
+
+def e4m3_round(x):
+    return default().e4m3_round(x)
+
+
+def coarse_matrix(ref, q):
+    return default().coarse_matrix(ref, q)
+
+
+def knn_coarse(ref, q, kk, m, threads=0):
+    return default().knn_coarse(ref, q, kk, m, threads)
+
+
+def local_nbnn_coarse(ref, labels, n_classes, q, offsets, k, m, threads=0):
+    return default().local_nbnn_coarse(ref, labels, n_classes, q, offsets, k, m, threads)
 
 
 def host_threads() -> int:

@@ -21,6 +21,16 @@
  *
  * Work is split across threads only over query descriptors, which Alg. 1 and
  * Alg. 2 treat independently; every per-descriptor step runs as written.
+ *
+ * The coarse-shortlist form (an approximate search of this project's own
+ * design, standing where the paper uses an approximate kd-tree search,
+ * Section 5) is stated here as:
+ *   - every coordinate is shifted, x' = x - 64, and rounded to the nearest
+ *     FP8 E4M3 value (3 mantissa bits, ties to even mantissa), x~;
+ *   - coarse(q, r) = ||q'||^2 + ||r'||^2 - 2 sum_t q~_t r~_t, an integer;
+ *   - the shortlist of a query is the m smallest (coarse, index) pairs;
+ *   - its exact distances are computed and the kk smallest (distance, index)
+ *     pairs of the shortlist are the neighbours; Alg. 2 then runs unchanged.
  */
 #include <pthread.h>
 #include <stdint.h>
@@ -92,9 +102,8 @@ static void class_min_one(const uint8_t *ref, const int32_t *labels, int64_t N, 
  *     dist_C = min over p_j of class C of ||d - p_j||^2;
  *     totals[C] += dist_C - dist_B.
  * nd, nj: scratch of k+1 entries. */
-static void lnbnn_one(const uint8_t *ref, const int32_t *labels, int64_t N, const uint8_t *q,
-                      int32_t k, int64_t *nd, int64_t *nj, int64_t *totals) {
-  knn_one(ref, N, q, k + 1, nd, nj);
+static void score_one(const int32_t *labels, int32_t k, const int64_t *nd, const int64_t *nj,
+                      int64_t *totals) {
   const int64_t dist_B = nd[k];
   for (int32_t a = 0; a < k; ++a) {
     const int32_t c = labels[nj[a]];
@@ -106,6 +115,79 @@ static void lnbnn_one(const uint8_t *ref, const int32_t *labels, int64_t N, cons
     for (int32_t b = 0; b < k; ++b)
       if (labels[nj[b]] == c && nd[b] < dist_C) dist_C = nd[b];
     totals[c] += dist_C - dist_B;
+  }
+}
+
+static void lnbnn_one(const uint8_t *ref, const int32_t *labels, int64_t N, const uint8_t *q,
+                      int32_t k, int64_t *nd, int64_t *nj, int64_t *totals) {
+  knn_one(ref, N, q, k + 1, nd, nj);
+  score_one(labels, k, nd, nj, totals);
+}
+
+/* ------------------------------------------------------ coarse shortlist */
+
+#define ORACLE_SHIFT 64
+
+/* Nearest FP8 E4M3 value to the integer x (|x| <= 448), ties to the even
+ * mantissa.  E4M3 holds every integer below 16; from 2^p (p >= 4) up to
+ * 2^(p+1) its values are 2^(p-3) apart.  The result is an integer. */
+static int32_t e4m3_round(int32_t x) {
+  const int32_t a = x < 0 ? -x : x;
+  if (a < 16) return x;
+  int32_t p = 4;
+  while (a >= (1 << (p + 1))) ++p;
+  const int32_t step = 1 << (p - 3);
+  int32_t n = a / step, rem = a % step;
+  if (2 * rem > step || (2 * rem == step && (n & 1))) ++n;
+  const int32_t r = n * step;
+  return x < 0 ? -r : r;
+}
+
+/* coarse(q, r) = ||q'||^2 + ||r'||^2 - 2 q~ . r~  with x' = x - 64 and x~ its
+ * E4M3 rounding. */
+static int64_t coarse(const uint8_t *q, const uint8_t *r) {
+  int64_t nq = 0, nr = 0, dot = 0;
+  for (int t = 0; t < ORACLE_D; ++t) {
+    const int32_t qs = (int32_t)q[t] - ORACLE_SHIFT, rs = (int32_t)r[t] - ORACLE_SHIFT;
+    nq += qs * qs;
+    nr += rs * rs;
+    dot += (int64_t)e4m3_round(qs) * e4m3_round(rs);
+  }
+  return nq + nr - 2 * dot;
+}
+
+/* The kk nearest of q among its coarse shortlist: the m smallest
+ * (coarse, index) pairs over all N references (m >= kk; m > N means all),
+ * reranked by exact (distance, index).  cd, cj: scratch of m entries. */
+static void knn_coarse_one(const uint8_t *ref, int64_t N, const uint8_t *q, int32_t kk, int32_t m,
+                           int64_t *cd, int64_t *cj, int64_t *od, int64_t *oj) {
+  if ((int64_t)m > N) m = (int32_t)N;
+  int32_t len = 0;
+  for (int64_t j = 0; j < N; ++j) {
+    const int64_t c = coarse(q, ref + j * ORACLE_D);
+    if (len == m && !before(c, j, cd[m - 1], cj[m - 1])) continue;
+    int32_t p = (len < m) ? len++ : m - 1;
+    while (p > 0 && before(c, j, cd[p - 1], cj[p - 1])) {
+      cd[p] = cd[p - 1];
+      cj[p] = cj[p - 1];
+      --p;
+    }
+    cd[p] = c;
+    cj[p] = j;
+  }
+  /* rerank: exact distance of each candidate, keep the kk smallest */
+  int32_t n = 0;
+  for (int32_t a = 0; a < m; ++a) {
+    const int64_t j = cj[a], d = sqdist(q, ref + j * ORACLE_D);
+    if (n == kk && !before(d, j, od[kk - 1], oj[kk - 1])) continue;
+    int32_t p = (n < kk) ? n++ : kk - 1;
+    while (p > 0 && before(d, j, od[p - 1], oj[p - 1])) {
+      od[p] = od[p - 1];
+      oj[p] = oj[p - 1];
+      --p;
+    }
+    od[p] = d;
+    oj[p] = j;
   }
 }
 
@@ -163,7 +245,7 @@ static int check_offsets(const int64_t *offsets, int64_t n_img, int64_t M) {
 
 /* -------------------------------------------------------------- threading */
 
-enum { JOB_KNN, JOB_CLASS_MIN, JOB_LNBNN, JOB_CLOSED, JOB_NBNN };
+enum { JOB_KNN, JOB_CLASS_MIN, JOB_LNBNN, JOB_CLOSED, JOB_NBNN, JOB_KNN_COARSE, JOB_LNBNN_COARSE };
 
 typedef struct {
   int kind;
@@ -174,6 +256,7 @@ typedef struct {
   const uint8_t *q;
   int64_t M;
   int32_t k;             /* kk for JOB_KNN, k for the classifiers */
+  int32_t m;             /* shortlist length of the coarse jobs */
   const int64_t *img_of; /* descriptor -> image, classifiers only */
   int64_t n_img;
   int64_t *out_d;        /* JOB_KNN [M*kk]; JOB_CLASS_MIN [M*C] */
@@ -194,7 +277,13 @@ static void *worker(void *arg) {
   job_t *J = w->job;
   const int64_t chunk = 4;
   int64_t *s1 = NULL, *s2 = NULL;
-  if (J->kind == JOB_LNBNN) {
+  int64_t *s3 = NULL, *s4 = NULL;
+  if (J->kind == JOB_KNN_COARSE || J->kind == JOB_LNBNN_COARSE) {
+    s3 = (int64_t *)malloc(sizeof(int64_t) * (size_t)J->m);
+    s4 = (int64_t *)malloc(sizeof(int64_t) * (size_t)J->m);
+    if (!s3 || !s4) goto oom;
+  }
+  if (J->kind == JOB_LNBNN || J->kind == JOB_LNBNN_COARSE) {
     s1 = (int64_t *)malloc(sizeof(int64_t) * (size_t)(J->k + 1));
     s2 = (int64_t *)malloc(sizeof(int64_t) * (size_t)(J->k + 1));
   } else if (J->kind == JOB_CLOSED) {
@@ -203,7 +292,7 @@ static void *worker(void *arg) {
   } else if (J->kind == JOB_NBNN) {
     s1 = (int64_t *)malloc(sizeof(int64_t) * (size_t)J->C);
   }
-  if ((J->kind == JOB_LNBNN || J->kind == JOB_CLOSED) && (!s1 || !s2)) goto oom;
+  if ((J->kind == JOB_LNBNN || J->kind == JOB_CLOSED || J->kind == JOB_LNBNN_COARSE) && (!s1 || !s2)) goto oom;
   if (J->kind == JOB_NBNN && !s1) goto oom;
   int64_t *mine = J->partial ? J->partial + (size_t)w->tid * (size_t)(J->n_img * J->C) : NULL;
   for (;;) {
@@ -226,6 +315,13 @@ static void *worker(void *arg) {
           closed_form_one(J->ref, J->labels, J->N, J->C, qi, J->k, s1, s2,
                           mine + J->img_of[i] * J->C);
           break;
+        case JOB_KNN_COARSE:
+          knn_coarse_one(J->ref, J->N, qi, J->k, J->m, s3, s4, J->out_d + i * J->k, J->out_j + i * J->k);
+          break;
+        case JOB_LNBNN_COARSE:
+          knn_coarse_one(J->ref, J->N, qi, J->k + 1, J->m, s3, s4, s1, s2);
+          score_one(J->labels, J->k, s1, s2, mine + J->img_of[i] * J->C);
+          break;
         case JOB_NBNN: {
           /* Alg. 1: totals[C] += ||d_i - NN_C(d_i)||^2 for every class C */
           class_min_one(J->ref, J->labels, J->N, J->C, qi, s1);
@@ -238,10 +334,14 @@ static void *worker(void *arg) {
   }
   free(s1);
   free(s2);
+  free(s3);
+  free(s4);
   return NULL;
 oom:
   free(s1);
   free(s2);
+  free(s3);
+  free(s4);
   __atomic_store_n(&J->status, ORACLE_ERR_NOMEM, __ATOMIC_RELAXED);
   return NULL;
 }
@@ -270,13 +370,14 @@ static int run(job_t *J, int nthreads) {
 /* Classifier driver: per-thread partial totals, summed (integer sums are
  * exact in any order), then the per-image argmin. */
 static int classify(int kind, const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
-                    const uint8_t *q, const int64_t *offsets, int64_t n_img, int32_t k,
+                    const uint8_t *q, const int64_t *offsets, int64_t n_img, int32_t k, int32_t m,
                     int64_t *totals, int32_t *classes, int nthreads) {
   int st = check_ref(N, C, labels);
   if (st) return st;
   const int64_t M = offsets[n_img];
   if ((st = check_offsets(offsets, n_img, M))) return st;
   if (kind != JOB_NBNN && (k < 1 || (int64_t)k + 1 > N)) return ORACLE_ERR_K;
+  if (kind == JOB_LNBNN_COARSE && m < k + 1) return ORACLE_ERR_K;
   if (kind == JOB_NBNN) {
     char *has = (char *)calloc((size_t)C, 1);
     if (!has) return ORACLE_ERR_NOMEM;
@@ -301,6 +402,7 @@ static int classify(int kind, const uint8_t *ref, const int32_t *labels, int64_t
   J.q = q;
   J.M = M;
   J.k = k;
+  J.m = m;
   J.img_of = img_of;
   J.n_img = n_img;
   if (nthreads <= 0) nthreads = (int)sysconf(_SC_NPROCESSORS_ONLN);
@@ -374,19 +476,61 @@ int oracle_class_min(const uint8_t *ref, const int32_t *labels, int64_t N, int32
 int oracle_lnbnn(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
                  const uint8_t *q, const int64_t *offsets, int64_t n_img, int32_t k,
                  int64_t *totals, int32_t *classes, int nthreads) {
-  return classify(JOB_LNBNN, ref, labels, N, C, q, offsets, n_img, k, totals, classes, nthreads);
+  return classify(JOB_LNBNN, ref, labels, N, C, q, offsets, n_img, k, 0, totals, classes, nthreads);
 }
 
 /* Local NBNN totals by the closed form sum_i min(0, NN_C(d_i) - dist_B(d_i)). */
 int oracle_lnbnn_closed_form(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
                              const uint8_t *q, const int64_t *offsets, int64_t n_img, int32_t k,
                              int64_t *totals, int32_t *classes, int nthreads) {
-  return classify(JOB_CLOSED, ref, labels, N, C, q, offsets, n_img, k, totals, classes, nthreads);
+  return classify(JOB_CLOSED, ref, labels, N, C, q, offsets, n_img, k, 0, totals, classes, nthreads);
 }
 
 /* Alg. 1 (original NBNN): totals [n_img*C] int64, classes [n_img] int32. */
 int oracle_nbnn(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
                 const uint8_t *q, const int64_t *offsets, int64_t n_img, int64_t *totals,
                 int32_t *classes, int nthreads) {
-  return classify(JOB_NBNN, ref, labels, N, C, q, offsets, n_img, 0, totals, classes, nthreads);
+  return classify(JOB_NBNN, ref, labels, N, C, q, offsets, n_img, 0, 0, totals, classes, nthreads);
+}
+
+/* E4M3 rounding of each x[i] (|x[i]| <= 448), for the pins. */
+int oracle_e4m3_round(const int32_t *x, int64_t n, int32_t *out) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (x[i] < -448 || x[i] > 448) return ORACLE_ERR_ARG;
+    out[i] = e4m3_round(x[i]);
+  }
+  return ORACLE_OK;
+}
+
+/* Full matrix of coarse values, out[i*N + j] = coarse(q_i, r_j) (tiny inputs). */
+int oracle_coarse_matrix(const uint8_t *ref, int64_t N, const uint8_t *q, int64_t M, int64_t *out) {
+  if (N < 0 || M < 0) return ORACLE_ERR_ARG;
+  for (int64_t i = 0; i < M; ++i)
+    for (int64_t j = 0; j < N; ++j) out[i * N + j] = coarse(q + i * ORACLE_D, ref + j * ORACLE_D);
+  return ORACLE_OK;
+}
+
+/* kk nearest by the coarse shortlist of m and exact rerank: dist/idx [M*kk]. */
+int oracle_knn_coarse(const uint8_t *ref, int64_t N, const uint8_t *q, int64_t M, int32_t kk, int32_t m,
+                      int64_t *dist, int64_t *idx, int nthreads) {
+  if (N < 1 || M < 0 || kk < 1 || (int64_t)kk > N || m < kk) return ORACLE_ERR_K;
+  job_t J;
+  memset(&J, 0, sizeof J);
+  J.kind = JOB_KNN_COARSE;
+  J.ref = ref;
+  J.N = N;
+  J.q = q;
+  J.M = M;
+  J.k = kk;
+  J.m = m;
+  J.out_d = dist;
+  J.out_j = idx;
+  return run(&J, nthreads);
+}
+
+/* Alg. 2 on the neighbours of the coarse shortlist (m >= k + 1). */
+int oracle_lnbnn_coarse(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
+                        const uint8_t *q, const int64_t *offsets, int64_t n_img, int32_t k, int32_t m,
+                        int64_t *totals, int32_t *classes, int nthreads) {
+  return classify(JOB_LNBNN_COARSE, ref, labels, N, C, q, offsets, n_img, k, m, totals, classes, nthreads);
 }

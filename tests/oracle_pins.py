@@ -331,4 +331,113 @@ def pin_nbnn_ties_and_errors(orc):
         raise AssertionError("empty class accepted")
 
 
+# ------------------------------------------------------------ coarse shortlist
+#
+# The coarse-shortlist form is this project's approximate search (shift each
+# coordinate by 64, round to FP8 E4M3, coarse = ||q'||^2 + ||r'||^2 - 2 q~.r~,
+# keep the m smallest, rerank by exact distance).  Its pins: PyTorch's own
+# E4M3 conversion, hand-worked values, the identity coarse == exact distance
+# when no coordinate needs rounding, and the reduction to exact search when
+# the shortlist holds every reference.
+
+def _torch_e4m3(x):
+    import torch
+    t = torch.from_numpy(np.asarray(x, dtype=np.float32)).to(torch.float8_e4m3fn)
+    return t.to(torch.float32).numpy().astype(np.int64)
+
+
+def pin_e4m3_matches_torch(orc):
+    x = np.arange(-448, 449)
+    assert np.array_equal(orc.e4m3_round(x), _torch_e4m3(x))
+
+
+def pin_e4m3_hand_worked(orc):
+    # below 16 every integer is exact; 36 (step 4) exact; 68 is half-way between
+    # 64 and 72 -> even mantissa 64; 76 between 72 and 80 -> 80; 191 -> 192
+    x = np.array([0, 7, 15, -15, 17, 36, 68, 76, 191, -64, -68, 255])
+    assert orc.e4m3_round(x).tolist() == [0, 7, 15, -15, 16, 36, 64, 80, 192, -64, -64, 256]
+
+
+def pin_coarse_hand_worked(orc):
+    """One moving coordinate, all others 64 (shifted to 0):
+    (255, 0): 191^2 + 64^2 - 2 * 192 * (-64) = 65153 (exact 65025);
+    (100, 90): 36 and 26 are exact -> 10^2 = 100;
+    (147, 163): 83 -> 80, 99 -> 96: 83^2 + 99^2 - 2 * 80 * 96 = 1330 (exact 256);
+    (132, 140): 68 -> 64, 76 -> 80: 68^2 + 76^2 - 2 * 64 * 80 = 160 (exact 64)."""
+    def one(v):
+        a = np.full((1, 128), 64, np.uint8)
+        a[0, 0] = v
+        return a
+    got = [int(orc.coarse_matrix(one(b), one(a))[0, 0]) for a, b in [(255, 0), (100, 90), (147, 163), (132, 140)]]
+    assert got == [65153, 100, 1330, 160]
+
+
+def pin_coarse_exact_when_representable(orc):
+    # coordinates in [49, 79]: x - 64 in [-15, 15] needs no rounding, so the
+    # coarse value is ||q' - r'||^2 = ||q - r||^2 exactly
+    rng = np.random.default_rng(30)
+    ref = rng.integers(49, 80, size=(40, 128)).astype(np.uint8)
+    q = rng.integers(49, 80, size=(6, 128)).astype(np.uint8)
+    assert np.array_equal(orc.coarse_matrix(ref, q), _cd(q, ref))
+
+
+def pin_knn_coarse_full_shortlist_is_exact(orc):
+    rng = np.random.default_rng(31)
+    ref = _u8(rng, 50, hi=6)  # few values: many ties
+    q = _u8(rng, 7, hi=6)
+    d = _cd(q, ref)
+    for kk in (1, 5, 50):
+        od, oj = orc.knn_coarse(ref, q, kk, 50)
+        for i in range(len(q)):
+            order = np.lexsort((np.arange(50), d[i]))[:kk]
+            assert oj[i].tolist() == order.tolist() and od[i].tolist() == d[i][order].tolist()
+        od2, oj2 = orc.knn_coarse(ref, q, kk, 500)  # m > N: still all of them
+        assert np.array_equal(oj2, oj)
+
+
+def pin_knn_coarse_brute_force(orc):
+    """Shortlist by sorting the whole coarse matrix (coordinates rounded by
+    PyTorch), rerank by scipy distances, on 60 references."""
+    rng = np.random.default_rng(32)
+    ref = _u8(rng, 60)
+    q = _u8(rng, 8)
+    qs = _torch_e4m3(q.astype(np.int64) - 64)
+    rs = _torch_e4m3(ref.astype(np.int64) - 64)
+    cz = ((q.astype(np.int64) - 64) ** 2).sum(1)[:, None] + ((ref.astype(np.int64) - 64) ** 2).sum(1)[None, :] \
+        - 2 * qs @ rs.T
+    d = _cd(q, ref)
+    for kk, m in ((3, 3), (4, 9), (10, 20)):
+        od, oj = orc.knn_coarse(ref, q, kk, m)
+        for i in range(len(q)):
+            short = np.lexsort((np.arange(60), cz[i]))[:m]
+            best = short[np.lexsort((short, d[i][short]))][:kk]
+            assert oj[i].tolist() == best.tolist() and od[i].tolist() == d[i][best].tolist()
+
+
+def pin_lnbnn_coarse_full_shortlist_is_exact(orc):
+    ref, lab, q, off = _small_case(33, N=45, C=4, n_img=3, per_img=6)
+    for k in (1, 4, 44):
+        t, c = orc.local_nbnn_coarse(ref, lab, 4, q, off, k, 45)
+        assert np.array_equal(t, _numpy_closed_form(ref, lab, 4, q, off, k))
+        assert c.tolist() == [int(np.argmin(r)) for r in t]
+
+
+def pin_lnbnn_coarse_short_list(orc):
+    """With a short list the neighbours are the exact nearest of the shortlist:
+    totals follow Alg. 2 on them (hand-check through knn_coarse)."""
+    ref, lab, q, off = _small_case(34, N=80, C=5, n_img=2, per_img=5)
+    k, m = 3, 6
+    t, _ = orc.local_nbnn_coarse(ref, lab, 5, q, off, k, m)
+    nd, nj = orc.knn_coarse(ref, q, k + 1, m)
+    want = np.zeros_like(t)
+    for i in range(2):
+        for row in range(off[i], off[i + 1]):
+            for c in set(lab[nj[row][:k]].tolist()):
+                want[i, c] += min(int(nd[row][a]) for a in range(k) if lab[nj[row][a]] == c) - int(nd[row][k])
+    assert np.array_equal(t, want)
+    # the reranked distances are the exact distances of the returned rows
+    d = _cd(q, ref)
+    assert np.array_equal(nd, np.take_along_axis(d, nj, axis=1))
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

@@ -30,6 +30,16 @@ MUTANTS = [
     ("insertion drops the wrong slot", "int32_t p = (len < kk) ? len++ : kk - 1;",
      "int32_t p = (len < kk) ? len++ : (kk > 1 ? kk - 2 : 0);"),
     ("closed form uses the k-th value", "const int64_t dist_B = all[k];", "const int64_t dist_B = all[k - 1];"),
+    ("coarse: no shift", "#define ORACLE_SHIFT 64", "#define ORACLE_SHIFT 0"),
+    ("E4M3: ties away from zero", "if (2 * rem > step || (2 * rem == step && (n & 1))) ++n;",
+     "if (2 * rem >= step) ++n;"),
+    ("E4M3: one mantissa bit short", "const int32_t step = 1 << (p - 3);", "const int32_t step = 1 << (p - 2);"),
+    ("coarse: dropped reference norm", "nr += rs * rs;", "nr += 0;"),
+    ("coarse: cross term not doubled", "return nq + nr - 2 * dot;", "return nq + nr - dot;"),
+    ("coarse: no rerank", "const int64_t j = cj[a], d = sqdist(q, ref + j * ORACLE_D);",
+     "const int64_t j = cj[a], d = cd[a];"),
+    ("coarse: shortlist by exact distance", "const int64_t c = coarse(q, ref + j * ORACLE_D);",
+     "const int64_t c = sqdist(q, ref + j * ORACLE_D);"),
 ]
 
 
