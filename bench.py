@@ -52,6 +52,10 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--shortlist", type=int, default=None,
+                   help="time the FP8 E4M3 shortlist search (shortlist length m) instead of the exact one")
+    p.add_argument("--fp8-shortlist", type=int, default=32,
+                   help="shortlist of the FP8 block and FP8 serving runs reported beside the exact form (0: skip)")
     p.add_argument("--serve-rates", default="100,300,1000",
                    help="Poisson arrival rates (images/s) of the serving runs; empty to skip them")
     p.add_argument("--serve-seconds", type=float, default=2.5, help="arrival window of each serving run")
@@ -234,12 +238,12 @@ def run_reference(args, w):
 
 def run_ours(args, w):
     import torch
-    world, rank, local = dist_init()
+    world, rank, local_rank = dist_init()
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
+        torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    dev = torch.device("cuda", local_rank if world > 1 else torch.cuda.current_device())
     from paper_1112_0059_gb300 import lnbnn
     lnbnn.load_library()
 
@@ -247,23 +251,30 @@ def run_ours(args, w):
     q, off, _ = synth.query_set(w)
     M, n_img = int(q.shape[0]), int(off.shape[0] - 1)
     k = args.k
+    local = args.method == "local"
+    shortlist = args.shortlist if local else None  # the timed form: exact, or the FP8 shortlist search
+    fp8_m = args.fp8_shortlist if local and not shortlist else 0  # FP8 form reported beside the exact one
     ref_d = torch.from_numpy(ref).to(dev)
     lab_d = torch.from_numpy(labels).to(dev)
     q_d = torch.from_numpy(q).to(dev)
     off_d = torch.from_numpy(off).to(dev)
     index = lnbnn.Index(ref_d, lab_d, w.n_classes)
     del ref_d, lab_d
+    if shortlist or fp8_m:
+        index.prepare_fp8()
     totals = torch.empty((n_img, w.n_classes), dtype=torch.int64, device=dev)
     classes = torch.empty((n_img,), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    local = args.method == "local"
 
-    def step():
-        if local:
-            index.lnbnn_classify(q_d, off_d, k, out=(totals, classes))
-        else:
-            index.nbnn_classify(q_d, off_d, out=(totals, classes))
+    def make_step(m_short, out):
+        def step():
+            if local:
+                index.lnbnn_classify(q_d, off_d, k, out=out, shortlist=m_short)
+            else:
+                index.nbnn_classify(q_d, off_d, out=out)
+        return step
 
+    step = make_step(shortlist, (totals, classes))
     for _ in range(args.warmup):
         step()
     index.sync()
@@ -273,47 +284,46 @@ def run_ours(args, w):
             import torch.distributed as dist
             dist.barrier()
 
+    def max_over_ranks(x):
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([x], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
+    def timed(fn, steps):
+        """Device time of `steps` calls of fn (CUDA events on the launching stream) and the call profile."""
+        index.profile_enable(True)
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        index.sync()
+        prof = index.profile_read()
+        index.profile_enable(False)
+        return max_over_ranks(ev0.elapsed_time(ev1) / 1e3), prof
+
     gpu_uuid = None
     try:
         gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         pass
-    index.profile_enable(True)
-    barrier()
-    torch.cuda.synchronize(dev)
     clocks = ClockSampler(gpu_uuid)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier()
+    elapsed, prof = timed(step, args.steps)
     clk = clocks.stop()
-    index.sync()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    prof = index.profile_read()
-    index.profile_enable(False)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
 
     value = M * args.steps * world / elapsed
     peaks, peak_src = measured_peaks()
-    search_ms = prof["search_ms"] / max(prof["search_launches"], 1)
-    flops = 2.0 * 128 * w.n_ref * M  # algorithmic, per launch
-    achieved = flops / (search_ms / 1e3) / 1e12
-    # both methods run the same tensor-core scan (K = 128 + a 16-wide extension);
-    # the roofline counts the algorithmic 2 * 128 flops per (query, reference) pair
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": float(peaks["bf16_tflops_sustained"]),
-                "unit": "TFLOP/s", "traffic": traffic_per_launch(M) if local else None,
-                "kernel": "tc_scan_kernel<KnnEpilogue<16>>" if local else "tc_scan_kernel<NbnnEpilogue>",
-                "peak_source": f"bf16_tflops_sustained ({peak_src})"}
-    roofline.update({"frac": roofline["achieved"] / roofline["peak"], "flops_per_launch": flops,
-                     "avg_launch_ms": search_ms})
+    roofline = scan_roofline(prof, w.n_ref, M, peaks, peak_src, local, shortlist)
+    if not shortlist:
+        roofline["traffic"] = traffic_per_launch(M) if local else None
 
     e2e = None
     if not args.no_e2e:
@@ -323,48 +333,85 @@ def run_ours(args, w):
         cls_h = torch.empty((n_img,), dtype=torch.int32).pin_memory()
         qn, on, tn, cn = q_h.numpy(), off_h.numpy(), tot_h.numpy(), cls_h.numpy()
         hk = k if local else None
-        index.classify_host(qn, on, hk, tn, cn)  # warm the staging buffer
+        index.classify_host(qn, on, hk, tn, cn, shortlist=shortlist)  # warm the staging buffer
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            index.classify_host(qn, on, hk, tn, cn)
-        e2e_dt = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_dt = float(t.item())
+            index.classify_host(qn, on, hk, tn, cn, shortlist=shortlist)
+        e2e_dt = max_over_ranks(time.perf_counter() - t0)
+        api = "lnbnn_classify_fp8_host" if shortlist else ("lnbnn" if local else "nbnn") + "_classify_host"
         e2e = {"value": M * args.steps * world / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(q.nbytes + off.nbytes),
                "d2h_bytes_per_step": int(tn.nbytes + cn.nbytes),
-               "api": ("lnbnn" if local else "nbnn") + "_classify_host (pinned host buffers; copies, classify, "
-                      "copy-back, sync per step)"}
+               "api": api + " (pinned host buffers; copies, classify, copy-back, sync per step)"}
+
+    # accuracy of the FP8 form against the exact search (parity-tested against the oracle)
+    fp8_block = None
+    if local and (shortlist or fp8_m):
+        m_short = shortlist or fp8_m
+        t_x = torch.empty_like(totals)
+        c_x = torch.empty_like(classes)
+        t_f = torch.empty_like(totals)
+        c_f = torch.empty_like(classes)
+        make_step(None, (t_x, c_x))()
+        fp8_step = make_step(m_short, (t_f, c_f))
+        if shortlist:
+            fp8_step()
+            fp8_block = {"shortlist": m_short}
+        else:
+            for _ in range(args.warmup):
+                fp8_step()
+            el8, prof8 = timed(fp8_step, args.steps)
+            fp8_block = {"shortlist": m_short, "value": M * args.steps * world / el8, "unit": UNIT,
+                         "images_per_s": n_img * args.steps * world / el8, "ms_per_step": el8 / args.steps * 1e3,
+                         "roofline": scan_roofline(prof8, w.n_ref, M, peaks, peak_src, True, m_short),
+                         "gpu_launches": int(prof8["kernel_launches"])}
+        index.sync()
+        sample = min(M, 8192)
+        i_x, _ = index.knn_search(q_d[:sample], k + 1)
+        i_f, _ = index.knn_search(q_d[:sample], k + 1, shortlist=m_short)
+        index.sync()
+        ix_, if_ = i_x.cpu().numpy(), i_f.cpu().numpy()
+        recall = float(np.mean([len(set(ix_[r]) & set(if_[r])) for r in range(sample)]) / (k + 1))
+        tx, tf = t_x.cpu().numpy(), t_f.cpu().numpy()
+        fp8_block.update({
+            "knn_recall": recall, "recall_sample": f"first {sample} query descriptors, the k+1 = {k + 1} neighbours",
+            "class_agreement": float((c_x.cpu().numpy() == c_f.cpu().numpy()).mean()),
+            "score_rel_error": float(np.abs(tf - tx).sum() / max(1, np.abs(tx).sum())),
+            "score_max_abs_error": int(np.abs(tf - tx).max()),
+            "reference": "the exact tensor-core search (bit-exact with the oracle in the parity tests)"})
 
     serve_block = None
     rates = [float(r) for r in args.serve_rates.split(",") if r.strip()]
-    if rates and args.method == "local" and w.n_classes == synth.workload("serving").n_classes:
-        serve_block = run_serving(index, rates, args.serve_seconds, k)
+    if rates and local and w.n_classes == synth.workload("serving").n_classes:
+        serve_block = {"exact": run_serving(index, rates, args.serve_seconds, k, None)}
+        if fp8_m or shortlist:
+            serve_block["fp8"] = run_serving(index, rates, args.serve_seconds, k, shortlist or fp8_m)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(args.method, ref, labels, w.n_classes, q, k, args.cpu_seconds, int(off[1]))
 
     if rank == 0:
+        cfg = workload_config(w, k, args.method)
+        if shortlist:
+            cfg["method"] = f"Local NBNN (Alg. 2), FP8 E4M3 shortlist search (m = {shortlist}) + exact rerank"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": workload_config(w, k, args.method),
+            "scaling": "weak", "vs_baseline": None, "dtype": "e4m3" if shortlist else "bf16", "data": "synthetic",
+            "config": cfg,
             "images_per_s": n_img * args.steps * world / elapsed,
             "roofline": roofline,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "fp8": fp8_block,
             "serve": serve_block,
             "gpu_launches": int(prof["kernel_launches"]),
             "clocks": clk,
             "profile": {"search_ms_total": prof["search_ms"], "other_ms_total": prof["other_ms"],
                         "calls": prof["calls"], "search_sm_clock_ghz": prof["search_sm_clock_ghz"],
                         "search_cycles_per_tile": prof["search_cycles_per_tile"],
-                        "mma_cycles_per_tile": 9 * 128},
+                        "mma_cycles_per_tile": 5 * 128 if shortlist else 9 * 128},
         }
         print(json.dumps(line), flush=True)
     index.close()
@@ -373,14 +420,34 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
-def run_serving(index, rates, seconds, k) -> dict:
+def scan_roofline(prof, n_ref, M, peaks, peak_src, local, shortlist) -> dict:
+    """Roofline of the search kernel from the call profile: algorithmic
+    2 * 128 flops per (query, reference) pair over its mean launch time."""
+    search_ms = prof["search_ms"] / max(prof["search_launches"], 1)
+    flops = 2.0 * 128 * n_ref * M
+    achieved = flops / (search_ms / 1e3) / 1e12
+    if shortlist:
+        # E4M3 contraction: twice the BF16 rate (nominal dense 4.5 vs 2.25 PFLOP/s)
+        peak = 2.0 * float(peaks["bf16_tflops_sustained"])
+        src = f"2 x bf16_tflops_sustained ({peak_src}), the nominal fp8/bf16 ratio"
+        kernel = "tc_scan_kernel<FmtE4m3, KnnEpilogue<%d>>" % (16 if shortlist <= 16 else 32 if shortlist <= 32 else 0)
+    else:
+        peak = float(peaks["bf16_tflops_sustained"])
+        src = f"bf16_tflops_sustained ({peak_src})"
+        kernel = "tc_scan_kernel<FmtBf16, KnnEpilogue<16>>" if local else "tc_scan_kernel<FmtBf16, NbnnEpilogue>"
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": kernel, "peak_source": src, "flops_per_launch": flops,
+            "avg_launch_ms": search_ms}
+
+
+def run_serving(index, rates, seconds, k, shortlist) -> dict:
     """The continuous-batching server over the resident index: Poisson
     arrivals of query images with log-uniform [100, 4000] descriptors."""
     from paper_1112_0059_gb300 import serve
     w = synth.workload("serving")
     cfg = {"slots": 3, "max_batch_queries": 16384, "max_batch_images": 256, "graphs": True, "graph_granule": 2048}
     runs, first = [], 0
-    with serve.Server(index, k=k, method="local", **cfg) as srv:
+    with serve.Server(index, k=k, method="local", shortlist=shortlist, **cfg) as srv:
         srv.run(serve.poisson_requests(w, 1000.0, 8, seed=99, first_image=100000))  # warm-up
         for rate in rates:
             n = max(8, int(rate * seconds))
@@ -391,7 +458,8 @@ def run_serving(index, rates, seconds, k) -> dict:
             st = serve.latency_stats(done, srv.log)
             st["rate_offered"] = rate
             runs.append(st)
-    return {"form": "exact", "k": k, "workload": "256-class index; Poisson arrivals; log-uniform [100, 4000] "
+    form = "exact" if shortlist is None else f"FP8 E4M3 shortlist m = {shortlist} + exact rerank"
+    return {"form": form, "k": k, "workload": "256-class index; Poisson arrivals; log-uniform [100, 4000] "
             "descriptors per image; latency = arrival to totals and class on the host", **cfg, "runs": runs}
 
 

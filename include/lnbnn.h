@@ -58,7 +58,8 @@ typedef enum lnbnn_status {
   LNBNN_ERR_TIMEOUT = 7,      /* a bounded device wait expired */
   LNBNN_ERR_UNSUPPORTED = 8,  /* device is not compute capability 10.3 (sm_103) */
   LNBNN_ERR_OFFSETS = 9,      /* offsets not 0 = o[0] <= ... <= o[n_images] = n_queries */
-  LNBNN_ERR_SCRATCH_LIMIT = 10 /* problem larger than a workspace or the scratch of knn_search_noalloc */
+  LNBNN_ERR_SCRATCH_LIMIT = 10, /* problem larger than a workspace or the scratch of knn_search_noalloc */
+  LNBNN_ERR_NO_FP8 = 11         /* an FP8 call on an index without lnbnn_index_prepare_fp8 */
 } lnbnn_status;
 
 /*
@@ -162,7 +163,46 @@ LNBNN_API lnbnn_status nbnn_classify_ws(lnbnn_index *index, lnbnn_workspace *wor
                                         int64_t *totals, int32_t *classes, void *stream);
 
 /*
- * Host-buffer forms of the two classifiers: queries, offsets, totals and
+ * FP8 shortlist search: an approximate search of this library's own design,
+ * in the place the paper fills with an approximate kd-tree search (Section
+ * 5, "Approximate nearest neighbors"); the paper has no FP8 step.  A coarse
+ * tensor-core pass over FP8 E4M3 operands ranks every reference by
+ *     coarse(q, r) = ||q'||^2 + ||r'||^2 - 2 E4M3(q') . E4M3(r'),
+ * x' = x - 64 per coordinate, E4M3 = round to nearest even on 3 mantissa bits;
+ * the `shortlist` smallest (coarse, row) pairs are then reranked by their
+ * exact squared distance, and the k (knn) or k + 1 (classify) smallest exact
+ * (distance, row) pairs of the shortlist are the neighbours.  Distances and
+ * totals are therefore exact for the neighbours found; a true neighbour
+ * outside the shortlist is missed (recall < 1).  With shortlist >= n_ref the
+ * result equals the exact search.  The result of a query does not depend on
+ * the other queries of the call.
+ *
+ * lnbnn_index_prepare_fp8 builds the E4M3 operand once (about 160 bytes per
+ * reference) and synchronises `stream`; until then the FP8 calls return
+ * NO_FP8.  Repeated calls are no-ops.
+ *
+ *   shortlist   knn: k <= shortlist; classify: k + 1 <= shortlist; at most
+ *               LNBNN_MAX_K + 1 (K_RANGE otherwise)
+ * Other arguments, outputs and errors as knn_search / lnbnn_classify.  A
+ * workspace serves an FP8 call when max_queries >= n_queries and
+ * max_k + 1 >= shortlist.
+ */
+LNBNN_API lnbnn_status lnbnn_index_prepare_fp8(lnbnn_index *index, void *stream);
+LNBNN_API lnbnn_status knn_search_fp8(lnbnn_index *index, const uint8_t *queries, int64_t n_queries, int32_t k,
+                                      int32_t shortlist, int32_t *idx, int32_t *dist, void *stream);
+LNBNN_API lnbnn_status lnbnn_classify_fp8(lnbnn_index *index, const uint8_t *queries, int64_t n_queries,
+                                          const int64_t *offsets, int64_t n_images, int32_t k, int32_t shortlist,
+                                          int64_t *totals, int32_t *classes, void *stream);
+LNBNN_API lnbnn_status knn_search_fp8_ws(lnbnn_index *index, lnbnn_workspace *workspace, const uint8_t *queries,
+                                         int64_t n_queries, int32_t k, int32_t shortlist, int32_t *idx,
+                                         int32_t *dist, void *stream);
+LNBNN_API lnbnn_status lnbnn_classify_fp8_ws(lnbnn_index *index, lnbnn_workspace *workspace,
+                                             const uint8_t *queries, int64_t n_queries, const int64_t *offsets,
+                                             int64_t n_images, int32_t k, int32_t shortlist, int64_t *totals,
+                                             int32_t *classes, void *stream);
+
+/*
+ * Host-buffer forms of the classifiers: queries, offsets, totals and
  * classes are HOST pointers.  The call copies the inputs to the device
  * (into the index's device staging buffer), classifies, copies the
  * results back and synchronises `stream` before returning.  Pinned (page-locked)
@@ -174,6 +214,9 @@ LNBNN_API lnbnn_status lnbnn_classify_host(lnbnn_index *index, const uint8_t *qu
 LNBNN_API lnbnn_status nbnn_classify_host(lnbnn_index *index, const uint8_t *queries, int64_t n_queries,
                                 const int64_t *offsets, int64_t n_images, int64_t *totals,
                                 int32_t *classes, void *stream);
+LNBNN_API lnbnn_status lnbnn_classify_fp8_host(lnbnn_index *index, const uint8_t *queries, int64_t n_queries,
+                                               const int64_t *offsets, int64_t n_images, int32_t k,
+                                               int32_t shortlist, int64_t *totals, int32_t *classes, void *stream);
 
 /*
  * Wait for `stream`, then report (and clear) any device-side error recorded

@@ -30,6 +30,10 @@ constexpr int kQueryPad = 128;
 // MMA K-step of 16 BF16 columns.  All these values are exact in BF16.
 constexpr int kExt = 16;
 
+// Added to every coarse value of the FP8 shortlist search so that it stays
+// positive (float bit patterns then order like the values).
+constexpr int32_t kCoarseBias = 1 << 21;
+
 // Bits of the per-index device error word.
 enum : uint32_t { kDevErrTimeout = 1u, kDevErrOffsets = 2u };
 
@@ -83,6 +87,18 @@ cudaError_t launch_nbnn_sum(const int32_t* mins, int64_t m, int32_t C, const int
 // Offsets validation (0 = o[0] <= ... <= o[n_img] = m); flags kDevErrOffsets.
 cudaError_t launch_check_offsets(const int64_t* offsets, int64_t n_img, int64_t m, uint32_t* dev_err,
                                  cudaStream_t s);
+// FP8 shortlist search: E4M3 operands of the coarse pass (see coarse.cu).
+// ref_f8 [n_pad, 128] bytes of E4M3(r - 64), ref_ext [n_pad, kExt] digits of
+// ||r - 64||^2; qf8 [m_pad, 128] bytes of -2 E4M3(q - 64), qext [m_pad, kExt]
+// digits of ||q - 64||^2 + kCoarseBias.
+cudaError_t launch_prep_ref_e4m3(const uint8_t* ref, int64_t n_ref, int64_t n_pad, uint8_t* ref_f8,
+                                 __nv_bfloat16* ref_ext, cudaStream_t s);
+cudaError_t launch_prep_query_e4m3(const uint8_t* q, int64_t m, int64_t m_pad, uint8_t* qf8, __nv_bfloat16* qext,
+                                   cudaStream_t s);
+// Exact rerank: for each query row, the K1 smallest exact (distance, row) keys
+// among the rows of its shortlist [m, M1] (kEmptyKey entries are no row).
+cudaError_t launch_rerank(const uint64_t* shortlist, int64_t m, int M1, const uint8_t* q, const uint8_t* ref,
+                          int64_t n_ref, int K1, uint64_t* out, cudaStream_t s);
 // argmin over classes per image, lowest class on ties.
 cudaError_t launch_argmin(const int64_t* totals, int64_t n_img, int32_t C, int32_t* classes, cudaStream_t s);
 

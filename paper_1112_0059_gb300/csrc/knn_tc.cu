@@ -21,6 +21,17 @@
 // for the slowest; measured on the 256-class workload, single CTAs were ~5%
 // faster, so kTcCluster is 1.
 //
+// The same scan runs the coarse pass of the FP8 shortlist search: operands
+// are the E4M3 roundings of the coordinates shifted by -64 (queries scaled by
+// -2, exact in E4M3), one 128-byte K-chunk per tile and four kind::f8f6f4
+// MMAs (K = 32 each), and the K-extension carries ||q'||^2 + 2^21 and ||r'||^2
+// of the shifted (unrounded) coordinates.  The accumulator then holds
+//     coarse = ||q'||^2 + ||r'||^2 - 2 q~ . r~ + 2^21,
+// an integer: the bias keeps it positive (E4M3 rounding is within 2^-4 of
+// each coordinate, so 2 q~.r~ is within 2 * 0.129 * 128 * 191^2 < 1.21e6 of
+// 2 q'.r'), and with the extension issued first every partial sum stays in
+// [0, 2^24), so FP32 holds it exactly.
+//
 // Roles (one CTA = 128 query rows x one reference split):
 //   warp 0, one thread : TMA producer (query tile once; reference K-chunks
 //                        into a 4-stage ring, the K-extension riding with the
@@ -49,9 +60,9 @@ using namespace sm103;
 constexpr int kBM = kTcQueryTile;         // query rows per CTA (MMA M)
 constexpr int kCluster = kTcCluster;      // CTAs sharing each reference tile by multicast
 constexpr int kBN = kTcRefTile;           // reference rows per tile (MMA N)
-constexpr int kBK = 64;                   // K elements per 128-byte swizzle row
-constexpr int kKChunks = kDim / kBK;      // 2
-constexpr int kUmmaK = 16;                // K per tcgen05.mma (kind::f16)
+constexpr int kBK = 64;                   // BF16 K elements per 128-byte swizzle row
+constexpr int kKChunks = kDim / kBK;      // K-chunks of the BF16 operand (shared memory is laid out for these)
+constexpr int kMmaPerChunk = 4;           // 32-byte K-steps per 128-byte chunk (16 BF16 or 32 E4M3)
 constexpr int kStages = 4;                // reference ring depth (K-chunks)
 constexpr uint32_t kAChunkBytes = kBM * kBK * 2;     // 16 KB
 constexpr uint32_t kAExtBytes = kBM * kExt * 2;      // 4 KB
@@ -80,6 +91,25 @@ constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;  // + alignment slack
 static_assert(kStages % kKChunks == 0, "a tile's chunks map to fixed stage parities");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
+
+// Operand formats.  Either way one K-chunk is one 128-byte (swizzled) row
+// per operand row and one MMA consumes 32 bytes of it.
+struct FmtBf16 {  // exact search: 128 BF16 coordinates, two chunks
+  static constexpr int kChunks = 2;
+  static constexpr bool kExtFirst = false;
+  static constexpr uint32_t kIdesc = idesc_bf16_f32(kBM, kBN);
+  static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    mma_bf16(d, a, b, kIdesc, acc);
+  }
+};
+struct FmtE4m3 {  // coarse pass: 128 E4M3 coordinates, one chunk
+  static constexpr int kChunks = 1;
+  static constexpr bool kExtFirst = true;
+  static constexpr uint32_t kIdesc = idesc_e4m3_f32(kBM, kBN);
+  static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    mma_f8(d, a, b, kIdesc, acc);
+  }
+};
 
 struct Bars {
   uint32_t base;
@@ -312,12 +342,14 @@ struct NbnnEpilogue {
   __device__ __forceinline__ void finish() { flush(); }
 };
 
-template <class Epilogue>
+template <class Fmt, class Epilogue>
 __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
     tc_scan_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_qe,
                    const __grid_constant__ CUtensorMap tmap_r, const __grid_constant__ CUtensorMap tmap_re, int64_t m,
                    int64_t n_ref, int64_t split_len, ScanOut out, uint32_t* __restrict__ dev_err,
                    unsigned long long* __restrict__ stats) {
+  constexpr int KC = Fmt::kChunks;
+  static_assert(KC <= kKChunks && kStages % KC == 0, "a tile's chunks map to fixed stage parities");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
@@ -364,14 +396,14 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
       prefetch_tmap(&tmap_qe);
       prefetch_tmap(&tmap_r);
       prefetch_tmap(&tmap_re);
-      mbar_arrive_expect_tx(bars.afull(), kKChunks * kAChunkBytes + kAExtBytes);
-      for (int kc = 0; kc < kKChunks; ++kc)
+      mbar_arrive_expect_tx(bars.afull(), KC * kAChunkBytes + kAExtBytes);
+      for (int kc = 0; kc < KC; ++kc)
         tma_load_2d(sbase + kOffA + kc * kAChunkBytes, &tmap_q, kc * kBK, (int32_t)m0, bars.afull());
       tma_load_2d(sbase + kOffAExt, &tmap_qe, 0, (int32_t)m0, bars.afull());
       int it = 0;
       for (int t = 0; t < ntiles && !*abort_flag; ++t) {
         const int32_t row = (int32_t)(j_begin + (int64_t)t * kBN);
-        for (int kc = 0; kc < kKChunks; ++kc, ++it) {
+        for (int kc = 0; kc < KC; ++kc, ++it) {
           const int s = it % kStages;
           const uint32_t round = (uint32_t)(it / kStages);
           if (!mbar_wait(bars.empty(s), (round & 1u) ^ 1u, kWaitLimitNs, abort_flag)) {
@@ -379,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
             break;
           }
           const uint32_t dst = sbase + kOffB + s * kStageBytes;
-          const bool last = kc == kKChunks - 1;
+          const bool last = kc == KC - 1;
           // the whole chunk lands here: this CTA's half and the partner's
           mbar_arrive_expect_tx(bars.full(s), kBChunkBytes + (last ? kBExtBytes : 0u));
           if constexpr (kCluster == 1) {
@@ -405,7 +437,6 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------------------------------------------------- MMA issuer
-      constexpr uint32_t idesc = idesc_bf16_f32(kBM, kBN);
       const long long clk0 = clock64();
       const uint64_t ns0 = globaltimer_ns();
       bool ok = mbar_wait(bars.afull(), 0, kWaitLimitNs, abort_flag);
@@ -421,7 +452,7 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
         }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + b * kAccCols;
-        for (int kc = 0; kc < kKChunks; ++kc, ++it) {
+        for (int kc = 0; kc < KC; ++kc, ++it) {
           const int s = it % kStages;
           const uint32_t round = (uint32_t)(it / kStages);
           if (!mbar_wait(bars.full(s), round & 1u, kWaitLimitNs, abort_flag)) {
@@ -432,13 +463,18 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
           tc_fence_after();
           const uint32_t a_base = sbase + kOffA + kc * kAChunkBytes;
           const uint32_t b_base = sbase + kOffB + s * kStageBytes;
+          const bool last = kc == KC - 1;  // the norms' K-extension rides with the last chunk
+          if (Fmt::kExtFirst && last)
+            mma_bf16(d_tmem, sw32_kmajor_desc(sbase + kOffAExt), sw32_kmajor_desc(b_base + kBChunkBytes),
+                     FmtBf16::kIdesc, kc != 0 ? 1u : 0u);
 #pragma unroll
-          for (int kk = 0; kk < kBK / kUmmaK; ++kk) {
-            mma_bf16(d_tmem, sw128_kmajor_desc(a_base + kk * 32), sw128_kmajor_desc(b_base + kk * 32), idesc,
-                     (kc | kk) != 0 ? 1u : 0u);
+          for (int kk = 0; kk < kMmaPerChunk; ++kk) {
+            Fmt::mma(d_tmem, sw128_kmajor_desc(a_base + kk * 32), sw128_kmajor_desc(b_base + kk * 32),
+                     (kc | kk) != 0 || (Fmt::kExtFirst && last) ? 1u : 0u);
           }
-          if (kc == kKChunks - 1)  // ||r||^2 through the K-extension
-            mma_bf16(d_tmem, sw32_kmajor_desc(sbase + kOffAExt), sw32_kmajor_desc(b_base + kBChunkBytes), idesc, 1u);
+          if (!Fmt::kExtFirst && last)
+            mma_bf16(d_tmem, sw32_kmajor_desc(sbase + kOffAExt), sw32_kmajor_desc(b_base + kBChunkBytes),
+                     FmtBf16::kIdesc, 1u);
           if constexpr (kCluster == 1) {
             mma_commit(bars.empty(s));
           } else {
@@ -538,6 +574,20 @@ bool encode_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint32_t col
   return r == CUDA_SUCCESS;
 }
 
+// E4M3 bytes [rows, 128] row-major, boxes of 128 x box_rows, 128-byte swizzle.
+bool encode_e4m3(CUtensorMap* map, const void* base, uint64_t rows, uint32_t box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t gdim[2] = {(cuuint64_t)kDim, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)kDim};
+  cuuint32_t box[2] = {(cuuint32_t)kDim, box_rows};
+  cuuint32_t estride[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), gdim, gstride, box, estride,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 // Main operand (128 K-columns, 64-column boxes, 128-byte swizzle) and its
 // 16-column K-extension (32-byte swizzle).
 bool encode_operand(CUtensorMap* main, CUtensorMap* ext, const void* bf, const void* ext_base, uint64_t rows,
@@ -554,34 +604,56 @@ bool make_tc_tensor_maps(const __nv_bfloat16* ref_bf, const __nv_bfloat16* sref_
          encode_operand(&out->sref, &out->sref_ext, sref_bf, sref_ext, (uint64_t)n_pad, kBRowsPerCta);
 }
 
+bool make_tc_tensor_maps_e4m3(const uint8_t* ref_f8, const __nv_bfloat16* ref_f8_ext, int64_t n_pad,
+                              TcTensorMaps* out) {
+  return encode_e4m3(&out->f8, ref_f8, (uint64_t)n_pad, kBRowsPerCta) &&
+         encode_bf16(&out->f8_ext, ref_f8_ext, (uint64_t)n_pad, kExt, kExt, kBRowsPerCta, CU_TENSOR_MAP_SWIZZLE_32B);
+}
+
 namespace {
 
-template <class Epilogue>
-cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const __nv_bfloat16* qbf,
+template <class Fmt, class Epilogue>
+cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const void* qop,
                         const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
                         int64_t split_len, const ScanOut& out, uint32_t* dev_err, unsigned long long* stats,
                         cudaStream_t s) {
   if (m == 0) return cudaSuccess;
   if (m_pad % (kBM * kCluster) != 0 || split_len % kBN != 0) return cudaErrorInvalidValue;
   CUtensorMap tq, tqe;
-  if (!encode_operand(&tq, &tqe, qbf, qext, (uint64_t)m_pad, kBM)) return cudaErrorInvalidValue;
+  const bool ok = Fmt::kChunks == 1
+                      ? encode_e4m3(&tq, qop, (uint64_t)m_pad, kBM) &&
+                            encode_bf16(&tqe, qext, (uint64_t)m_pad, kExt, kExt, kBM, CU_TENSOR_MAP_SWIZZLE_32B)
+                      : encode_operand(&tq, &tqe, qop, qext, (uint64_t)m_pad, kBM);
+  if (!ok) return cudaErrorInvalidValue;
   dim3 grid((unsigned)(m_pad / kBM), (unsigned)splits);
-  tc_scan_kernel<Epilogue><<<grid, kThreads, kSmemBytes, s>>>(tq, tqe, tr, tre, m, n_ref, split_len, out, dev_err,
-                                                              stats);
+  tc_scan_kernel<Fmt, Epilogue><<<grid, kThreads, kSmemBytes, s>>>(tq, tqe, tr, tre, m, n_ref, split_len, out,
+                                                                   dev_err, stats);
   return cudaGetLastError();
+}
+
+// Registers per thread above which the 10 warps of a CTA cannot share one SM
+// (three warps on a sub-partition of 16,384 registers).
+constexpr int kMaxRegs = 168;
+
+template <class Fmt, class Epilogue>
+cudaError_t prepare_one() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, tc_scan_kernel<Fmt, Epilogue>);
+  if (e != cudaSuccess) return e;
+  if (a.numRegs > kMaxRegs) return cudaErrorInvalidKernelImage;
+  return cudaFuncSetAttribute(tc_scan_kernel<Fmt, Epilogue>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kSmemBytes);
 }
 
 }  // namespace
 
 cudaError_t prepare_tc_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(tc_scan_kernel<KnnEpilogue<kTcRegListMax>>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tc_scan_kernel<KnnEpilogue<0>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tc_scan_kernel<NbnnEpilogue>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes);
+  cudaError_t e = prepare_one<FmtBf16, KnnEpilogue<kTcRegListMax>>();
+  if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnEpilogue<0>>();
+  if (e == cudaSuccess) e = prepare_one<FmtBf16, NbnnEpilogue>();
+  if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<kTcRegListMax>>();
+  if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<kTcCoarseRegListMax>>();
+  if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<0>>();
   return e;
 }
 
@@ -596,9 +668,27 @@ cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv
   const CUtensorMap& tr = sorted_copy ? maps.sref : maps.ref;
   const CUtensorMap& tre = sorted_copy ? maps.sref_ext : maps.ref_ext;
   if (K1 <= kTcRegListMax)
-    return launch_scan<KnnEpilogue<kTcRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len, out,
-                                                   dev_err, stats, s);
-  return launch_scan<KnnEpilogue<0>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len, out, dev_err, stats, s);
+    return launch_scan<FmtBf16, KnnEpilogue<kTcRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len,
+                                                            out, dev_err, stats, s);
+  return launch_scan<FmtBf16, KnnEpilogue<0>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len, out, dev_err,
+                                              stats, s);
+}
+
+cudaError_t launch_coarse_tc(const TcTensorMaps& maps, const uint8_t* qf8, const __nv_bfloat16* qext, int64_t m,
+                             int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int K1, uint64_t* lists,
+                             int64_t stride, uint32_t* dev_err, unsigned long long* stats, cudaStream_t s) {
+  ScanOut out{};
+  out.lists = lists;
+  out.stride = stride;
+  out.K1 = K1;
+  if (K1 <= kTcRegListMax)
+    return launch_scan<FmtE4m3, KnnEpilogue<kTcRegListMax>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref, splits,
+                                                            split_len, out, dev_err, stats, s);
+  if (K1 <= kTcCoarseRegListMax)
+    return launch_scan<FmtE4m3, KnnEpilogue<kTcCoarseRegListMax>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref,
+                                                                  splits, split_len, out, dev_err, stats, s);
+  return launch_scan<FmtE4m3, KnnEpilogue<0>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref, splits, split_len,
+                                              out, dev_err, stats, s);
 }
 
 cudaError_t launch_nbnn_tc(const TcTensorMaps& maps, const __nv_bfloat16* qbf, const __nv_bfloat16* qext, int64_t m,
@@ -608,8 +698,8 @@ cudaError_t launch_nbnn_tc(const TcTensorMaps& maps, const __nv_bfloat16* qbf, c
   out.mins = mins;
   out.C = C;
   out.class_off = class_off;
-  return launch_scan<NbnnEpilogue>(maps.sref, maps.sref_ext, qbf, qext, m, m_pad, n_ref, splits, split_len, out,
-                                   dev_err, stats, s);
+  return launch_scan<FmtBf16, NbnnEpilogue>(maps.sref, maps.sref_ext, qbf, qext, m, m_pad, n_ref, splits, split_len,
+                                            out, dev_err, stats, s);
 }
 
 }  // namespace lnbnn

@@ -38,7 +38,11 @@ struct lnbnn_index {
   size_t ws_bytes = 0;
   void* stage = nullptr;  // device staging for the _host calls
   size_t stage_bytes = 0;
-  TcTensorMaps tc;  // tensor maps over ref_bf / sref_bf for the tensor-core kernels
+  // E4M3 operand of the FP8 shortlist search (lnbnn_index_prepare_fp8)
+  uint8_t* ref_f8 = nullptr;             // [n_pad, 128]
+  __nv_bfloat16* ref_f8_ext = nullptr;   // [n_pad, 16]
+  bool fp8 = false;
+  TcTensorMaps tc;  // tensor maps over ref_bf / sref_bf (and ref_f8) for the tensor-core kernels
   // optional device-time profile (lnbnn_profile_enable)
   struct CallEvents {
     cudaEvent_t e[4];
@@ -91,6 +95,8 @@ void free_index(lnbnn_index* ix) {
     cudaFree(ix->srnorm);
     cudaFree(ix->slabels);
   }
+  cudaFree(ix->ref_f8);
+  cudaFree(ix->ref_f8_ext);
   cudaFree(ix->ref_u8);
   cudaFree(ix->ref_bf);
   cudaFree(ix->ref_ext);
@@ -286,6 +292,43 @@ lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_
   return LNBNN_OK;
 }
 
+// The FP8 shortlist search: coarse pass keeping the M1 smallest coarse keys,
+// merge, exact rerank; *lists receives m sorted lists of K1 exact keys.
+lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_t m, int K1, int M1,
+                         cudaStream_t s, const uint64_t** lists, CallProfile& prof) {
+  KnnPlan p = plan_knn(ix, m, M1);
+  char* ws = nullptr;
+  lnbnn_status st = scratch.get(p.bytes, &ws);
+  if (st != LNBNN_OK) return st;
+  // the BF16 query operand's space holds the E4M3 bytes (half its size)
+  uint8_t* qf8 = reinterpret_cast<uint8_t*>(ws + p.off_qbf);
+  __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(ws + p.off_qext);
+  uint64_t* part = reinterpret_cast<uint64_t*>(ws + p.off_lists);
+  uint64_t* merged = reinterpret_cast<uint64_t*>(ws + p.off_merged);
+  CK(launch_prep_query_e4m3(q, m, p.m_pad, qf8, qext, s));
+  prof.launched(1);
+  prof.mark(1);
+  CK(launch_coarse_tc(ix->tc, qf8, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, M1, part, p.m_pad,
+                      ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, s));
+  prof.launched(1, true);
+  prof.mark(2);
+  // lists > 1 always (kTcListsPerSplit > 1): merged is apart from part, which
+  // then receives the reranked lists
+  CK(launch_merge_lists(part, p.lists, m, p.m_pad, M1, merged, s));
+  CK(launch_rerank(merged, m, M1, q, ix->ref_u8, ix->n_ref, K1, part, s));
+  prof.launched(2);
+  *lists = part;
+  return LNBNN_OK;
+}
+
+// Shortlist length of an FP8 call needing K1 neighbours: K1 <= shortlist <=
+// LNBNN_MAX_K + 1; more than n_ref means all references.
+bool shortlist_ok(const lnbnn_index* ix, int32_t shortlist, int K1, int* M1) {
+  if (shortlist < K1 || shortlist > LNBNN_MAX_K + 1) return false;
+  *M1 = (int)std::min<int64_t>(shortlist, ix->n_ref);
+  return true;
+}
+
 bool device_ok(int* sm_count, int* dev) {
   if (cudaGetDevice(dev) != cudaSuccess) return false;
   cudaDeviceProp prop;
@@ -311,6 +354,7 @@ const char* lnbnn_status_string(lnbnn_status st) {
     case LNBNN_ERR_UNSUPPORTED: return "unsupported device (needs compute capability 10.3)";
     case LNBNN_ERR_OFFSETS: return "invalid image offsets";
     case LNBNN_ERR_SCRATCH_LIMIT: return "problem larger than the fixed scratch (workspace or knn_search_noalloc)";
+    case LNBNN_ERR_NO_FP8: return "the index has no FP8 operand (call lnbnn_index_prepare_fp8 first)";
   }
   return "unknown status";
 }
@@ -419,6 +463,19 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
 
 void lnbnn_index_destroy(lnbnn_index* index) { free_index(index); }
 
+lnbnn_status lnbnn_index_prepare_fp8(lnbnn_index* index, void* stream) {
+  if (!index) return LNBNN_ERR_INVALID_ARG;
+  if (index->fp8) return LNBNN_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(dmalloc(&index->ref_f8, (size_t)index->n_pad * kDim));
+  CK(dmalloc(&index->ref_f8_ext, (size_t)index->n_pad * kExt));
+  CK(launch_prep_ref_e4m3(index->ref_u8, index->n_ref, index->n_pad, index->ref_f8, index->ref_f8_ext, s));
+  if (!make_tc_tensor_maps_e4m3(index->ref_f8, index->ref_f8_ext, index->n_pad, &index->tc)) return LNBNN_ERR_CUDA;
+  CK(cudaStreamSynchronize(s));
+  index->fp8 = true;
+  return LNBNN_OK;
+}
+
 lnbnn_status lnbnn_index_info(const lnbnn_index* index, int64_t* n_ref, int32_t* n_classes) {
   if (!index) return LNBNN_ERR_INVALID_ARG;
   if (n_ref) *n_ref = index->n_ref;
@@ -443,11 +500,37 @@ static lnbnn_status do_knn_search(lnbnn_index* index, lnbnn_workspace* w, const 
   return LNBNN_OK;
 }
 
+static lnbnn_status do_knn_search_fp8(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries,
+                                      int64_t n_queries, int32_t k, int32_t shortlist, int32_t* idx, int32_t* dist,
+                                      void* stream) {
+  if (!index || n_queries < 0) return LNBNN_ERR_INVALID_ARG;
+  int M1 = 0;
+  if (!k_ok(index, k, 0) || !shortlist_ok(index, shortlist, k, &M1)) return LNBNN_ERR_K_RANGE;
+  if (!index->fp8) return LNBNN_ERR_NO_FP8;
+  if (n_queries == 0) return LNBNN_OK;
+  if (!queries || !idx || !dist) return LNBNN_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CallProfile prof(index, s);
+  Scratch scratch{index, w};
+  const uint64_t* lists = nullptr;
+  lnbnn_status st = run_knn_fp8(index, scratch, queries, n_queries, k, M1, s, &lists, prof);
+  if (st != LNBNN_OK) return st;
+  CK(launch_extract_knn(lists, n_queries, k, k, idx, dist, s));
+  prof.launched(1);
+  return LNBNN_OK;
+}
+
+// shortlist = 0: exact search; otherwise the FP8 shortlist search.
 static lnbnn_status do_lnbnn_classify(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries,
                                       int64_t n_queries, const int64_t* offsets, int64_t n_images, int32_t k,
-                                      int64_t* totals, int32_t* classes, void* stream) {
+                                      int32_t shortlist, int64_t* totals, int32_t* classes, void* stream) {
   if (!index || n_queries < 0 || n_images < 0) return LNBNN_ERR_INVALID_ARG;
   if (!k_ok(index, k, 1)) return LNBNN_ERR_K_RANGE;
+  int M1 = 0;
+  if (shortlist != 0) {
+    if (!shortlist_ok(index, shortlist, k + 1, &M1)) return LNBNN_ERR_K_RANGE;
+    if (!index->fp8) return LNBNN_ERR_NO_FP8;
+  }
   if (n_images == 0) return n_queries == 0 ? LNBNN_OK : LNBNN_ERR_OFFSETS;
   if (!offsets || !totals || !classes || (n_queries > 0 && !queries)) return LNBNN_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -459,7 +542,8 @@ static lnbnn_status do_lnbnn_classify(lnbnn_index* index, lnbnn_workspace* w, co
   if (n_queries > 0) {
     Scratch scratch{index, w};
     const uint64_t* lists = nullptr;
-    lnbnn_status st = run_knn(index, scratch, queries, n_queries, k + 1, s, &lists, prof);
+    lnbnn_status st = shortlist ? run_knn_fp8(index, scratch, queries, n_queries, k + 1, M1, s, &lists, prof)
+                                : run_knn(index, scratch, queries, n_queries, k + 1, s, &lists, prof);
     if (st != LNBNN_OK) return st;
     CK(launch_lnbnn_score(lists, n_queries, k + 1, k, index->labels, offsets, n_images, C, totals, index->dev_err, s));
     prof.launched(1);
@@ -524,7 +608,20 @@ lnbnn_status knn_search(lnbnn_index* index, const uint8_t* queries, int64_t n_qu
 
 lnbnn_status lnbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
                             int64_t n_images, int32_t k, int64_t* totals, int32_t* classes, void* stream) {
-  return do_lnbnn_classify(index, nullptr, queries, n_queries, offsets, n_images, k, totals, classes, stream);
+  return do_lnbnn_classify(index, nullptr, queries, n_queries, offsets, n_images, k, 0, totals, classes, stream);
+}
+
+lnbnn_status knn_search_fp8(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, int32_t k,
+                            int32_t shortlist, int32_t* idx, int32_t* dist, void* stream) {
+  return do_knn_search_fp8(index, nullptr, queries, n_queries, k, shortlist, idx, dist, stream);
+}
+
+lnbnn_status lnbnn_classify_fp8(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
+                                int64_t n_images, int32_t k, int32_t shortlist, int64_t* totals, int32_t* classes,
+                                void* stream) {
+  if (shortlist == 0) return LNBNN_ERR_K_RANGE;
+  return do_lnbnn_classify(index, nullptr, queries, n_queries, offsets, n_images, k, shortlist, totals, classes,
+                           stream);
 }
 
 lnbnn_status nbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
@@ -566,7 +663,21 @@ lnbnn_status lnbnn_classify_ws(lnbnn_index* index, lnbnn_workspace* w, const uin
                                const int64_t* offsets, int64_t n_images, int32_t k, int64_t* totals, int32_t* classes,
                                void* stream) {
   if (!w || w->index != index) return LNBNN_ERR_INVALID_ARG;
-  return do_lnbnn_classify(index, w, queries, n_queries, offsets, n_images, k, totals, classes, stream);
+  return do_lnbnn_classify(index, w, queries, n_queries, offsets, n_images, k, 0, totals, classes, stream);
+}
+
+lnbnn_status knn_search_fp8_ws(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries, int64_t n_queries,
+                               int32_t k, int32_t shortlist, int32_t* idx, int32_t* dist, void* stream) {
+  if (!w || w->index != index) return LNBNN_ERR_INVALID_ARG;
+  return do_knn_search_fp8(index, w, queries, n_queries, k, shortlist, idx, dist, stream);
+}
+
+lnbnn_status lnbnn_classify_fp8_ws(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries,
+                                   int64_t n_queries, const int64_t* offsets, int64_t n_images, int32_t k,
+                                   int32_t shortlist, int64_t* totals, int32_t* classes, void* stream) {
+  if (!w || w->index != index) return LNBNN_ERR_INVALID_ARG;
+  if (shortlist == 0) return LNBNN_ERR_K_RANGE;
+  return do_lnbnn_classify(index, w, queries, n_queries, offsets, n_images, k, shortlist, totals, classes, stream);
 }
 
 lnbnn_status nbnn_classify_ws(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries, int64_t n_queries,
@@ -577,8 +688,8 @@ lnbnn_status nbnn_classify_ws(lnbnn_index* index, lnbnn_workspace* w, const uint
 }
 
 static lnbnn_status classify_host(lnbnn_index* index, bool local, const uint8_t* queries, int64_t n_queries,
-                                  const int64_t* offsets, int64_t n_images, int32_t k, int64_t* totals,
-                                  int32_t* classes, void* stream) {
+                                  const int64_t* offsets, int64_t n_images, int32_t k, int32_t shortlist,
+                                  int64_t* totals, int32_t* classes, void* stream) {
   if (!index || n_queries < 0 || n_images < 0) return LNBNN_ERR_INVALID_ARG;
   if (n_images == 0) return n_queries == 0 ? LNBNN_OK : LNBNN_ERR_OFFSETS;
   if (!offsets || !totals || !classes || (n_queries > 0 && !queries)) return LNBNN_ERR_INVALID_ARG;
@@ -597,8 +708,9 @@ static lnbnn_status classify_host(lnbnn_index* index, bool local, const uint8_t*
   int32_t* dcls = reinterpret_cast<int32_t*>(b + oc);
   if (n_queries > 0) CK(cudaMemcpyAsync(dq, queries, (size_t)n_queries * kDim, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(doff, offsets, sizeof(int64_t) * (n_images + 1), cudaMemcpyHostToDevice, s));
-  lnbnn_status st = local ? lnbnn_classify(index, dq, n_queries, doff, n_images, k, dtot, dcls, stream)
-                          : nbnn_classify(index, dq, n_queries, doff, n_images, dtot, dcls, stream);
+  lnbnn_status st =
+      local ? do_lnbnn_classify(index, nullptr, dq, n_queries, doff, n_images, k, shortlist, dtot, dcls, stream)
+            : nbnn_classify(index, dq, n_queries, doff, n_images, dtot, dcls, stream);
   if (st != LNBNN_OK) return st;
   CK(cudaMemcpyAsync(totals, dtot, sizeof(int64_t) * (size_t)n_images * C, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(classes, dcls, sizeof(int32_t) * (size_t)n_images, cudaMemcpyDeviceToHost, s));
@@ -608,13 +720,22 @@ static lnbnn_status classify_host(lnbnn_index* index, bool local, const uint8_t*
 lnbnn_status lnbnn_classify_host(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
                                  int64_t n_images, int32_t k, int64_t* totals, int32_t* classes, void* stream) {
   if (index && !k_ok(index, k, 1)) return LNBNN_ERR_K_RANGE;
-  return classify_host(index, true, queries, n_queries, offsets, n_images, k, totals, classes, stream);
+  return classify_host(index, true, queries, n_queries, offsets, n_images, k, 0, totals, classes, stream);
+}
+
+lnbnn_status lnbnn_classify_fp8_host(lnbnn_index* index, const uint8_t* queries, int64_t n_queries,
+                                     const int64_t* offsets, int64_t n_images, int32_t k, int32_t shortlist,
+                                     int64_t* totals, int32_t* classes, void* stream) {
+  int M1 = 0;
+  if (index && (!k_ok(index, k, 1) || !shortlist_ok(index, shortlist, k + 1, &M1))) return LNBNN_ERR_K_RANGE;
+  if (index && !index->fp8) return LNBNN_ERR_NO_FP8;
+  return classify_host(index, true, queries, n_queries, offsets, n_images, k, shortlist, totals, classes, stream);
 }
 
 lnbnn_status nbnn_classify_host(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
                                 int64_t n_images, int64_t* totals, int32_t* classes, void* stream) {
   if (index && index->has_empty_class) return LNBNN_ERR_EMPTY_CLASS;
-  return classify_host(index, false, queries, n_queries, offsets, n_images, 0, totals, classes, stream);
+  return classify_host(index, false, queries, n_queries, offsets, n_images, 0, 0, totals, classes, stream);
 }
 
 lnbnn_status lnbnn_profile_enable(lnbnn_index* index, int enable) {

@@ -31,13 +31,16 @@ STATUS = {
     8: "unsupported device",
     9: "invalid image offsets",
     10: "problem larger than a workspace or the scratch of knn_search_noalloc",
+    11: "the index has no FP8 operand (call prepare_fp8 first)",
 }
 MAX_K = 255
 
 EXPORTS = ["lnbnn_index_create", "lnbnn_index_destroy", "lnbnn_index_info", "knn_search", "lnbnn_classify",
            "nbnn_classify", "lnbnn_classify_host", "nbnn_classify_host", "lnbnn_sync", "lnbnn_profile_enable",
            "lnbnn_profile_read", "lnbnn_status_string", "knn_search_noalloc", "lnbnn_workspace_create",
-           "lnbnn_workspace_destroy", "knn_search_ws", "lnbnn_classify_ws", "nbnn_classify_ws"]
+           "lnbnn_workspace_destroy", "knn_search_ws", "lnbnn_classify_ws", "nbnn_classify_ws",
+           "lnbnn_index_prepare_fp8", "knn_search_fp8", "lnbnn_classify_fp8", "knn_search_fp8_ws",
+           "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host"]
 
 
 class Profile(ctypes.Structure):
@@ -88,12 +91,19 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.knn_search_ws.argtypes = [P, P, P, I64, I32, P, P, P]
         lib.lnbnn_classify_ws.argtypes = [P, P, P, I64, P, I64, I32, P, P, P]
         lib.nbnn_classify_ws.argtypes = [P, P, P, I64, P, I64, P, P, P]
+        lib.lnbnn_index_prepare_fp8.argtypes = [P, P]
+        lib.knn_search_fp8.argtypes = [P, P, I64, I32, I32, P, P, P]
+        lib.lnbnn_classify_fp8.argtypes = [P, P, I64, P, I64, I32, I32, P, P, P]
+        lib.knn_search_fp8_ws.argtypes = [P, P, P, I64, I32, I32, P, P, P]
+        lib.lnbnn_classify_fp8_ws.argtypes = [P, P, P, I64, P, I64, I32, I32, P, P, P]
+        lib.lnbnn_classify_fp8_host.argtypes = [P, P, I64, P, I64, I32, I32, P, P, P]
         lib.lnbnn_status_string.argtypes = [ctypes.c_int]
         lib.lnbnn_status_string.restype = ctypes.c_char_p
         for name in ("lnbnn_index_create", "lnbnn_index_info", "knn_search", "lnbnn_classify", "nbnn_classify",
                      "lnbnn_classify_host", "nbnn_classify_host", "lnbnn_sync", "lnbnn_profile_enable",
                      "lnbnn_profile_read", "lnbnn_workspace_create", "knn_search_ws", "lnbnn_classify_ws",
-                     "nbnn_classify_ws"):
+                     "nbnn_classify_ws", "lnbnn_index_prepare_fp8", "knn_search_fp8", "lnbnn_classify_fp8",
+                     "knn_search_fp8_ws", "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host"):
             getattr(lib, name).restype = ctypes.c_int
         if path == LIB_PATH:
             _lib = lib
@@ -167,34 +177,53 @@ class Index:
         (no allocation inside those calls; one per concurrent stream)."""
         return Workspace(self, max_queries, max_k)
 
-    def knn_search(self, queries, k: int, stream=None, workspace=None, out=None):
-        """NN(d, k): ``(idx int32 [M, k], dist int32 [M, k])``, exact, by (distance, row)."""
+    def prepare_fp8(self, stream=None) -> None:
+        """Build the E4M3 operand of the FP8 shortlist search (once)."""
+        _check(self._lib.lnbnn_index_prepare_fp8(self.handle, _stream_ptr(stream)), "lnbnn_index_prepare_fp8")
+
+    def knn_search(self, queries, k: int, stream=None, workspace=None, out=None, shortlist: int | None = None):
+        """NN(d, k): ``(idx int32 [M, k], dist int32 [M, k])`` by (distance, row); exact, or
+        with ``shortlist`` the FP8 shortlist search (exact distances of the rows it finds)."""
         import torch
         m = int(queries.shape[0])
         idx, dist = out if out is not None else (
             torch.empty((m, k), dtype=torch.int32, device=queries.device),
             torch.empty((m, k), dtype=torch.int32, device=queries.device))
-        args = (_dev(queries, torch.uint8, "queries"), m, k, _dev(idx, torch.int32, "idx"),
-                _dev(dist, torch.int32, "dist"), _stream_ptr(stream))
-        if workspace is None:
-            _check(self._lib.knn_search(self.handle, *args), "knn_search")
+        q = _dev(queries, torch.uint8, "queries")
+        tail = (_dev(idx, torch.int32, "idx"), _dev(dist, torch.int32, "dist"), _stream_ptr(stream))
+        if shortlist is None:
+            if workspace is None:
+                _check(self._lib.knn_search(self.handle, q, m, k, *tail), "knn_search")
+            else:
+                _check(self._lib.knn_search_ws(self.handle, workspace.handle, q, m, k, *tail), "knn_search_ws")
+        elif workspace is None:
+            _check(self._lib.knn_search_fp8(self.handle, q, m, k, int(shortlist), *tail), "knn_search_fp8")
         else:
-            _check(self._lib.knn_search_ws(self.handle, workspace.handle, *args), "knn_search_ws")
+            _check(self._lib.knn_search_fp8_ws(self.handle, workspace.handle, q, m, k, int(shortlist), *tail),
+                   "knn_search_fp8_ws")
         return idx, dist
 
-    def lnbnn_classify(self, queries, offsets, k: int, stream=None, out=None, workspace=None):
-        """Alg. 2: ``(totals int64 [n_img, C], classes int32 [n_img])``."""
+    def lnbnn_classify(self, queries, offsets, k: int, stream=None, out=None, workspace=None,
+                       shortlist: int | None = None):
+        """Alg. 2: ``(totals int64 [n_img, C], classes int32 [n_img])``; with ``shortlist``
+        the neighbours come from the FP8 shortlist search."""
         import torch
         m, n_img = int(queries.shape[0]), int(offsets.shape[0]) - 1
         totals, classes = out if out is not None else (
             torch.empty((n_img, self.n_classes), dtype=torch.int64, device=queries.device),
             torch.empty((n_img,), dtype=torch.int32, device=queries.device))
-        args = (_dev(queries, torch.uint8, "queries"), m, _dev(offsets, torch.int64, "offsets"), n_img, k,
-                _dev(totals, torch.int64, "totals"), _dev(classes, torch.int32, "classes"), _stream_ptr(stream))
-        if workspace is None:
-            _check(self._lib.lnbnn_classify(self.handle, *args), "lnbnn_classify")
+        head = (_dev(queries, torch.uint8, "queries"), m, _dev(offsets, torch.int64, "offsets"), n_img, k)
+        tail = (_dev(totals, torch.int64, "totals"), _dev(classes, torch.int32, "classes"), _stream_ptr(stream))
+        if shortlist is None:
+            if workspace is None:
+                _check(self._lib.lnbnn_classify(self.handle, *head, *tail), "lnbnn_classify")
+            else:
+                _check(self._lib.lnbnn_classify_ws(self.handle, workspace.handle, *head, *tail), "lnbnn_classify_ws")
+        elif workspace is None:
+            _check(self._lib.lnbnn_classify_fp8(self.handle, *head, int(shortlist), *tail), "lnbnn_classify_fp8")
         else:
-            _check(self._lib.lnbnn_classify_ws(self.handle, workspace.handle, *args), "lnbnn_classify_ws")
+            _check(self._lib.lnbnn_classify_fp8_ws(self.handle, workspace.handle, *head, int(shortlist), *tail),
+                   "lnbnn_classify_fp8_ws")
         return totals, classes
 
     def nbnn_classify(self, queries, offsets, stream=None, out=None, workspace=None):
@@ -213,9 +242,9 @@ class Index:
         return totals, classes
 
     def classify_host(self, queries: np.ndarray, offsets: np.ndarray, k: int | None, totals: np.ndarray | None = None,
-                      classes: np.ndarray | None = None, stream=None):
-        """Host-buffer form (k=None -> original NBNN).  numpy in, numpy out;
-        pinned host arrays give the fastest copies."""
+                      classes: np.ndarray | None = None, stream=None, shortlist: int | None = None):
+        """Host-buffer form (k=None -> original NBNN; shortlist -> FP8 shortlist
+        search).  numpy in, numpy out; pinned host arrays give the fastest copies."""
         q = np.ascontiguousarray(queries, dtype=np.uint8)
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         n_img = off.shape[0] - 1
@@ -224,7 +253,10 @@ class Index:
         if classes is None:
             classes = np.empty((n_img,), dtype=np.int32)
         p = lambda a: ctypes.c_void_p(a.ctypes.data)
-        if k is None:
+        if shortlist is not None:
+            code = self._lib.lnbnn_classify_fp8_host(self.handle, p(q), q.shape[0], p(off), n_img, k, int(shortlist),
+                                                     p(totals), p(classes), _stream_ptr(stream))
+        elif k is None:
             code = self._lib.nbnn_classify_host(self.handle, p(q), q.shape[0], p(off), n_img, p(totals), p(classes),
                                                 _stream_ptr(stream))
         else:

@@ -84,6 +84,8 @@ class Server:
     """Continuous-batching classifier over one ``lnbnn.Index``.
 
     method: "local" (Alg. 2 with neighbourhood k) or "nbnn" (Alg. 1).
+    shortlist: None for the exact search, else the FP8 shortlist length of
+    the approximate search ("local" only; the index needs prepare_fp8()).
     slots: batches that can be in flight at once.
     max_batch_queries / max_batch_images: the capacity of one slot.
     graphs: replay captured CUDA graphs (one per slot and bucket of
@@ -91,11 +93,15 @@ class Server:
     """
 
     def __init__(self, index, k: int = 10, method: str = "local", slots: int = 3, max_batch_queries: int = 16384,
-                 max_batch_images: int = 256, graphs: bool = False, graph_granule: int = 2048):
+                 max_batch_images: int = 256, graphs: bool = False, graph_granule: int = 2048,
+                 shortlist: int | None = None):
         import torch
 
         if method not in ("local", "nbnn"):
             raise ValueError("method must be 'local' or 'nbnn'")
+        if shortlist is not None and method != "local":
+            raise ValueError("the FP8 shortlist search serves Local NBNN only")
+        self.shortlist = shortlist
         if graphs and max_batch_queries % graph_granule:
             raise ValueError("max_batch_queries must be a multiple of graph_granule")
         self.index, self.k, self.method = index, int(k), method
@@ -108,7 +114,7 @@ class Server:
         self.slots = []
         for _ in range(slots):
             self.slots.append(_Slot(
-                ws=index.workspace(self.max_q, self.k),
+                ws=index.workspace(self.max_q, max(self.k, (shortlist or 0) - 1)),
                 stream=torch.cuda.Stream(dev),
                 q_host=torch.zeros((self.max_q, 128), dtype=torch.uint8).pin_memory(),
                 off_host=torch.empty((n_img_cap + 1,), dtype=torch.int64).pin_memory(),
@@ -149,7 +155,7 @@ class Server:
         out = (slot.tot_dev[:b], slot.cls_dev[:b])
         if self.method == "local":
             self.index.lnbnn_classify(slot.q_dev[:n], slot.off_dev[:b + 1], self.k, stream=s, out=out,
-                                      workspace=slot.ws)
+                                      workspace=slot.ws, shortlist=self.shortlist)
         else:
             self.index.nbnn_classify(slot.q_dev[:n], slot.off_dev[:b + 1], stream=s, out=out, workspace=slot.ws)
         slot.tot_host[:b].copy_(slot.tot_dev[:b], non_blocking=True)

@@ -39,8 +39,9 @@ def test_binding_names_match_header():
 
 
 def test_status_strings(lib):
-    for code in range(10):
-        assert lib.lnbnn_status_string(code)
+    for code in range(12):
+        assert lib.lnbnn_status_string(code) != b"unknown status"
+    assert b"prepare_fp8" in lib.lnbnn_status_string(11)
     assert b"k out of range" in lib.lnbnn_status_string(4)
 
 
@@ -54,6 +55,11 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.lnbnn_classify(None, None, 0, None, 0, 1, None, None, None) == 1
     assert lib.nbnn_classify(None, None, 0, None, 0, None, None, None) == 1
     assert lib.lnbnn_sync(None, None) == 1
+    assert lib.lnbnn_index_prepare_fp8(None, None) == 1
+    assert lib.knn_search_fp8(None, None, 0, 1, 8, None, None, None) == 1
+    assert lib.lnbnn_classify_fp8(None, None, 0, None, 0, 1, 8, None, None, None) == 1
+    assert lib.lnbnn_classify_fp8(None, None, 0, None, 0, 1, 0, None, None, None) == 4  # shortlist 0: no FP8 call
+    assert lib.lnbnn_classify_fp8_ws(None, None, None, 0, None, 0, 1, 8, None, None, None) == 1
     lib.lnbnn_index_destroy(None)
 
 
