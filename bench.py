@@ -445,7 +445,7 @@ def run_serving(index, rates, seconds, k, shortlist) -> dict:
     arrivals of query images with log-uniform [100, 4000] descriptors."""
     from paper_1112_0059_gb300 import serve
     w = synth.workload("serving")
-    cfg = {"slots": 3, "max_batch_queries": 16384, "max_batch_images": 256, "graphs": True, "graph_granule": 2048}
+    cfg = {"slots": 3, "max_batch_queries": 16384, "max_batch_images": 256, "graphs": True}
     runs, first = [], 0
     with serve.Server(index, k=k, method="local", shortlist=shortlist, **cfg) as srv:
         srv.run(serve.poisson_requests(w, 1000.0, 8, seed=99, first_image=100000))  # warm-up
@@ -460,7 +460,9 @@ def run_serving(index, rates, seconds, k, shortlist) -> dict:
             runs.append(st)
     form = "exact" if shortlist is None else f"FP8 E4M3 shortlist m = {shortlist} + exact rerank"
     return {"form": form, "k": k, "workload": "256-class index; Poisson arrivals; log-uniform [100, 4000] "
-            "descriptors per image; latency = arrival to totals and class on the host", **cfg, "runs": runs}
+            "descriptors per image; latency = arrival to totals and class on the host", **cfg,
+            "graph_buckets": f"{len(serve.graph_buckets(cfg['max_batch_queries']))} query-count buckets, "
+                             "multiples of 128 about 25% apart", "runs": runs}
 
 
 def main():

@@ -202,6 +202,35 @@ LNBNN_API lnbnn_status lnbnn_classify_fp8_ws(lnbnn_index *index, lnbnn_workspace
                                              int32_t *classes, void *stream);
 
 /*
+ * Split-N schedule.  Each search launch runs ceil(n_queries / 128) query tiles
+ * x `splits` reference ranges as CTAs, one per SM, and merges the splits'
+ * lists; the split count is chosen per call by a device-time model
+ *   waves(tiles * splits) * (a * tiles_per_CTA + b) + c * tiles * splits.
+ * lnbnn_autotune times a dozen search launches of 1 to 64 query tiles (query
+ * rows copied from the index's own references) with several split counts on
+ * `stream`, fits a, b, c by least squares and keeps them in the index; it
+ * synchronises `stream`, allocates and frees its own scratch, and changes no
+ * result (every schedule gives bit-identical output), only speed.  Call it
+ * outside stream capture.  out (may be NULL) receives the fitted milliseconds
+ * per tile, per wave and per (query tile, split), the number of timed runs and
+ * the largest relative error of the fit (tile_ms = 0: no fit, the model is
+ * unchanged).  lnbnn_plan_splits reports the
+ * split count a call with n_queries query descriptors would use.
+ * Workspaces are sized for the largest split count any model may choose, so
+ * they stay valid after tuning.
+ */
+typedef struct lnbnn_tuning {
+  double tile_ms;
+  double wave_ms;
+  double list_ms;
+  double max_rel_error;
+  int32_t runs;
+} lnbnn_tuning;
+
+LNBNN_API lnbnn_status lnbnn_autotune(lnbnn_index *index, void *stream, lnbnn_tuning *out);
+LNBNN_API lnbnn_status lnbnn_plan_splits(const lnbnn_index *index, int64_t n_queries, int32_t *splits);
+
+/*
  * Host-buffer forms of the classifiers: queries, offsets, totals and
  * classes are HOST pointers.  The call copies the inputs to the device
  * (into the index's device staging buffer), classifies, copies the

@@ -71,7 +71,9 @@ cudaError_t launch_gather_ref(const int64_t* perm, int64_t n, const __nv_bfloat1
 // dst[0..n) = v
 cudaError_t launch_fill_float(float* dst, int64_t n, float v, cudaStream_t s);
 
-// Merge `splits` sorted lists per row into one sorted list of K1 keys.
+// Merge `splits` sorted lists per row into one sorted list of K1 keys
+// (at most 32 * kMaxListsPerLane lists).
+constexpr int kMaxListsPerLane = 20;
 cudaError_t launch_merge_lists(const uint64_t* lists, int splits, int64_t m, int64_t list_stride_rows,
                                int K1, uint64_t* out, cudaStream_t s);
 // knn_search output: first k entries of each sorted list as (row, distance).

@@ -42,7 +42,7 @@
 //                        taking a 128-column half of every tile with one
 //                        thread per query row (TMEM lane); each keeps its own
 //                        sorted list of the k+1 nearest (in registers for
-//                        k+1 <= 16, otherwise a heap in global memory); two
+//                        k+1 <= 32, otherwise a heap in global memory); two
 //                        256-column FP32 accumulators in flight
 // Every wait is bounded; on expiry the CTA records a timeout in the index's
 // device error word, drains what it issued and returns.
@@ -649,6 +649,7 @@ cudaError_t prepare_one() {
 
 cudaError_t prepare_tc_kernels() {
   cudaError_t e = prepare_one<FmtBf16, KnnEpilogue<kTcRegListMax>>();
+  if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnEpilogue<kTcCoarseRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnEpilogue<0>>();
   if (e == cudaSuccess) e = prepare_one<FmtBf16, NbnnEpilogue>();
   if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<kTcRegListMax>>();
@@ -670,6 +671,9 @@ cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv
   if (K1 <= kTcRegListMax)
     return launch_scan<FmtBf16, KnnEpilogue<kTcRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len,
                                                             out, dev_err, stats, s);
+  if (K1 <= kTcCoarseRegListMax)
+    return launch_scan<FmtBf16, KnnEpilogue<kTcCoarseRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
+                                                                  split_len, out, dev_err, stats, s);
   return launch_scan<FmtBf16, KnnEpilogue<0>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len, out, dev_err,
                                               stats, s);
 }

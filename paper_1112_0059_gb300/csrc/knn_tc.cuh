@@ -3,6 +3,8 @@
 
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace lnbnn {
@@ -18,8 +20,9 @@ static_assert(kQueryPad % (kTcQueryTile * kTcCluster) == 0, "query padding must 
 // tile and keeps its own top-K1 list per query row, so one reference split
 // yields this many sorted lists per row (merged afterwards).
 constexpr int kTcListsPerSplit = 2;
-// Largest K1 kept in registers; larger lists live in global memory.  The
-// coarse pass also has a 32-entry register list (its shortlists are longer).
+// Largest K1 kept in registers: lists of up to 16 use a 16-entry register
+// list (the fewest registers), up to 32 a 32-entry one; longer lists live in
+// global memory as heaps.
 constexpr int kTcRegListMax = 16;
 constexpr int kTcCoarseRegListMax = 32;
 static_assert(kTcListsPerSplit > 1, "the shortlist search merges into a buffer apart from the lists");
@@ -31,6 +34,47 @@ struct TcTensorMaps {
   CUtensorMap sref, sref_ext;  // the same over the class-sorted copy
   CUtensorMap f8, f8_ext;      // E4M3 coarse operand [n_pad,128] and its extension [n_pad,16]
 };
+
+// Split-N schedule of one scan launch over T query tiles: s reference splits
+// make T * s CTAs, run one per SM in waves of sm_count.  Modelled device time:
+//   ceil(T * s / sm_count) * (a * tiles_per_cta(s) + b) + c * T * s,
+// tiles_per_cta(s) = ceil(ceil(n_ref / s) / kTcRefTile): a is the time of one
+// 128 x 256 tile, b the fixed time of a wave (CTA start, drain, epilogue
+// store), c the merge time per (query tile, split).  lnbnn_autotune fits
+// a, b, c on the device; these defaults are in tile units.
+struct SplitModel {
+  double a = 1.0, b = 64.0, c = 0.02;
+};
+
+// Largest split count considered for T query tiles: at most four waves of
+// CTAs (so workspace sizes do not depend on the fitted model), at least 4,096
+// references per split, at most max_splits.
+inline int64_t max_splits_for(int64_t T, int64_t n_ref, int sm_count, int64_t max_splits) {
+  int64_t hi = (4 * (int64_t)sm_count + T - 1) / T;
+  hi = std::min<int64_t>(hi, std::max<int64_t>(1, n_ref / 4096));
+  return std::max<int64_t>(1, std::min<int64_t>(hi, max_splits));
+}
+
+inline double split_cost(const SplitModel& md, int64_t T, int64_t s, int64_t n_ref, int sm_count) {
+  const int64_t tiles = ((n_ref + s - 1) / s + kTcRefTile - 1) / kTcRefTile;
+  const int64_t waves = (T * s + sm_count - 1) / sm_count;
+  return (double)waves * (md.a * (double)tiles + md.b) + md.c * (double)(T * s);
+}
+
+// The split count of least modelled time (the smaller one on ties).
+inline int choose_splits_model(const SplitModel& md, int64_t T, int64_t n_ref, int sm_count, int64_t max_splits) {
+  const int64_t hi = max_splits_for(T, n_ref, sm_count, max_splits);
+  int64_t best = 1;
+  double best_cost = split_cost(md, T, 1, n_ref, sm_count);
+  for (int64_t s = 2; s <= hi; ++s) {
+    const double c = split_cost(md, T, s, n_ref, sm_count);
+    if (c < best_cost * (1.0 - 1e-9)) {
+      best_cost = c;
+      best = s;
+    }
+  }
+  return (int)best;
+}
 
 // Sets the kernels' shared-memory size on the current device; call once per
 // device before launching (and before any stream capture).

@@ -1,6 +1,7 @@
 // The C ABI of include/lnbnn.h: index ownership, argument checks, workspace
 // and the launch sequence of each call.  All arithmetic runs in the kernels.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -43,6 +44,7 @@ struct lnbnn_index {
   __nv_bfloat16* ref_f8_ext = nullptr;   // [n_pad, 16]
   bool fp8 = false;
   TcTensorMaps tc;  // tensor maps over ref_bf / sref_bf (and ref_f8) for the tensor-core kernels
+  SplitModel split_model;  // split-N schedule (defaults, or fitted by lnbnn_autotune)
   // optional device-time profile (lnbnn_profile_enable)
   struct CallEvents {
     cudaEvent_t e[4];
@@ -182,16 +184,14 @@ bool k_ok(const lnbnn_index* ix, int32_t k, int extra) {
   return k >= 1 && k <= LNBNN_MAX_K && (int64_t)k + extra <= ix->n_ref;
 }
 
-constexpr int kMaxSplits = 32;
+// Most reference splits of one launch: two CTAs per SM for a single query
+// tile, within what the list merge takes (two lists per split).
+int64_t max_splits(const lnbnn_index* ix) {
+  return std::min<int64_t>(2 * (int64_t)ix->sm_count, 32 * kMaxListsPerLane / kTcListsPerSplit);
+}
 
-// Number of reference splits so that query tiles x splits fill the GPU.
 int choose_splits(const lnbnn_index* ix, int64_t m_pad) {
-  const int64_t tiles = m_pad / kTcQueryTile;
-  const int64_t want = 2 * (int64_t)ix->sm_count;
-  int64_t s = tiles >= want ? 1 : (want + tiles - 1) / tiles;
-  s = std::min<int64_t>(s, std::max<int64_t>(1, ix->n_ref / 4096));
-  s = std::min<int64_t>(s, kMaxSplits);
-  return (int)std::max<int64_t>(s, 1);
+  return choose_splits_model(ix->split_model, m_pad / kTcQueryTile, ix->n_ref, ix->sm_count, max_splits(ix));
 }
 
 struct KnnPlan {
@@ -203,11 +203,13 @@ struct KnnPlan {
   size_t off_qnorm, off_qbf, off_qext, off_lists, off_merged, bytes;
 };
 
-KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1) {
+// splits = 0: the modelled best; otherwise that many (an upper bound after
+// rounding the split length to whole tiles).
+KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, int splits = 0) {
   KnnPlan p{};
   p.m_pad = round_up(m, kQueryPad);
   p.K1 = K1;
-  p.splits = choose_splits(ix, p.m_pad);
+  p.splits = splits > 0 ? splits : choose_splits(ix, p.m_pad);
   p.split_len = round_up((ix->n_ref + p.splits - 1) / p.splits, kTcRefTile);
   p.splits = (int)((ix->n_ref + p.split_len - 1) / p.split_len);
   Carve c;
@@ -256,19 +258,23 @@ NbnnPlan plan_nbnn(const lnbnn_index* ix, int64_t m) {
 }
 
 // Largest scratch any call with at most max_q queries and lists of K1 needs.
+// The lists grow with the split count, so the bound takes the largest count
+// the schedule may choose, whatever model lnbnn_autotune fits later.
 size_t scratch_bound(const lnbnn_index* ix, int64_t max_q, int K1) {
   size_t b = 0;
   for (int64_t m = kQueryPad; m < max_q + kQueryPad; m += kQueryPad) {
-    b = std::max(b, plan_knn(ix, std::min(m, max_q), K1).bytes);
-    b = std::max(b, plan_nbnn(ix, std::min(m, max_q)).bytes);
+    const int64_t mm = std::min(m, max_q);
+    const int64_t hi = max_splits_for(round_up(mm, kQueryPad) / kTcQueryTile, ix->n_ref, ix->sm_count, max_splits(ix));
+    b = std::max(b, plan_knn(ix, mm, K1, (int)hi).bytes);
+    b = std::max(b, plan_nbnn(ix, mm).bytes);
   }
   return b;
 }
 
 // Runs the exact search; *lists receives m sorted lists of K1 keys.
 lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_t m, int K1, cudaStream_t s,
-                     const uint64_t** lists, CallProfile& prof) {
-  KnnPlan p = plan_knn(ix, m, K1);
+                     const uint64_t** lists, CallProfile& prof, int force_splits = 0) {
+  KnnPlan p = plan_knn(ix, m, K1, force_splits);
   char* ws = nullptr;
   lnbnn_status st = scratch.get(p.bytes, &ws);
   if (st != LNBNN_OK) return st;
@@ -462,6 +468,158 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
 }
 
 void lnbnn_index_destroy(lnbnn_index* index) { free_index(index); }
+
+lnbnn_status lnbnn_plan_splits(const lnbnn_index* index, int64_t n_queries, int32_t* splits) {
+  if (!index || !splits || n_queries < 1) return LNBNN_ERR_INVALID_ARG;
+  *splits = plan_knn(index, n_queries, 1).splits;
+  return LNBNN_OK;
+}
+
+lnbnn_status lnbnn_autotune(lnbnn_index* index, void* stream, lnbnn_tuning* out) {
+  if (!index) return LNBNN_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int P = index->sm_count;
+  const int64_t n_ref = index->n_ref;
+  // query tiles up to 64 (a few waves of CTAs with few splits), copied from
+  // reference rows spread over the set, so their neighbour structure is real
+  const int64_t t_max = std::min<int64_t>(64, n_ref / kTcQueryTile);
+  if (t_max < 1) {  // too few references for a whole query tile: keep the defaults
+    if (out) *out = lnbnn_tuning{};
+    return LNBNN_OK;
+  }
+  struct Run {
+    int64_t T, splits;
+    double ms;
+  };
+  std::vector<Run> runs;
+  for (int64_t T = 1; T <= t_max; T *= 2) {
+    const int64_t hi = max_splits_for(T, n_ref, P, max_splits(index));
+    int64_t last = 0;
+    for (int64_t w : {1, 2, 4}) {
+      const int64_t sp = std::min<int64_t>(hi, std::max<int64_t>(1, w * P / T));
+      if (sp != last) runs.push_back({T, sp, 0.0});
+      last = sp;
+    }
+  }
+  const int K1 = 11;
+  const int64_t m_max = t_max * kTcQueryTile;
+  size_t need = 0;
+  for (const Run& r : runs) need = std::max(need, plan_knn(index, r.T * kTcQueryTile, K1, (int)r.splits).bytes);
+  lnbnn_workspace w;
+  w.index = index;
+  w.bytes = need;
+  uint8_t* q = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  lnbnn_status st = LNBNN_OK;
+  auto cleanup = [&]() {
+    cudaFree(q);
+    cudaFree(w.base);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+#define CKA(call)                         \
+  do {                                    \
+    cudaError_t e_ = (call);              \
+    if (e_ != cudaSuccess) {              \
+      st = status_of(e_);                 \
+      cleanup();                          \
+      return st;                          \
+    }                                     \
+  } while (0)
+  CKA(dmalloc(&q, (size_t)m_max * kDim));
+  CKA(cudaMalloc(&w.base, need));
+  CKA(cudaEventCreate(&e0));
+  CKA(cudaEventCreate(&e1));
+  const int64_t step = n_ref / m_max;  // >= 1
+  CKA(cudaMemcpy2DAsync(q, kDim, index->ref_u8, (size_t)step * kDim, kDim, (size_t)m_max, cudaMemcpyDeviceToDevice, s));
+  const bool prof_was_on = index->prof_on;
+  index->prof_on = false;
+  for (Run& r : runs) {
+    float best = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {  // the first is a warm-up
+      Scratch scratch{index, &w};
+      CallProfile prof(index, s);
+      const uint64_t* lists = nullptr;
+      CKA(cudaEventRecord(e0, s));
+      st = run_knn(index, scratch, q, r.T * kTcQueryTile, K1, s, &lists, prof, (int)r.splits);
+      if (st != LNBNN_OK) {
+        index->prof_on = prof_was_on;
+        cleanup();
+        return st;
+      }
+      CKA(cudaEventRecord(e1, s));
+      CKA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CKA(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep == 1 || (rep > 1 && ms < best)) best = ms;
+    }
+    r.ms = best;
+  }
+  index->prof_on = prof_was_on;
+  cleanup();
+#undef CKA
+  // least squares for ms = a * waves * tiles + b * waves + c * T * splits + d,
+  // dropping a term whose coefficient comes out negative
+  bool use[4] = {true, true, true, true};
+  double coef[4] = {0, 0, 0, 0};
+  auto feat = [&](const Run& r, int j) {
+    const int64_t split_len = round_up((n_ref + r.splits - 1) / r.splits, kTcRefTile);
+    const int64_t sp = (n_ref + split_len - 1) / split_len;
+    const double waves = (double)((r.T * sp + P - 1) / P);
+    const double tiles = (double)(split_len / kTcRefTile);
+    return j == 0 ? waves * tiles : j == 1 ? waves : j == 2 ? (double)(r.T * sp) : 1.0;
+  };
+  for (int pass = 0; pass < 4; ++pass) {
+    double A[4][5] = {};
+    for (const Run& r : runs)
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) A[i][j] += use[i] && use[j] ? feat(r, i) * feat(r, j) : 0.0;
+    for (const Run& r : runs)
+      for (int i = 0; i < 4; ++i) A[i][4] += use[i] ? feat(r, i) * r.ms : 0.0;
+    for (int i = 0; i < 4; ++i)
+      if (!use[i]) A[i][i] = 1.0;
+    // Gaussian elimination with partial pivoting
+    for (int c = 0; c < 4; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < 4; ++r)
+        if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+      for (int j = 0; j < 5; ++j) std::swap(A[c][j], A[piv][j]);
+      if (std::fabs(A[c][c]) < 1e-300) continue;
+      for (int r = 0; r < 4; ++r) {
+        if (r == c) continue;
+        const double f = A[r][c] / A[c][c];
+        for (int j = c; j < 5; ++j) A[r][j] -= f * A[c][j];
+      }
+    }
+    for (int i = 0; i < 4; ++i) coef[i] = use[i] && std::fabs(A[i][i]) > 1e-300 ? A[i][4] / A[i][i] : 0.0;
+    int worst = -1;
+    for (int i = 0; i < 3; ++i)
+      if (use[i] && coef[i] < 0 && (worst < 0 || coef[i] < coef[worst])) worst = i;
+    if (worst < 0) break;
+    use[worst] = false;
+  }
+  if (coef[0] <= 0) {  // measurements no schedule model explains: keep the current model
+    if (out) *out = lnbnn_tuning{0.0, 0.0, 0.0, 0.0, (int32_t)runs.size()};
+    return LNBNN_OK;
+  }
+  index->split_model.a = coef[0];
+  index->split_model.b = std::max(0.0, coef[1]);
+  index->split_model.c = std::max(0.0, coef[2]);
+  if (out) {
+    out->tile_ms = coef[0];
+    out->wave_ms = index->split_model.b;
+    out->list_ms = index->split_model.c;
+    out->runs = (int32_t)runs.size();
+    double worst = 0;
+    for (const Run& r : runs) {
+      double pred = coef[3];
+      for (int j = 0; j < 3; ++j) pred += (j == 0 ? coef[0] : j == 1 ? index->split_model.b : index->split_model.c) * feat(r, j);
+      worst = std::max(worst, std::fabs(pred - r.ms) / r.ms);
+    }
+    out->max_rel_error = worst;
+  }
+  return LNBNN_OK;
+}
 
 lnbnn_status lnbnn_index_prepare_fp8(lnbnn_index* index, void* stream) {
   if (!index) return LNBNN_ERR_INVALID_ARG;

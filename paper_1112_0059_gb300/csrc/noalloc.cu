@@ -86,13 +86,11 @@ extern "C" LNBNN_API lnbnn_status knn_search_noalloc(const uint8_t* ref, int64_t
   lnbnn_status st = scratch_on_current_device(&base, &sm_count);
   if (st != LNBNN_OK) return st;
 
-  // Same plan as the index path: enough reference splits to fill the GPU.
+  // The index path's split schedule with the default model, at most 32
+  // splits (which bounds the scratch the lists take).
   const int64_t n_pad = round_up(n_ref, kRefPad);
   const int64_t m_pad = round_up(n_queries, kQueryPad);
-  const int64_t tiles = m_pad / kTcQueryTile;
-  const int64_t want = 2 * (int64_t)sm_count;
-  int64_t splits = tiles >= want ? 1 : (want + tiles - 1) / tiles;
-  splits = std::min<int64_t>(std::min<int64_t>(splits, std::max<int64_t>(1, n_ref / 4096)), 32);
+  int64_t splits = choose_splits_model(SplitModel{}, m_pad / kTcQueryTile, n_ref, sm_count, 32);
   const int64_t split_len = round_up((n_ref + splits - 1) / splits, kTcRefTile);
   splits = (n_ref + split_len - 1) / split_len;
 

@@ -5,30 +5,49 @@
 namespace lnbnn {
 namespace {
 
-constexpr int kMaxSplitsMerge = 64;
+// Row i's `n_lists` partial lists live at lists[(l * stride + i) * K1]; each is
+// sorted ascending.  One warp per row writes the K1 smallest keys of their
+// union, ascending: lane j holds the heads of lists j, j + 32, ...; each round
+// the warp minimum is written and the list that held it advances.  Keys are
+// unique (each holds a distinct reference row), except the empty key.
+constexpr int kMergeWarps = 4;
 
-// Row i's `splits` partial lists live at lists[(s * stride + i) * K1]; each is
-// sorted ascending.  Writes the K1 smallest keys of their union, ascending.
-__global__ void merge_lists_kernel(const uint64_t* __restrict__ lists, int splits, int64_t m, int64_t stride,
-                                   int K1, uint64_t* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * kMergeWarps)
+    merge_lists_kernel(const uint64_t* __restrict__ lists, int n_lists, int64_t m, int64_t stride, int K1,
+                       uint64_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * kMergeWarps + (threadIdx.x >> 5);
   if (i >= m) return;
-  int pos[kMaxSplitsMerge];
-  for (int s = 0; s < splits; ++s) pos[s] = 0;
+  uint64_t head[kMaxListsPerLane];
+  int pos[kMaxListsPerLane];
+#pragma unroll
+  for (int c = 0; c < kMaxListsPerLane; ++c) {
+    const int l = c * 32 + lane;
+    pos[c] = 0;
+    head[c] = l < n_lists ? lists[((int64_t)l * stride + i) * K1] : kEmptyKey;
+  }
   for (int t = 0; t < K1; ++t) {
     uint64_t best = kEmptyKey;
-    int bs = -1;
-    for (int s = 0; s < splits; ++s) {
-      if (pos[s] < K1) {
-        const uint64_t v = lists[((int64_t)s * stride + i) * K1 + pos[s]];
-        if (v < best) {
-          best = v;
-          bs = s;
-        }
+    int bc = 0;
+#pragma unroll
+    for (int c = 0; c < kMaxListsPerLane; ++c)
+      if (head[c] < best) {
+        best = head[c];
+        bc = c;
       }
+    uint64_t wmin = best;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) wmin = min(wmin, __shfl_xor_sync(0xffffffffu, wmin, off));
+    if (lane == 0) out[i * K1 + t] = wmin;
+    if (wmin != kEmptyKey && best == wmin) {
+#pragma unroll
+      for (int c = 0; c < kMaxListsPerLane; ++c)
+        if (c == bc) {
+          const int l = c * 32 + lane;
+          ++pos[c];
+          head[c] = pos[c] < K1 ? lists[((int64_t)l * stride + i) * K1 + pos[c]] : kEmptyKey;
+        }
     }
-    if (bs >= 0) ++pos[bs];
-    out[i * K1 + t] = best;
   }
 }
 
@@ -140,8 +159,9 @@ __global__ void argmin_kernel(const int64_t* __restrict__ totals, int64_t n_img,
 cudaError_t launch_merge_lists(const uint64_t* lists, int splits, int64_t m, int64_t stride, int K1, uint64_t* out,
                                cudaStream_t s) {
   if (m == 0) return cudaSuccess;
-  if (splits > kMaxSplitsMerge) return cudaErrorInvalidValue;
-  merge_lists_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(lists, splits, m, stride, K1, out);
+  if (splits < 1 || splits > 32 * kMaxListsPerLane) return cudaErrorInvalidValue;
+  merge_lists_kernel<<<(unsigned)((m + kMergeWarps - 1) / kMergeWarps), 32 * kMergeWarps, 0, s>>>(lists, splits, m,
+                                                                                                stride, K1, out);
   return cudaGetLastError();
 }
 

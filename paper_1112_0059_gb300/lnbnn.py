@@ -40,7 +40,7 @@ EXPORTS = ["lnbnn_index_create", "lnbnn_index_destroy", "lnbnn_index_info", "knn
            "lnbnn_profile_read", "lnbnn_status_string", "knn_search_noalloc", "lnbnn_workspace_create",
            "lnbnn_workspace_destroy", "knn_search_ws", "lnbnn_classify_ws", "nbnn_classify_ws",
            "lnbnn_index_prepare_fp8", "knn_search_fp8", "lnbnn_classify_fp8", "knn_search_fp8_ws",
-           "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host"]
+           "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host", "lnbnn_autotune", "lnbnn_plan_splits"]
 
 
 class Profile(ctypes.Structure):
@@ -48,6 +48,15 @@ class Profile(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("search_launches", ctypes.c_int64), ("search_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
                 ("search_sm_clock_ghz", ctypes.c_double), ("search_cycles_per_tile", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Tuning(ctypes.Structure):
+    """Mirror of ``lnbnn_tuning`` (include/lnbnn.h)."""
+    _fields_ = [("tile_ms", ctypes.c_double), ("wave_ms", ctypes.c_double), ("list_ms", ctypes.c_double),
+                ("max_rel_error", ctypes.c_double), ("runs", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -97,13 +106,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.knn_search_fp8_ws.argtypes = [P, P, P, I64, I32, I32, P, P, P]
         lib.lnbnn_classify_fp8_ws.argtypes = [P, P, P, I64, P, I64, I32, I32, P, P, P]
         lib.lnbnn_classify_fp8_host.argtypes = [P, P, I64, P, I64, I32, I32, P, P, P]
+        lib.lnbnn_autotune.argtypes = [P, P, ctypes.POINTER(Tuning)]
+        lib.lnbnn_plan_splits.argtypes = [P, I64, ctypes.POINTER(I32)]
         lib.lnbnn_status_string.argtypes = [ctypes.c_int]
         lib.lnbnn_status_string.restype = ctypes.c_char_p
         for name in ("lnbnn_index_create", "lnbnn_index_info", "knn_search", "lnbnn_classify", "nbnn_classify",
                      "lnbnn_classify_host", "nbnn_classify_host", "lnbnn_sync", "lnbnn_profile_enable",
                      "lnbnn_profile_read", "lnbnn_workspace_create", "knn_search_ws", "lnbnn_classify_ws",
                      "nbnn_classify_ws", "lnbnn_index_prepare_fp8", "knn_search_fp8", "lnbnn_classify_fp8",
-                     "knn_search_fp8_ws", "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host"):
+                     "knn_search_fp8_ws", "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host", "lnbnn_autotune",
+                     "lnbnn_plan_splits"):
             getattr(lib, name).restype = ctypes.c_int
         if path == LIB_PATH:
             _lib = lib
@@ -176,6 +188,18 @@ class Index:
         """Device scratch for calls of at most max_queries descriptors and k <= max_k
         (no allocation inside those calls; one per concurrent stream)."""
         return Workspace(self, max_queries, max_k)
+
+    def autotune(self, stream=None) -> dict:
+        """Fit the split-N schedule model on the device (changes speed, never results)."""
+        t = Tuning()
+        _check(self._lib.lnbnn_autotune(self.handle, _stream_ptr(stream), ctypes.byref(t)), "lnbnn_autotune")
+        return t.as_dict()
+
+    def plan_splits(self, n_queries: int) -> int:
+        """Reference splits a search of n_queries descriptors would use."""
+        out = ctypes.c_int32()
+        _check(self._lib.lnbnn_plan_splits(self.handle, int(n_queries), ctypes.byref(out)), "lnbnn_plan_splits")
+        return out.value
 
     def prepare_fp8(self, stream=None) -> None:
         """Build the E4M3 operand of the FP8 shortlist search (once)."""

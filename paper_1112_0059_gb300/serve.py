@@ -10,10 +10,10 @@ host->device copy, one classify call and one device->host copy on the slot's
 stream.  Batches on different slots overlap on the GPU, and requests that
 arrive while batches are in flight are admitted as soon as a slot frees up.
 
-With ``graphs=True`` each slot captures, per query-count bucket, one CUDA
-graph holding the copies and the classify call; a batch is padded up to its
-bucket with zero descriptors that form one extra image, whose scores are
-dropped.  The padding changes no real image's result: Alg. 2 scores every
+With ``graphs=True`` each slot captures, per query-count bucket (multiples
+of 128 descriptors, about 25% apart), one CUDA graph holding the copies and
+the classify call; a batch is padded up to its bucket with zero descriptors
+that form one extra image, whose scores are dropped.  The padding changes no real image's result: Alg. 2 scores every
 descriptor on its own, and a descriptor counts only toward its own image.
 
 All classification runs in the CUDA library; this module moves bytes and
@@ -57,9 +57,24 @@ def take_batch(pending: collections.deque, max_queries: int, max_images: int) ->
     return batch
 
 
-def bucket_of(n: int, granule: int) -> int:
-    """Padded query count of a graph bucket: n rounded up to ``granule``."""
-    return max(granule, -(-n // granule) * granule)
+def graph_buckets(max_queries: int, granule: int = 128, ratio: float = 1.25) -> list[int]:
+    """Query counts the server captures graphs for: multiples of ``granule``
+    growing by about ``ratio`` (padding a batch to its bucket wastes at most
+    that fraction of the search), ending at ``max_queries``."""
+    out, b = [], granule
+    while b < max_queries:
+        out.append(b)
+        b = max(b + granule, -(-int(b * ratio) // granule) * granule)
+    out.append(max_queries)
+    return out
+
+
+def bucket_of(n: int, buckets: list[int]) -> int:
+    """Smallest bucket that holds n descriptors."""
+    for b in buckets:
+        if n <= b:
+            return b
+    raise ValueError(f"{n} descriptors exceed the largest bucket {buckets[-1]}")
 
 
 @dataclass
@@ -88,13 +103,12 @@ class Server:
     the approximate search ("local" only; the index needs prepare_fp8()).
     slots: batches that can be in flight at once.
     max_batch_queries / max_batch_images: the capacity of one slot.
-    graphs: replay captured CUDA graphs (one per slot and bucket of
-    ``graph_granule`` descriptors) instead of launching each call.
+    graphs: replay captured CUDA graphs (one per slot and query-count
+    bucket, see ``graph_buckets``) instead of launching each call.
     """
 
     def __init__(self, index, k: int = 10, method: str = "local", slots: int = 3, max_batch_queries: int = 16384,
-                 max_batch_images: int = 256, graphs: bool = False, graph_granule: int = 2048,
-                 shortlist: int | None = None):
+                 max_batch_images: int = 256, graphs: bool = False, shortlist: int | None = None):
         import torch
 
         if method not in ("local", "nbnn"):
@@ -102,11 +116,10 @@ class Server:
         if shortlist is not None and method != "local":
             raise ValueError("the FP8 shortlist search serves Local NBNN only")
         self.shortlist = shortlist
-        if graphs and max_batch_queries % graph_granule:
-            raise ValueError("max_batch_queries must be a multiple of graph_granule")
         self.index, self.k, self.method = index, int(k), method
         self.max_q, self.max_img = int(max_batch_queries), int(max_batch_images)
-        self.use_graphs, self.granule = bool(graphs), int(graph_granule)
+        self.use_graphs = bool(graphs)
+        self.buckets = graph_buckets(self.max_q)
         C = index.n_classes
         dev = torch.device("cuda", torch.cuda.current_device())
         # Graph mode adds one image that holds the padding descriptors.
@@ -169,11 +182,11 @@ class Server:
         b = self.max_img + 1
         for slot in self.slots:
             slot.off_host.zero_()
-            slot.off_host[b] = self.granule  # all descriptors in the last image
+            slot.off_host[b] = self.buckets[0]  # all descriptors in the last image
             with torch.cuda.stream(slot.stream):  # one eager run: lazy initialisation happens outside capture
-                self._enqueue(slot, self.granule, b)
+                self._enqueue(slot, self.buckets[0], b)
             slot.stream.synchronize()
-            for n in range(self.granule, self.max_q + 1, self.granule):
+            for n in self.buckets:
                 g = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(g, stream=slot.stream):
                     self._enqueue(slot, n, b)
@@ -197,7 +210,7 @@ class Server:
         b, n = len(batch), int(oh[len(batch)])
         with torch.cuda.stream(slot.stream):
             if self.use_graphs:
-                nb = bucket_of(n, self.granule)
+                nb = bucket_of(n, self.buckets)
                 qh[n:nb] = 0  # padding descriptors: the extra image b
                 oh[b + 1:] = nb
                 slot.graphs[nb].replay()

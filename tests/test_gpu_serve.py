@@ -42,7 +42,7 @@ def test_served_equals_alone_and_oracle(setup, method, graphs):
     w, ref, labels, reqs, q, off, ix = setup
     reqs = [dataclasses.replace(r, totals=None, cls=None, done=None, batch=None) for r in reqs]
     with serve.Server(ix, k=10, method=method, slots=3, max_batch_queries=6144, max_batch_images=8,
-                      graphs=graphs, graph_granule=1024) as srv:
+                      graphs=graphs) as srv:
         done = srv.run(reqs)
         log = srv.log
     assert len(done) == len(reqs)

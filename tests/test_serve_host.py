@@ -34,11 +34,17 @@ def test_take_batch_image_cap_and_oversize():
         serve.take_batch(collections.deque([req(9, 1001)]), 1000, 3)
 
 
-def test_bucket_of():
-    assert serve.bucket_of(1, 2048) == 2048
-    assert serve.bucket_of(2048, 2048) == 2048
-    assert serve.bucket_of(2049, 2048) == 4096
-    assert serve.bucket_of(0, 512) == 512
+def test_graph_buckets():
+    b = serve.graph_buckets(16384)
+    assert b[0] == 128 and b[-1] == 16384 and b == sorted(set(b))
+    assert all(x % 128 == 0 for x in b)
+    # consecutive buckets at most ~25% (or one query tile) apart
+    assert all(y <= max(x + 128, 1.25 * x + 128) for x, y in zip(b, b[1:]))
+    assert serve.bucket_of(1, b) == 128 and serve.bucket_of(128, b) == 128 and serve.bucket_of(129, b) == 256
+    assert serve.bucket_of(16384, b) == 16384
+    with pytest.raises(ValueError):
+        serve.bucket_of(16385, b)
+    assert serve.graph_buckets(1000)[-1] == 1000
 
 
 def test_poisson_requests_shape_and_rate():
