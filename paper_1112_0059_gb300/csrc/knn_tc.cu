@@ -9,9 +9,10 @@
 // base-256 digits.  BF16 holds 0..255, -2q and the digits exactly; every
 // product and partial sum is an integer below 2^24 in magnitude, so acc is the
 // exact squared distance.  Non-negative floats order like their bit patterns,
-// so the epilogue tests 32 columns with an integer minimum and one compare
-// against the row's current (k+1)-th distance, and keeps the k+1 smallest
-// (distance, row) pairs.  The distance matrix never leaves the SM.
+// so the epilogue tests 32 columns with one compare of their minimum, which
+// the TMEM load itself returns (tcgen05.ld.red ... .min.u32), against the
+// row's current (k+1)-th distance, and keeps the k+1 smallest (distance, row)
+// pairs.  The distance matrix never leaves the SM.
 //
 // With kTcCluster > 1, the CTAs of a cluster (consecutive query tiles, same
 // reference split) share every reference tile: each loads its share of each
@@ -43,7 +44,8 @@
 //                        thread per query row (TMEM lane); each keeps its own
 //                        sorted list of the k+1 nearest (in registers for
 //                        k+1 <= 32, otherwise a heap in global memory); two
-//                        256-column FP32 accumulators in flight
+//                        256-column FP32 accumulators in flight; each
+//                        32-column load also returns the columns' minimum
 // Every wait is bounded; on expiry the CTA records a timeout in the index's
 // device error word, drains what it issued and returns.
 #include <cudaTypedefs.h>
@@ -230,16 +232,13 @@ __device__ __forceinline__ void offer_group<0>(RegList<0>&, TopK& top, int32_t& 
   }
 }
 
-// One 32-column group: integer minimum of the bit patterns, one compare.  A
-// column at exactly the threshold distance cannot enter: its row is higher
-// than every kept row's.
+// One 32-column group: one compare of the group's minimum bit pattern (mn,
+// from the reducing TMEM load).  A column at exactly the threshold distance
+// cannot enter: its row is higher than every kept row's.
 template <int KMAX>
 __device__ __forceinline__ void scan_group(RegList<KMAX>& L, TopK& top, int32_t& thr, bool active,
-                                           const uint32_t (&v)[32], int64_t col0) {
-  int32_t mn = (int32_t)v[0];
-#pragma unroll
-  for (int j = 1; j < 32; ++j) mn = min(mn, (int32_t)v[j]);
-  const bool hit = active && mn < thr;
+                                           const uint32_t (&v)[32], uint32_t mn, int64_t col0) {
+  const bool hit = active && (int32_t)mn < thr;
   if (__any_sync(0xffffffffu, hit)) {
     if (hit) offer_group<KMAX>(L, top, thr, v, col0);
     __syncwarp();
@@ -275,8 +274,8 @@ struct KnnEpilogue {
         out(o.lists + ((int64_t)list * o.stride + (act ? row : 0)) * o.K1) {
     L.init(K1);
   }
-  __device__ __forceinline__ void group(const uint32_t (&v)[32], int64_t col0) {
-    scan_group<KMAX>(L, top, thr, active, v, col0);
+  __device__ __forceinline__ void group(const uint32_t (&v)[32], uint32_t mn, int64_t col0) {
+    scan_group<KMAX>(L, top, thr, active, v, mn, col0);
   }
   __device__ __forceinline__ void finish() {
     if (!active) return;
@@ -319,12 +318,9 @@ struct NbnnEpilogue {
     if (active && run != INT32_MAX) atomicMin(dst + cls, __float2int_rn(__int_as_float(run)));
     run = INT32_MAX;
   }
-  __device__ __forceinline__ void group(const uint32_t (&v)[32], int64_t col0) {
+  __device__ __forceinline__ void group(const uint32_t (&v)[32], uint32_t mn, int64_t col0) {
     if (col0 + 32 <= next) {  // the whole group lies in class cls
-      int32_t mn = (int32_t)v[0];
-#pragma unroll
-      for (int j = 1; j < 32; ++j) mn = min(mn, (int32_t)v[j]);
-      run = min(run, mn);
+      run = min(run, (int32_t)mn);
       return;
     }
 #pragma unroll 1
@@ -515,24 +511,26 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
       const uint32_t taddr = tmem_base + lane_addr + b * kAccCols + half * kEpiCols;
       const int64_t col0 = j_begin + (int64_t)t * kBN + half * kEpiCols;
       {
-        uint32_t v0[32], v1[32];
-        tmem_ld_32x32b_x32(taddr, v0);
-        tmem_ld_32x32b_x32(taddr + 32, v1);
-        tmem_ld_wait(v0);
+        uint32_t v0[32], v1[32], m0, m1;
+        tmem_ld_min_32x32b_x32(taddr, v0, m0);
+        tmem_ld_min_32x32b_x32(taddr + 32, v1, m1);
+        tmem_ld_wait(v0, m0);
         reg_fence(v1);
-        epi.group(v0, col0);
-        epi.group(v1, col0 + 32);
+        asm volatile("" : "+r"(m1));
+        epi.group(v0, m0, col0);
+        epi.group(v1, m1, col0 + 32);
       }
       {
-        uint32_t v2[32], v3[32];
-        tmem_ld_32x32b_x32(taddr + 64, v2);
-        tmem_ld_32x32b_x32(taddr + 96, v3);
-        tmem_ld_wait(v2);
+        uint32_t v2[32], v3[32], m2, m3;
+        tmem_ld_min_32x32b_x32(taddr + 64, v2, m2);
+        tmem_ld_min_32x32b_x32(taddr + 96, v3, m3);
+        tmem_ld_wait(v2, m2);
         reg_fence(v3);
+        asm volatile("" : "+r"(m3));
         tc_fence_before();
         mbar_arrive(bars.tempty(b));
-        epi.group(v2, col0 + 64);
-        epi.group(v3, col0 + 96);
+        epi.group(v2, m2, col0 + 64);
+        epi.group(v3, m3, col0 + 96);
       }
     }
     epi.finish();

@@ -167,6 +167,22 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
       : "memory");
 }
 
+// The same load with a reduction: mn also receives the minimum of the 32
+// columns as unsigned 32-bit integers (which orders non-negative float bit
+// patterns like the floats).
+__device__ __forceinline__ void tmem_ld_min_32x32b_x32(uint32_t taddr, uint32_t (&r)[32], uint32_t& mn) {
+  asm volatile(
+      "tcgen05.ld.red.sync.aligned.32x32b.x32.min.u32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, %32, [%33];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(mn)
+      : "r"(taddr)
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Wait for this thread's TMEM loads; the registers are passed through the
@@ -180,6 +196,12 @@ __device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
         "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
       :
       : "memory");
+}
+
+// The wait for loads that also produced a reduction value.
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32], uint32_t& mn) {
+  tmem_ld_wait(r);
+  asm volatile("" : "+r"(mn));
 }
 
 // Orders later uses of r after every preceding volatile asm (e.g. a TMEM wait
