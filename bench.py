@@ -182,16 +182,29 @@ def measured_peaks() -> tuple[dict, str]:
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def traffic_per_launch(n_query_rows: int) -> float | None:
-    """DRAM bytes per launch of the search kernel from a committed ncu capture,
-    scaled to this launch by query rows; None if the kernel changed since."""
+def traffic_per_launch(kernel: str, n_query_rows: int) -> float | None:
+    """DRAM bytes per launch of a search kernel from a committed ncu capture,
+    scaled to this launch by query rows; None if the kernel changed since or
+    was not captured."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     with open(TRAFFIC_FILE) as f:
         t = json.load(f)
-    if t.get("kernel_hash") != kernel_hash():
+    if t.get("kernel_hash") != kernel_hash() or kernel not in t.get("kernels", {}):
         return None
-    return t["dram_bytes_per_launch"] * n_query_rows / t["query_rows"]
+    k = t["kernels"][kernel]
+    return k["dram_bytes_per_launch"] * n_query_rows / k["query_rows"]
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest value of x over all ranks (x itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_init():
@@ -284,14 +297,6 @@ def run_ours(args, w):
             import torch.distributed as dist
             dist.barrier()
 
-    def max_over_ranks(x):
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([x], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return x
-
     def timed(fn, steps):
         """Device time of `steps` calls of fn (CUDA events on the launching stream) and the call profile."""
         index.profile_enable(True)
@@ -308,7 +313,7 @@ def run_ours(args, w):
         index.sync()
         prof = index.profile_read()
         index.profile_enable(False)
-        return max_over_ranks(ev0.elapsed_time(ev1) / 1e3), prof
+        return max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dev), prof
 
     gpu_uuid = None
     try:
@@ -322,8 +327,7 @@ def run_ours(args, w):
     value = M * args.steps * world / elapsed
     peaks, peak_src = measured_peaks()
     roofline = scan_roofline(prof, w.n_ref, M, peaks, peak_src, local, shortlist)
-    if not shortlist:
-        roofline["traffic"] = traffic_per_launch(M) if local else None
+    roofline["traffic"] = traffic_per_launch(roofline["kernel"], M)
 
     e2e = None
     if not args.no_e2e:
@@ -338,7 +342,7 @@ def run_ours(args, w):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             index.classify_host(qn, on, hk, tn, cn, shortlist=shortlist)
-        e2e_dt = max_over_ranks(time.perf_counter() - t0)
+        e2e_dt = max_over_ranks(time.perf_counter() - t0, dev)
         api = "lnbnn_classify_fp8_host" if shortlist else ("lnbnn" if local else "nbnn") + "_classify_host"
         e2e = {"value": M * args.steps * world / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(q.nbytes + off.nbytes),
                "d2h_bytes_per_step": int(tn.nbytes + cn.nbytes),
@@ -365,6 +369,7 @@ def run_ours(args, w):
                          "images_per_s": n_img * args.steps * world / el8, "ms_per_step": el8 / args.steps * 1e3,
                          "roofline": scan_roofline(prof8, w.n_ref, M, peaks, peak_src, True, m_short),
                          "gpu_launches": int(prof8["kernel_launches"])}
+            fp8_block["roofline"]["traffic"] = traffic_per_launch(fp8_block["roofline"]["kernel"], M)
         index.sync()
         sample = min(M, 8192)
         i_x, _ = index.knn_search(q_d[:sample], k + 1)

@@ -11,6 +11,40 @@ namespace {
 // the warp minimum is written and the list that held it advances.  Keys are
 // unique (each holds a distinct reference row), except the empty key.
 constexpr int kMergeWarps = 4;
+// Up to this many lists a thread merges a row on its own (few lists: the
+// warp form would leave most lanes idle).
+constexpr int kThreadMergeLists = 8;
+
+__global__ void merge_lists_thread_kernel(const uint64_t* __restrict__ lists, int n_lists, int64_t m, int64_t stride,
+                                          int K1, uint64_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  int pos[kThreadMergeLists];
+  uint64_t head[kThreadMergeLists];
+#pragma unroll
+  for (int l = 0; l < kThreadMergeLists; ++l) {
+    pos[l] = 0;
+    head[l] = l < n_lists ? lists[((int64_t)l * stride + i) * K1] : kEmptyKey;
+  }
+  for (int t = 0; t < K1; ++t) {
+    uint64_t best = head[0];
+    int bl = 0;
+#pragma unroll
+    for (int l = 1; l < kThreadMergeLists; ++l)
+      if (head[l] < best) {
+        best = head[l];
+        bl = l;
+      }
+    out[i * K1 + t] = best;
+    if (best == kEmptyKey) continue;
+#pragma unroll
+    for (int l = 0; l < kThreadMergeLists; ++l)
+      if (l == bl) {
+        ++pos[l];
+        head[l] = pos[l] < K1 ? lists[((int64_t)l * stride + i) * K1 + pos[l]] : kEmptyKey;
+      }
+  }
+}
 
 __global__ void __launch_bounds__(32 * kMergeWarps)
     merge_lists_kernel(const uint64_t* __restrict__ lists, int n_lists, int64_t m, int64_t stride, int K1,
@@ -160,6 +194,10 @@ cudaError_t launch_merge_lists(const uint64_t* lists, int splits, int64_t m, int
                                cudaStream_t s) {
   if (m == 0) return cudaSuccess;
   if (splits < 1 || splits > 32 * kMaxListsPerLane) return cudaErrorInvalidValue;
+  if (splits <= kThreadMergeLists) {
+    merge_lists_thread_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(lists, splits, m, stride, K1, out);
+    return cudaGetLastError();
+  }
   merge_lists_kernel<<<(unsigned)((m + kMergeWarps - 1) / kMergeWarps), 32 * kMergeWarps, 0, s>>>(lists, splits, m,
                                                                                                 stride, K1, out);
   return cudaGetLastError();
