@@ -14,13 +14,13 @@
 // row's current (k+1)-th distance, and keeps the k+1 smallest (distance, row)
 // pairs.  The distance matrix never leaves the SM.
 //
-// With kTcCluster > 1, the CTAs of a cluster (consecutive query tiles, same
-// reference split) share every reference tile: each loads its share of each
-// K-chunk and multicasts it into all of them, and a stage is refilled only
-// after every CTA's MMAs have consumed it.  That divides the reference
-// traffic per SM by the cluster size but couples the CTAs, each stage waiting
-// for the slowest; measured on the 256-class workload, single CTAs were ~5%
-// faster, so kTcCluster is 1.
+// With a cluster size above 1 (per operand format: kTcCluster for the exact
+// scan, kTcCoarseCluster for the FP8 coarse pass), the CTAs of a cluster
+// (consecutive query tiles, same reference split) share every reference tile:
+// each loads its share of each K-chunk and multicasts it into all of them, and
+// a stage is refilled only after every CTA's MMAs have consumed it.  That
+// divides the reference traffic per SM by the cluster size but couples the
+// CTAs, each stage waiting for the slowest.
 //
 // The same scan runs the coarse pass of the FP8 shortlist search: operands
 // are the E4M3 roundings of the coordinates shifted by -64 (queries scaled by
@@ -43,7 +43,9 @@
 //                        taking a 128-column half of every tile with one
 //                        thread per query row (TMEM lane); each keeps its own
 //                        sorted list of the k+1 nearest (in registers for
-//                        k+1 <= 32, otherwise a heap in global memory); two
+//                        k+1 <= 64, otherwise a heap in global memory; for
+//                        33..64 one warp per quarter takes all 256 columns,
+//                        to have the registers); two
 //                        256-column FP32 accumulators in flight; each
 //                        32-column load also returns the columns' minimum
 // Every wait is bounded; on expiry the CTA records a timeout in the index's
@@ -60,7 +62,6 @@ namespace {
 using namespace sm103;
 
 constexpr int kBM = kTcQueryTile;         // query rows per CTA (MMA M)
-constexpr int kCluster = kTcCluster;      // CTAs sharing each reference tile by multicast
 constexpr int kBN = kTcRefTile;           // reference rows per tile (MMA N)
 constexpr int kBK = 64;                   // BF16 K elements per 128-byte swizzle row
 constexpr int kKChunks = kDim / kBK;      // K-chunks of the BF16 operand (shared memory is laid out for these)
@@ -71,14 +72,14 @@ constexpr uint32_t kAExtBytes = kBM * kExt * 2;      // 4 KB
 constexpr uint32_t kBChunkBytes = kBN * kBK * 2;     // 32 KB
 constexpr uint32_t kBExtBytes = kBN * kExt * 2;      // 8 KB
 constexpr uint32_t kStageBytes = kBChunkBytes + kBExtBytes;
-constexpr int kBRowsPerCta = kBN / kCluster;                 // rows of each tile one CTA loads
-constexpr uint32_t kBChunkPart = kBChunkBytes / kCluster;   // its share of a chunk
-constexpr uint32_t kBExtPart = kBExtBytes / kCluster;       // its share of the extension
-constexpr int kEpiPerQuarter = kTcListsPerSplit;  // epilogue warps per TMEM lane quarter
-constexpr int kEpiWarps = 4 * kEpiPerQuarter;
-constexpr int kEpiCols = kBN / kEpiPerQuarter;     // columns of a tile per epilogue warp
-constexpr int kThreads = 64 + 32 * kEpiWarps;
-static_assert(kEpiCols == 128, "each epilogue warp reads its slice as four 32-column TMEM loads");
+// Threads of a CTA whose epilogue has `epq` warps per TMEM lane quarter: the
+// producer warp, the MMA warp and 4 * epq epilogue warps.
+constexpr int threads_for(int epq) { return 64 + 32 * 4 * epq; }
+// Registers per thread above which the CTA's warps cannot share one SM (the
+// sub-partition holding the most warps has 16,384 registers).
+constexpr int max_regs_for(int epq) {
+  return (16384 / (32 * ((2 + 4 * epq + 3) / 4))) / 8 * 8 > 255 ? 255 : (16384 / (32 * ((2 + 4 * epq + 3) / 4))) / 8 * 8;
+}
 constexpr uint32_t kAccCols = kBN;        // FP32 columns per accumulator
 constexpr uint32_t kTmemCols = 2 * kAccCols;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
@@ -98,6 +99,7 @@ static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 // per operand row and one MMA consumes 32 bytes of it.
 struct FmtBf16 {  // exact search: 128 BF16 coordinates, two chunks
   static constexpr int kChunks = 2;
+  static constexpr int kCluster = kTcCluster;  // CTAs sharing each reference tile by multicast
   static constexpr bool kExtFirst = false;
   static constexpr uint32_t kIdesc = idesc_bf16_f32(kBM, kBN);
   static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
@@ -106,6 +108,7 @@ struct FmtBf16 {  // exact search: 128 BF16 coordinates, two chunks
 };
 struct FmtE4m3 {  // coarse pass: 128 E4M3 coordinates, one chunk
   static constexpr int kChunks = 1;
+  static constexpr int kCluster = kTcCoarseCluster;
   static constexpr bool kExtFirst = true;
   static constexpr uint32_t kIdesc = idesc_e4m3_f32(kBM, kBN);
   static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
@@ -248,7 +251,7 @@ __device__ __forceinline__ void scan_group(RegList<KMAX>& L, TopK& top, int32_t&
 // KMAX > 0: per-row lists in registers (K1 <= KMAX); KMAX = 0: heaps in global memory.
 // What the epilogue writes (see the two epilogues below).
 struct ScanOut {
-  uint64_t* lists;           // kNN: sorted lists, [splits * kTcListsPerSplit][stride][K1]
+  uint64_t* lists;           // kNN: sorted lists, [splits * lists per split][stride][K1]
   int64_t stride;
   int K1;
   int32_t* mins;             // NBNN: per (query row, class) minimum distance, [m_pad][C], atomicMin
@@ -260,6 +263,7 @@ struct ScanOut {
 // thread sees (Alg. 2's NN(d, k+1) restricted to a slice of the references).
 template <int KMAX>
 struct KnnEpilogue {
+  static constexpr int kWarpsPerQuarter = KMAX == kTcWideRegListMax ? 1 : 2;
   RegList<KMAX> L;
   TopK top;
   int32_t thr;
@@ -294,6 +298,7 @@ struct KnnEpilogue {
 // class).  All lanes of a warp see the same columns, so the class bookkeeping
 // is uniform across the warp.
 struct NbnnEpilogue {
+  static constexpr int kWarpsPerQuarter = 2;
   int32_t* dst;          // mins + row * C
   const int64_t* class_off;
   int64_t n_ref;
@@ -339,12 +344,20 @@ struct NbnnEpilogue {
 };
 
 template <class Fmt, class Epilogue>
-__global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
+__global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __cluster_dims__(Fmt::kCluster, 1, 1)
     tc_scan_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_qe,
                    const __grid_constant__ CUtensorMap tmap_r, const __grid_constant__ CUtensorMap tmap_re, int64_t m,
                    int64_t n_ref, int64_t split_len, ScanOut out, uint32_t* __restrict__ dev_err,
                    unsigned long long* __restrict__ stats) {
   constexpr int KC = Fmt::kChunks;
+  constexpr int kEpiPerQuarter = Epilogue::kWarpsPerQuarter;  // epilogue warps per TMEM lane quarter
+  constexpr int kEpiWarps = 4 * kEpiPerQuarter;
+  constexpr int kEpiCols = kBN / kEpiPerQuarter;  // columns of a tile per epilogue warp
+  constexpr int kRounds = kEpiCols / 64;          // rounds of two 32-column loads per tile
+  constexpr int kCluster = Fmt::kCluster;
+  constexpr int kBRowsPerCta = kBN / kCluster;                 // rows of each tile one CTA loads
+  constexpr uint32_t kBChunkPart = kBChunkBytes / kCluster;   // its share of a chunk
+  constexpr uint32_t kBExtPart = kBExtBytes / kCluster;       // its share of the extension
   static_assert(KC <= kKChunks && kStages % KC == 0, "a tile's chunks map to fixed stage parities");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -493,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
   } else {
     // ------------------------------------------------------------- epilogue
     const int quarter = warp & 3;          // this warp may read TMEM lanes [32*quarter, 32*quarter+32)
-    const int half = (warp - 2) >> 2;      // its 128-column half of every tile
+    const int half = (warp - 2) >> 2;      // its column slice of every tile
     const int64_t row = m0 + quarter * 32 + lane;
     const bool active = row < m;
     Epilogue epi(out, (int)blockIdx.y * kEpiPerQuarter + half, row, active, j_begin + half * kEpiCols);
@@ -506,31 +519,24 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(kCluster, 1, 1)
         break;
       }
       tc_fence_after();
-      // two rounds of 64 columns; the accumulator goes back as soon as the
-      // second round is in registers
+      // rounds of 64 columns; the accumulator goes back as soon as the last
+      // round is in registers
       const uint32_t taddr = tmem_base + lane_addr + b * kAccCols + half * kEpiCols;
       const int64_t col0 = j_begin + (int64_t)t * kBN + half * kEpiCols;
-      {
-        uint32_t v0[32], v1[32], m0, m1;
-        tmem_ld_min_32x32b_x32(taddr, v0, m0);
-        tmem_ld_min_32x32b_x32(taddr + 32, v1, m1);
-        tmem_ld_wait(v0, m0);
+#pragma unroll
+      for (int r = 0; r < kRounds; ++r) {
+        uint32_t v0[32], v1[32], mn0, mn1;
+        tmem_ld_min_32x32b_x32(taddr + 64 * r, v0, mn0);
+        tmem_ld_min_32x32b_x32(taddr + 64 * r + 32, v1, mn1);
+        tmem_ld_wait(v0, mn0);
         reg_fence(v1);
-        asm volatile("" : "+r"(m1));
-        epi.group(v0, m0, col0);
-        epi.group(v1, m1, col0 + 32);
-      }
-      {
-        uint32_t v2[32], v3[32], m2, m3;
-        tmem_ld_min_32x32b_x32(taddr + 64, v2, m2);
-        tmem_ld_min_32x32b_x32(taddr + 96, v3, m3);
-        tmem_ld_wait(v2, m2);
-        reg_fence(v3);
-        asm volatile("" : "+r"(m3));
-        tc_fence_before();
-        mbar_arrive(bars.tempty(b));
-        epi.group(v2, m2, col0 + 64);
-        epi.group(v3, m3, col0 + 96);
+        asm volatile("" : "+r"(mn1));
+        if (r == kRounds - 1) {
+          tc_fence_before();
+          mbar_arrive(bars.tempty(b));
+        }
+        epi.group(v0, mn0, col0 + 64 * r);
+        epi.group(v1, mn1, col0 + 64 * r + 32);
       }
     }
     epi.finish();
@@ -598,14 +604,16 @@ bool encode_operand(CUtensorMap* main, CUtensorMap* ext, const void* bf, const v
 
 bool make_tc_tensor_maps(const __nv_bfloat16* ref_bf, const __nv_bfloat16* sref_bf, const __nv_bfloat16* ref_ext,
                          const __nv_bfloat16* sref_ext, int64_t n_pad, TcTensorMaps* out) {
-  return encode_operand(&out->ref, &out->ref_ext, ref_bf, ref_ext, (uint64_t)n_pad, kBRowsPerCta) &&
-         encode_operand(&out->sref, &out->sref_ext, sref_bf, sref_ext, (uint64_t)n_pad, kBRowsPerCta);
+  constexpr uint32_t rows = kBN / FmtBf16::kCluster;  // the rows of a tile one CTA of a cluster loads
+  return encode_operand(&out->ref, &out->ref_ext, ref_bf, ref_ext, (uint64_t)n_pad, rows) &&
+         encode_operand(&out->sref, &out->sref_ext, sref_bf, sref_ext, (uint64_t)n_pad, rows);
 }
 
 bool make_tc_tensor_maps_e4m3(const uint8_t* ref_f8, const __nv_bfloat16* ref_f8_ext, int64_t n_pad,
                               TcTensorMaps* out) {
-  return encode_e4m3(&out->f8, ref_f8, (uint64_t)n_pad, kBRowsPerCta) &&
-         encode_bf16(&out->f8_ext, ref_f8_ext, (uint64_t)n_pad, kExt, kExt, kBRowsPerCta, CU_TENSOR_MAP_SWIZZLE_32B);
+  constexpr uint32_t rows = kBN / FmtE4m3::kCluster;
+  return encode_e4m3(&out->f8, ref_f8, (uint64_t)n_pad, rows) &&
+         encode_bf16(&out->f8_ext, ref_f8_ext, (uint64_t)n_pad, kExt, kExt, rows, CU_TENSOR_MAP_SWIZZLE_32B);
 }
 
 namespace {
@@ -616,7 +624,7 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const voi
                         int64_t split_len, const ScanOut& out, uint32_t* dev_err, unsigned long long* stats,
                         cudaStream_t s) {
   if (m == 0) return cudaSuccess;
-  if (m_pad % (kBM * kCluster) != 0 || split_len % kBN != 0) return cudaErrorInvalidValue;
+  if (m_pad % (kBM * Fmt::kCluster) != 0 || split_len % kBN != 0) return cudaErrorInvalidValue;
   CUtensorMap tq, tqe;
   const bool ok = Fmt::kChunks == 1
                       ? encode_e4m3(&tq, qop, (uint64_t)m_pad, kBM) &&
@@ -624,21 +632,18 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const voi
                       : encode_operand(&tq, &tqe, qop, qext, (uint64_t)m_pad, kBM);
   if (!ok) return cudaErrorInvalidValue;
   dim3 grid((unsigned)(m_pad / kBM), (unsigned)splits);
-  tc_scan_kernel<Fmt, Epilogue><<<grid, kThreads, kSmemBytes, s>>>(tq, tqe, tr, tre, m, n_ref, split_len, out,
+  tc_scan_kernel<Fmt, Epilogue><<<grid, threads_for(Epilogue::kWarpsPerQuarter), kSmemBytes, s>>>(
+      tq, tqe, tr, tre, m, n_ref, split_len, out,
                                                                    dev_err, stats);
   return cudaGetLastError();
 }
-
-// Registers per thread above which the 10 warps of a CTA cannot share one SM
-// (three warps on a sub-partition of 16,384 registers).
-constexpr int kMaxRegs = 168;
 
 template <class Fmt, class Epilogue>
 cudaError_t prepare_one() {
   cudaFuncAttributes a;
   cudaError_t e = cudaFuncGetAttributes(&a, tc_scan_kernel<Fmt, Epilogue>);
   if (e != cudaSuccess) return e;
-  if (a.numRegs > kMaxRegs) return cudaErrorInvalidKernelImage;
+  if (a.numRegs > max_regs_for(Epilogue::kWarpsPerQuarter)) return cudaErrorInvalidKernelImage;
   return cudaFuncSetAttribute(tc_scan_kernel<Fmt, Epilogue>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kSmemBytes);
 }
@@ -648,10 +653,12 @@ cudaError_t prepare_one() {
 cudaError_t prepare_tc_kernels() {
   cudaError_t e = prepare_one<FmtBf16, KnnEpilogue<kTcRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnEpilogue<kTcCoarseRegListMax>>();
+  if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnEpilogue<kTcWideRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnEpilogue<0>>();
   if (e == cudaSuccess) e = prepare_one<FmtBf16, NbnnEpilogue>();
   if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<kTcRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<kTcCoarseRegListMax>>();
+  if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<kTcWideRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<0>>();
   return e;
 }
@@ -672,6 +679,9 @@ cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv
   if (K1 <= kTcCoarseRegListMax)
     return launch_scan<FmtBf16, KnnEpilogue<kTcCoarseRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
                                                                   split_len, out, dev_err, stats, s);
+  if (K1 <= kTcWideRegListMax)
+    return launch_scan<FmtBf16, KnnEpilogue<kTcWideRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
+                                                                split_len, out, dev_err, stats, s);
   return launch_scan<FmtBf16, KnnEpilogue<0>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len, out, dev_err,
                                               stats, s);
 }
@@ -689,6 +699,9 @@ cudaError_t launch_coarse_tc(const TcTensorMaps& maps, const uint8_t* qf8, const
   if (K1 <= kTcCoarseRegListMax)
     return launch_scan<FmtE4m3, KnnEpilogue<kTcCoarseRegListMax>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref,
                                                                   splits, split_len, out, dev_err, stats, s);
+  if (K1 <= kTcWideRegListMax)
+    return launch_scan<FmtE4m3, KnnEpilogue<kTcWideRegListMax>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref,
+                                                                splits, split_len, out, dev_err, stats, s);
   return launch_scan<FmtE4m3, KnnEpilogue<0>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref, splits, split_len,
                                               out, dev_err, stats, s);
 }

@@ -14,18 +14,28 @@ constexpr int kTcRefTile = 256;
 // Query rows per CTA (the MMA M extent) and CTAs per cluster; the query
 // operand must be padded to kTcQueryTile * kTcCluster rows.
 constexpr int kTcQueryTile = 128;
+// Exact scan: single CTAs (pairs measured ~5% slower: it is tensor-bound).
+// FP8 coarse pass: pairs (measured 4.5% faster on the 256-class workload:
+// half the reference traffic, less DRAM power, a higher SM clock).
 constexpr int kTcCluster = 1;
+constexpr int kTcCoarseCluster = 2;
 static_assert(kQueryPad % (kTcQueryTile * kTcCluster) == 0, "query padding must cover whole clusters");
-// Epilogue warps per TMEM lane quarter.  Each owns a column slice of every
-// tile and keeps its own top-K1 list per query row, so one reference split
-// yields this many sorted lists per row (merged afterwards).
-constexpr int kTcListsPerSplit = 2;
-// Largest K1 kept in registers: lists of up to 16 use a 16-entry register
-// list (the fewest registers), up to 32 a 32-entry one; longer lists live in
-// global memory as heaps.
+// Query rows of the FP8 coarse pass are padded to whole clusters.
+constexpr int kCoarseQueryPad = kTcQueryTile * kTcCoarseCluster > kQueryPad ? kTcQueryTile * kTcCoarseCluster
+                                                                             : kQueryPad;
+// Lists of the k+1 (or shortlist) nearest per query row: up to 16 entries a
+// 16-entry register list (the fewest registers), up to 32 a 32-entry one, up
+// to 64 a 64-entry one, longer ones a heap in global memory.
 constexpr int kTcRegListMax = 16;
 constexpr int kTcCoarseRegListMax = 32;
-static_assert(kTcListsPerSplit > 1, "the shortlist search merges into a buffer apart from the lists");
+constexpr int kTcWideRegListMax = 64;
+// Epilogue warps per TMEM lane quarter.  Each owns a column slice of every
+// tile and keeps its own top-K1 list per query row, so one reference split
+// yields this many sorted lists per row (merged afterwards).  Two, except for
+// the 64-entry register lists, which need one warp per quarter (all 256
+// columns of a tile) to have the registers.
+constexpr int kTcListsPerSplit = 2;
+inline int tc_lists_per_split(int K1) { return K1 > kTcCoarseRegListMax && K1 <= kTcWideRegListMax ? 1 : 2; }
 
 // TMA descriptors over an index's BF16 reference operands (caller's row order
 // and class-sorted order).  Encoded once at index creation.
@@ -88,8 +98,8 @@ bool make_tc_tensor_maps_e4m3(const uint8_t* ref_f8, const __nv_bfloat16* ref_f8
 
 // Exact top-K1 search on tensor cores.  qbf: BF16 -2q operand [m_pad, 128];
 // qext: its K-extension [m_pad, 16].  Split s scans reference rows
-// [s * split_len, min((s+1) * split_len, n_ref)) and writes kTcListsPerSplit
-// sorted lists per query row i, list w at lists[((s * kTcListsPerSplit + w) *
+// [s * split_len, min((s+1) * split_len, n_ref)) and writes L =
+// tc_lists_per_split(K1) sorted lists per query row i, list w at lists[((s * L + w) *
 // stride + i) * K1]; the K1 smallest keys of their union are the split's answer.
 cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf,
                           const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,

@@ -187,7 +187,7 @@ bool k_ok(const lnbnn_index* ix, int32_t k, int extra) {
 // Most reference splits of one launch: two CTAs per SM for a single query
 // tile, within what the list merge takes (two lists per split).
 int64_t max_splits(const lnbnn_index* ix) {
-  return std::min<int64_t>(2 * (int64_t)ix->sm_count, 32 * kMaxListsPerLane / kTcListsPerSplit);
+  return std::min<int64_t>(2 * (int64_t)ix->sm_count, 32 * kMaxListsPerLane / 2);
 }
 
 int choose_splits(const lnbnn_index* ix, int64_t m_pad) {
@@ -205,9 +205,9 @@ struct KnnPlan {
 
 // splits = 0: the modelled best; otherwise that many (an upper bound after
 // rounding the split length to whole tiles).
-KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, int splits = 0) {
+KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, int splits = 0, int64_t pad = kQueryPad) {
   KnnPlan p{};
-  p.m_pad = round_up(m, kQueryPad);
+  p.m_pad = round_up(m, pad);
   p.K1 = K1;
   p.splits = splits > 0 ? splits : choose_splits(ix, p.m_pad);
   p.split_len = round_up((ix->n_ref + p.splits - 1) / p.splits, kTcRefTile);
@@ -216,9 +216,9 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, int splits = 0) {
   p.off_qnorm = c.take<int32_t>(p.m_pad);
   p.off_qbf = c.take<__nv_bfloat16>(p.m_pad * kDim);
   p.off_qext = c.take<__nv_bfloat16>(p.m_pad * kExt);
-  p.lists = p.splits * kTcListsPerSplit;
+  p.lists = p.splits * tc_lists_per_split(K1);
   p.off_lists = c.take<uint64_t>((size_t)p.lists * p.m_pad * K1);
-  p.off_merged = p.lists > 1 ? c.take<uint64_t>((size_t)p.m_pad * K1) : p.off_lists;
+  p.off_merged = c.take<uint64_t>((size_t)p.m_pad * K1);  // apart from the lists even for one list (rerank)
   p.bytes = c.off;
   return p;
 }
@@ -266,6 +266,7 @@ size_t scratch_bound(const lnbnn_index* ix, int64_t max_q, int K1) {
     const int64_t mm = std::min(m, max_q);
     const int64_t hi = max_splits_for(round_up(mm, kQueryPad) / kTcQueryTile, ix->n_ref, ix->sm_count, max_splits(ix));
     b = std::max(b, plan_knn(ix, mm, K1, (int)hi).bytes);
+    b = std::max(b, plan_knn(ix, mm, K1, (int)hi, kCoarseQueryPad).bytes);
     b = std::max(b, plan_nbnn(ix, mm).bytes);
   }
   return b;
@@ -294,7 +295,7 @@ lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_
     CK(launch_merge_lists(part, p.lists, m, p.m_pad, K1, merged, s));
     prof.launched(1);
   }
-  *lists = merged;
+  *lists = p.lists > 1 ? merged : part;
   return LNBNN_OK;
 }
 
@@ -302,7 +303,7 @@ lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_
 // merge, exact rerank; *lists receives m sorted lists of K1 exact keys.
 lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_t m, int K1, int M1,
                          cudaStream_t s, const uint64_t** lists, CallProfile& prof) {
-  KnnPlan p = plan_knn(ix, m, M1);
+  KnnPlan p = plan_knn(ix, m, M1, 0, kCoarseQueryPad);
   char* ws = nullptr;
   lnbnn_status st = scratch.get(p.bytes, &ws);
   if (st != LNBNN_OK) return st;
@@ -318,12 +319,18 @@ lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, in
                       ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, s));
   prof.launched(1, true);
   prof.mark(2);
-  // lists > 1 always (kTcListsPerSplit > 1): merged is apart from part, which
-  // then receives the reranked lists
-  CK(launch_merge_lists(part, p.lists, m, p.m_pad, M1, merged, s));
-  CK(launch_rerank(merged, m, M1, q, ix->ref_u8, ix->n_ref, K1, part, s));
-  prof.launched(2);
-  *lists = part;
+  // the shortlist is the merged lists (or the one list); the reranked lists
+  // go to the other buffer
+  if (p.lists > 1) {
+    CK(launch_merge_lists(part, p.lists, m, p.m_pad, M1, merged, s));
+    CK(launch_rerank(merged, m, M1, q, ix->ref_u8, ix->n_ref, K1, part, s));
+    prof.launched(2);
+    *lists = part;
+  } else {
+    CK(launch_rerank(part, m, M1, q, ix->ref_u8, ix->n_ref, K1, merged, s));
+    prof.launched(1);
+    *lists = merged;
+  }
   return LNBNN_OK;
 }
 

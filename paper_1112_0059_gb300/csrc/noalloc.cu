@@ -102,7 +102,7 @@ extern "C" LNBNN_API lnbnn_status knn_search_noalloc(const uint8_t* ref, int64_t
   const size_t o_qn = L.take<int32_t>((size_t)m_pad);
   const size_t o_qbf = L.take<__nv_bfloat16>((size_t)m_pad * kDim);
   const size_t o_qext = L.take<__nv_bfloat16>((size_t)m_pad * kExt);
-  const int64_t n_lists = splits * kTcListsPerSplit;
+  const int64_t n_lists = splits * tc_lists_per_split(k);
   const size_t o_lists = L.take<uint64_t>((size_t)n_lists * m_pad * k);
   const size_t o_merged = n_lists > 1 ? L.take<uint64_t>((size_t)m_pad * k) : o_lists;
   if (L.off > (size_t)LNBNN_NOALLOC_SCRATCH_BYTES) return LNBNN_ERR_SCRATCH_LIMIT;
