@@ -143,6 +143,16 @@ static int32_t e4m3_round(int32_t x) {
   return x < 0 ? -r : r;
 }
 
+/* E4M3 rounding of every shifted coordinate value, x~ = e4m3_round(x - 64)
+ * for x = 0..255: a table of e4m3_round, filled before any search starts
+ * (the searches only read it), so that a pair costs no more than a lookup
+ * per coordinate. */
+static int32_t rounded_shifted[256];
+
+static void fill_rounded_shifted(void) {
+  for (int x = 0; x < 256; ++x) rounded_shifted[x] = e4m3_round(x - ORACLE_SHIFT);
+}
+
 /* coarse(q, r) = ||q'||^2 + ||r'||^2 - 2 q~ . r~  with x' = x - 64 and x~ its
  * E4M3 rounding. */
 static int64_t coarse(const uint8_t *q, const uint8_t *r) {
@@ -151,7 +161,7 @@ static int64_t coarse(const uint8_t *q, const uint8_t *r) {
     const int32_t qs = (int32_t)q[t] - ORACLE_SHIFT, rs = (int32_t)r[t] - ORACLE_SHIFT;
     nq += qs * qs;
     nr += rs * rs;
-    dot += (int64_t)e4m3_round(qs) * e4m3_round(rs);
+    dot += (int64_t)rounded_shifted[q[t]] * rounded_shifted[r[t]];
   }
   return nq + nr - 2 * dot;
 }
@@ -505,6 +515,7 @@ int oracle_e4m3_round(const int32_t *x, int64_t n, int32_t *out) {
 /* Full matrix of coarse values, out[i*N + j] = coarse(q_i, r_j) (tiny inputs). */
 int oracle_coarse_matrix(const uint8_t *ref, int64_t N, const uint8_t *q, int64_t M, int64_t *out) {
   if (N < 0 || M < 0) return ORACLE_ERR_ARG;
+  fill_rounded_shifted();
   for (int64_t i = 0; i < M; ++i)
     for (int64_t j = 0; j < N; ++j) out[i * N + j] = coarse(q + i * ORACLE_D, ref + j * ORACLE_D);
   return ORACLE_OK;
@@ -514,6 +525,7 @@ int oracle_coarse_matrix(const uint8_t *ref, int64_t N, const uint8_t *q, int64_
 int oracle_knn_coarse(const uint8_t *ref, int64_t N, const uint8_t *q, int64_t M, int32_t kk, int32_t m,
                       int64_t *dist, int64_t *idx, int nthreads) {
   if (N < 1 || M < 0 || kk < 1 || (int64_t)kk > N || m < kk) return ORACLE_ERR_K;
+  fill_rounded_shifted();
   job_t J;
   memset(&J, 0, sizeof J);
   J.kind = JOB_KNN_COARSE;
@@ -532,5 +544,6 @@ int oracle_knn_coarse(const uint8_t *ref, int64_t N, const uint8_t *q, int64_t M
 int oracle_lnbnn_coarse(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
                         const uint8_t *q, const int64_t *offsets, int64_t n_img, int32_t k, int32_t m,
                         int64_t *totals, int32_t *classes, int nthreads) {
+  fill_rounded_shifted();
   return classify(JOB_LNBNN_COARSE, ref, labels, N, C, q, offsets, n_img, k, m, totals, classes, nthreads);
 }
