@@ -147,3 +147,51 @@ def test_errors_and_workspace(lnbnn):
         # host-buffer form
         th, ch = ix.classify_host(q, off, 10, shortlist=16)
         assert np.array_equal(th, ot) and np.array_equal(ch, oc)
+
+
+# ------------------------------------------------------------------ full-size workloads (sampled)
+
+def _sample_rows(M, n, seed):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([[0, M - 1], rng.integers(0, M, size=n)]))
+
+
+def test_fp8_caltech256_full_size_sampled(lnbnn):
+    """The bench's launch configuration (all 750k query rows in one call, one
+    reference split, clusters of two CTAs) against the oracle on sampled rows."""
+    from paper_1112_0059_gb300 import synth
+    w = synth.workload("caltech256-like")
+    ref, labels = synth.reference_set(w)
+    q, off, _ = synth.query_set(w)
+    rows = _sample_rows(len(q), 14, 21)
+    with lnbnn.Index(dev(ref), dev(labels), w.n_classes) as ix:
+        ix.prepare_fp8()
+        idx, dist = ix.knn_search(dev(q), 11, shortlist=32)
+        ix.sync()
+    od, oj = oracle.knn_coarse(ref, q[rows], 11, 32)
+    assert np.array_equal(idx.cpu().numpy()[rows], oj.astype(np.int32))
+    assert np.array_equal(dist.cpu().numpy()[rows], od.astype(np.int32))
+
+
+def test_fp8_caltech101_full_size(lnbnn):
+    from paper_1112_0059_gb300 import synth
+    w = synth.workload("caltech101-like")
+    ref, labels = synth.reference_set(w)
+    q, off, _ = synth.query_set(w)
+    rows = _sample_rows(len(q), 16, 22)
+    with lnbnn.Index(dev(ref), dev(labels), w.n_classes) as ix:
+        ix.prepare_fp8()
+        qd = dev(q)
+        for m in (16, 64):
+            idx, dist = ix.knn_search(qd, 11, shortlist=m)
+            ix.sync()
+            od, oj = oracle.knn_coarse(ref, q[rows], 11, m)
+            assert np.array_equal(idx.cpu().numpy()[rows], oj.astype(np.int32)), m
+            assert np.array_equal(dist.cpu().numpy()[rows], od.astype(np.int32)), m
+        t, c = ix.lnbnn_classify(qd, dev(off), 10, shortlist=32)
+        ix.sync()
+    img = 37  # one whole image through the oracle
+    qi = q[off[img]:off[img + 1]]
+    ot, oc = oracle.local_nbnn_coarse(ref, labels, w.n_classes, qi, np.array([0, len(qi)]), 10, 32)
+    assert np.array_equal(t.cpu().numpy()[img], ot[0]) and c.cpu().numpy()[img] == oc[0]
+    assert (t.cpu().numpy() <= 0).all()
