@@ -326,7 +326,7 @@ def run_ours(args, w):
 
     value = M * args.steps * world / elapsed
     peaks, peak_src = measured_peaks()
-    roofline = scan_roofline(prof, w.n_ref, M, peaks, peak_src, local, shortlist)
+    roofline = scan_roofline(prof, w.n_ref, M, peaks, peak_src, local, shortlist, k)
     roofline["traffic"] = traffic_per_launch(roofline["kernel"], M)
 
     e2e = None
@@ -367,7 +367,7 @@ def run_ours(args, w):
             el8, prof8 = timed(fp8_step, args.steps)
             fp8_block = {"shortlist": m_short, "value": M * args.steps * world / el8, "unit": UNIT,
                          "images_per_s": n_img * args.steps * world / el8, "ms_per_step": el8 / args.steps * 1e3,
-                         "roofline": scan_roofline(prof8, w.n_ref, M, peaks, peak_src, True, m_short),
+                         "roofline": scan_roofline(prof8, w.n_ref, M, peaks, peak_src, True, m_short, k),
                          "gpu_launches": int(prof8["kernel_launches"])}
             fp8_block["roofline"]["traffic"] = traffic_per_launch(fp8_block["roofline"]["kernel"], M)
         index.sync()
@@ -425,7 +425,12 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
-def scan_roofline(prof, n_ref, M, peaks, peak_src, local, shortlist) -> dict:
+def list_kind(K1: int) -> int:
+    """Register-list size the search kernel uses for lists of K1 (0: heap)."""
+    return 16 if K1 <= 16 else 32 if K1 <= 32 else 64 if K1 <= 64 else 0
+
+
+def scan_roofline(prof, n_ref, M, peaks, peak_src, local, shortlist, k: int = 10) -> dict:
     """Roofline of the search kernel from the call profile: algorithmic
     2 * 128 flops per (query, reference) pair over its mean launch time."""
     search_ms = prof["search_ms"] / max(prof["search_launches"], 1)
@@ -435,11 +440,12 @@ def scan_roofline(prof, n_ref, M, peaks, peak_src, local, shortlist) -> dict:
         # E4M3 contraction: twice the BF16 rate (nominal dense 4.5 vs 2.25 PFLOP/s)
         peak = 2.0 * float(peaks["bf16_tflops_sustained"])
         src = f"2 x bf16_tflops_sustained ({peak_src}), the nominal fp8/bf16 ratio"
-        kernel = "tc_scan_kernel<FmtE4m3, KnnEpilogue<%d>>" % (16 if shortlist <= 16 else 32 if shortlist <= 32 else 0)
+        kernel = "tc_scan_kernel<FmtE4m3, KnnEpilogue<%d>>" % list_kind(shortlist)
     else:
         peak = float(peaks["bf16_tflops_sustained"])
         src = f"bf16_tflops_sustained ({peak_src})"
-        kernel = "tc_scan_kernel<FmtBf16, KnnEpilogue<16>>" if local else "tc_scan_kernel<FmtBf16, NbnnEpilogue>"
+        kernel = ("tc_scan_kernel<FmtBf16, KnnEpilogue<%d>>" % list_kind(k + 1) if local
+                  else "tc_scan_kernel<FmtBf16, NbnnEpilogue>")
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "kernel": kernel, "peak_source": src, "flops_per_launch": flops,
             "avg_launch_ms": search_ms}

@@ -1,0 +1,68 @@
+"""Host-side logic of the measurement scripts: roofline arithmetic, the
+committed ncu traffic lookup, workload descriptions and sweep tables."""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1112_0059_gb300 import sweep, synth  # noqa: E402
+
+
+def test_scan_roofline_arithmetic():
+    prof = {"search_ms": 2000.0, "search_launches": 2}
+    peaks = {"bf16_tflops_sustained": 1000.0}
+    r = bench.scan_roofline(prof, 1_000_000, 500_000, peaks, "measured", True, None)
+    flops = 2.0 * 128 * 1_000_000 * 500_000
+    assert r["flops_per_launch"] == flops and r["avg_launch_ms"] == 1000.0
+    assert abs(r["achieved"] - flops / 1.0 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 1000.0) < 1e-12
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["kernel"] == "tc_scan_kernel<FmtBf16, KnnEpilogue<16>>"
+    f = bench.scan_roofline(prof, 1_000_000, 500_000, peaks, "measured", True, 32)
+    assert f["peak"] == 2000.0 and f["kernel"] == "tc_scan_kernel<FmtE4m3, KnnEpilogue<32>>"
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 64)["kernel"].endswith("KnnEpilogue<64>>")
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 128)["kernel"].endswith("KnnEpilogue<0>>")
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, None, 20)["kernel"].endswith("<FmtBf16, KnnEpilogue<32>>")
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, None, 100)["kernel"].endswith("<FmtBf16, KnnEpilogue<0>>")
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", False, None)["kernel"].endswith("NbnnEpilogue>")
+
+
+def test_traffic_lookup_matches_committed_capture():
+    with open(bench.TRAFFIC_FILE) as f:
+        t = json.load(f)
+    name = "tc_scan_kernel<FmtBf16, KnnEpilogue<16>>"
+    got = bench.traffic_per_launch(name, 750000)
+    if t["kernel_hash"] == bench.kernel_hash():
+        assert got == pytest.approx(t["kernels"][name]["dram_bytes_per_launch"])
+        assert bench.traffic_per_launch(name, 375000) == pytest.approx(got / 2)
+    else:  # sources changed since the capture: no stale number is reported
+        assert got is None
+    assert bench.traffic_per_launch("no such kernel", 750000) is None
+
+
+def test_measured_peaks_and_workload_config():
+    peaks, src = bench.measured_peaks()
+    assert src in ("measured", "fallback") and peaks["bf16_tflops_sustained"] > 0
+    cfg = bench.workload_config(synth.workload("caltech256-like"), 10)
+    assert cfg["n_ref"] == 11_520_000 and cfg["query_descriptors"] == 750_000 and cfg["k"] == 10
+    assert "larger than L2" in cfg["l2"]
+    assert bench.workload_config(synth.workload("tiny"), 10, "nbnn")["k"] is None
+
+
+def test_sweep_tables():
+    rows = [{"part": "kc", "method": "local", "C": 32, "n_ref": 1440000, "k": 10, "desc_per_s": 4e6, "tflops": 1500.0},
+            {"part": "kc", "method": "nbnn", "C": 32, "n_ref": 1440000, "k": None, "desc_per_s": 4.5e6,
+             "tflops": 1700.0},
+            {"part": "fp8", "form": "fp8", "shortlist": 32, "desc_per_s": 7e5, "knn_recall": 1.0,
+             "class_agreement": 1.0, "score_rel_error": 0.0},
+            {"part": "uneven", "form": "exact", "autotuned": False, "splits": 1, "desc_per_s": 5e5,
+             "images_per_s": 300.0}]
+    t = sweep.tables(rows)
+    assert "| 32 | 1,440,000 | 10 | 4,000,000 | 1500 |" in t
+    assert "| 32 | 1,440,000 | NBNN |" in t
+    assert "| fp8 | 32 | 700,000 |" in t and "| exact | False | 1 | 500,000 | 300.0 |" in t
