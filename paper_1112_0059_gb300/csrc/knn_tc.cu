@@ -66,7 +66,6 @@ constexpr int kBN = kTcRefTile;           // reference rows per tile (MMA N)
 constexpr int kBK = 64;                   // BF16 K elements per 128-byte swizzle row
 constexpr int kKChunks = kDim / kBK;      // K-chunks of the BF16 operand (shared memory is laid out for these)
 constexpr int kMmaPerChunk = 4;           // 32-byte K-steps per 128-byte chunk (16 BF16 or 32 E4M3)
-constexpr int kStages = 4;                // reference ring depth (K-chunks)
 constexpr uint32_t kAChunkBytes = kBM * kBK * 2;     // 16 KB
 constexpr uint32_t kAExtBytes = kBM * kExt * 2;      // 4 KB
 constexpr uint32_t kBChunkBytes = kBN * kBK * 2;     // 32 KB
@@ -84,16 +83,25 @@ constexpr uint32_t kAccCols = kBN;        // FP32 columns per accumulator
 constexpr uint32_t kTmemCols = 2 * kAccCols;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
 
-constexpr uint32_t kOffA = 0;                                   // 2 chunks, 128-byte swizzle
-constexpr uint32_t kOffAExt = kOffA + kKChunks * kAChunkBytes;  // extension, 32-byte swizzle
-constexpr uint32_t kOffB = kOffAExt + 1024 * ((kAExtBytes + 1023) / 1024);
-constexpr uint32_t kOffBar = kOffB + kStages * kStageBytes;
-constexpr int kNumBars = 2 * kStages + 2 + 2 + 2;  // full, empty, tmem full, tmem empty, A, drain
-constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;  // TMEM address, abort flag
-constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;  // + alignment slack
-static_assert(kStages % kKChunks == 0, "a tile's chunks map to fixed stage parities");
-static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
-
+// Shared-memory layout of one CTA: the query tile (AChunks 128-byte-swizzle
+// chunks + the 32-byte-swizzle extension), the reference ring (Stages stages,
+// each room for one K-chunk and the extension), the mbarriers, the TMEM
+// address and abort flag, and ListBytes for an epilogue that keeps its lists
+// in shared memory.
+template <int AChunks, int Stages, uint32_t ListBytes>
+struct Layout {
+  static constexpr int kStages = Stages;
+  static constexpr uint32_t kOffA = 0;
+  static constexpr uint32_t kOffAExt = kOffA + AChunks * kAChunkBytes;
+  static constexpr uint32_t kOffB = kOffAExt + 1024 * ((kAExtBytes + 1023) / 1024);
+  static constexpr uint32_t kOffBar = kOffB + Stages * kStageBytes;
+  static constexpr int kNumBars = 2 * Stages + 2 + 2 + 2;  // full, empty, tmem full, tmem empty, A, drain
+  static constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;  // TMEM address, abort flag
+  static constexpr uint32_t kOffList = (kOffMisc + 16 + 1023) / 1024 * 1024;
+  static constexpr uint32_t kSmemBytes = kOffList + ListBytes + 1024;  // + alignment slack
+  static_assert(Stages % AChunks == 0, "a tile's chunks map to fixed stage parities");
+  static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+};
 
 // Operand formats.  Either way one K-chunk is one 128-byte (swizzled) row
 // per operand row and one MMA consumes 32 bytes of it.
@@ -116,6 +124,7 @@ struct FmtE4m3 {  // coarse pass: 128 E4M3 coordinates, one chunk
   }
 };
 
+template <int kStages>
 struct Bars {
   uint32_t base;
   __device__ uint32_t full(int s) const { return base + 8 * s; }
@@ -125,6 +134,11 @@ struct Bars {
   __device__ uint32_t afull() const { return base + 8 * (2 * kStages + 4); }
   __device__ uint32_t drain() const { return base + 8 * (2 * kStages + 5); }
 };
+
+// The layout of a kernel instantiation: the format's query chunks; four ring
+// stages, or three when the epilogue's lists take shared memory.
+template <class Fmt, class Epilogue>
+using LayoutOf = Layout<Fmt::kChunks, Epilogue::kListBytes ? 3 : 4, Epilogue::kListBytes>;
 
 __device__ __forceinline__ void flag_timeout(volatile uint32_t* abort_flag, uint32_t* dev_err) {
   *abort_flag = 1u;
@@ -264,13 +278,14 @@ struct ScanOut {
 template <int KMAX>
 struct KnnEpilogue {
   static constexpr int kWarpsPerQuarter = KMAX == kTcWideRegListMax ? 1 : 2;
+  static constexpr uint32_t kListBytes = 0;
   RegList<KMAX> L;
   TopK top;
   int32_t thr;
   bool active;
   int K1;
   uint64_t* out;
-  __device__ __forceinline__ KnnEpilogue(const ScanOut& o, int list, int64_t row, bool act, int64_t)
+  __device__ __forceinline__ KnnEpilogue(const ScanOut& o, int list, int64_t row, bool act, int64_t, uint8_t*, int)
       : top(o.lists + ((int64_t)list * o.stride + (act ? row : 0)) * o.K1, o.K1),
         thr(thr_bits(INT32_MAX)),
         active(act),
@@ -299,6 +314,7 @@ struct KnnEpilogue {
 // is uniform across the warp.
 struct NbnnEpilogue {
   static constexpr int kWarpsPerQuarter = 2;
+  static constexpr uint32_t kListBytes = 0;
   int32_t* dst;          // mins + row * C
   const int64_t* class_off;
   int64_t n_ref;
@@ -307,7 +323,8 @@ struct NbnnEpilogue {
   int64_t next;          // first row of the next class
   int32_t run;           // float bits of the running minimum over cls
   bool active;
-  __device__ __forceinline__ NbnnEpilogue(const ScanOut& o, int, int64_t row, bool act, int64_t j_begin)
+  __device__ __forceinline__ NbnnEpilogue(const ScanOut& o, int, int64_t row, bool act, int64_t j_begin, uint8_t*,
+                                          int)
       : dst(o.mins + (act ? row : 0) * (int64_t)o.C), class_off(o.class_off), n_ref(o.class_off[o.C]), C(o.C),
         run(INT32_MAX), active(act) {
     // class of j_begin: the last c with class_off[c] <= j_begin
@@ -350,6 +367,8 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
                    int64_t n_ref, int64_t split_len, ScanOut out, uint32_t* __restrict__ dev_err,
                    unsigned long long* __restrict__ stats) {
   constexpr int KC = Fmt::kChunks;
+  using L = LayoutOf<Fmt, Epilogue>;
+  constexpr int kStages = L::kStages;
   constexpr int kEpiPerQuarter = Epilogue::kWarpsPerQuarter;  // epilogue warps per TMEM lane quarter
   constexpr int kEpiWarps = 4 * kEpiPerQuarter;
   constexpr int kEpiCols = kBN / kEpiPerQuarter;  // columns of a tile per epilogue warp
@@ -358,12 +377,12 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
   constexpr int kBRowsPerCta = kBN / kCluster;                 // rows of each tile one CTA loads
   constexpr uint32_t kBChunkPart = kBChunkBytes / kCluster;   // its share of a chunk
   constexpr uint32_t kBExtPart = kBExtBytes / kCluster;       // its share of the extension
-  static_assert(KC <= kKChunks && kStages % KC == 0, "a tile's chunks map to fixed stage parities");
+  static_assert(KC <= kKChunks, "the query tile fits the chunks shared memory is laid out for");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = smem_u32(smem);
-  const Bars bars{sbase + kOffBar};
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffMisc);
+  const Bars<kStages> bars{sbase + L::kOffBar};
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kOffMisc);
   volatile uint32_t* abort_flag = tmem_slot + 1;
 
   const int warp = threadIdx.x >> 5;
@@ -407,8 +426,8 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
       prefetch_tmap(&tmap_re);
       mbar_arrive_expect_tx(bars.afull(), KC * kAChunkBytes + kAExtBytes);
       for (int kc = 0; kc < KC; ++kc)
-        tma_load_2d(sbase + kOffA + kc * kAChunkBytes, &tmap_q, kc * kBK, (int32_t)m0, bars.afull());
-      tma_load_2d(sbase + kOffAExt, &tmap_qe, 0, (int32_t)m0, bars.afull());
+        tma_load_2d(sbase + L::kOffA + kc * kAChunkBytes, &tmap_q, kc * kBK, (int32_t)m0, bars.afull());
+      tma_load_2d(sbase + L::kOffAExt, &tmap_qe, 0, (int32_t)m0, bars.afull());
       int it = 0;
       for (int t = 0; t < ntiles && !*abort_flag; ++t) {
         const int32_t row = (int32_t)(j_begin + (int64_t)t * kBN);
@@ -419,7 +438,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
             flag_timeout(abort_flag, dev_err);
             break;
           }
-          const uint32_t dst = sbase + kOffB + s * kStageBytes;
+          const uint32_t dst = sbase + L::kOffB + s * kStageBytes;
           const bool last = kc == KC - 1;
           // the whole chunk lands here: this CTA's half and the partner's
           mbar_arrive_expect_tx(bars.full(s), kBChunkBytes + (last ? kBExtBytes : 0u));
@@ -470,11 +489,11 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
             break;
           }
           tc_fence_after();
-          const uint32_t a_base = sbase + kOffA + kc * kAChunkBytes;
-          const uint32_t b_base = sbase + kOffB + s * kStageBytes;
+          const uint32_t a_base = sbase + L::kOffA + kc * kAChunkBytes;
+          const uint32_t b_base = sbase + L::kOffB + s * kStageBytes;
           const bool last = kc == KC - 1;  // the norms' K-extension rides with the last chunk
           if (Fmt::kExtFirst && last)
-            mma_bf16(d_tmem, sw32_kmajor_desc(sbase + kOffAExt), sw32_kmajor_desc(b_base + kBChunkBytes),
+            mma_bf16(d_tmem, sw32_kmajor_desc(sbase + L::kOffAExt), sw32_kmajor_desc(b_base + kBChunkBytes),
                      FmtBf16::kIdesc, kc != 0 ? 1u : 0u);
 #pragma unroll
           for (int kk = 0; kk < kMmaPerChunk; ++kk) {
@@ -482,7 +501,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
                      (kc | kk) != 0 || (Fmt::kExtFirst && last) ? 1u : 0u);
           }
           if (!Fmt::kExtFirst && last)
-            mma_bf16(d_tmem, sw32_kmajor_desc(sbase + kOffAExt), sw32_kmajor_desc(b_base + kBChunkBytes),
+            mma_bf16(d_tmem, sw32_kmajor_desc(sbase + L::kOffAExt), sw32_kmajor_desc(b_base + kBChunkBytes),
                      FmtBf16::kIdesc, 1u);
           if constexpr (kCluster == 1) {
             mma_commit(bars.empty(s));
@@ -509,7 +528,8 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
     const int half = (warp - 2) >> 2;      // its column slice of every tile
     const int64_t row = m0 + quarter * 32 + lane;
     const bool active = row < m;
-    Epilogue epi(out, (int)blockIdx.y * kEpiPerQuarter + half, row, active, j_begin + half * kEpiCols);
+    Epilogue epi(out, (int)blockIdx.y * kEpiPerQuarter + half, row, active, j_begin + half * kEpiCols,
+                 smem + L::kOffList, warp - 2);
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
@@ -632,7 +652,7 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const voi
                       : encode_operand(&tq, &tqe, qop, qext, (uint64_t)m_pad, kBM);
   if (!ok) return cudaErrorInvalidValue;
   dim3 grid((unsigned)(m_pad / kBM), (unsigned)splits);
-  tc_scan_kernel<Fmt, Epilogue><<<grid, threads_for(Epilogue::kWarpsPerQuarter), kSmemBytes, s>>>(
+  tc_scan_kernel<Fmt, Epilogue><<<grid, threads_for(Epilogue::kWarpsPerQuarter), LayoutOf<Fmt, Epilogue>::kSmemBytes, s>>>(
       tq, tqe, tr, tre, m, n_ref, split_len, out,
                                                                    dev_err, stats);
   return cudaGetLastError();
@@ -645,7 +665,7 @@ cudaError_t prepare_one() {
   if (e != cudaSuccess) return e;
   if (a.numRegs > max_regs_for(Epilogue::kWarpsPerQuarter)) return cudaErrorInvalidKernelImage;
   return cudaFuncSetAttribute(tc_scan_kernel<Fmt, Epilogue>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kSmemBytes);
+                              (int)LayoutOf<Fmt, Epilogue>::kSmemBytes);
 }
 
 }  // namespace
