@@ -51,7 +51,7 @@ def lib():
 def test_noalloc_matches_knn_search_on_two_calls(lib):
     from paper_1112_0059_gb300 import lnbnn
     # a larger call, then a smaller one that finds the first call's data in the scratch
-    for seed, n_ref, n_q, k in ((0, 20000 + 77, 3000 + 5, 10), (1, 5000 + 3, 700, 25)):
+    for seed, n_ref, n_q, k in ((0, 20000 + 77, 3000 + 5, 10), (1, 5000 + 3, 700, 25), (2, 6000 + 11, 500, 50)):
         ref, q = _case(seed, n_ref, n_q)
         ref_d, q_d = torch.from_numpy(ref).cuda(), torch.from_numpy(q).cuda()
         code, idx, dist = _noalloc(lib, ref_d, q_d, k)
