@@ -312,6 +312,25 @@ LNBNN_API lnbnn_status knn_search_noalloc(const uint8_t *ref, int64_t n_ref, con
                                           int64_t n_queries, int32_t k, int32_t *idx, int32_t *dist,
                                           void *stream);
 
+/*
+ * Test hooks for the failure paths (no part of the method).
+ *
+ * lnbnn_debug_fail_allocations: the library's next `count` device allocations
+ * (in any call: index creation, workspaces, the index's own scratch, FP8
+ * preparation, autotuning) fail as if the device were out of memory, so the
+ * call returns OOM and frees what it had allocated.  count <= 0 clears it.
+ * Process-wide; needs no device.
+ *
+ * lnbnn_set_start_gate: search kernels of this index wait, before loading any
+ * operand, until the device word *gate is nonzero; gate = NULL (the default)
+ * removes the wait.  The wait is bounded like every other wait in the search
+ * kernels (1 s): a gate that nothing opens makes the call's kernels give up,
+ * record a timeout and return, and lnbnn_sync then reports TIMEOUT.  The
+ * pointer must stay valid while calls may run.
+ */
+LNBNN_API void lnbnn_debug_fail_allocations(int32_t count);
+LNBNN_API lnbnn_status lnbnn_set_start_gate(lnbnn_index *index, const uint32_t *gate);
+
 /* Static English text for a status code. */
 LNBNN_API const char *lnbnn_status_string(lnbnn_status status);
 

@@ -145,6 +145,19 @@ __device__ __forceinline__ void flag_timeout(volatile uint32_t* abort_flag, uint
   atomicOr(dev_err, kDevErrTimeout);
 }
 
+// Wait until the gate word is nonzero, for at most limit_ns, giving up early
+// once another role of the CTA has given up.  Returns false on expiry.
+__device__ __forceinline__ bool wait_gate(const uint32_t* gate, uint64_t limit_ns,
+                                          const volatile uint32_t* abort_flag) {
+  const volatile uint32_t* g = gate;
+  if (*g != 0u) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (*g != 0u) return true;
+    if ((it & 255u) == 0 && (*abort_flag || globaltimer_ns() - t0 > limit_ns)) return false;
+  }
+}
+
 // Sorted list of the K1 smallest (distance, row) pairs seen so far, held in
 // registers: ascending in slots [KMAX-K1, KMAX); the slots below hold the
 // distance -1, which no real distance displaces, so the list always has K1
@@ -271,6 +284,7 @@ struct ScanOut {
   int32_t* mins;             // NBNN: per (query row, class) minimum distance, [m_pad][C], atomicMin
   int32_t C;
   const int64_t* class_off;  // NBNN: class c owns sorted rows [class_off[c], class_off[c+1])
+  const uint32_t* gate;      // null, or a word the producer waits to see nonzero before loading
 };
 
 // kNN epilogue: the K1 smallest (distance, row) keys of the columns one
@@ -420,16 +434,25 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
   if (warp == 0) {
     if (lane == 0) {
       // ------------------------------------------------------------ producer
-      prefetch_tmap(&tmap_q);
-      prefetch_tmap(&tmap_qe);
-      prefetch_tmap(&tmap_r);
-      prefetch_tmap(&tmap_re);
-      mbar_arrive_expect_tx(bars.afull(), KC * kAChunkBytes + kAExtBytes);
-      for (int kc = 0; kc < KC; ++kc)
-        tma_load_2d(sbase + L::kOffA + kc * kAChunkBytes, &tmap_q, kc * kBK, (int32_t)m0, bars.afull());
-      tma_load_2d(sbase + L::kOffAExt, &tmap_qe, 0, (int32_t)m0, bars.afull());
+      // an optional start gate; with nothing loaded the other roles' waits
+      // run out on the abort flag
+      bool go = true;
+      if (out.gate != nullptr && ntiles > 0 && !wait_gate(out.gate, kWaitLimitNs, abort_flag)) {
+        flag_timeout(abort_flag, dev_err);
+        go = false;
+      }
+      if (go) {
+        prefetch_tmap(&tmap_q);
+        prefetch_tmap(&tmap_qe);
+        prefetch_tmap(&tmap_r);
+        prefetch_tmap(&tmap_re);
+        mbar_arrive_expect_tx(bars.afull(), KC * kAChunkBytes + kAExtBytes);
+        for (int kc = 0; kc < KC; ++kc)
+          tma_load_2d(sbase + L::kOffA + kc * kAChunkBytes, &tmap_q, kc * kBK, (int32_t)m0, bars.afull());
+        tma_load_2d(sbase + L::kOffAExt, &tmap_qe, 0, (int32_t)m0, bars.afull());
+      }
       int it = 0;
-      for (int t = 0; t < ntiles && !*abort_flag; ++t) {
+      for (int t = 0; go && t < ntiles && !*abort_flag; ++t) {
         const int32_t row = (int32_t)(j_begin + (int64_t)t * kBN);
         for (int kc = 0; kc < KC; ++kc, ++it) {
           const int s = it % kStages;
@@ -456,7 +479,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
       }
       // every load issued must land before the CTA may exit
       const uint32_t never = 0;
-      mbar_wait(bars.afull(), 0, kWaitLimitNs, &never);
+      if (go) mbar_wait(bars.afull(), 0, kWaitLimitNs, &never);
       for (int s = 0; s < kStages; ++s) {
         const int issued = it / kStages + (s < it % kStages ? 1 : 0);
         if (issued > 0) mbar_wait(bars.full(s), (uint32_t)((issued - 1) & 1), kWaitLimitNs, &never);
@@ -686,8 +709,9 @@ cudaError_t prepare_tc_kernels() {
 cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf,
                           const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
                           int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
-                          unsigned long long* stats, cudaStream_t s) {
+                          unsigned long long* stats, const uint32_t* gate, cudaStream_t s) {
   ScanOut out{};
+  out.gate = gate;
   out.lists = lists;
   out.stride = stride;
   out.K1 = K1;
@@ -708,8 +732,10 @@ cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv
 
 cudaError_t launch_coarse_tc(const TcTensorMaps& maps, const uint8_t* qf8, const __nv_bfloat16* qext, int64_t m,
                              int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int K1, uint64_t* lists,
-                             int64_t stride, uint32_t* dev_err, unsigned long long* stats, cudaStream_t s) {
+                             int64_t stride, uint32_t* dev_err, unsigned long long* stats, const uint32_t* gate,
+                             cudaStream_t s) {
   ScanOut out{};
+  out.gate = gate;
   out.lists = lists;
   out.stride = stride;
   out.K1 = K1;
@@ -728,8 +754,10 @@ cudaError_t launch_coarse_tc(const TcTensorMaps& maps, const uint8_t* qf8, const
 
 cudaError_t launch_nbnn_tc(const TcTensorMaps& maps, const __nv_bfloat16* qbf, const __nv_bfloat16* qext, int64_t m,
                            int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int32_t* mins, int32_t C,
-                           const int64_t* class_off, uint32_t* dev_err, unsigned long long* stats, cudaStream_t s) {
+                           const int64_t* class_off, uint32_t* dev_err, unsigned long long* stats,
+                           const uint32_t* gate, cudaStream_t s) {
   ScanOut out{};
+  out.gate = gate;
   out.mins = mins;
   out.C = C;
   out.class_off = class_off;

@@ -104,22 +104,27 @@ bool make_tc_tensor_maps_e4m3(const uint8_t* ref_f8, const __nv_bfloat16* ref_f8
 cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf,
                           const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
                           int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
-                          unsigned long long* stats, cudaStream_t s);
+                          unsigned long long* stats, const uint32_t* gate, cudaStream_t s);
 // Coarse pass of the FP8 shortlist search: the same scan over the E4M3
 // operands (qf8 [m_pad, 128] bytes of -2 E4M3(q - 64), qext its extension),
 // keeping the K1 smallest (coarse + 2^21, row) keys per list in the same
 // layout as launch_knn_tc.
 cudaError_t launch_coarse_tc(const TcTensorMaps& maps, const uint8_t* qf8, const __nv_bfloat16* qext, int64_t m,
                              int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int K1, uint64_t* lists,
-                             int64_t stride, uint32_t* dev_err, unsigned long long* stats, cudaStream_t s);
+                             int64_t stride, uint32_t* dev_err, unsigned long long* stats, const uint32_t* gate,
+                             cudaStream_t s);
 // Original NBNN on the same tensor-core scan over the class-sorted copy:
 // mins [m_pad, C] (int32, filled with INT32_MAX-like values beforehand) gets
 // atomicMin(mins[i][c], ||q_i - r||^2) over every reference r of class c that
 // split's range covers, so after all splits mins[i][c] = NN_c(q_i).
 cudaError_t launch_nbnn_tc(const TcTensorMaps& maps, const __nv_bfloat16* qbf, const __nv_bfloat16* qext, int64_t m,
                            int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int32_t* mins, int32_t C,
-                           const int64_t* class_off, uint32_t* dev_err, unsigned long long* stats, cudaStream_t s);
+                           const int64_t* class_off, uint32_t* dev_err, unsigned long long* stats,
+                           const uint32_t* gate, cudaStream_t s);
 // stats (may be null): the MMA thread of every CTA adds its SM cycles,
 // globaltimer nanoseconds and tile count to stats[0..2] and 1 to stats[3].
+// gate (may be null): each CTA's producer waits, at most 1 s, until *gate is
+// nonzero before it loads anything; on expiry the launch reports a timeout
+// like any other wait (lnbnn_set_start_gate).
 
 }  // namespace lnbnn

@@ -1,6 +1,7 @@
 // The C ABI of include/lnbnn.h: index ownership, argument checks, workspace
 // and the launch sequence of each call.  All arithmetic runs in the kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -45,6 +46,7 @@ struct lnbnn_index {
   bool fp8 = false;
   TcTensorMaps tc;  // tensor maps over ref_bf / sref_bf (and ref_f8) for the tensor-core kernels
   SplitModel split_model;  // split-N schedule (defaults, or fitted by lnbnn_autotune)
+  const uint32_t* gate = nullptr;  // lnbnn_set_start_gate: search kernels wait for *gate != 0
   // optional device-time profile (lnbnn_profile_enable)
   struct CallEvents {
     cudaEvent_t e[4];
@@ -79,11 +81,21 @@ lnbnn_status status_of(cudaError_t e) {
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Allocations the test hook lnbnn_debug_fail_allocations still has to fail.
+std::atomic<int> g_fail_allocs{0};
+
+// Every device allocation of the library goes through here.
+cudaError_t lib_malloc(void** p, size_t bytes) {
+  *p = nullptr;
+  for (int n = g_fail_allocs.load(); n > 0;)
+    if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
 template <typename T>
 cudaError_t dmalloc(T** p, size_t count) {
-  *p = nullptr;
   if (count == 0) count = 1;
-  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  return lib_malloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
 void free_index(lnbnn_index* ix) {
@@ -175,7 +187,7 @@ cudaError_t ensure(void** buf, size_t* have, size_t need) {
     if (e != cudaSuccess) return e;
   }
   need = (need + (1u << 20) - 1) & ~size_t((1u << 20) - 1);
-  cudaError_t e = cudaMalloc(buf, need);
+  cudaError_t e = lib_malloc(buf, need);
   if (e == cudaSuccess) *have = need;
   return e;
 }
@@ -288,7 +300,7 @@ lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_
   prof.launched(1);
   prof.mark(1);
   CK(launch_knn_tc(ix->tc, /*sorted_copy=*/false, qbf, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, K1, part,
-                   p.m_pad, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, s));
+                   p.m_pad, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, ix->gate, s));
   prof.launched(1, true);
   prof.mark(2);
   if (p.lists > 1) {
@@ -316,7 +328,7 @@ lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, in
   prof.launched(1);
   prof.mark(1);
   CK(launch_coarse_tc(ix->tc, qf8, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, M1, part, p.m_pad,
-                      ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, s));
+                      ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, ix->gate, s));
   prof.launched(1, true);
   prof.mark(2);
   // the shortlist is the merged lists (or the one list); the reranked lists
@@ -476,6 +488,14 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
 
 void lnbnn_index_destroy(lnbnn_index* index) { free_index(index); }
 
+void lnbnn_debug_fail_allocations(int32_t count) { g_fail_allocs.store(count > 0 ? count : 0); }
+
+lnbnn_status lnbnn_set_start_gate(lnbnn_index* index, const uint32_t* gate) {
+  if (!index) return LNBNN_ERR_INVALID_ARG;
+  index->gate = gate;
+  return LNBNN_OK;
+}
+
 lnbnn_status lnbnn_plan_splits(const lnbnn_index* index, int64_t n_queries, int32_t* splits) {
   if (!index || !splits || n_queries < 1) return LNBNN_ERR_INVALID_ARG;
   *splits = plan_knn(index, n_queries, 1).splits;
@@ -534,7 +554,7 @@ lnbnn_status lnbnn_autotune(lnbnn_index* index, void* stream, lnbnn_tuning* out)
     }                                     \
   } while (0)
   CKA(dmalloc(&q, (size_t)m_max * kDim));
-  CKA(cudaMalloc(&w.base, need));
+  CKA(lib_malloc(&w.base, need));
   CKA(cudaEventCreate(&e0));
   CKA(cudaEventCreate(&e1));
   const int64_t step = n_ref / m_max;  // >= 1
@@ -632,11 +652,24 @@ lnbnn_status lnbnn_index_prepare_fp8(lnbnn_index* index, void* stream) {
   if (!index) return LNBNN_ERR_INVALID_ARG;
   if (index->fp8) return LNBNN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  CK(dmalloc(&index->ref_f8, (size_t)index->n_pad * kDim));
-  CK(dmalloc(&index->ref_f8_ext, (size_t)index->n_pad * kExt));
-  CK(launch_prep_ref_e4m3(index->ref_u8, index->n_ref, index->n_pad, index->ref_f8, index->ref_f8_ext, s));
-  if (!make_tc_tensor_maps_e4m3(index->ref_f8, index->ref_f8_ext, index->n_pad, &index->tc)) return LNBNN_ERR_CUDA;
-  CK(cudaStreamSynchronize(s));
+  auto undo = [&](lnbnn_status st) {  // a failed preparation keeps nothing
+    cudaFree(index->ref_f8);
+    cudaFree(index->ref_f8_ext);
+    index->ref_f8 = nullptr;
+    index->ref_f8_ext = nullptr;
+    return st;
+  };
+  cudaError_t e = dmalloc(&index->ref_f8, (size_t)index->n_pad * kDim);
+  if (e == cudaSuccess) e = dmalloc(&index->ref_f8_ext, (size_t)index->n_pad * kExt);
+  if (e == cudaSuccess)
+    e = launch_prep_ref_e4m3(index->ref_u8, index->n_ref, index->n_pad, index->ref_f8, index->ref_f8_ext, s);
+  if (e != cudaSuccess) return undo(status_of(e));
+  if (!make_tc_tensor_maps_e4m3(index->ref_f8, index->ref_f8_ext, index->n_pad, &index->tc)) {
+    cudaStreamSynchronize(s);
+    return undo(LNBNN_ERR_CUDA);
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return undo(status_of(e));
   index->fp8 = true;
   return LNBNN_OK;
 }
@@ -755,7 +788,8 @@ static lnbnn_status do_nbnn_classify(lnbnn_index* index, lnbnn_workspace* w, con
     prof.launched(1);
     prof.mark(1);
     CK(launch_nbnn_tc(index->tc, qbf, qext, n_queries, p.m_pad, index->n_ref, p.splits, p.split_len, mins, C,
-                      index->class_off_d, index->dev_err, index->prof_on ? index->prof_stats : nullptr, s));
+                      index->class_off_d, index->dev_err, index->prof_on ? index->prof_stats : nullptr, index->gate,
+                      s));
     prof.launched(1, true);
     prof.mark(2);
     CK(launch_nbnn_sum(mins, n_queries, C, offsets, n_images, totals, s));
@@ -803,7 +837,7 @@ lnbnn_status lnbnn_workspace_create(lnbnn_index* index, int64_t max_queries, int
   if (!w) return LNBNN_ERR_OOM;
   w->index = index;
   w->bytes = scratch_bound(index, max_queries, std::min<int>(max_k + 1, LNBNN_MAX_K + 1));
-  cudaError_t e = cudaMalloc(&w->base, w->bytes);
+  cudaError_t e = lib_malloc(&w->base, w->bytes);
   if (e != cudaSuccess) {
     delete w;
     return status_of(e);
@@ -913,7 +947,7 @@ lnbnn_status lnbnn_profile_enable(lnbnn_index* index, int enable) {
   index->prof = lnbnn_profile{};
   index->prof_on = enable != 0;
   if (index->prof_on) {
-    if (!index->prof_stats) CK(cudaMalloc(&index->prof_stats, 4 * sizeof(unsigned long long)));
+    if (!index->prof_stats) CK(dmalloc(&index->prof_stats, 4));
     CK(cudaMemset(index->prof_stats, 0, 4 * sizeof(unsigned long long)));
   }
   return LNBNN_OK;

@@ -40,7 +40,8 @@ EXPORTS = ["lnbnn_index_create", "lnbnn_index_destroy", "lnbnn_index_info", "knn
            "lnbnn_profile_read", "lnbnn_status_string", "knn_search_noalloc", "lnbnn_workspace_create",
            "lnbnn_workspace_destroy", "knn_search_ws", "lnbnn_classify_ws", "nbnn_classify_ws",
            "lnbnn_index_prepare_fp8", "knn_search_fp8", "lnbnn_classify_fp8", "knn_search_fp8_ws",
-           "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host", "lnbnn_autotune", "lnbnn_plan_splits"]
+           "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host", "lnbnn_autotune", "lnbnn_plan_splits",
+           "lnbnn_debug_fail_allocations", "lnbnn_set_start_gate"]
 
 
 class Profile(ctypes.Structure):
@@ -108,6 +109,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.lnbnn_classify_fp8_host.argtypes = [P, P, I64, P, I64, I32, I32, P, P, P]
         lib.lnbnn_autotune.argtypes = [P, P, ctypes.POINTER(Tuning)]
         lib.lnbnn_plan_splits.argtypes = [P, I64, ctypes.POINTER(I32)]
+        lib.lnbnn_debug_fail_allocations.argtypes = [I32]
+        lib.lnbnn_debug_fail_allocations.restype = None
+        lib.lnbnn_set_start_gate.argtypes = [P, P]
+        lib.lnbnn_set_start_gate.restype = ctypes.c_int
         lib.lnbnn_status_string.argtypes = [ctypes.c_int]
         lib.lnbnn_status_string.restype = ctypes.c_char_p
         for name in ("lnbnn_index_create", "lnbnn_index_info", "knn_search", "lnbnn_classify", "nbnn_classify",
@@ -200,6 +205,16 @@ class Index:
         out = ctypes.c_int32()
         _check(self._lib.lnbnn_plan_splits(self.handle, int(n_queries), ctypes.byref(out)), "lnbnn_plan_splits")
         return out.value
+
+    def set_start_gate(self, gate=None) -> None:
+        """Test hook: search kernels wait (at most 1 s) for the uint32/int32 device
+        word ``gate`` to be nonzero; None removes the gate."""
+        import torch
+        ptr = None if gate is None else _dev(gate, gate.dtype, "gate")
+        if gate is not None and gate.dtype not in (torch.int32,):
+            raise TypeError("gate must be an int32 CUDA tensor")
+        _check(self._lib.lnbnn_set_start_gate(self.handle, ptr), "lnbnn_set_start_gate")
+        self._gate = gate  # keep the word alive while it is installed
 
     def prepare_fp8(self, stream=None) -> None:
         """Build the E4M3 operand of the FP8 shortlist search (once)."""
@@ -338,6 +353,11 @@ class Workspace:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def debug_fail_allocations(count: int) -> None:
+    """Test hook: the library's next ``count`` device allocations fail (OOM)."""
+    load_library().lnbnn_debug_fail_allocations(int(count))
 
 
 def knn_search_noalloc(ref, queries, k: int, stream=None):

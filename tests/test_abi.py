@@ -60,6 +60,9 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.lnbnn_classify_fp8(None, None, 0, None, 0, 1, 8, None, None, None) == 1
     assert lib.lnbnn_classify_fp8(None, None, 0, None, 0, 1, 0, None, None, None) == 4  # shortlist 0: no FP8 call
     assert lib.lnbnn_classify_fp8_ws(None, None, None, 0, None, 0, 1, 8, None, None, None) == 1
+    assert lib.lnbnn_set_start_gate(None, None) == 1
+    lib.lnbnn_debug_fail_allocations(2)  # a process-wide counter: needs no device
+    lib.lnbnn_debug_fail_allocations(0)
     lib.lnbnn_index_destroy(None)
 
 

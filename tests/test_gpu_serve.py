@@ -36,13 +36,16 @@ def setup(lnbnn):
     ix.close()
 
 
-@pytest.mark.parametrize("method,graphs", [("local", False), ("local", True), ("nbnn", False)])
-def test_served_equals_alone_and_oracle(setup, method, graphs):
+@pytest.mark.parametrize("method,graphs,shortlist", [("local", False, None), ("local", True, None),
+                                                     ("nbnn", False, None), ("local", True, 32)])
+def test_served_equals_alone_and_oracle(setup, method, graphs, shortlist):
     from paper_1112_0059_gb300 import serve
     w, ref, labels, reqs, q, off, ix = setup
     reqs = [dataclasses.replace(r, totals=None, cls=None, done=None, batch=None) for r in reqs]
+    if shortlist:
+        ix.prepare_fp8()
     with serve.Server(ix, k=10, method=method, slots=3, max_batch_queries=6144, max_batch_images=8,
-                      graphs=graphs) as srv:
+                      graphs=graphs, shortlist=shortlist) as srv:
         done = srv.run(reqs)
         log = srv.log
     assert len(done) == len(reqs)
@@ -50,7 +53,9 @@ def test_served_equals_alone_and_oracle(setup, method, graphs):
     # continuous batching happened: several images per batch, several batches in flight
     assert stats["mean_images_per_batch"] > 1.0
     assert stats["max_batches_in_flight"] >= 2
-    if method == "local":
+    if shortlist:
+        ot, oc = oracle.local_nbnn_coarse(ref, labels, w.n_classes, q, off, 10, shortlist)
+    elif method == "local":
         ot, oc = oracle.local_nbnn(ref, labels, w.n_classes, q, off, 10)
     else:
         ot, oc = oracle.nbnn(ref, labels, w.n_classes, q, off)
@@ -62,7 +67,7 @@ def test_served_equals_alone_and_oracle(setup, method, graphs):
     for i in range(0, len(reqs), 5):
         qd = torch.from_numpy(reqs[i].descriptors).cuda()
         od = torch.tensor([0, len(reqs[i].descriptors)], dtype=torch.int64, device="cuda")
-        t, c = ix.lnbnn_classify(qd, od, 10) if method == "local" else ix.nbnn_classify(qd, od)
+        t, c = ix.lnbnn_classify(qd, od, 10, shortlist=shortlist) if method == "local" else ix.nbnn_classify(qd, od)
         ix.sync()
         assert np.array_equal(t.cpu().numpy()[0], by_id[reqs[i].rid].totals) and int(c[0]) == by_id[reqs[i].rid].cls
 
