@@ -388,9 +388,14 @@ def run_ours(args, w):
     serve_block = None
     rates = [float(r) for r in args.serve_rates.split(",") if r.strip()]
     if rates and local and w.n_classes == synth.workload("serving").n_classes:
-        serve_block = {"exact": run_serving(index, rates, args.serve_seconds, k, None)}
+        cls_x, cls_f = {}, {}
+        serve_block = {"exact": run_serving(index, rates, args.serve_seconds, k, None, cls_x)}
         if fp8_m or shortlist:
-            serve_block["fp8"] = run_serving(index, rates, args.serve_seconds, k, shortlist or fp8_m)
+            serve_block["fp8"] = run_serving(index, rates, args.serve_seconds, k, shortlist or fp8_m, cls_f)
+            # both forms served the same images (same seeds): their class decisions, image by image
+            same = [cls_x[key] == cls_f[key] for key in cls_x if key in cls_f]
+            serve_block["fp8_class_agreement_with_exact"] = {
+                "images": len(same), "agreement": float(np.mean(same)) if same else None}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -451,9 +456,11 @@ def scan_roofline(prof, n_ref, M, peaks, peak_src, local, shortlist, k: int = 10
             "avg_launch_ms": search_ms}
 
 
-def run_serving(index, rates, seconds, k, shortlist) -> dict:
+def run_serving(index, rates, seconds, k, shortlist, classes_out: dict | None = None) -> dict:
     """The continuous-batching server over the resident index: Poisson
-    arrivals of query images with log-uniform [100, 4000] descriptors."""
+    arrivals of query images with log-uniform [100, 4000] descriptors.
+    classes_out (optional) receives {(rate, request id): class} of every
+    served image."""
     from paper_1112_0059_gb300 import serve
     w = synth.workload("serving")
     cfg = {"slots": 3, "max_batch_queries": 16384, "max_batch_images": 256, "graphs": True}
@@ -466,6 +473,8 @@ def run_serving(index, rates, seconds, k, shortlist) -> dict:
             first += n
             srv.log = []
             done = srv.run(reqs)
+            if classes_out is not None:
+                classes_out.update({(rate, r.rid): r.cls for r in done})
             st = serve.latency_stats(done, srv.log)
             st["rate_offered"] = rate
             runs.append(st)

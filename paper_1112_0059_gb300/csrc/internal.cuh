@@ -79,8 +79,9 @@ cudaError_t launch_merge_lists(const uint64_t* lists, int splits, int64_t m, int
 // knn_search output: first k entries of each sorted list as (row, distance).
 cudaError_t launch_extract_knn(const uint64_t* lists, int64_t m, int K1, int k, int32_t* idx,
                                int32_t* dist, cudaStream_t s);
-// Alg. 2 per-descriptor update: totals[img][C] += dist_C - dist_B.
-cudaError_t launch_lnbnn_score(const uint64_t* lists, int64_t m, int K1, int k, const int32_t* labels,
+// Alg. 2 per-descriptor update: totals[img][C] += dist_C - dist_B (rows whose
+// list is incomplete, which only a search that gave up leaves, are skipped).
+cudaError_t launch_lnbnn_score(const uint64_t* lists, int64_t m, int K1, int k, const int32_t* labels, int64_t n_ref,
                                const int64_t* offsets, int64_t n_img, int32_t C, int64_t* totals,
                                uint32_t* dev_err, cudaStream_t s);
 // Alg. 1 sum: totals[img][c] = sum of mins[row][c] over the image's rows.

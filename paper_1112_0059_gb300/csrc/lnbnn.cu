@@ -743,7 +743,8 @@ static lnbnn_status do_lnbnn_classify(lnbnn_index* index, lnbnn_workspace* w, co
     lnbnn_status st = shortlist ? run_knn_fp8(index, scratch, queries, n_queries, k + 1, M1, s, &lists, prof)
                                 : run_knn(index, scratch, queries, n_queries, k + 1, s, &lists, prof);
     if (st != LNBNN_OK) return st;
-    CK(launch_lnbnn_score(lists, n_queries, k + 1, k, index->labels, offsets, n_images, C, totals, index->dev_err, s));
+    CK(launch_lnbnn_score(lists, n_queries, k + 1, k, index->labels, index->n_ref, offsets, n_images, C, totals,
+                          index->dev_err, s));
     prof.launched(1);
   } else {
     prof.mark(1);

@@ -111,9 +111,9 @@ __device__ __forceinline__ int64_t image_of(const int64_t* __restrict__ offsets,
 // the first k is updated once with dist_C - dist_B, where dist_C is the
 // distance of its first (hence nearest) occurrence in the sorted list.
 __global__ void lnbnn_score_kernel(const uint64_t* __restrict__ lists, int64_t m, int K1, int k,
-                                   const int32_t* __restrict__ labels, const int64_t* __restrict__ offsets,
-                                   int64_t n_img, int32_t C, int64_t* __restrict__ totals,
-                                   uint32_t* __restrict__ dev_err) {
+                                   const int32_t* __restrict__ labels, int64_t n_ref,
+                                   const int64_t* __restrict__ offsets, int64_t n_img, int32_t C,
+                                   int64_t* __restrict__ totals, uint32_t* __restrict__ dev_err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   const int64_t img = image_of(offsets, n_img, i);
@@ -122,6 +122,11 @@ __global__ void lnbnn_score_kernel(const uint64_t* __restrict__ lists, int64_t m
     return;
   }
   const uint64_t* L = lists + i * K1;
+  // A complete list holds k+1 real rows.  Only a search that gave up (a
+  // timeout, reported by lnbnn_sync) leaves empty keys: skip such a row
+  // rather than gather labels[] at an empty key's row.
+  for (int a = 0; a <= k; ++a)
+    if ((int64_t)key_row(L[a]) >= n_ref) return;
   const int64_t dist_B = (int64_t)key_dist(L[k]);
   unsigned long long* t = reinterpret_cast<unsigned long long*>(totals + img * C);
   for (int a = 0; a < k; ++a) {
@@ -211,12 +216,12 @@ cudaError_t launch_extract_knn(const uint64_t* lists, int64_t m, int K1, int k, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_lnbnn_score(const uint64_t* lists, int64_t m, int K1, int k, const int32_t* labels,
+cudaError_t launch_lnbnn_score(const uint64_t* lists, int64_t m, int K1, int k, const int32_t* labels, int64_t n_ref,
                                const int64_t* offsets, int64_t n_img, int32_t C, int64_t* totals, uint32_t* dev_err,
                                cudaStream_t s) {
   if (m == 0 || n_img == 0) return cudaSuccess;
-  lnbnn_score_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(lists, m, K1, k, labels, offsets, n_img, C, totals,
-                                                                  dev_err);
+  lnbnn_score_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(lists, m, K1, k, labels, n_ref, offsets, n_img, C,
+                                                                  totals, dev_err);
   return cudaGetLastError();
 }
 
