@@ -59,7 +59,8 @@ typedef enum lnbnn_status {
   LNBNN_ERR_UNSUPPORTED = 8,  /* device is not compute capability 10.3 (sm_103) */
   LNBNN_ERR_OFFSETS = 9,      /* offsets not 0 = o[0] <= ... <= o[n_images] = n_queries */
   LNBNN_ERR_SCRATCH_LIMIT = 10, /* problem larger than a workspace or the scratch of knn_search_noalloc */
-  LNBNN_ERR_NO_FP8 = 11         /* an FP8 call on an index without lnbnn_index_prepare_fp8 */
+  LNBNN_ERR_NO_FP8 = 11,        /* an FP8 call on an index without lnbnn_index_prepare_fp8 */
+  LNBNN_ERR_IO = 12             /* a file could not be written or read, or is not an intact index file */
 } lnbnn_status;
 
 /*
@@ -311,6 +312,24 @@ LNBNN_API lnbnn_status lnbnn_profile_read(lnbnn_index *index, lnbnn_profile *out
 LNBNN_API lnbnn_status knn_search_noalloc(const uint8_t *ref, int64_t n_ref, const uint8_t *queries,
                                           int64_t n_queries, int32_t k, int32_t *idx, int32_t *dist,
                                           void *stream);
+
+/*
+ * Index persistence (no part of the method; lets a server restart without
+ * the original arrays).  lnbnn_index_save writes what lnbnn_index_create was
+ * given — the reference descriptors and their labels — to the file `path`:
+ * a 32-byte header (the 8 bytes "LNBNNIX1", uint32 format version 1, uint32
+ * descriptor length 128, int64 n_ref, int32 n_classes, uint32 0), the uint8
+ * descriptors [n_ref * 128], the int32 labels [n_ref], and an 8-byte FNV-1a
+ * 64-bit hash of everything before it; all integers little-endian.  The call
+ * waits for the device copies.  lnbnn_index_load checks the header, sizes and
+ * hash before it touches the device, then builds the index exactly as
+ * lnbnn_index_create would (the same results; derived operands, the FP8
+ * operand and a fitted schedule are rebuilt, not stored).
+ * Errors: INVALID_ARG, IO (cannot open, short read or write, wrong magic,
+ * version or sizes, hash mismatch), and those of lnbnn_index_create.
+ */
+LNBNN_API lnbnn_status lnbnn_index_save(const lnbnn_index *index, const char *path);
+LNBNN_API lnbnn_status lnbnn_index_load(const char *path, void *stream, lnbnn_index **out);
 
 /*
  * Test hooks for the failure paths (no part of the method).

@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 #include "knn_tc.cuh"
 
@@ -123,6 +125,15 @@ void free_index(lnbnn_index* ix) {
   cudaFree(ix->stage);
   delete ix;
 }
+
+// An NVTX range for the duration of a scope: calls and their phases show up
+// by name on a profiler's timeline (nothing is recorded without a tool).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 // Carves aligned sub-buffers out of one allocation.
 struct Carve {
@@ -296,6 +307,7 @@ lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_
   __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(ws + p.off_qext);
   uint64_t* part = reinterpret_cast<uint64_t*>(ws + p.off_lists);
   uint64_t* merged = reinterpret_cast<uint64_t*>(ws + p.off_merged);
+  Range range("lnbnn: exact k+1 search");
   CK(launch_prep_query(q, m, p.m_pad, qnorm, qbf, qext, s));
   prof.launched(1);
   prof.mark(1);
@@ -324,6 +336,7 @@ lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, in
   __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(ws + p.off_qext);
   uint64_t* part = reinterpret_cast<uint64_t*>(ws + p.off_lists);
   uint64_t* merged = reinterpret_cast<uint64_t*>(ws + p.off_merged);
+  Range range("lnbnn: FP8 shortlist search");
   CK(launch_prep_query_e4m3(q, m, p.m_pad, qf8, qext, s));
   prof.launched(1);
   prof.mark(1);
@@ -380,12 +393,14 @@ const char* lnbnn_status_string(lnbnn_status st) {
     case LNBNN_ERR_OFFSETS: return "invalid image offsets";
     case LNBNN_ERR_SCRATCH_LIMIT: return "problem larger than the fixed scratch (workspace or knn_search_noalloc)";
     case LNBNN_ERR_NO_FP8: return "the index has no FP8 operand (call lnbnn_index_prepare_fp8 first)";
+    case LNBNN_ERR_IO: return "file could not be written or read, or is not an intact index file";
   }
   return "unknown status";
 }
 
 lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64_t n_ref, int32_t n_classes,
                                 void* stream, lnbnn_index** out) {
+  Range range("lnbnn: lnbnn_index_create");
   if (!out) return LNBNN_ERR_INVALID_ARG;
   *out = nullptr;
   if (!ref || !labels || n_ref < 1 || n_classes < 1 || n_ref > (int64_t)INT32_MAX - kRefPad)
@@ -488,6 +503,123 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
 
 void lnbnn_index_destroy(lnbnn_index* index) { free_index(index); }
 
+// ------------------------------------------------------------ persistence
+
+namespace {
+
+constexpr char kFileMagic[8] = {'L', 'N', 'B', 'N', 'N', 'I', 'X', '1'};
+constexpr uint32_t kFileVersion = 1;
+constexpr size_t kFileChunk = size_t(64) << 20;  // bytes staged through host memory at a time
+
+struct FileHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t dim;
+  int64_t n_ref;
+  int32_t n_classes;
+  uint32_t reserved;
+};
+static_assert(sizeof(FileHeader) == 32, "the file header is 32 bytes");
+
+// FNV-1a, 64-bit.
+struct Fnv64 {
+  uint64_t h = 1469598103934665603ull;
+  void add(const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  }
+};
+
+struct File {
+  FILE* f = nullptr;
+  File(const char* path, const char* mode) : f(fopen(path, mode)) {}
+  ~File() {
+    if (f) fclose(f);
+  }
+};
+
+// Copies `bytes` of device memory to the file through a host buffer, hashing them.
+bool write_device(FILE* f, const void* dev, size_t bytes, std::vector<unsigned char>& buf, Fnv64& h) {
+  for (size_t off = 0; off < bytes; off += kFileChunk) {
+    const size_t n = std::min(kFileChunk, bytes - off);
+    if (cudaMemcpy(buf.data(), static_cast<const unsigned char*>(dev) + off, n, cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return false;
+    h.add(buf.data(), n);
+    if (fwrite(buf.data(), 1, n, f) != n) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+lnbnn_status lnbnn_index_save(const lnbnn_index* index, const char* path) {
+  if (!index || !path) return LNBNN_ERR_INVALID_ARG;
+  Range range("lnbnn: lnbnn_index_save");
+  File file(path, "wb");
+  if (!file.f) return LNBNN_ERR_IO;
+  FileHeader hd{};
+  memcpy(hd.magic, kFileMagic, sizeof kFileMagic);
+  hd.version = kFileVersion;
+  hd.dim = kDim;
+  hd.n_ref = index->n_ref;
+  hd.n_classes = index->n_classes;
+  Fnv64 h;
+  h.add(&hd, sizeof hd);
+  if (fwrite(&hd, sizeof hd, 1, file.f) != 1) return LNBNN_ERR_IO;
+  std::vector<unsigned char> buf(kFileChunk);
+  if (!write_device(file.f, index->ref_u8, (size_t)index->n_ref * kDim, buf, h) ||
+      !write_device(file.f, index->labels, sizeof(int32_t) * (size_t)index->n_ref, buf, h))
+    return LNBNN_ERR_IO;
+  if (fwrite(&h.h, sizeof h.h, 1, file.f) != 1 || fflush(file.f) != 0) return LNBNN_ERR_IO;
+  return LNBNN_OK;
+}
+
+lnbnn_status lnbnn_index_load(const char* path, void* stream, lnbnn_index** out) {
+  if (!out) return LNBNN_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!path) return LNBNN_ERR_INVALID_ARG;
+  Range range("lnbnn: lnbnn_index_load");
+  File file(path, "rb");
+  if (!file.f) return LNBNN_ERR_IO;
+  FileHeader hd{};
+  if (fread(&hd, sizeof hd, 1, file.f) != 1) return LNBNN_ERR_IO;
+  if (memcmp(hd.magic, kFileMagic, sizeof kFileMagic) != 0 || hd.version != kFileVersion || hd.dim != kDim ||
+      hd.n_ref < 1 || hd.n_ref > (int64_t)INT32_MAX - kRefPad || hd.n_classes < 1 || hd.reserved != 0)
+    return LNBNN_ERR_IO;
+  // the whole payload is read and its hash checked before the device is touched
+  const size_t ref_bytes = (size_t)hd.n_ref * kDim, lab_bytes = sizeof(int32_t) * (size_t)hd.n_ref;
+  std::vector<unsigned char> ref, lab;
+  try {
+    ref.resize(ref_bytes);
+    lab.resize(lab_bytes);
+  } catch (const std::bad_alloc&) {
+    return LNBNN_ERR_OOM;
+  }
+  Fnv64 h;
+  h.add(&hd, sizeof hd);
+  uint64_t stored = 0;
+  if (fread(ref.data(), 1, ref_bytes, file.f) != ref_bytes || fread(lab.data(), 1, lab_bytes, file.f) != lab_bytes ||
+      fread(&stored, sizeof stored, 1, file.f) != 1 || fgetc(file.f) != EOF)
+    return LNBNN_ERR_IO;
+  h.add(ref.data(), ref_bytes);
+  h.add(lab.data(), lab_bytes);
+  if (h.h != stored) return LNBNN_ERR_IO;
+  uint8_t* ref_d = nullptr;
+  int32_t* lab_d = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  lnbnn_status st = LNBNN_OK;
+  cudaError_t e = dmalloc(&ref_d, ref_bytes);
+  if (e == cudaSuccess) e = dmalloc(&lab_d, (size_t)hd.n_ref);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ref_d, ref.data(), ref_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lab_d, lab.data(), lab_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  st = e == cudaSuccess ? lnbnn_index_create(ref_d, lab_d, hd.n_ref, hd.n_classes, stream, out) : status_of(e);
+  cudaFree(ref_d);
+  cudaFree(lab_d);
+  return st;
+}
+
 void lnbnn_debug_fail_allocations(int32_t count) { g_fail_allocs.store(count > 0 ? count : 0); }
 
 lnbnn_status lnbnn_set_start_gate(lnbnn_index* index, const uint32_t* gate) {
@@ -503,6 +635,7 @@ lnbnn_status lnbnn_plan_splits(const lnbnn_index* index, int64_t n_queries, int3
 }
 
 lnbnn_status lnbnn_autotune(lnbnn_index* index, void* stream, lnbnn_tuning* out) {
+  Range range("lnbnn: lnbnn_autotune");
   if (!index) return LNBNN_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int P = index->sm_count;
@@ -649,6 +782,7 @@ lnbnn_status lnbnn_autotune(lnbnn_index* index, void* stream, lnbnn_tuning* out)
 }
 
 lnbnn_status lnbnn_index_prepare_fp8(lnbnn_index* index, void* stream) {
+  Range range("lnbnn: lnbnn_index_prepare_fp8");
   if (!index) return LNBNN_ERR_INVALID_ARG;
   if (index->fp8) return LNBNN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -683,6 +817,7 @@ lnbnn_status lnbnn_index_info(const lnbnn_index* index, int64_t* n_ref, int32_t*
 
 static lnbnn_status do_knn_search(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries, int64_t n_queries,
                                   int32_t k, int32_t* idx, int32_t* dist, void* stream) {
+  Range range("lnbnn: knn_search");
   if (!index || n_queries < 0) return LNBNN_ERR_INVALID_ARG;
   if (!k_ok(index, k, 0)) return LNBNN_ERR_K_RANGE;
   if (n_queries == 0) return LNBNN_OK;
@@ -701,6 +836,7 @@ static lnbnn_status do_knn_search(lnbnn_index* index, lnbnn_workspace* w, const 
 static lnbnn_status do_knn_search_fp8(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries,
                                       int64_t n_queries, int32_t k, int32_t shortlist, int32_t* idx, int32_t* dist,
                                       void* stream) {
+  Range range("lnbnn: knn_search_fp8");
   if (!index || n_queries < 0) return LNBNN_ERR_INVALID_ARG;
   int M1 = 0;
   if (!k_ok(index, k, 0) || !shortlist_ok(index, shortlist, k, &M1)) return LNBNN_ERR_K_RANGE;
@@ -722,6 +858,7 @@ static lnbnn_status do_knn_search_fp8(lnbnn_index* index, lnbnn_workspace* w, co
 static lnbnn_status do_lnbnn_classify(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries,
                                       int64_t n_queries, const int64_t* offsets, int64_t n_images, int32_t k,
                                       int32_t shortlist, int64_t* totals, int32_t* classes, void* stream) {
+  Range range("lnbnn: lnbnn_classify");
   if (!index || n_queries < 0 || n_images < 0) return LNBNN_ERR_INVALID_ARG;
   if (!k_ok(index, k, 1)) return LNBNN_ERR_K_RANGE;
   int M1 = 0;
@@ -758,6 +895,7 @@ static lnbnn_status do_lnbnn_classify(lnbnn_index* index, lnbnn_workspace* w, co
 static lnbnn_status do_nbnn_classify(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries,
                                      int64_t n_queries, const int64_t* offsets, int64_t n_images, int64_t* totals,
                                      int32_t* classes, void* stream) {
+  Range range("lnbnn: nbnn_classify");
   if (!index || n_queries < 0 || n_images < 0) return LNBNN_ERR_INVALID_ARG;
   if (index->has_empty_class) return LNBNN_ERR_EMPTY_CLASS;
   if (n_images == 0) return n_queries == 0 ? LNBNN_OK : LNBNN_ERR_OFFSETS;
@@ -890,6 +1028,7 @@ lnbnn_status nbnn_classify_ws(lnbnn_index* index, lnbnn_workspace* w, const uint
 static lnbnn_status classify_host(lnbnn_index* index, bool local, const uint8_t* queries, int64_t n_queries,
                                   const int64_t* offsets, int64_t n_images, int32_t k, int32_t shortlist,
                                   int64_t* totals, int32_t* classes, void* stream) {
+  Range range("lnbnn: classify_host");
   if (!index || n_queries < 0 || n_images < 0) return LNBNN_ERR_INVALID_ARG;
   if (n_images == 0) return n_queries == 0 ? LNBNN_OK : LNBNN_ERR_OFFSETS;
   if (!offsets || !totals || !classes || (n_queries > 0 && !queries)) return LNBNN_ERR_INVALID_ARG;

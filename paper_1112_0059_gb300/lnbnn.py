@@ -32,6 +32,7 @@ STATUS = {
     9: "invalid image offsets",
     10: "problem larger than a workspace or the scratch of knn_search_noalloc",
     11: "the index has no FP8 operand (call prepare_fp8 first)",
+    12: "file could not be written or read, or is not an intact index file",
 }
 MAX_K = 255
 
@@ -41,7 +42,7 @@ EXPORTS = ["lnbnn_index_create", "lnbnn_index_destroy", "lnbnn_index_info", "knn
            "lnbnn_workspace_destroy", "knn_search_ws", "lnbnn_classify_ws", "nbnn_classify_ws",
            "lnbnn_index_prepare_fp8", "knn_search_fp8", "lnbnn_classify_fp8", "knn_search_fp8_ws",
            "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host", "lnbnn_autotune", "lnbnn_plan_splits",
-           "lnbnn_debug_fail_allocations", "lnbnn_set_start_gate"]
+           "lnbnn_debug_fail_allocations", "lnbnn_set_start_gate", "lnbnn_index_save", "lnbnn_index_load"]
 
 
 class Profile(ctypes.Structure):
@@ -113,6 +114,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.lnbnn_debug_fail_allocations.restype = None
         lib.lnbnn_set_start_gate.argtypes = [P, P]
         lib.lnbnn_set_start_gate.restype = ctypes.c_int
+        lib.lnbnn_index_save.argtypes = [P, ctypes.c_char_p]
+        lib.lnbnn_index_save.restype = ctypes.c_int
+        lib.lnbnn_index_load.argtypes = [ctypes.c_char_p, P, ctypes.POINTER(P)]
+        lib.lnbnn_index_load.restype = ctypes.c_int
         lib.lnbnn_status_string.argtypes = [ctypes.c_int]
         lib.lnbnn_status_string.restype = ctypes.c_char_p
         for name in ("lnbnn_index_create", "lnbnn_index_info", "knn_search", "lnbnn_classify", "nbnn_classify",
@@ -165,6 +170,23 @@ class Index:
                                             self.n_ref, self.n_classes, _stream_ptr(stream), ctypes.byref(h)),
                "lnbnn_index_create")
         self._h = h
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Index":
+        """An index from a file written by ``save`` (checked before use)."""
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.lnbnn_index_load(os.fsencode(path), _stream_ptr(stream), ctypes.byref(h)), "lnbnn_index_load")
+        ix = cls.__new__(cls)
+        ix._lib, ix._h = lib, h
+        n_ref, n_cls = ctypes.c_int64(), ctypes.c_int32()
+        _check(lib.lnbnn_index_info(h, ctypes.byref(n_ref), ctypes.byref(n_cls)), "lnbnn_index_info")
+        ix.n_ref, ix.n_classes = int(n_ref.value), int(n_cls.value)
+        return ix
+
+    def save(self, path: str) -> None:
+        """Write the index's references and labels to ``path`` (lnbnn_index_save)."""
+        _check(self._lib.lnbnn_index_save(self.handle, os.fsencode(path)), "lnbnn_index_save")
 
     def close(self) -> None:
         if getattr(self, "_h", None):

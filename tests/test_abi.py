@@ -39,7 +39,7 @@ def test_binding_names_match_header():
 
 
 def test_status_strings(lib):
-    for code in range(12):
+    for code in range(13):
         assert lib.lnbnn_status_string(code) != b"unknown status"
     assert b"prepare_fp8" in lib.lnbnn_status_string(11)
     assert b"k out of range" in lib.lnbnn_status_string(4)
