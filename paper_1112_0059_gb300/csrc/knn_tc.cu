@@ -71,6 +71,10 @@ constexpr uint32_t kAExtBytes = kBM * kExt * 2;      // 4 KB
 constexpr uint32_t kBChunkBytes = kBN * kBK * 2;     // 32 KB
 constexpr uint32_t kBExtBytes = kBN * kExt * 2;      // 8 KB
 constexpr uint32_t kStageBytes = kBChunkBytes + kBExtBytes;
+// Longest reference split for which the exact scan keeps 33..64-entry lists
+// in shared memory rather than registers.
+constexpr int64_t kSmemListMaxRefs = int64_t(8) << 20;
+
 // Threads of a CTA whose epilogue has `epq` warps per TMEM lane quarter: the
 // producer warp, the MMA warp and 4 * epq epilogue warps.
 constexpr int threads_for(int epq) { return 64 + 32 * 4 * epq; }
@@ -138,7 +142,7 @@ struct Bars {
 // The layout of a kernel instantiation: the format's query chunks; four ring
 // stages, or three when the epilogue's lists take shared memory.
 template <class Fmt, class Epilogue>
-using LayoutOf = Layout<Fmt::kChunks, Epilogue::kListBytes ? 3 : 4, Epilogue::kListBytes>;
+using LayoutOf = Layout<Fmt::kChunks, Epilogue::kListBytes ? (Fmt::kChunks == 2 ? 2 : 3) : 4, Epilogue::kListBytes>;
 
 __device__ __forceinline__ void flag_timeout(volatile uint32_t* abort_flag, uint32_t* dev_err) {
   *abort_flag = 1u;
@@ -316,6 +320,125 @@ struct KnnEpilogue {
       L.store(out, K1);
     } else {
       top.finish();
+    }
+  }
+};
+
+// kNN epilogue with the lists in shared memory, for lists of up to KM = 64
+// entries on the one-warp-per-quarter layout (register lists that long leave
+// the insert as the bottleneck: a 64-wide insertion network per list and
+// only four warps to hide it).  Each epilogue warp keeps its 32 rows' lists
+// in shared memory, list by list, as float bit patterns and rows, and inserts
+// with the whole warp: lane i computes entries i and i + 32 of the list
+// (shifted, the new key, or unchanged) from their predecessors, so an insert
+// is a few instructions per lane whatever the list length.  Candidates are
+// taken lane by lane (the lowest lane with a hit first) and, within a lane,
+// in column order, so each list still receives its columns in increasing row
+// order.
+template <int KM>
+struct KnnSmemEpilogue {
+  static constexpr int kWarpsPerQuarter = 1;
+  static constexpr int kPerLane = KM / 32;  // list entries each lane computes in an insert
+  static constexpr uint32_t kListBytes = 4 * kWarpsPerQuarter * 32 * KM * 8;
+  static constexpr int32_t kInf = 0x7F800000;  // bits of +inf, above every distance
+  static_assert(KM % 32 == 0 && KM <= 64, "entries i and i + 32 per lane");
+  uint32_t* D;  // this warp's lists: D[list * KM + i] bit patterns, R[list * KM + i] rows
+  uint32_t* R;
+  int32_t thr;  // bit pattern of this lane's list's K1-th entry
+  bool active;
+  int K1;
+  int lane;
+  uint64_t* out;
+  __device__ __forceinline__ KnnSmemEpilogue(const ScanOut& o, int list, int64_t row, bool act, int64_t,
+                                             uint8_t* smem_list, int epi_warp)
+      : D(reinterpret_cast<uint32_t*>(smem_list) + (size_t)epi_warp * 32 * KM * 2),
+        R(D + 32 * KM),
+        thr(kInf),
+        active(act),
+        K1(o.K1),
+        lane((int)(threadIdx.x & 31)),
+        out(o.lists + ((int64_t)list * o.stride + (act ? row : 0)) * o.K1) {
+    for (int l = 0; l < 32; ++l)
+#pragma unroll
+      for (int e = 0; e < kPerLane; ++e) {
+        D[l * KM + e * 32 + lane] = (uint32_t)kInf;
+        R[l * KM + e * 32 + lane] = 0xFFFFFFFFu;
+      }
+    __syncwarp();
+  }
+  // Insert (x, row) into list L; every lane takes part.  Requires x below the
+  // list's K1-th entry.
+  __device__ __forceinline__ void insert(int L, int32_t x, uint32_t row) {
+    uint32_t* d = D + L * KM;
+    uint32_t* r = R + L * KM;
+    int32_t a[kPerLane];
+    uint32_t ra[kPerLane];
+#pragma unroll
+    for (int e = 0; e < kPerLane; ++e) {
+      a[e] = (int32_t)d[e * 32 + lane];
+      ra[e] = r[e * 32 + lane];
+    }
+    int32_t nd[kPerLane];
+#pragma unroll
+    for (int e = 0; e < kPerLane; ++e) {
+      // predecessor of entry e * 32 + lane: lane - 1 of the same half, or
+      // lane 31 of the previous half for lane 0
+      const int32_t up = __shfl_up_sync(0xffffffffu, a[e], 1);
+      const uint32_t upr = __shfl_up_sync(0xffffffffu, ra[e], 1);
+      int32_t b = up;
+      uint32_t rb = upr;
+      bool has_pred = lane > 0;
+      if (e > 0) {
+        const int32_t w = __shfl_sync(0xffffffffu, a[e - 1], 31);
+        const uint32_t wr = __shfl_sync(0xffffffffu, ra[e - 1], 31);
+        if (lane == 0) {
+          b = w;
+          rb = wr;
+          has_pred = true;
+        }
+      }
+      const bool shift = has_pred && x < b;
+      const bool place = !shift && x < a[e];
+      nd[e] = shift ? b : (place ? x : a[e]);
+      const uint32_t nr = shift ? rb : (place ? row : ra[e]);
+      if (e * 32 + lane < K1) {
+        d[e * 32 + lane] = (uint32_t)nd[e];
+        r[e * 32 + lane] = nr;
+      }
+    }
+    // the list's new K1-th entry
+    const int last = K1 - 1;
+    int32_t v = nd[0];
+#pragma unroll
+    for (int e = 1; e < kPerLane; ++e)
+      if ((last >> 5) == e) v = nd[e];
+    const int32_t nt = __shfl_sync(0xffffffffu, v, last & 31);
+    if (lane == L) thr = nt;
+    __syncwarp();
+  }
+  __device__ __forceinline__ void group(const uint32_t (&v)[32], uint32_t mn, int64_t col0) {
+    const bool hit = active && (int32_t)mn < thr;
+    if (!__any_sync(0xffffffffu, hit)) return;
+    uint32_t mask = hit ? hit_mask(v, thr) : 0u;
+    for (;;) {
+      const uint32_t who = __ballot_sync(0xffffffffu, mask != 0u);
+      if (who == 0u) break;
+      const int L = __ffs(who) - 1;
+      const int j = mask ? __ffs(mask) - 1 : 0;
+      const int32_t x = __shfl_sync(0xffffffffu, select32(v, j), L);
+      const int jl = __shfl_sync(0xffffffffu, j, L);
+      const int32_t tl = __shfl_sync(0xffffffffu, thr, L);
+      if (lane == L) mask &= mask - 1;
+      if (x < tl) insert(L, x, (uint32_t)(col0 + jl));  // warp-uniform
+    }
+  }
+  __device__ __forceinline__ void finish() {
+    __syncwarp();
+    if (!active) return;
+    for (int i = 0; i < K1; ++i) {
+      const uint32_t bits = D[lane * KM + i];
+      out[i] = (int32_t)bits == kInf ? kEmptyKey
+                                      : make_key((uint32_t)__float2int_rn(__uint_as_float(bits)), R[lane * KM + i]);
     }
   }
 };
@@ -696,12 +819,13 @@ cudaError_t prepare_one() {
 cudaError_t prepare_tc_kernels() {
   cudaError_t e = prepare_one<FmtBf16, KnnEpilogue<kTcRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnEpilogue<kTcCoarseRegListMax>>();
+  if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnSmemEpilogue<kTcWideRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnEpilogue<kTcWideRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnEpilogue<0>>();
   if (e == cudaSuccess) e = prepare_one<FmtBf16, NbnnEpilogue>();
   if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<kTcRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<kTcCoarseRegListMax>>();
-  if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<kTcWideRegListMax>>();
+  if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnSmemEpilogue<kTcWideRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<0>>();
   return e;
 }
@@ -723,9 +847,17 @@ cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv
   if (K1 <= kTcCoarseRegListMax)
     return launch_scan<FmtBf16, KnnEpilogue<kTcCoarseRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
                                                                   split_len, out, dev_err, stats, s);
-  if (K1 <= kTcWideRegListMax)
+  if (K1 <= kTcWideRegListMax) {
+    // Lists in shared memory make inserts cheap but leave room for only a
+    // two-stage ring; register lists keep four stages.  Measured on the
+    // 256-class data (k = 50): shared memory is faster while a split holds up
+    // to 5.76M references (26% at 2.88M, 8% at 5.76M), registers at 11.52M (16%).
+    if (split_len <= kSmemListMaxRefs)
+      return launch_scan<FmtBf16, KnnSmemEpilogue<kTcWideRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
+                                                                      split_len, out, dev_err, stats, s);
     return launch_scan<FmtBf16, KnnEpilogue<kTcWideRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
                                                                 split_len, out, dev_err, stats, s);
+  }
   return launch_scan<FmtBf16, KnnEpilogue<0>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len, out, dev_err,
                                               stats, s);
 }
@@ -746,8 +878,8 @@ cudaError_t launch_coarse_tc(const TcTensorMaps& maps, const uint8_t* qf8, const
     return launch_scan<FmtE4m3, KnnEpilogue<kTcCoarseRegListMax>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref,
                                                                   splits, split_len, out, dev_err, stats, s);
   if (K1 <= kTcWideRegListMax)
-    return launch_scan<FmtE4m3, KnnEpilogue<kTcWideRegListMax>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref,
-                                                                splits, split_len, out, dev_err, stats, s);
+    return launch_scan<FmtE4m3, KnnSmemEpilogue<kTcWideRegListMax>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad,
+                                                                    n_ref, splits, split_len, out, dev_err, stats, s);
   return launch_scan<FmtE4m3, KnnEpilogue<0>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref, splits, split_len,
                                               out, dev_err, stats, s);
 }

@@ -25,7 +25,9 @@ constexpr int kCoarseQueryPad = kTcQueryTile * kTcCoarseCluster > kQueryPad ? kT
                                                                              : kQueryPad;
 // Lists of the k+1 (or shortlist) nearest per query row: up to 16 entries a
 // 16-entry register list (the fewest registers), up to 32 a 32-entry one, up
-// to 64 a 64-entry one, longer ones a heap in global memory.
+// to 64 a 64-entry list in shared memory with warp-cooperative inserts (in
+// registers for an exact scan of long splits), longer ones a heap in global
+// memory.
 constexpr int kTcRegListMax = 16;
 constexpr int kTcCoarseRegListMax = 32;
 constexpr int kTcWideRegListMax = 64;
