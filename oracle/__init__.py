@@ -22,6 +22,10 @@ approximate kd-tree search of Section 5; exact neighbours on the shortlist):
   coarse_matrix  -- ||q'||^2 + ||r'||^2 - 2 q~.r~ with x' = x - 64, x~ = E4M3(x')
   knn_coarse     -- the m smallest coarse values, reranked by exact distance
   local_nbnn_coarse -- Alg. 2 on the reranked neighbours
+
+NBNN as a sum of log-odds increments (Section 3.1, with the "positive
+increments only" variant of Table 1) is float64 numpy in ``logodds.py``, on
+top of ``class_min``.
 """
 from __future__ import annotations
 
