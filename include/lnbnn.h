@@ -164,6 +164,41 @@ LNBNN_API lnbnn_status nbnn_classify_ws(lnbnn_index *index, lnbnn_workspace *wor
                                         int64_t *totals, int32_t *classes, void *stream);
 
 /*
+ * NBNN as a sum of log-odds increments, Section 3.1.  Each descriptor d of
+ * image i adds to every class C
+ *   inc(d, C) = log [P(C|d) P(Cbar)] / [P(Cbar|d) P(C)]           Eq. (eqn:log-odds)
+ * (Cbar: all other classes; equal priors P(C) = 1 / n_classes, so the prior
+ * term of Eq. (eqn:log-increments) is dropped), with the posterior of the NBNN
+ * Gaussian kernel on each class's nearest neighbour:
+ *   P(C|d) = exp(-beta ||d - NN_C(d)||^2) / sum_C' exp(-beta ||d - NN_C'(d)||^2),
+ * beta = 1 / (2 sigma^2); the paper leaves sigma unstated, so beta is the
+ * caller's.  totals[i][C] = sum of the increments (positive_only != 0: only
+ * those > 0, the variant of Table 1), classes[i] = argmax_C totals[i][C]
+ * (lowest class on ties); n_increments[i] (optional) = how many increments
+ * were added (n_classes per descriptor for the full rule).
+ *
+ *   beta          0 <= beta <= 1e250 (finite); 0 makes every increment 0
+ *   totals        device float64 [n_images * n_classes], overwritten; each
+ *                 image's sums are taken in descriptor order (deterministic)
+ *   classes       device int32 [n_images]
+ *   n_increments  device int64 [n_images] or NULL
+ * Other arguments as nbnn_classify.  An empty image gets all-zero totals,
+ * class 0 and no increments.  The distances NN_C(d) are exact (the scan of
+ * nbnn_classify); the increments are float64 (device exp and log).
+ * Errors: as nbnn_classify, plus INVALID_ARG for beta outside the range or an
+ * index with fewer than two classes.
+ */
+LNBNN_API lnbnn_status nbnn_logodds_classify(lnbnn_index *index, const uint8_t *queries, int64_t n_queries,
+                                             const int64_t *offsets, int64_t n_images, double beta,
+                                             int32_t positive_only, double *totals, int32_t *classes,
+                                             int64_t *n_increments, void *stream);
+LNBNN_API lnbnn_status nbnn_logodds_classify_ws(lnbnn_index *index, lnbnn_workspace *workspace,
+                                                const uint8_t *queries, int64_t n_queries, const int64_t *offsets,
+                                                int64_t n_images, double beta, int32_t positive_only,
+                                                double *totals, int32_t *classes, int64_t *n_increments,
+                                                void *stream);
+
+/*
  * FP8 shortlist search: an approximate search of this library's own design,
  * in the place the paper fills with an approximate kd-tree search (Section
  * 5, "Approximate nearest neighbors"); the paper has no FP8 step.  A coarse

@@ -102,6 +102,19 @@ cudaError_t launch_prep_query_e4m3(const uint8_t* q, int64_t m, int64_t m_pad, u
 // among the rows of its shortlist [m, M1] (kEmptyKey entries are no row).
 cudaError_t launch_rerank(const uint64_t* shortlist, int64_t m, int M1, const uint8_t* q, const uint8_t* ref,
                           int64_t n_ref, int K1, uint64_t* out, cudaStream_t s);
+// NBNN as a sum of log-odds increments (logodds.cu).  Per descriptor row of the
+// [m, C] class-minimum table, the statistics of its posterior (32 bytes a row);
+// then per image and class the sum of the increments (all, or only those > 0)
+// in row order, and per image the number of increments added (counts may be
+// null; it is added to, so the caller zeroes it).
+constexpr int kLogoddsRowStatBytes = 32;
+cudaError_t launch_logodds_rowstat(const int32_t* mins, int64_t m, int32_t C, double beta, void* rowstat,
+                                   cudaStream_t s);
+cudaError_t launch_logodds_sum(const int32_t* mins, const void* rowstat, int64_t m, int32_t C, double beta,
+                               bool positive_only, const int64_t* offsets, int64_t n_img, double* totals,
+                               int64_t* counts, cudaStream_t s);
+// argmax over classes per image, lowest class on ties.
+cudaError_t launch_argmax_f64(const double* totals, int64_t n_img, int32_t C, int32_t* classes, cudaStream_t s);
 // argmin over classes per image, lowest class on ties.
 cudaError_t launch_argmin(const int64_t* totals, int64_t n_img, int32_t C, int32_t* classes, cudaStream_t s);
 

@@ -265,7 +265,7 @@ struct Scratch {
 
 struct NbnnPlan {
   KnnPlan k;
-  size_t off_qnorm, off_qbf, off_qext, off_mins, bytes;
+  size_t off_qnorm, off_qbf, off_qext, off_mins, off_rowstat, bytes;
 };
 
 NbnnPlan plan_nbnn(const lnbnn_index* ix, int64_t m) {
@@ -276,6 +276,7 @@ NbnnPlan plan_nbnn(const lnbnn_index* ix, int64_t m) {
   p.off_qbf = c.take<__nv_bfloat16>(p.k.m_pad * kDim);
   p.off_qext = c.take<__nv_bfloat16>(p.k.m_pad * kExt);
   p.off_mins = c.take<int32_t>((size_t)p.k.m_pad * ix->n_classes);
+  p.off_rowstat = c.take<char>((size_t)p.k.m_pad * kLogoddsRowStatBytes);  // log-odds rule only
   p.bytes = c.off;
   return p;
 }
@@ -892,6 +893,36 @@ static lnbnn_status do_lnbnn_classify(lnbnn_index* index, lnbnn_workspace* w, co
   return LNBNN_OK;
 }
 
+// The [m_pad, C] table of class minima NN_C(d), one row per query row, filled
+// by the tensor-core scan of the class-sorted references (Alg. 1's inner
+// loop).  Sets *mins and, when rowstat is given, the row-statistics buffer of
+// the same workspace.
+static lnbnn_status scan_class_minima(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries,
+                                      int64_t n_queries, cudaStream_t s, CallProfile& prof, int32_t** mins,
+                                      void** rowstat) {
+  const NbnnPlan np = plan_nbnn(index, n_queries);
+  const KnnPlan& p = np.k;
+  Scratch scratch{index, w};
+  char* ws = nullptr;
+  lnbnn_status st = scratch.get(np.bytes, &ws);
+  if (st != LNBNN_OK) return st;
+  int32_t* qnorm = reinterpret_cast<int32_t*>(ws + np.off_qnorm);
+  __nv_bfloat16* qbf = reinterpret_cast<__nv_bfloat16*>(ws + np.off_qbf);
+  __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(ws + np.off_qext);
+  *mins = reinterpret_cast<int32_t*>(ws + np.off_mins);
+  if (rowstat) *rowstat = ws + np.off_rowstat;
+  CK(launch_prep_query(queries, n_queries, p.m_pad, qnorm, qbf, qext, s));
+  CK(cudaMemsetAsync(*mins, 0x7F, sizeof(int32_t) * (size_t)p.m_pad * index->n_classes, s));  // > any distance
+  prof.launched(1);
+  prof.mark(1);
+  CK(launch_nbnn_tc(index->tc, qbf, qext, n_queries, p.m_pad, index->n_ref, p.splits, p.split_len, *mins,
+                    index->n_classes, index->class_off_d, index->dev_err,
+                    index->prof_on ? index->prof_stats : nullptr, index->gate, s));
+  prof.launched(1, true);
+  prof.mark(2);
+  return LNBNN_OK;
+}
+
 static lnbnn_status do_nbnn_classify(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries,
                                      int64_t n_queries, const int64_t* offsets, int64_t n_images, int64_t* totals,
                                      int32_t* classes, void* stream) {
@@ -910,31 +941,48 @@ static lnbnn_status do_nbnn_classify(lnbnn_index* index, lnbnn_workspace* w, con
     prof.mark(1);
     prof.mark(2);
   } else {
-    // one query per row of a [m_pad, C] table of class minima, filled by the
-    // tensor-core scan of the class-sorted copy and summed per image
-    const NbnnPlan np = plan_nbnn(index, n_queries);
-    const KnnPlan& p = np.k;
-    Scratch scratch{index, w};
-    char* ws = nullptr;
-    lnbnn_status st = scratch.get(np.bytes, &ws);
+    int32_t* mins = nullptr;
+    lnbnn_status st = scan_class_minima(index, w, queries, n_queries, s, prof, &mins, nullptr);
     if (st != LNBNN_OK) return st;
-    int32_t* qnorm = reinterpret_cast<int32_t*>(ws + np.off_qnorm);
-    __nv_bfloat16* qbf = reinterpret_cast<__nv_bfloat16*>(ws + np.off_qbf);
-    __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(ws + np.off_qext);
-    int32_t* mins = reinterpret_cast<int32_t*>(ws + np.off_mins);
-    CK(launch_prep_query(queries, n_queries, p.m_pad, qnorm, qbf, qext, s));
-    CK(cudaMemsetAsync(mins, 0x7F, sizeof(int32_t) * (size_t)p.m_pad * C, s));  // 0x7F7F7F7F > any distance
-    prof.launched(1);
-    prof.mark(1);
-    CK(launch_nbnn_tc(index->tc, qbf, qext, n_queries, p.m_pad, index->n_ref, p.splits, p.split_len, mins, C,
-                      index->class_off_d, index->dev_err, index->prof_on ? index->prof_stats : nullptr, index->gate,
-                      s));
-    prof.launched(1, true);
-    prof.mark(2);
     CK(launch_nbnn_sum(mins, n_queries, C, offsets, n_images, totals, s));
     prof.launched(1);
   }
   CK(launch_argmin(totals, n_images, C, classes, s));
+  prof.launched(1);
+  return LNBNN_OK;
+}
+
+static lnbnn_status do_nbnn_logodds_classify(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries,
+                                             int64_t n_queries, const int64_t* offsets, int64_t n_images,
+                                             double beta, bool positive_only, double* totals, int32_t* classes,
+                                             int64_t* n_increments, void* stream) {
+  Range range("lnbnn: nbnn_logodds_classify");
+  if (!index || n_queries < 0 || n_images < 0) return LNBNN_ERR_INVALID_ARG;
+  if (!(beta >= 0.0 && beta <= 1e250) || index->n_classes < 2) return LNBNN_ERR_INVALID_ARG;
+  if (index->has_empty_class) return LNBNN_ERR_EMPTY_CLASS;
+  if (n_images == 0) return n_queries == 0 ? LNBNN_OK : LNBNN_ERR_OFFSETS;
+  if (!offsets || !totals || !classes || (n_queries > 0 && !queries)) return LNBNN_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CallProfile prof(index, s);
+  const int32_t C = index->n_classes;
+  CK(cudaMemsetAsync(totals, 0, sizeof(double) * (size_t)n_images * C, s));
+  if (n_increments) CK(cudaMemsetAsync(n_increments, 0, sizeof(int64_t) * (size_t)n_images, s));
+  CK(launch_check_offsets(offsets, n_images, n_queries, index->dev_err, s));
+  prof.launched(1);
+  if (n_queries == 0) {
+    prof.mark(1);
+    prof.mark(2);
+  } else {
+    int32_t* mins = nullptr;
+    void* rowstat = nullptr;
+    lnbnn_status st = scan_class_minima(index, w, queries, n_queries, s, prof, &mins, &rowstat);
+    if (st != LNBNN_OK) return st;
+    CK(launch_logodds_rowstat(mins, n_queries, C, beta, rowstat, s));
+    CK(launch_logodds_sum(mins, rowstat, n_queries, C, beta, positive_only, offsets, n_images, totals,
+                          n_increments, s));
+    prof.launched(2);
+  }
+  CK(launch_argmax_f64(totals, n_images, C, classes, s));
   prof.launched(1);
   return LNBNN_OK;
 }
@@ -965,6 +1013,13 @@ lnbnn_status lnbnn_classify_fp8(lnbnn_index* index, const uint8_t* queries, int6
 lnbnn_status nbnn_classify(lnbnn_index* index, const uint8_t* queries, int64_t n_queries, const int64_t* offsets,
                            int64_t n_images, int64_t* totals, int32_t* classes, void* stream) {
   return do_nbnn_classify(index, nullptr, queries, n_queries, offsets, n_images, totals, classes, stream);
+}
+
+lnbnn_status nbnn_logodds_classify(lnbnn_index* index, const uint8_t* queries, int64_t n_queries,
+                                   const int64_t* offsets, int64_t n_images, double beta, int32_t positive_only,
+                                   double* totals, int32_t* classes, int64_t* n_increments, void* stream) {
+  return do_nbnn_logodds_classify(index, nullptr, queries, n_queries, offsets, n_images, beta, positive_only != 0,
+                                  totals, classes, n_increments, stream);
 }
 
 lnbnn_status lnbnn_workspace_create(lnbnn_index* index, int64_t max_queries, int32_t max_k, lnbnn_workspace** out) {
@@ -1023,6 +1078,15 @@ lnbnn_status nbnn_classify_ws(lnbnn_index* index, lnbnn_workspace* w, const uint
                               void* stream) {
   if (!w || w->index != index) return LNBNN_ERR_INVALID_ARG;
   return do_nbnn_classify(index, w, queries, n_queries, offsets, n_images, totals, classes, stream);
+}
+
+lnbnn_status nbnn_logodds_classify_ws(lnbnn_index* index, lnbnn_workspace* w, const uint8_t* queries,
+                                      int64_t n_queries, const int64_t* offsets, int64_t n_images, double beta,
+                                      int32_t positive_only, double* totals, int32_t* classes,
+                                      int64_t* n_increments, void* stream) {
+  if (!w || w->index != index) return LNBNN_ERR_INVALID_ARG;
+  return do_nbnn_logodds_classify(index, w, queries, n_queries, offsets, n_images, beta, positive_only != 0, totals,
+                                  classes, n_increments, stream);
 }
 
 static lnbnn_status classify_host(lnbnn_index* index, bool local, const uint8_t* queries, int64_t n_queries,

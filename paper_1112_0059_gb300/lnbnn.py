@@ -42,7 +42,8 @@ EXPORTS = ["lnbnn_index_create", "lnbnn_index_destroy", "lnbnn_index_info", "knn
            "lnbnn_workspace_destroy", "knn_search_ws", "lnbnn_classify_ws", "nbnn_classify_ws",
            "lnbnn_index_prepare_fp8", "knn_search_fp8", "lnbnn_classify_fp8", "knn_search_fp8_ws",
            "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host", "lnbnn_autotune", "lnbnn_plan_splits",
-           "lnbnn_debug_fail_allocations", "lnbnn_set_start_gate", "lnbnn_index_save", "lnbnn_index_load"]
+           "lnbnn_debug_fail_allocations", "lnbnn_set_start_gate", "lnbnn_index_save", "lnbnn_index_load",
+           "nbnn_logodds_classify", "nbnn_logodds_classify_ws"]
 
 
 class Profile(ctypes.Structure):
@@ -118,6 +119,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.lnbnn_index_save.restype = ctypes.c_int
         lib.lnbnn_index_load.argtypes = [ctypes.c_char_p, P, ctypes.POINTER(P)]
         lib.lnbnn_index_load.restype = ctypes.c_int
+        lib.nbnn_logodds_classify.argtypes = [P, P, I64, P, I64, ctypes.c_double, I32, P, P, P, P]
+        lib.nbnn_logodds_classify_ws.argtypes = [P, P, P, I64, P, I64, ctypes.c_double, I32, P, P, P, P]
         lib.lnbnn_status_string.argtypes = [ctypes.c_int]
         lib.lnbnn_status_string.restype = ctypes.c_char_p
         for name in ("lnbnn_index_create", "lnbnn_index_info", "knn_search", "lnbnn_classify", "nbnn_classify",
@@ -125,7 +128,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                      "lnbnn_profile_read", "lnbnn_workspace_create", "knn_search_ws", "lnbnn_classify_ws",
                      "nbnn_classify_ws", "lnbnn_index_prepare_fp8", "knn_search_fp8", "lnbnn_classify_fp8",
                      "knn_search_fp8_ws", "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host", "lnbnn_autotune",
-                     "lnbnn_plan_splits"):
+                     "lnbnn_plan_splits", "nbnn_logodds_classify", "nbnn_logodds_classify_ws"):
             getattr(lib, name).restype = ctypes.c_int
         if path == LIB_PATH:
             _lib = lib
@@ -301,6 +304,29 @@ class Index:
         else:
             _check(self._lib.nbnn_classify_ws(self.handle, workspace.handle, *args), "nbnn_classify_ws")
         return totals, classes
+
+    def nbnn_logodds_classify(self, queries, offsets, beta: float, positive_only: bool = False, stream=None,
+                              out=None, workspace=None):
+        """NBNN as a sum of log-odds increments (Section 3.1), posterior
+        P(C|d) ~ exp(-beta ||d - NN_C(d)||^2); positive_only keeps only the
+        increments > 0 (Table 1).  Returns ``(totals float64 [n_img, C],
+        classes int32 [n_img], increments added int64 [n_img])``."""
+        import torch
+        m, n_img = int(queries.shape[0]), int(offsets.shape[0]) - 1
+        totals, classes, counts = out if out is not None else (
+            torch.empty((n_img, self.n_classes), dtype=torch.float64, device=queries.device),
+            torch.empty((n_img,), dtype=torch.int32, device=queries.device),
+            torch.empty((n_img,), dtype=torch.int64, device=queries.device))
+        args = (_dev(queries, torch.uint8, "queries"), m, _dev(offsets, torch.int64, "offsets"), n_img,
+                float(beta), int(bool(positive_only)), _dev(totals, torch.float64, "totals"),
+                _dev(classes, torch.int32, "classes"), _dev(counts, torch.int64, "n_increments"),
+                _stream_ptr(stream))
+        if workspace is None:
+            _check(self._lib.nbnn_logodds_classify(self.handle, *args), "nbnn_logodds_classify")
+        else:
+            _check(self._lib.nbnn_logodds_classify_ws(self.handle, workspace.handle, *args),
+                   "nbnn_logodds_classify_ws")
+        return totals, classes, counts
 
     def classify_host(self, queries: np.ndarray, offsets: np.ndarray, k: int | None, totals: np.ndarray | None = None,
                       classes: np.ndarray | None = None, stream=None, shortlist: int | None = None):

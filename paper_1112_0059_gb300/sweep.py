@@ -1,6 +1,6 @@
 """Measurement sweeps on the synthetic workloads (GPU, CUDA events).
 
-    python -m paper_1112_0059_gb300.sweep [--parts kc,fp8,uneven] [--query-images Q] [--reps R]
+    python -m paper_1112_0059_gb300.sweep [--parts kc,fp8,logodds,uneven] [--query-images Q] [--reps R]
 
 kc      Local NBNN (Alg. 2) run time against k, on the first C classes of the
         256-class index (N = C x 45,000 references), with original NBNN
@@ -8,6 +8,11 @@ kc      Local NBNN (Alg. 2) run time against k, on the first C classes of the
 fp8     the FP8 E4M3 shortlist search at several shortlist lengths m against
         the exact search on the 256-class index: throughput, kNN recall of the
         k+1 neighbours, int64 score error and class agreement.
+logodds NBNN as a sum of log-odds increments (Section 3.1) on the 256-class
+        index for several kernel widths beta: run time, the share of device
+        time outside the scan, the average number of increments added per
+        descriptor (all, or only the positive ones: Table 1's measure) and the
+        agreement of the chosen classes with NBNN's (Alg. 1).
 uneven  1,024 query images with uniform [200, 3000] descriptors, flattened
         with offsets, one classify call, exact and FP8, before and after the
         split-schedule autotuner.
@@ -104,6 +109,30 @@ def part_fp8(ref, labels, shortlists, k, q_imgs, reps, sample, rows):
             _emit(rows, rec)
 
 
+def part_logodds(ref, labels, betas, q_imgs, reps, rows):
+    import torch
+    w = synth.workload("caltech256-like").with_query_imgs(q_imgs)
+    q, off, _ = synth.query_set(w)
+    qd, od = torch.from_numpy(q).cuda(), torch.from_numpy(off).cuda()
+    C = w.n_classes
+    with lnbnn.Index(torch.from_numpy(ref).cuda(), torch.from_numpy(labels).cuda(), C) as ix:
+        _, c_nbnn = ix.nbnn_classify(qd, od)
+        c_nbnn = c_nbnn.cpu().numpy()
+        for beta in betas:
+            for pos in (False, True):
+                t = _timed(lambda: ix.nbnn_logodds_classify(qd, od, beta, pos), reps)
+                ix.profile_enable(True)
+                _, c, n = ix.nbnn_logodds_classify(qd, od, beta, pos)
+                prof = ix.profile_read()
+                ix.profile_enable(False)
+                ix.sync()
+                _emit(rows, {"part": "logodds", "beta": beta, "positive_only": pos, "queries": len(q),
+                             "seconds": t, "desc_per_s": len(q) / t,
+                             "other_share": prof["other_ms"] / max(1e-9, prof["other_ms"] + prof["search_ms"]),
+                             "increments_per_desc": float(n.cpu().numpy().sum()) / len(q), "classes": C,
+                             "agreement_with_nbnn": float((c.cpu().numpy() == c_nbnn).mean())})
+
+
 def part_uneven(ref, labels, k, m, reps, sample, rows):
     import torch
     w = synth.workload("batched-uneven")
@@ -139,6 +168,14 @@ def tables(rows) -> str:
         for r in fp:
             out.append(f"| {r['form']} | {r.get('shortlist', '')} | {r['desc_per_s']:,.0f} | {r.get('knn_recall', '')} "
                        f"| {r.get('class_agreement', '')} | {r.get('score_rel_error', '')} |")
+    lo = [r for r in rows if r["part"] == "logodds"]
+    if lo:
+        out.append("\n| beta | increments | desc/s | share outside the scan | increments per descriptor "
+                   "| class agreement with NBNN |\n|---|---|---|---|---|---|")
+        for r in lo:
+            out.append(f"| {r['beta']:g} | {'positive' if r['positive_only'] else 'all'} | {r['desc_per_s']:,.0f} "
+                       f"| {r['other_share']:.3f} | {r['increments_per_desc']:.1f} of {r['classes']} "
+                       f"| {r['agreement_with_nbnn']:.3f} |")
     un = [r for r in rows if r["part"] == "uneven"]
     if un:
         out.append("\n| form | autotuned | splits | desc/s | images/s |\n|---|---|---|---|---|")
@@ -150,10 +187,11 @@ def tables(rows) -> str:
 
 def main():
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    p.add_argument("--parts", default="kc,fp8,uneven")
+    p.add_argument("--parts", default="kc,fp8,logodds,uneven")
     p.add_argument("--classes", default="32,64,128,256")
     p.add_argument("--ks", default="1,2,5,10,20,50,100")
     p.add_argument("--shortlists", default="16,32,64,128")
+    p.add_argument("--betas", default="1e-6,1e-5,1e-4,1e-3")
     p.add_argument("--query-images", type=int, default=100)
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--k", type=int, default=10)
@@ -169,6 +207,8 @@ def main():
     if "fp8" in parts:
         part_fp8(ref, labels, [int(m) for m in a.shortlists.split(",")], a.k, a.query_images, a.reps,
                  a.recall_sample, rows)
+    if "logodds" in parts:
+        part_logodds(ref, labels, [float(b) for b in a.betas.split(",")], a.query_images, a.reps, rows)
     if "uneven" in parts:
         part_uneven(ref, labels, a.k, 32, a.reps, a.recall_sample, rows)
     print(tables(rows), flush=True)
