@@ -16,6 +16,10 @@ Functions (paper: McCann & Lowe, "Local Naive Bayes Nearest Neighbor"):
   local_nbnn_closed_form -- the same totals by sum_i min(0, NN_C - dist_B)
   nbnn           -- Alg. 1 (original NBNN), per-image int64 totals + argmin
 
+Each of these also takes 130-byte rows (128 appearance bytes, then 2 location
+bytes) with ``location_weight=w``: the distance adds w times the squared
+location difference (the alpha location weighting fixed in Section 5).
+
 Coarse-shortlist form (this project's approximate search, in the place of the
 approximate kd-tree search of Section 5; exact neighbours on the shortlist):
   e4m3_round     -- nearest FP8 E4M3 value of integers, ties to even mantissa
@@ -88,39 +92,47 @@ class Oracle:
         lib.oracle_coarse_matrix.argtypes = [P, I64, P, I64, P]
         lib.oracle_knn_coarse.argtypes = [P, I64, P, I64, I32, I32, P, P, INT]
         lib.oracle_lnbnn_coarse.argtypes = [P, P, I64, I32, P, P, I64, I32, I32, P, P, INT]
+        lib.oracle_sqdist_matrix_w.argtypes = [P, I64, P, I64, I32, I64, P]
+        lib.oracle_knn_w.argtypes = [P, I64, P, I64, I32, I32, I64, P, P, INT]
+        lib.oracle_class_min_w.argtypes = [P, P, I64, I32, P, I64, I32, I64, P, INT]
+        for f in (lib.oracle_lnbnn_w, lib.oracle_lnbnn_closed_form_w):
+            f.argtypes = [P, P, I64, I32, P, P, I64, I32, I32, I64, P, P, INT]
+        lib.oracle_nbnn_w.argtypes = [P, P, I64, I32, P, P, I64, I32, I64, P, P, INT]
         for f in (lib.oracle_sqdist_matrix, lib.oracle_knn, lib.oracle_class_min,
                   lib.oracle_lnbnn, lib.oracle_lnbnn_closed_form, lib.oracle_nbnn, lib.oracle_e4m3_round,
-                  lib.oracle_coarse_matrix, lib.oracle_knn_coarse, lib.oracle_lnbnn_coarse):
+                  lib.oracle_coarse_matrix, lib.oracle_knn_coarse, lib.oracle_lnbnn_coarse,
+                  lib.oracle_sqdist_matrix_w, lib.oracle_knn_w, lib.oracle_class_min_w, lib.oracle_lnbnn_w,
+                  lib.oracle_lnbnn_closed_form_w, lib.oracle_nbnn_w):
             f.restype = ctypes.c_int
         self.lib = lib
 
-    def sqdist_matrix(self, ref, q) -> np.ndarray:
-        """int64 [M, N] with entry (i, j) = ||q_i - r_j||^2."""
-        ref, q = _u8(ref), _u8(q)
+    def sqdist_matrix(self, ref, q, location_weight=None) -> np.ndarray:
+        """int64 [M, N] with entry (i, j) = ||q_i - r_j||^2 (location-weighted for 130-byte rows)."""
+        ref, q, stride, w = _rows(ref, q, location_weight)
         out = np.empty((q.shape[0], ref.shape[0]), dtype=np.int64)
-        _check(self.lib.oracle_sqdist_matrix(_p(ref), ref.shape[0], _p(q), q.shape[0], _p(out)))
+        _check(self.lib.oracle_sqdist_matrix_w(_p(ref), ref.shape[0], _p(q), q.shape[0], stride, w, _p(out)))
         return out
 
-    def knn(self, ref, q, kk: int, threads: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    def knn(self, ref, q, kk: int, threads: int = 0, location_weight=None) -> tuple[np.ndarray, np.ndarray]:
         """``(dist int64 [M, kk], idx int64 [M, kk])``: the kk nearest by (distance, index)."""
-        ref, q = _u8(ref), _u8(q)
+        ref, q, stride, w = _rows(ref, q, location_weight)
         dist = np.empty((q.shape[0], kk), dtype=np.int64)
         idx = np.empty((q.shape[0], kk), dtype=np.int64)
-        _check(self.lib.oracle_knn(_p(ref), ref.shape[0], _p(q), q.shape[0], kk, _p(dist),
-                                   _p(idx), threads))
+        _check(self.lib.oracle_knn_w(_p(ref), ref.shape[0], _p(q), q.shape[0], kk, stride, w, _p(dist),
+                                     _p(idx), threads))
         return dist, idx
 
-    def class_min(self, ref, labels, n_classes: int, q, threads: int = 0) -> np.ndarray:
+    def class_min(self, ref, labels, n_classes: int, q, threads: int = 0, location_weight=None) -> np.ndarray:
         """int64 [M, C]: NN_C(q_i); int64 max where class C has no reference."""
-        ref, q = _u8(ref), _u8(q)
+        ref, q, stride, w = _rows(ref, q, location_weight)
         labels = np.ascontiguousarray(labels, dtype=np.int32)
         out = np.empty((q.shape[0], n_classes), dtype=np.int64)
-        _check(self.lib.oracle_class_min(_p(ref), _p(labels), ref.shape[0], n_classes, _p(q),
-                                         q.shape[0], _p(out), threads))
+        _check(self.lib.oracle_class_min_w(_p(ref), _p(labels), ref.shape[0], n_classes, _p(q),
+                                           q.shape[0], stride, w, _p(out), threads))
         return out
 
-    def _classify(self, fn, ref, labels, n_classes, q, offsets, k, threads):
-        ref, q = _u8(ref), _u8(q)
+    def _classify(self, fn, ref, labels, n_classes, q, offsets, k, threads, location_weight):
+        ref, q, stride, w = _rows(ref, q, location_weight)
         labels = np.ascontiguousarray(labels, dtype=np.int32)
         offsets = np.ascontiguousarray(offsets, dtype=np.int64)
         n_img = offsets.shape[0] - 1
@@ -130,27 +142,28 @@ class Oracle:
         classes = np.empty(n_img, dtype=np.int32)
         if k is None:
             code = fn(_p(ref), _p(labels), ref.shape[0], n_classes, _p(q), _p(offsets), n_img,
-                      _p(totals), _p(classes), threads)
+                      stride, w, _p(totals), _p(classes), threads)
         else:
             code = fn(_p(ref), _p(labels), ref.shape[0], n_classes, _p(q), _p(offsets), n_img, k,
-                      _p(totals), _p(classes), threads)
+                      stride, w, _p(totals), _p(classes), threads)
         _check(code)
         return totals, classes
 
-    def local_nbnn(self, ref, labels, n_classes, q, offsets, k, threads: int = 0):
+    def local_nbnn(self, ref, labels, n_classes, q, offsets, k, threads: int = 0, location_weight=None):
         """Alg. 2: ``(totals int64 [n_img, C], classes int32 [n_img])``."""
-        return self._classify(self.lib.oracle_lnbnn, ref, labels, n_classes, q, offsets, k, threads)
+        return self._classify(self.lib.oracle_lnbnn_w, ref, labels, n_classes, q, offsets, k, threads,
+                              location_weight)
 
-    def local_nbnn_closed_form(self, ref, labels, n_classes, q, offsets, k, threads: int = 0):
+    def local_nbnn_closed_form(self, ref, labels, n_classes, q, offsets, k, threads: int = 0,
+                               location_weight=None):
         """Local NBNN totals as sum_i min(0, NN_C(d_i) - dist_B(d_i)); small inputs."""
-        return self._classify(self.lib.oracle_lnbnn_closed_form, ref, labels, n_classes, q,
-                              offsets, k, threads)
+        return self._classify(self.lib.oracle_lnbnn_closed_form_w, ref, labels, n_classes, q,
+                              offsets, k, threads, location_weight)
 
-    def nbnn(self, ref, labels, n_classes, q, offsets, threads: int = 0):
+    def nbnn(self, ref, labels, n_classes, q, offsets, threads: int = 0, location_weight=None):
         """Alg. 1: ``(totals int64 [n_img, C], classes int32 [n_img])``."""
-        return self._classify(self.lib.oracle_nbnn, ref, labels, n_classes, q, offsets, None,
-                              threads)
-
+        return self._classify(self.lib.oracle_nbnn_w, ref, labels, n_classes, q, offsets, None,
+                              threads, location_weight)
 
     def e4m3_round(self, x) -> np.ndarray:
         """Nearest FP8 E4M3 value of each integer (|x| <= 448), ties to even mantissa."""
@@ -197,6 +210,22 @@ def _u8(a) -> np.ndarray:
     return a
 
 
+def _rows(ref, q, location_weight):
+    """Reference and query rows of one layout (128 bytes, or 130 with a
+    location weight), their stride and the weight."""
+    ref = np.ascontiguousarray(ref, dtype=np.uint8)
+    q = np.ascontiguousarray(q, dtype=np.uint8)
+    if ref.ndim != 2 or q.ndim != 2 or ref.shape[1] != q.shape[1] or ref.shape[1] not in (128, 130):
+        raise ValueError("descriptors must be uint8 [n, 128] or [n, 130], the same for references and queries")
+    if ref.shape[1] == 130:
+        if location_weight is None or int(location_weight) < 0:
+            raise ValueError("130-byte rows need a location weight >= 0")
+        return ref, q, 130, int(location_weight)
+    if location_weight not in (None, 0):
+        raise ValueError("a location weight needs 130-byte rows")
+    return ref, q, 128, 0
+
+
 def _p(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
@@ -229,28 +258,28 @@ def default() -> Oracle:
     return _lib
 
 
-def sqdist_matrix(ref, q):
-    return default().sqdist_matrix(ref, q)
+def sqdist_matrix(ref, q, location_weight=None):
+    return default().sqdist_matrix(ref, q, location_weight)
 
 
-def knn(ref, q, kk, threads=0):
-    return default().knn(ref, q, kk, threads)
+def knn(ref, q, kk, threads=0, location_weight=None):
+    return default().knn(ref, q, kk, threads, location_weight)
 
 
-def class_min(ref, labels, n_classes, q, threads=0):
-    return default().class_min(ref, labels, n_classes, q, threads)
+def class_min(ref, labels, n_classes, q, threads=0, location_weight=None):
+    return default().class_min(ref, labels, n_classes, q, threads, location_weight)
 
 
-def local_nbnn(ref, labels, n_classes, q, offsets, k, threads=0):
-    return default().local_nbnn(ref, labels, n_classes, q, offsets, k, threads)
+def local_nbnn(ref, labels, n_classes, q, offsets, k, threads=0, location_weight=None):
+    return default().local_nbnn(ref, labels, n_classes, q, offsets, k, threads, location_weight)
 
 
-def local_nbnn_closed_form(ref, labels, n_classes, q, offsets, k, threads=0):
-    return default().local_nbnn_closed_form(ref, labels, n_classes, q, offsets, k, threads)
+def local_nbnn_closed_form(ref, labels, n_classes, q, offsets, k, threads=0, location_weight=None):
+    return default().local_nbnn_closed_form(ref, labels, n_classes, q, offsets, k, threads, location_weight)
 
 
-def nbnn(ref, labels, n_classes, q, offsets, threads=0):
-    return default().nbnn(ref, labels, n_classes, q, offsets, threads)
+def nbnn(ref, labels, n_classes, q, offsets, threads=0, location_weight=None):
+    return default().nbnn(ref, labels, n_classes, q, offsets, threads, location_weight)
 
 
 def e4m3_round(x):

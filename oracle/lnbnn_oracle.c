@@ -19,6 +19,16 @@
  *   - k >= 1 and k + 1 <= N are required (Alg. 2 reads the (k+1)-th neighbour);
  *   - original NBNN needs every class to own at least one reference (NN_C).
  *
+ * Location-weighted descriptors (the alpha weighting of descriptor location
+ * that Section 5 fixes at 1.6 for its experiments, an option of the original
+ * NBNN): a descriptor row may carry 2 location bytes after its 128
+ * appearance bytes (130 bytes a row), and the distance is then
+ *   sum over the 128 appearance coordinates of (q_t - r_t)^2
+ *   + w * sum over the 2 location coordinates of (q_t - r_t)^2,
+ * with an integer weight w >= 0: the squared Euclidean distance of the
+ * descriptors with the location appended at scale sqrt(w) (alpha^2 = w in
+ * the units of the location grid).  The FP8 shortlist form is 128-byte only.
+ *
  * Work is split across threads only over query descriptors, which Alg. 1 and
  * Alg. 2 treat independently; every per-descriptor step runs as written.
  *
@@ -39,6 +49,16 @@
 #include <unistd.h>
 
 #define ORACLE_D 128
+#define ORACLE_LOC 2
+
+/* Row layout and weight of the distance: stride ORACLE_D (appearance only) or
+ * ORACLE_D + ORACLE_LOC (appearance, then location weighted by w). */
+typedef struct {
+  int32_t stride;
+  int64_t w;
+} metric_t;
+
+static const metric_t plain_metric = {ORACLE_D, 0};
 
 enum {
   ORACLE_OK = 0,
@@ -50,15 +70,21 @@ enum {
   ORACLE_ERR_NOMEM = -6,
 };
 
-/* ||a - b||^2 over the 128 coordinates.  Each term is at most 255^2 and the
- * sum at most 128 * 255^2 = 8,323,200 < 2^31, so 32-bit sums are exact. */
-static int64_t sqdist(const uint8_t *a, const uint8_t *b) {
+/* ||a - b||^2 over the 128 appearance coordinates (each term at most 255^2,
+ * the sum at most 128 * 255^2 = 8,323,200 < 2^31, so 32-bit sums are exact),
+ * plus w times the squared difference of the location coordinates, if any. */
+static int64_t sqdist(const uint8_t *a, const uint8_t *b, const metric_t *mt) {
   int32_t s = 0;
   for (int t = 0; t < ORACLE_D; ++t) {
     int32_t e = (int32_t)a[t] - (int32_t)b[t];
     s += e * e;
   }
-  return (int64_t)s;
+  int64_t loc = 0;
+  for (int t = ORACLE_D; t < mt->stride; ++t) {
+    int32_t e = (int32_t)a[t] - (int32_t)b[t];
+    loc += e * e;
+  }
+  return (int64_t)s + mt->w * loc;
 }
 
 /* (d1, j1) comes before (d2, j2): smaller distance, then smaller index. */
@@ -69,10 +95,10 @@ static int before(int64_t d1, int64_t j1, int64_t d2, int64_t j2) {
 /* NN(q, kk): the kk references with the smallest (distance, index), ascending.
  * Scans every reference and keeps the kk best seen so far in a sorted list. */
 static void knn_one(const uint8_t *ref, int64_t N, const uint8_t *q, int32_t kk,
-                    int64_t *od, int64_t *oj) {
+                    int64_t *od, int64_t *oj, const metric_t *mt) {
   int32_t len = 0;
   for (int64_t j = 0; j < N; ++j) {
-    int64_t d = sqdist(q, ref + j * ORACLE_D);
+    int64_t d = sqdist(q, ref + j * mt->stride, mt);
     if (len == kk && !before(d, j, od[kk - 1], oj[kk - 1])) continue;
     int32_t p = (len < kk) ? len++ : kk - 1; /* slot freed at the end of the list */
     while (p > 0 && before(d, j, od[p - 1], oj[p - 1])) {
@@ -88,10 +114,10 @@ static void knn_one(const uint8_t *ref, int64_t N, const uint8_t *q, int32_t kk,
 /* NN_C(q) for every class C: the smallest distance to a reference of class C
  * (Alg. 1's per-class search).  Classes without references keep INT64_MAX. */
 static void class_min_one(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
-                          const uint8_t *q, int64_t *cmin) {
+                          const uint8_t *q, int64_t *cmin, const metric_t *mt) {
   for (int32_t c = 0; c < C; ++c) cmin[c] = INT64_MAX;
   for (int64_t j = 0; j < N; ++j) {
-    int64_t d = sqdist(q, ref + j * ORACLE_D);
+    int64_t d = sqdist(q, ref + j * mt->stride, mt);
     if (d < cmin[labels[j]]) cmin[labels[j]] = d;
   }
 }
@@ -119,8 +145,8 @@ static void score_one(const int32_t *labels, int32_t k, const int64_t *nd, const
 }
 
 static void lnbnn_one(const uint8_t *ref, const int32_t *labels, int64_t N, const uint8_t *q,
-                      int32_t k, int64_t *nd, int64_t *nj, int64_t *totals) {
-  knn_one(ref, N, q, k + 1, nd, nj);
+                      int32_t k, int64_t *nd, int64_t *nj, int64_t *totals, const metric_t *mt) {
+  knn_one(ref, N, q, k + 1, nd, nj, mt);
   score_one(labels, k, nd, nj, totals);
 }
 
@@ -188,7 +214,7 @@ static void knn_coarse_one(const uint8_t *ref, int64_t N, const uint8_t *q, int3
   /* rerank: exact distance of each candidate, keep the kk smallest */
   int32_t n = 0;
   for (int32_t a = 0; a < m; ++a) {
-    const int64_t j = cj[a], d = sqdist(q, ref + j * ORACLE_D);
+    const int64_t j = cj[a], d = sqdist(q, ref + j * ORACLE_D, &plain_metric);
     if (n == kk && !before(d, j, od[kk - 1], oj[kk - 1])) continue;
     int32_t p = (n < kk) ? n++ : kk - 1;
     while (p > 0 && before(d, j, od[p - 1], oj[p - 1])) {
@@ -215,8 +241,8 @@ static int cmp_i64(const void *x, const void *y) {
  * with dist_B the (k+1)-th smallest of all N distances (values only). */
 static int closed_form_one(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
                            const uint8_t *q, int32_t k, int64_t *all, int64_t *cmin,
-                           int64_t *totals) {
-  for (int64_t j = 0; j < N; ++j) all[j] = sqdist(q, ref + j * ORACLE_D);
+                           int64_t *totals, const metric_t *mt) {
+  for (int64_t j = 0; j < N; ++j) all[j] = sqdist(q, ref + j * mt->stride, mt);
   for (int32_t c = 0; c < C; ++c) cmin[c] = INT64_MAX;
   for (int64_t j = 0; j < N; ++j)
     if (all[j] < cmin[labels[j]]) cmin[labels[j]] = all[j];
@@ -267,6 +293,7 @@ typedef struct {
   int64_t M;
   int32_t k;             /* kk for JOB_KNN, k for the classifiers */
   int32_t m;             /* shortlist length of the coarse jobs */
+  metric_t mt;           /* row stride and location weight (coarse jobs: plain) */
   const int64_t *img_of; /* descriptor -> image, classifiers only */
   int64_t n_img;
   int64_t *out_d;        /* JOB_KNN [M*kk]; JOB_CLASS_MIN [M*C] */
@@ -310,20 +337,20 @@ static void *worker(void *arg) {
     if (i0 >= J->M) break;
     int64_t i1 = i0 + chunk < J->M ? i0 + chunk : J->M;
     for (int64_t i = i0; i < i1; ++i) {
-      const uint8_t *qi = J->q + i * ORACLE_D;
+      const uint8_t *qi = J->q + i * J->mt.stride;
       switch (J->kind) {
         case JOB_KNN:
-          knn_one(J->ref, J->N, qi, J->k, J->out_d + i * J->k, J->out_j + i * J->k);
+          knn_one(J->ref, J->N, qi, J->k, J->out_d + i * J->k, J->out_j + i * J->k, &J->mt);
           break;
         case JOB_CLASS_MIN:
-          class_min_one(J->ref, J->labels, J->N, J->C, qi, J->out_d + i * J->C);
+          class_min_one(J->ref, J->labels, J->N, J->C, qi, J->out_d + i * J->C, &J->mt);
           break;
         case JOB_LNBNN:
-          lnbnn_one(J->ref, J->labels, J->N, qi, J->k, s1, s2, mine + J->img_of[i] * J->C);
+          lnbnn_one(J->ref, J->labels, J->N, qi, J->k, s1, s2, mine + J->img_of[i] * J->C, &J->mt);
           break;
         case JOB_CLOSED:
           closed_form_one(J->ref, J->labels, J->N, J->C, qi, J->k, s1, s2,
-                          mine + J->img_of[i] * J->C);
+                          mine + J->img_of[i] * J->C, &J->mt);
           break;
         case JOB_KNN_COARSE:
           knn_coarse_one(J->ref, J->N, qi, J->k, J->m, s3, s4, J->out_d + i * J->k, J->out_j + i * J->k);
@@ -334,7 +361,7 @@ static void *worker(void *arg) {
           break;
         case JOB_NBNN: {
           /* Alg. 1: totals[C] += ||d_i - NN_C(d_i)||^2 for every class C */
-          class_min_one(J->ref, J->labels, J->N, J->C, qi, s1);
+          class_min_one(J->ref, J->labels, J->N, J->C, qi, s1, &J->mt);
           int64_t *t = mine + J->img_of[i] * J->C;
           for (int32_t c = 0; c < J->C; ++c) t[c] += s1[c];
           break;
@@ -381,7 +408,7 @@ static int run(job_t *J, int nthreads) {
  * exact in any order), then the per-image argmin. */
 static int classify(int kind, const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
                     const uint8_t *q, const int64_t *offsets, int64_t n_img, int32_t k, int32_t m,
-                    int64_t *totals, int32_t *classes, int nthreads) {
+                    int64_t *totals, int32_t *classes, int nthreads, metric_t mt) {
   int st = check_ref(N, C, labels);
   if (st) return st;
   const int64_t M = offsets[n_img];
@@ -413,6 +440,7 @@ static int classify(int kind, const uint8_t *ref, const int32_t *labels, int64_t
   J.M = M;
   J.k = k;
   J.m = m;
+  J.mt = mt;
   J.img_of = img_of;
   J.n_img = n_img;
   if (nthreads <= 0) nthreads = (int)sysconf(_SC_NPROCESSORS_ONLN);
@@ -438,21 +466,32 @@ static int classify(int kind, const uint8_t *ref, const int32_t *labels, int64_t
 
 /* ------------------------------------------------------------- public API */
 
+/* The metric of a row stride (128: appearance only; 130: appearance and
+ * location) and location weight w >= 0; 0 if invalid. */
+static int make_metric(int32_t stride, int64_t w, metric_t *mt) {
+  if (!(stride == ORACLE_D || stride == ORACLE_D + ORACLE_LOC) || w < 0 || (stride == ORACLE_D && w != 0)) return 0;
+  mt->stride = stride;
+  mt->w = w;
+  return 1;
+}
+
 /* Full matrix of squared distances, out[i*N + j] = ||q_i - r_j||^2 (tiny inputs). */
-int oracle_sqdist_matrix(const uint8_t *ref, int64_t N, const uint8_t *q, int64_t M,
-                         int64_t *out) {
-  if (N < 0 || M < 0) return ORACLE_ERR_ARG;
+int oracle_sqdist_matrix_w(const uint8_t *ref, int64_t N, const uint8_t *q, int64_t M, int32_t stride,
+                           int64_t w, int64_t *out) {
+  metric_t mt;
+  if (N < 0 || M < 0 || !make_metric(stride, w, &mt)) return ORACLE_ERR_ARG;
   for (int64_t i = 0; i < M; ++i)
-    for (int64_t j = 0; j < N; ++j) out[i * N + j] = sqdist(q + i * ORACLE_D, ref + j * ORACLE_D);
+    for (int64_t j = 0; j < N; ++j) out[i * N + j] = sqdist(q + i * mt.stride, ref + j * mt.stride, &mt);
   return ORACLE_OK;
 }
 
 /* NN(q_i, kk) for every query: dist/idx [M*kk], ascending by (dist, idx). */
-int oracle_knn(const uint8_t *ref, int64_t N, const uint8_t *q, int64_t M, int32_t kk,
-               int64_t *dist, int64_t *idx, int nthreads) {
+int oracle_knn_w(const uint8_t *ref, int64_t N, const uint8_t *q, int64_t M, int32_t kk, int32_t stride,
+                 int64_t w, int64_t *dist, int64_t *idx, int nthreads) {
   if (N < 1 || M < 0 || kk < 1 || (int64_t)kk > N) return ORACLE_ERR_K;
   job_t J;
   memset(&J, 0, sizeof J);
+  if (!make_metric(stride, w, &J.mt)) return ORACLE_ERR_ARG;
   J.kind = JOB_KNN;
   J.ref = ref;
   J.N = N;
@@ -465,12 +504,13 @@ int oracle_knn(const uint8_t *ref, int64_t N, const uint8_t *q, int64_t M, int32
 }
 
 /* NN_C(q_i) for every query and class: out [M*C]; INT64_MAX for empty classes. */
-int oracle_class_min(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
-                     const uint8_t *q, int64_t M, int64_t *out, int nthreads) {
+int oracle_class_min_w(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C, const uint8_t *q,
+                       int64_t M, int32_t stride, int64_t w, int64_t *out, int nthreads) {
   int st = check_ref(N, C, labels);
   if (st) return st;
   job_t J;
   memset(&J, 0, sizeof J);
+  if (!make_metric(stride, w, &J.mt)) return ORACLE_ERR_ARG;
   J.kind = JOB_CLASS_MIN;
   J.ref = ref;
   J.labels = labels;
@@ -483,24 +523,64 @@ int oracle_class_min(const uint8_t *ref, const int32_t *labels, int64_t N, int32
 }
 
 /* Alg. 2 (LocalNBNN): totals [n_img*C] int64, classes [n_img] int32. */
-int oracle_lnbnn(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
-                 const uint8_t *q, const int64_t *offsets, int64_t n_img, int32_t k,
-                 int64_t *totals, int32_t *classes, int nthreads) {
-  return classify(JOB_LNBNN, ref, labels, N, C, q, offsets, n_img, k, 0, totals, classes, nthreads);
+int oracle_lnbnn_w(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C, const uint8_t *q,
+                   const int64_t *offsets, int64_t n_img, int32_t k, int32_t stride, int64_t w, int64_t *totals,
+                   int32_t *classes, int nthreads) {
+  metric_t mt;
+  if (!make_metric(stride, w, &mt)) return ORACLE_ERR_ARG;
+  return classify(JOB_LNBNN, ref, labels, N, C, q, offsets, n_img, k, 0, totals, classes, nthreads, mt);
 }
 
 /* Local NBNN totals by the closed form sum_i min(0, NN_C(d_i) - dist_B(d_i)). */
-int oracle_lnbnn_closed_form(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
-                             const uint8_t *q, const int64_t *offsets, int64_t n_img, int32_t k,
-                             int64_t *totals, int32_t *classes, int nthreads) {
-  return classify(JOB_CLOSED, ref, labels, N, C, q, offsets, n_img, k, 0, totals, classes, nthreads);
+int oracle_lnbnn_closed_form_w(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
+                               const uint8_t *q, const int64_t *offsets, int64_t n_img, int32_t k, int32_t stride,
+                               int64_t w, int64_t *totals, int32_t *classes, int nthreads) {
+  metric_t mt;
+  if (!make_metric(stride, w, &mt)) return ORACLE_ERR_ARG;
+  return classify(JOB_CLOSED, ref, labels, N, C, q, offsets, n_img, k, 0, totals, classes, nthreads, mt);
 }
 
 /* Alg. 1 (original NBNN): totals [n_img*C] int64, classes [n_img] int32. */
+int oracle_nbnn_w(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C, const uint8_t *q,
+                  const int64_t *offsets, int64_t n_img, int32_t stride, int64_t w, int64_t *totals,
+                  int32_t *classes, int nthreads) {
+  metric_t mt;
+  if (!make_metric(stride, w, &mt)) return ORACLE_ERR_ARG;
+  return classify(JOB_NBNN, ref, labels, N, C, q, offsets, n_img, 0, 0, totals, classes, nthreads, mt);
+}
+
+/* The same on 128-byte descriptors (appearance only). */
+int oracle_sqdist_matrix(const uint8_t *ref, int64_t N, const uint8_t *q, int64_t M, int64_t *out) {
+  return oracle_sqdist_matrix_w(ref, N, q, M, ORACLE_D, 0, out);
+}
+
+int oracle_knn(const uint8_t *ref, int64_t N, const uint8_t *q, int64_t M, int32_t kk,
+               int64_t *dist, int64_t *idx, int nthreads) {
+  return oracle_knn_w(ref, N, q, M, kk, ORACLE_D, 0, dist, idx, nthreads);
+}
+
+int oracle_class_min(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
+                     const uint8_t *q, int64_t M, int64_t *out, int nthreads) {
+  return oracle_class_min_w(ref, labels, N, C, q, M, ORACLE_D, 0, out, nthreads);
+}
+
+int oracle_lnbnn(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
+                 const uint8_t *q, const int64_t *offsets, int64_t n_img, int32_t k,
+                 int64_t *totals, int32_t *classes, int nthreads) {
+  return oracle_lnbnn_w(ref, labels, N, C, q, offsets, n_img, k, ORACLE_D, 0, totals, classes, nthreads);
+}
+
+int oracle_lnbnn_closed_form(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
+                             const uint8_t *q, const int64_t *offsets, int64_t n_img, int32_t k,
+                             int64_t *totals, int32_t *classes, int nthreads) {
+  return oracle_lnbnn_closed_form_w(ref, labels, N, C, q, offsets, n_img, k, ORACLE_D, 0, totals, classes,
+                                    nthreads);
+}
+
 int oracle_nbnn(const uint8_t *ref, const int32_t *labels, int64_t N, int32_t C,
                 const uint8_t *q, const int64_t *offsets, int64_t n_img, int64_t *totals,
                 int32_t *classes, int nthreads) {
-  return classify(JOB_NBNN, ref, labels, N, C, q, offsets, n_img, 0, 0, totals, classes, nthreads);
+  return oracle_nbnn_w(ref, labels, N, C, q, offsets, n_img, ORACLE_D, 0, totals, classes, nthreads);
 }
 
 /* E4M3 rounding of each x[i] (|x[i]| <= 448), for the pins. */
@@ -529,6 +609,7 @@ int oracle_knn_coarse(const uint8_t *ref, int64_t N, const uint8_t *q, int64_t M
   job_t J;
   memset(&J, 0, sizeof J);
   J.kind = JOB_KNN_COARSE;
+  J.mt = plain_metric;
   J.ref = ref;
   J.N = N;
   J.q = q;
@@ -545,5 +626,6 @@ int oracle_lnbnn_coarse(const uint8_t *ref, const int32_t *labels, int64_t N, in
                         const uint8_t *q, const int64_t *offsets, int64_t n_img, int32_t k, int32_t m,
                         int64_t *totals, int32_t *classes, int nthreads) {
   fill_rounded_shifted();
-  return classify(JOB_LNBNN_COARSE, ref, labels, N, C, q, offsets, n_img, k, m, totals, classes, nthreads);
+  return classify(JOB_LNBNN_COARSE, ref, labels, N, C, q, offsets, n_img, k, m, totals, classes, nthreads,
+                  plain_metric);
 }

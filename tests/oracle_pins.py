@@ -10,6 +10,9 @@ oracle disagrees with what the paper and the mathematics fix:
 * closed forms: the Local NBNN totals equal sum_i min(0, NN_C(d_i) - dist_B(d_i))
   (derived from Alg. 2 for exact neighbours), the 1-class case, the
   1-descriptor case;
+* location-weighted rows (130 bytes): scipy distances and kd-tree neighbours
+  of the vectors with the location repeated w times, weight 0 against the
+  128-byte results, and Alg. 1 / Alg. 2 totals rebuilt from those distances;
 * invariants: permutation of the reference set, k + 1 = N reduces Local NBNN to
   NBNN minus a class-independent constant (Section 5.1: large k reverts to
   NBNN), the background-class discount does not move the argmin (Section 4),
@@ -438,6 +441,95 @@ def pin_lnbnn_coarse_short_list(orc):
     # the reranked distances are the exact distances of the returned rows
     d = _cd(q, ref)
     assert np.array_equal(nd, np.take_along_axis(d, nj, axis=1))
+
+
+# ----------------------------------------------------------------- location
+
+def _loc_case(seed, N, M, hi=256, loc_hi=256):
+    """130-byte rows: 128 appearance bytes, then 2 location bytes."""
+    rng = np.random.default_rng(seed)
+    ref = rng.integers(0, hi, size=(N, 130)).astype(np.uint8)
+    q = rng.integers(0, hi, size=(M, 130)).astype(np.uint8)
+    ref[:, 128:] = rng.integers(0, loc_hi, size=(N, 2))
+    q[:, 128:] = rng.integers(0, loc_hi, size=(M, 2))
+    return ref, q
+
+
+def _expanded(a, w):
+    """130-byte rows as float vectors of 128 + 2w coordinates, the location
+    repeated w times: their plain squared distances are the weighted ones."""
+    a = np.asarray(a, dtype=np.float64)
+    return np.concatenate([a[:, :128]] + [a[:, 128:130]] * w, axis=1)
+
+
+def _cd_loc(q, r, w):
+    return cdist(_expanded(q, w), _expanded(r, w), "sqeuclidean").round().astype(np.int64)
+
+
+def pin_location_matches_scipy(orc):
+    for w in (0, 1, 3, 48):
+        ref, q = _loc_case(30 + w, 50, 9)
+        assert np.array_equal(orc.sqdist_matrix(ref, q, location_weight=w), _cd_loc(q, ref, w)), w
+    a = np.zeros((1, 130), np.uint8)
+    b = a.copy()
+    b[0, 129] = 200
+    assert orc.sqdist_matrix(a, b, location_weight=7)[0, 0] == 7 * 40000
+    b[0, :128] = 255
+    assert orc.sqdist_matrix(a, b, location_weight=7)[0, 0] == 8323200 + 7 * 40000
+
+
+def pin_location_knn_matches_kdtree(orc):
+    ref, q = _loc_case(40, 500, 20)
+    w, kk = 5, 10
+    d, j = orc.knn(ref, q, kk, location_weight=w)
+    td, tj = cKDTree(_expanded(ref, w)).query(_expanded(q, w), k=kk)
+    assert np.array_equal(d, np.rint(td ** 2).astype(np.int64))
+    uniq = np.ones_like(d, dtype=bool)
+    uniq[:, 1:] &= d[:, 1:] != d[:, :-1]
+    uniq[:, :-1] &= d[:, :-1] != d[:, 1:]
+    assert np.array_equal(j[uniq], tj[uniq])
+
+
+def pin_location_weight_zero_is_appearance(orc):
+    ref, q = _loc_case(41, 80, 12)
+    lab = (np.arange(80) % 4).astype(np.int32)
+    off = np.array([0, 5, 12], np.int64)
+    for k in (1, 5):
+        a = orc.local_nbnn(ref, lab, 4, q, off, k, location_weight=0)
+        b = orc.local_nbnn(ref[:, :128], lab, 4, q[:, :128], off, k)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    a = orc.nbnn(ref, lab, 4, q, off, location_weight=0)
+    b = orc.nbnn(ref[:, :128], lab, 4, q[:, :128], off)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def pin_location_local_nbnn_closed_form(orc):
+    """Alg. 2 and Alg. 1 under the weighted distance, from scipy distances on the
+    expanded vectors: sum_i min(0, NN_C - dist_B) and sum_i NN_C; many ties."""
+    ref, q = _loc_case(42, 60, 10, hi=4, loc_hi=8)
+    lab = (np.arange(60) % 4).astype(np.int32)
+    off = np.array([0, 4, 4, 10], np.int64)
+    w = 3
+    D = _cd_loc(q, ref, w)
+    for k in (1, 3, 59):
+        want = np.zeros((3, 4), np.int64)
+        for i in range(3):
+            for row in range(off[i], off[i + 1]):
+                dist_b = np.sort(D[row])[k]
+                for c in range(4):
+                    want[i, c] += min(0, int(D[row][lab == c].min()) - int(dist_b))
+        t, c = orc.local_nbnn(ref, lab, 4, q, off, k, location_weight=w)
+        assert np.array_equal(t, want), k
+        t2, _ = orc.local_nbnn_closed_form(ref, lab, 4, q, off, k, location_weight=w)
+        assert np.array_equal(t2, want), k
+    nb = np.zeros((3, 4), np.int64)
+    for i in range(3):
+        for row in range(off[i], off[i + 1]):
+            nb[i] += [int(D[row][lab == c].min()) for c in range(4)]
+    t, c = orc.nbnn(ref, lab, 4, q, off, location_weight=w)
+    assert np.array_equal(t, nb)
+    assert np.array_equal(orc.class_min(ref, lab, 4, q, location_weight=w),
+                          np.array([[D[r][lab == c].min() for c in range(4)] for r in range(10)]))
 
 
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

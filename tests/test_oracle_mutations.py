@@ -36,10 +36,15 @@ MUTANTS = [
     ("E4M3: one mantissa bit short", "const int32_t step = 1 << (p - 3);", "const int32_t step = 1 << (p - 2);"),
     ("coarse: dropped reference norm", "nr += rs * rs;", "nr += 0;"),
     ("coarse: cross term not doubled", "return nq + nr - 2 * dot;", "return nq + nr - dot;"),
-    ("coarse: no rerank", "const int64_t j = cj[a], d = sqdist(q, ref + j * ORACLE_D);",
+    ("coarse: no rerank", "const int64_t j = cj[a], d = sqdist(q, ref + j * ORACLE_D, &plain_metric);",
      "const int64_t j = cj[a], d = cd[a];"),
     ("coarse: shortlist by exact distance", "const int64_t c = coarse(q, ref + j * ORACLE_D);",
-     "const int64_t c = sqdist(q, ref + j * ORACLE_D);"),
+     "const int64_t c = sqdist(q, ref + j * ORACLE_D, &plain_metric);"),
+    ("location: weight dropped", "return (int64_t)s + mt->w * loc;", "return (int64_t)s + loc;"),
+    ("location: weight squared", "return (int64_t)s + mt->w * loc;", "return (int64_t)s + mt->w * mt->w * loc;"),
+    ("location: ignored", "for (int t = ORACLE_D; t < mt->stride; ++t) {", "for (int t = ORACLE_D; t < ORACLE_D; ++t) {"),
+    ("location: references at 128-byte stride", "ref + j * mt->stride, mt)", "ref + j * ORACLE_D, mt)"),
+    ("location: queries at 128-byte stride", "J->q + i * J->mt.stride", "J->q + i * ORACLE_D"),
 ]
 
 
