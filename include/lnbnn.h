@@ -6,7 +6,10 @@
  * rule of Eq. (eqn:nbnn) (Section 3); Local NBNN is Alg. 2 (Section 4).
  *
  * Conventions for every call:
- *   - Descriptors are 128-dimensional uint8, row-major, 128 bytes per row.
+ *   - Descriptors are 128-dimensional uint8, row-major, 128 bytes per row;
+ *     an index made by lnbnn_index_create_located takes 130-byte rows (the
+ *     128 appearance bytes, then a 2-byte location) for its references and
+ *     for every query.
  *   - Unless a name ends in _host, every array argument is a DEVICE pointer
  *     (cudaMalloc / PyTorch CUDA storage) owned by the caller; the library
  *     never frees or keeps it beyond the call.
@@ -17,7 +20,8 @@
  *     kernels of that index skip their work, so results of calls made between
  *     the timeout and lnbnn_sync() are invalid.
  *   - Distances are exact squared Euclidean distances of the raw uint8
- *     values, as int32; totals are exact int64 sums.
+ *     values (plus the weighted location term of a located index), as int32;
+ *     totals are exact int64 sums.
  *   - Neighbours are ordered by (distance, reference row) ascending, so equal
  *     distances go to the lower row of the reference set given to create.
  *   - Calls without a workspace argument share the index's own workspace:
@@ -42,6 +46,10 @@ extern "C" {
 #endif
 
 #define LNBNN_DIM 128
+/* row bytes of a located descriptor: 128 appearance bytes, then (x, y) */
+#define LNBNN_LOCATED_DIM 130
+/* largest location weight (keeps the tensor-core distances exact) */
+#define LNBNN_MAX_LOCATION_WEIGHT 48
 /* largest neighbourhood size k (the search keeps k + 1 neighbours) */
 #define LNBNN_MAX_K 255
 
@@ -56,7 +64,7 @@ typedef enum lnbnn_status {
   LNBNN_ERR_OOM = 5,          /* device allocation failed */
   LNBNN_ERR_CUDA = 6,         /* a CUDA runtime call or launch failed */
   LNBNN_ERR_TIMEOUT = 7,      /* a bounded device wait expired */
-  LNBNN_ERR_UNSUPPORTED = 8,  /* device is not compute capability 10.3 (sm_103) */
+  LNBNN_ERR_UNSUPPORTED = 8,  /* device is not compute capability 10.3 (sm_103); FP8 on a located index */
   LNBNN_ERR_OFFSETS = 9,      /* offsets not 0 = o[0] <= ... <= o[n_images] = n_queries */
   LNBNN_ERR_SCRATCH_LIMIT = 10, /* problem larger than a workspace or the scratch of knn_search_noalloc */
   LNBNN_ERR_NO_FP8 = 11,        /* an FP8 call on an index without lnbnn_index_prepare_fp8 */
@@ -85,6 +93,33 @@ typedef enum lnbnn_status {
  */
 LNBNN_API lnbnn_status lnbnn_index_create(const uint8_t *ref, const int32_t *labels, int64_t n_ref,
                                 int32_t n_classes, void *stream, lnbnn_index **out);
+
+/*
+ * The same index over location-weighted descriptors: the alpha weighting of
+ * descriptor location that Section 5 fixes at 1.6 for its experiments (an
+ * option of the original NBNN, where the location is appended to the
+ * descriptor).  Each row is 130 bytes: 128 appearance coordinates, then the
+ * descriptor's location (x, y) on a 0..255 grid of the image, and
+ *   distance(q, r) = sum_{t<128} (q_t - r_t)^2
+ *                  + location_weight * ((q_x - r_x)^2 + (q_y - r_y)^2),
+ * the squared Euclidean distance with the location appended at scale
+ * sqrt(location_weight) (so location_weight = alpha^2 in grid units).  Every
+ * call on this index takes 130-byte query rows; the distances stay exact.
+ *
+ *   ref              device uint8 [n_ref * 130]
+ *   location_weight  0 <= location_weight <= LNBNN_MAX_LOCATION_WEIGHT
+ * Other arguments as lnbnn_index_create.  The FP8 shortlist search is not
+ * offered for such an index (lnbnn_index_prepare_fp8 returns UNSUPPORTED);
+ * knn_search_noalloc takes 128-byte rows only.
+ * Errors: as lnbnn_index_create, plus INVALID_ARG for a weight out of range.
+ */
+LNBNN_API lnbnn_status lnbnn_index_create_located(const uint8_t *ref, const int32_t *labels, int64_t n_ref,
+                                                  int32_t n_classes, int32_t location_weight, void *stream,
+                                                  lnbnn_index **out);
+
+/* Row layout of an index: bytes per descriptor row (128 or 130) and the
+ * location weight (0 for 128-byte rows).  Either pointer may be NULL. */
+LNBNN_API lnbnn_status lnbnn_index_layout(const lnbnn_index *index, int32_t *row_bytes, int32_t *location_weight);
 
 /* Release the index and all device memory it owns.  NULL is accepted. */
 LNBNN_API void lnbnn_index_destroy(lnbnn_index *index);
@@ -353,8 +388,9 @@ LNBNN_API lnbnn_status knn_search_noalloc(const uint8_t *ref, int64_t n_ref, con
  * the original arrays).  lnbnn_index_save writes what lnbnn_index_create was
  * given — the reference descriptors and their labels — to the file `path`:
  * a 32-byte header (the 8 bytes "LNBNNIX1", uint32 format version 1, uint32
- * descriptor length 128, int64 n_ref, int32 n_classes, uint32 0), the uint8
- * descriptors [n_ref * 128], the int32 labels [n_ref], and an 8-byte FNV-1a
+ * row bytes 128 or 130, int64 n_ref, int32 n_classes, uint32 location weight
+ * (0 for 128-byte rows)), the uint8 descriptors [n_ref * row bytes], the
+ * int32 labels [n_ref], and an 8-byte FNV-1a
  * 64-bit hash of everything before it; all integers little-endian.  The call
  * waits for the device copies.  lnbnn_index_load checks the header, sizes and
  * hash before it touches the device, then builds the index exactly as

@@ -76,12 +76,14 @@ def sum_increments(inc, offsets, positive_only: bool, tol: float = 0.0):
     return totals, classes, counts, near
 
 
-def nbnn_logodds(ref, labels, n_classes, q, offsets, beta: float, positive_only: bool, threads=0):
+def nbnn_logodds(ref, labels, n_classes, q, offsets, beta: float, positive_only: bool, threads=0,
+                 location_weight=None):
     """Classify every image by its summed log-odds increments (Eq. (eqn:log-increments)).
 
     Returns (totals float64 [n_img, C], classes int32 [n_img],
-    increments added int64 [n_img], increments within the decision tolerance of 0 int64 [n_img])."""
-    D = class_min(ref, labels, n_classes, q, threads)
+    increments added int64 [n_img], increments within the decision tolerance of 0 int64 [n_img]).
+    130-byte rows take a location weight, as ``class_min`` does."""
+    D = class_min(ref, labels, n_classes, q, threads, location_weight)
     inc = logodds_increments(D, beta) if len(D) else np.zeros((0, n_classes))
     tol = decision_tolerance(D, beta) if len(D) else 0.0
     return sum_increments(inc, offsets, positive_only, tol)

@@ -48,15 +48,24 @@ __host__ __device__ __forceinline__ uint32_t key_row(uint64_t k) { return static
 // ----------------------------------------------------------- kernels (launchers)
 // Each launcher returns cudaGetLastError() after the launch.
 
-// Reference preparation: exact BF16 copy (rows padded to n_pad with zeros),
-// squared norms as fp32 (padding rows get kPadNorm) and the norm digits of the
-// K-extension [n_pad, kExt].
-cudaError_t launch_prep_ref(const uint8_t* ref, int64_t n_ref, int64_t n_pad, __nv_bfloat16* ref_bf,
-                            float* rnorm, __nv_bfloat16* ref_ext, cudaStream_t s);
+// Rows of descriptors are kDim bytes (appearance), or kDim + 2 with a location
+// (x, y) weighted by loc_w in [0, LNBNN_MAX_LOCATION_WEIGHT].
+__host__ __device__ __forceinline__ bool row_layout_ok(int row_bytes, int loc_w) {
+  return (row_bytes == kDim && loc_w == 0) ||
+         (row_bytes == LNBNN_LOCATED_DIM && loc_w >= 0 && loc_w <= LNBNN_MAX_LOCATION_WEIGHT);
+}
+
+// Reference preparation (rows of row_bytes bytes): exact BF16 copy of the
+// centred appearance coordinates x - 128 (padding rows up to n_pad: zero),
+// squared norms as fp32 (padding rows get kPadNorm) and the K-extension
+// [n_pad, kExt] (norm digits, location columns).
+cudaError_t launch_prep_ref(const uint8_t* ref, int64_t n_ref, int64_t n_pad, int row_bytes, int loc_w,
+                            __nv_bfloat16* ref_bf, float* rnorm, __nv_bfloat16* ref_ext, cudaStream_t s);
 // Query preparation: squared norms (int32) and, when qbf != nullptr, the BF16
-// operand -2q (rows padded to m_pad with zeros) and its K-extension
-// (1, 256, 65536, 0, ...) [m_pad, kExt].
-cudaError_t launch_prep_query(const uint8_t* q, int64_t m, int64_t m_pad, int32_t* qnorm,
+// operand -2 (q - 128) (padding rows up to m_pad: zero) and its K-extension
+// [m_pad, kExt] (the weights of the reference's norm digits, the query's norm
+// digits, the location cross-term columns).
+cudaError_t launch_prep_query(const uint8_t* q, int64_t m, int64_t m_pad, int row_bytes, int loc_w, int32_t* qnorm,
                               __nv_bfloat16* qbf, __nv_bfloat16* qext, cudaStream_t s);
 // Label histogram; sets *bad when a label is outside [0, C).
 cudaError_t launch_label_hist(const int32_t* labels, int64_t n, int32_t C, unsigned long long* counts,

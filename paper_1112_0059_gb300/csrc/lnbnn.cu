@@ -22,8 +22,10 @@ struct lnbnn_index {
   int64_t n_ref = 0;
   int64_t n_pad = 0;
   int32_t n_classes = 0;
+  int32_t row_bytes = kDim;  // bytes per descriptor row: 128, or 130 with a location
+  int32_t loc_w = 0;         // weight of the location term (130-byte rows)
   // merged reference set, caller's row order
-  uint8_t* ref_u8 = nullptr;         // [n_ref, 128] the descriptors as given
+  uint8_t* ref_u8 = nullptr;         // [n_ref, row_bytes] the descriptors as given
   __nv_bfloat16* ref_bf = nullptr;   // [n_pad, 128] exact BF16 copy, zero padding rows
   __nv_bfloat16* ref_ext = nullptr;  // [n_pad, 16] squared-norm digits (K-extension)
   float* rnorm = nullptr;            // [n_pad] squared norms, kPadNorm on padding rows
@@ -309,7 +311,7 @@ lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_
   uint64_t* part = reinterpret_cast<uint64_t*>(ws + p.off_lists);
   uint64_t* merged = reinterpret_cast<uint64_t*>(ws + p.off_merged);
   Range range("lnbnn: exact k+1 search");
-  CK(launch_prep_query(q, m, p.m_pad, qnorm, qbf, qext, s));
+  CK(launch_prep_query(q, m, p.m_pad, ix->row_bytes, ix->loc_w, qnorm, qbf, qext, s));
   prof.launched(1);
   prof.mark(1);
   CK(launch_knn_tc(ix->tc, /*sorted_copy=*/false, qbf, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, K1, part,
@@ -399,12 +401,13 @@ const char* lnbnn_status_string(lnbnn_status st) {
   return "unknown status";
 }
 
-lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64_t n_ref, int32_t n_classes,
-                                void* stream, lnbnn_index** out) {
+static lnbnn_status create_index(const uint8_t* ref, const int32_t* labels, int64_t n_ref, int32_t n_classes,
+                                 int32_t row_bytes, int32_t loc_w, void* stream, lnbnn_index** out) {
   Range range("lnbnn: lnbnn_index_create");
   if (!out) return LNBNN_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!ref || !labels || n_ref < 1 || n_classes < 1 || n_ref > (int64_t)INT32_MAX - kRefPad)
+  if (!ref || !labels || n_ref < 1 || n_classes < 1 || n_ref > (int64_t)INT32_MAX - kRefPad ||
+      !row_layout_ok(row_bytes, loc_w))
     return LNBNN_ERR_INVALID_ARG;
   int sm = 0, dev = 0;
   if (!device_ok(&sm, &dev)) return LNBNN_ERR_UNSUPPORTED;
@@ -416,6 +419,8 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
   ix->n_ref = n_ref;
   ix->n_pad = round_up(n_ref, kRefPad);
   ix->n_classes = n_classes;
+  ix->row_bytes = row_bytes;
+  ix->loc_w = loc_w;
   lnbnn_status st = LNBNN_OK;
   unsigned long long* counts = nullptr;
   uint32_t* bad = nullptr;
@@ -432,7 +437,7 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
     cudaError_t e_ = (call);                        \
     if (e_ != cudaSuccess) return fail(status_of(e_)); \
   } while (0)
-  CKF(dmalloc(&ix->ref_u8, (size_t)n_ref * kDim));
+  CKF(dmalloc(&ix->ref_u8, (size_t)n_ref * row_bytes));
   CKF(dmalloc(&ix->ref_bf, (size_t)ix->n_pad * kDim));
   CKF(dmalloc(&ix->ref_ext, (size_t)ix->n_pad * kExt));
   CKF(dmalloc(&ix->rnorm, (size_t)ix->n_pad));
@@ -443,10 +448,10 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
   CKF(cudaMemsetAsync(ix->dev_err, 0, sizeof(uint32_t), s));
   CKF(cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * n_classes, s));
   CKF(cudaMemsetAsync(bad, 0, sizeof(uint32_t), s));
-  CKF(cudaMemcpyAsync(ix->ref_u8, ref, (size_t)n_ref * kDim, cudaMemcpyDeviceToDevice, s));
+  CKF(cudaMemcpyAsync(ix->ref_u8, ref, (size_t)n_ref * row_bytes, cudaMemcpyDeviceToDevice, s));
   CKF(cudaMemcpyAsync(ix->labels, labels, sizeof(int32_t) * n_ref, cudaMemcpyDeviceToDevice, s));
   CKF(launch_label_hist(ix->labels, n_ref, n_classes, counts, bad, s));
-  CKF(launch_prep_ref(ix->ref_u8, n_ref, ix->n_pad, ix->ref_bf, ix->rnorm, ix->ref_ext, s));
+  CKF(launch_prep_ref(ix->ref_u8, n_ref, ix->n_pad, row_bytes, loc_w, ix->ref_bf, ix->rnorm, ix->ref_ext, s));
   std::vector<unsigned long long> cnt(n_classes);
   uint32_t bad_h = 0;
   std::vector<int32_t> lab_h(n_ref);
@@ -502,6 +507,25 @@ lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64
 #undef CKF
 }
 
+lnbnn_status lnbnn_index_create(const uint8_t* ref, const int32_t* labels, int64_t n_ref, int32_t n_classes,
+                                void* stream, lnbnn_index** out) {
+  return create_index(ref, labels, n_ref, n_classes, kDim, 0, stream, out);
+}
+
+lnbnn_status lnbnn_index_create_located(const uint8_t* ref, const int32_t* labels, int64_t n_ref, int32_t n_classes,
+                                        int32_t location_weight, void* stream, lnbnn_index** out) {
+  if (out) *out = nullptr;
+  if (location_weight < 0 || location_weight > LNBNN_MAX_LOCATION_WEIGHT) return LNBNN_ERR_INVALID_ARG;
+  return create_index(ref, labels, n_ref, n_classes, LNBNN_LOCATED_DIM, location_weight, stream, out);
+}
+
+lnbnn_status lnbnn_index_layout(const lnbnn_index* index, int32_t* row_bytes, int32_t* location_weight) {
+  if (!index) return LNBNN_ERR_INVALID_ARG;
+  if (row_bytes) *row_bytes = index->row_bytes;
+  if (location_weight) *location_weight = index->loc_w;
+  return LNBNN_OK;
+}
+
 void lnbnn_index_destroy(lnbnn_index* index) { free_index(index); }
 
 // ------------------------------------------------------------ persistence
@@ -518,7 +542,7 @@ struct FileHeader {
   uint32_t dim;
   int64_t n_ref;
   int32_t n_classes;
-  uint32_t reserved;
+  uint32_t location_weight;  // 0 for 128-byte rows
 };
 static_assert(sizeof(FileHeader) == 32, "the file header is 32 bytes");
 
@@ -562,14 +586,15 @@ lnbnn_status lnbnn_index_save(const lnbnn_index* index, const char* path) {
   FileHeader hd{};
   memcpy(hd.magic, kFileMagic, sizeof kFileMagic);
   hd.version = kFileVersion;
-  hd.dim = kDim;
+  hd.dim = (uint32_t)index->row_bytes;
+  hd.location_weight = (uint32_t)index->loc_w;
   hd.n_ref = index->n_ref;
   hd.n_classes = index->n_classes;
   Fnv64 h;
   h.add(&hd, sizeof hd);
   if (fwrite(&hd, sizeof hd, 1, file.f) != 1) return LNBNN_ERR_IO;
   std::vector<unsigned char> buf(kFileChunk);
-  if (!write_device(file.f, index->ref_u8, (size_t)index->n_ref * kDim, buf, h) ||
+  if (!write_device(file.f, index->ref_u8, (size_t)index->n_ref * index->row_bytes, buf, h) ||
       !write_device(file.f, index->labels, sizeof(int32_t) * (size_t)index->n_ref, buf, h))
     return LNBNN_ERR_IO;
   if (fwrite(&h.h, sizeof h.h, 1, file.f) != 1 || fflush(file.f) != 0) return LNBNN_ERR_IO;
@@ -585,11 +610,13 @@ lnbnn_status lnbnn_index_load(const char* path, void* stream, lnbnn_index** out)
   if (!file.f) return LNBNN_ERR_IO;
   FileHeader hd{};
   if (fread(&hd, sizeof hd, 1, file.f) != 1) return LNBNN_ERR_IO;
-  if (memcmp(hd.magic, kFileMagic, sizeof kFileMagic) != 0 || hd.version != kFileVersion || hd.dim != kDim ||
-      hd.n_ref < 1 || hd.n_ref > (int64_t)INT32_MAX - kRefPad || hd.n_classes < 1 || hd.reserved != 0)
+  if (memcmp(hd.magic, kFileMagic, sizeof kFileMagic) != 0 || hd.version != kFileVersion ||
+      hd.dim > (uint32_t)LNBNN_LOCATED_DIM || hd.location_weight > (uint32_t)LNBNN_MAX_LOCATION_WEIGHT ||
+      !row_layout_ok((int)hd.dim, (int)hd.location_weight) || hd.n_ref < 1 ||
+      hd.n_ref > (int64_t)INT32_MAX - kRefPad || hd.n_classes < 1)
     return LNBNN_ERR_IO;
   // the whole payload is read and its hash checked before the device is touched
-  const size_t ref_bytes = (size_t)hd.n_ref * kDim, lab_bytes = sizeof(int32_t) * (size_t)hd.n_ref;
+  const size_t ref_bytes = (size_t)hd.n_ref * hd.dim, lab_bytes = sizeof(int32_t) * (size_t)hd.n_ref;
   std::vector<unsigned char> ref, lab;
   try {
     ref.resize(ref_bytes);
@@ -615,7 +642,9 @@ lnbnn_status lnbnn_index_load(const char* path, void* stream, lnbnn_index** out)
   if (e == cudaSuccess) e = cudaMemcpyAsync(ref_d, ref.data(), ref_bytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(lab_d, lab.data(), lab_bytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  st = e == cudaSuccess ? lnbnn_index_create(ref_d, lab_d, hd.n_ref, hd.n_classes, stream, out) : status_of(e);
+  st = e == cudaSuccess ? create_index(ref_d, lab_d, hd.n_ref, hd.n_classes, (int32_t)hd.dim,
+                                        (int32_t)hd.location_weight, stream, out)
+                        : status_of(e);
   cudaFree(ref_d);
   cudaFree(lab_d);
   return st;
@@ -687,12 +716,13 @@ lnbnn_status lnbnn_autotune(lnbnn_index* index, void* stream, lnbnn_tuning* out)
       return st;                          \
     }                                     \
   } while (0)
-  CKA(dmalloc(&q, (size_t)m_max * kDim));
+  const int32_t rb = index->row_bytes;
+  CKA(dmalloc(&q, (size_t)m_max * rb));
   CKA(lib_malloc(&w.base, need));
   CKA(cudaEventCreate(&e0));
   CKA(cudaEventCreate(&e1));
   const int64_t step = n_ref / m_max;  // >= 1
-  CKA(cudaMemcpy2DAsync(q, kDim, index->ref_u8, (size_t)step * kDim, kDim, (size_t)m_max, cudaMemcpyDeviceToDevice, s));
+  CKA(cudaMemcpy2DAsync(q, rb, index->ref_u8, (size_t)step * rb, rb, (size_t)m_max, cudaMemcpyDeviceToDevice, s));
   const bool prof_was_on = index->prof_on;
   index->prof_on = false;
   for (Run& r : runs) {
@@ -785,6 +815,7 @@ lnbnn_status lnbnn_autotune(lnbnn_index* index, void* stream, lnbnn_tuning* out)
 lnbnn_status lnbnn_index_prepare_fp8(lnbnn_index* index, void* stream) {
   Range range("lnbnn: lnbnn_index_prepare_fp8");
   if (!index) return LNBNN_ERR_INVALID_ARG;
+  if (index->row_bytes != kDim) return LNBNN_ERR_UNSUPPORTED;  // the coarse operand has no location term
   if (index->fp8) return LNBNN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   auto undo = [&](lnbnn_status st) {  // a failed preparation keeps nothing
@@ -911,7 +942,7 @@ static lnbnn_status scan_class_minima(lnbnn_index* index, lnbnn_workspace* w, co
   __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(ws + np.off_qext);
   *mins = reinterpret_cast<int32_t*>(ws + np.off_mins);
   if (rowstat) *rowstat = ws + np.off_rowstat;
-  CK(launch_prep_query(queries, n_queries, p.m_pad, qnorm, qbf, qext, s));
+  CK(launch_prep_query(queries, n_queries, p.m_pad, index->row_bytes, index->loc_w, qnorm, qbf, qext, s));
   CK(cudaMemsetAsync(*mins, 0x7F, sizeof(int32_t) * (size_t)p.m_pad * index->n_classes, s));  // > any distance
   prof.launched(1);
   prof.mark(1);
@@ -1099,7 +1130,7 @@ static lnbnn_status classify_host(lnbnn_index* index, bool local, const uint8_t*
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int32_t C = index->n_classes;
   Carve c;
-  const size_t oq = c.take<uint8_t>((size_t)n_queries * kDim);
+  const size_t oq = c.take<uint8_t>((size_t)n_queries * index->row_bytes);
   const size_t oo = c.take<int64_t>((size_t)n_images + 1);
   const size_t ot = c.take<int64_t>((size_t)n_images * C);
   const size_t oc = c.take<int32_t>((size_t)n_images);
@@ -1109,7 +1140,8 @@ static lnbnn_status classify_host(lnbnn_index* index, bool local, const uint8_t*
   int64_t* doff = reinterpret_cast<int64_t*>(b + oo);
   int64_t* dtot = reinterpret_cast<int64_t*>(b + ot);
   int32_t* dcls = reinterpret_cast<int32_t*>(b + oc);
-  if (n_queries > 0) CK(cudaMemcpyAsync(dq, queries, (size_t)n_queries * kDim, cudaMemcpyHostToDevice, s));
+  if (n_queries > 0)
+    CK(cudaMemcpyAsync(dq, queries, (size_t)n_queries * index->row_bytes, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(doff, offsets, sizeof(int64_t) * (n_images + 1), cudaMemcpyHostToDevice, s));
   lnbnn_status st =
       local ? do_lnbnn_classify(index, nullptr, dq, n_queries, doff, n_images, k, shortlist, dtot, dcls, stream)

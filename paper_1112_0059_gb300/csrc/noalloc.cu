@@ -124,8 +124,8 @@ extern "C" LNBNN_API lnbnn_status knn_search_noalloc(const uint8_t* ref, int64_t
   // The array keeps the previous call's contents: the error word must start at
   // zero; every other buffer is fully written before it is read.
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
-  if (e == cudaSuccess) e = launch_prep_ref(ref, n_ref, n_pad, ref_bf, rnorm, ref_ext, s);
-  if (e == cudaSuccess) e = launch_prep_query(queries, n_queries, m_pad, qnorm, qbf, qext, s);
+  if (e == cudaSuccess) e = launch_prep_ref(ref, n_ref, n_pad, kDim, 0, ref_bf, rnorm, ref_ext, s);
+  if (e == cudaSuccess) e = launch_prep_query(queries, n_queries, m_pad, kDim, 0, qnorm, qbf, qext, s);
   if (e == cudaSuccess)
     e = launch_knn_tc(maps, false, qbf, qext, n_queries, m_pad, n_ref, (int)splits, split_len, k, lists, m_pad, err,
                       nullptr, nullptr, s);

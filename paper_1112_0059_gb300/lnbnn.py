@@ -43,7 +43,7 @@ EXPORTS = ["lnbnn_index_create", "lnbnn_index_destroy", "lnbnn_index_info", "knn
            "lnbnn_index_prepare_fp8", "knn_search_fp8", "lnbnn_classify_fp8", "knn_search_fp8_ws",
            "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host", "lnbnn_autotune", "lnbnn_plan_splits",
            "lnbnn_debug_fail_allocations", "lnbnn_set_start_gate", "lnbnn_index_save", "lnbnn_index_load",
-           "nbnn_logodds_classify", "nbnn_logodds_classify_ws"]
+           "nbnn_logodds_classify", "nbnn_logodds_classify_ws", "lnbnn_index_create_located", "lnbnn_index_layout"]
 
 
 class Profile(ctypes.Structure):
@@ -120,6 +120,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.lnbnn_index_load.argtypes = [ctypes.c_char_p, P, ctypes.POINTER(P)]
         lib.lnbnn_index_load.restype = ctypes.c_int
         lib.nbnn_logodds_classify.argtypes = [P, P, I64, P, I64, ctypes.c_double, I32, P, P, P, P]
+        lib.lnbnn_index_create_located.argtypes = [P, P, I64, I32, I32, P, ctypes.POINTER(P)]
+        lib.lnbnn_index_layout.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]
         lib.nbnn_logodds_classify_ws.argtypes = [P, P, P, I64, P, I64, ctypes.c_double, I32, P, P, P, P]
         lib.lnbnn_status_string.argtypes = [ctypes.c_int]
         lib.lnbnn_status_string.restype = ctypes.c_char_p
@@ -128,7 +130,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                      "lnbnn_profile_read", "lnbnn_workspace_create", "knn_search_ws", "lnbnn_classify_ws",
                      "nbnn_classify_ws", "lnbnn_index_prepare_fp8", "knn_search_fp8", "lnbnn_classify_fp8",
                      "knn_search_fp8_ws", "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host", "lnbnn_autotune",
-                     "lnbnn_plan_splits", "nbnn_logodds_classify", "nbnn_logodds_classify_ws"):
+                     "lnbnn_plan_splits", "nbnn_logodds_classify", "nbnn_logodds_classify_ws",
+                     "lnbnn_index_create_located", "lnbnn_index_layout"):
             getattr(lib, name).restype = ctypes.c_int
         if path == LIB_PATH:
             _lib = lib
@@ -159,20 +162,39 @@ def _dev(t, dtype, name):
 
 class Index:
     """Merged reference index (Alg. 2's single search structure plus the class
-    lookup), also serving original NBNN.  Owns device memory until ``close()``."""
+    lookup), also serving original NBNN.  Owns device memory until ``close()``.
 
-    def __init__(self, ref, labels, n_classes: int, stream=None):
+    ``ref`` is uint8 [N, 128], or [N, 130] with ``location_weight`` w: rows
+    carry a location (x, y) after the 128 appearance bytes and distances add
+    w times the squared location difference (lnbnn_index_create_located);
+    queries then have 130-byte rows too."""
+
+    def __init__(self, ref, labels, n_classes: int, stream=None, location_weight: int | None = None):
         import torch
         self._lib = load_library()
-        if ref.dim() != 2 or ref.shape[1] != 128:
-            raise ValueError("ref must be uint8 [N, 128]")
+        if ref.dim() != 2 or ref.shape[1] not in (128, 130):
+            raise ValueError("ref must be uint8 [N, 128] or [N, 130]")
+        if (ref.shape[1] == 130) != (location_weight is not None):
+            raise ValueError("130-byte rows go with a location_weight, 128-byte rows without")
         self.n_ref = int(ref.shape[0])
         self.n_classes = int(n_classes)
+        self.row_bytes = int(ref.shape[1])
+        self.location_weight = int(location_weight or 0)
         h = ctypes.c_void_p()
-        _check(self._lib.lnbnn_index_create(_dev(ref, torch.uint8, "ref"), _dev(labels, torch.int32, "labels"),
-                                            self.n_ref, self.n_classes, _stream_ptr(stream), ctypes.byref(h)),
-               "lnbnn_index_create")
+        args = (_dev(ref, torch.uint8, "ref"), _dev(labels, torch.int32, "labels"), self.n_ref, self.n_classes)
+        if location_weight is None:
+            _check(self._lib.lnbnn_index_create(*args, _stream_ptr(stream), ctypes.byref(h)), "lnbnn_index_create")
+        else:
+            _check(self._lib.lnbnn_index_create_located(*args, int(location_weight), _stream_ptr(stream),
+                                                        ctypes.byref(h)), "lnbnn_index_create_located")
         self._h = h
+
+    def _q(self, queries):
+        """Device pointer of a uint8 [M, row_bytes] query tensor."""
+        import torch
+        if queries.dim() != 2 or queries.shape[1] != self.row_bytes:
+            raise ValueError(f"queries must be uint8 [M, {self.row_bytes}] for this index")
+        return _dev(queries, torch.uint8, "queries")
 
     @classmethod
     def load(cls, path: str, stream=None) -> "Index":
@@ -185,6 +207,9 @@ class Index:
         n_ref, n_cls = ctypes.c_int64(), ctypes.c_int32()
         _check(lib.lnbnn_index_info(h, ctypes.byref(n_ref), ctypes.byref(n_cls)), "lnbnn_index_info")
         ix.n_ref, ix.n_classes = int(n_ref.value), int(n_cls.value)
+        rb, lw = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.lnbnn_index_layout(h, ctypes.byref(rb), ctypes.byref(lw)), "lnbnn_index_layout")
+        ix.row_bytes, ix.location_weight = int(rb.value), int(lw.value)
         return ix
 
     def save(self, path: str) -> None:
@@ -253,7 +278,7 @@ class Index:
         idx, dist = out if out is not None else (
             torch.empty((m, k), dtype=torch.int32, device=queries.device),
             torch.empty((m, k), dtype=torch.int32, device=queries.device))
-        q = _dev(queries, torch.uint8, "queries")
+        q = self._q(queries)
         tail = (_dev(idx, torch.int32, "idx"), _dev(dist, torch.int32, "dist"), _stream_ptr(stream))
         if shortlist is None:
             if workspace is None:
@@ -276,7 +301,7 @@ class Index:
         totals, classes = out if out is not None else (
             torch.empty((n_img, self.n_classes), dtype=torch.int64, device=queries.device),
             torch.empty((n_img,), dtype=torch.int32, device=queries.device))
-        head = (_dev(queries, torch.uint8, "queries"), m, _dev(offsets, torch.int64, "offsets"), n_img, k)
+        head = (self._q(queries), m, _dev(offsets, torch.int64, "offsets"), n_img, k)
         tail = (_dev(totals, torch.int64, "totals"), _dev(classes, torch.int32, "classes"), _stream_ptr(stream))
         if shortlist is None:
             if workspace is None:
@@ -297,7 +322,7 @@ class Index:
         totals, classes = out if out is not None else (
             torch.empty((n_img, self.n_classes), dtype=torch.int64, device=queries.device),
             torch.empty((n_img,), dtype=torch.int32, device=queries.device))
-        args = (_dev(queries, torch.uint8, "queries"), m, _dev(offsets, torch.int64, "offsets"), n_img,
+        args = (self._q(queries), m, _dev(offsets, torch.int64, "offsets"), n_img,
                 _dev(totals, torch.int64, "totals"), _dev(classes, torch.int32, "classes"), _stream_ptr(stream))
         if workspace is None:
             _check(self._lib.nbnn_classify(self.handle, *args), "nbnn_classify")
@@ -317,7 +342,7 @@ class Index:
             torch.empty((n_img, self.n_classes), dtype=torch.float64, device=queries.device),
             torch.empty((n_img,), dtype=torch.int32, device=queries.device),
             torch.empty((n_img,), dtype=torch.int64, device=queries.device))
-        args = (_dev(queries, torch.uint8, "queries"), m, _dev(offsets, torch.int64, "offsets"), n_img,
+        args = (self._q(queries), m, _dev(offsets, torch.int64, "offsets"), n_img,
                 float(beta), int(bool(positive_only)), _dev(totals, torch.float64, "totals"),
                 _dev(classes, torch.int32, "classes"), _dev(counts, torch.int64, "n_increments"),
                 _stream_ptr(stream))
@@ -333,6 +358,8 @@ class Index:
         """Host-buffer form (k=None -> original NBNN; shortlist -> FP8 shortlist
         search).  numpy in, numpy out; pinned host arrays give the fastest copies."""
         q = np.ascontiguousarray(queries, dtype=np.uint8)
+        if q.ndim != 2 or q.shape[1] != self.row_bytes:
+            raise ValueError(f"queries must be uint8 [M, {self.row_bytes}] for this index")
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         n_img = off.shape[0] - 1
         if totals is None:

@@ -121,6 +121,7 @@ class Server:
         self.use_graphs = bool(graphs)
         self.buckets = graph_buckets(self.max_q)
         C = index.n_classes
+        D = getattr(index, "row_bytes", 128)  # 130 for a location-weighted index
         dev = torch.device("cuda", torch.cuda.current_device())
         # Graph mode adds one image that holds the padding descriptors.
         n_img_cap = self.max_img + 1
@@ -129,11 +130,11 @@ class Server:
             self.slots.append(_Slot(
                 ws=index.workspace(self.max_q, max(self.k, (shortlist or 0) - 1)),
                 stream=torch.cuda.Stream(dev),
-                q_host=torch.zeros((self.max_q, 128), dtype=torch.uint8).pin_memory(),
+                q_host=torch.zeros((self.max_q, D), dtype=torch.uint8).pin_memory(),
                 off_host=torch.empty((n_img_cap + 1,), dtype=torch.int64).pin_memory(),
                 tot_host=torch.empty((n_img_cap, C), dtype=torch.int64).pin_memory(),
                 cls_host=torch.empty((n_img_cap,), dtype=torch.int32).pin_memory(),
-                q_dev=torch.empty((self.max_q, 128), dtype=torch.uint8, device=dev),
+                q_dev=torch.empty((self.max_q, D), dtype=torch.uint8, device=dev),
                 off_dev=torch.empty((n_img_cap + 1,), dtype=torch.int64, device=dev),
                 tot_dev=torch.empty((n_img_cap, C), dtype=torch.int64, device=dev),
                 cls_dev=torch.empty((n_img_cap,), dtype=torch.int32, device=dev),

@@ -15,6 +15,11 @@ Recipe (one reading of the workload description, applied to every size):
 * Reference images are laid out class by class (class 0's images first), so
   the merged reference set is class-sorted; label = class.
 * Query image ``j`` belongs to class ``j mod C``.
+* Locations (for location-weighted descriptors, 130-byte rows): every class
+  prototype has a home position ~ U[32, 224)^2 on a 0..255 image grid; a
+  descriptor's (x, y) is the home of the prototype it was drawn from plus
+  N(0, 24^2) per axis, clipped to [0, 255] and rounded half-to-even.  Drawn
+  from streams of their own, so the 128 appearance bytes do not change.
 
 Every random stream is keyed by (seed, purpose, class, image), so class ``c``'s
 reference descriptors are the same bytes whatever the number of classes in the
@@ -41,7 +46,9 @@ NOISE_SD = 12.0
 ZERO_PROB = 0.3
 
 # stream purposes
-_POOL, _CLASS, _REF, _QUERY, _COUNTS = 0, 1, 2, 3, 4
+_POOL, _CLASS, _REF, _QUERY, _COUNTS, _LOC = 0, 1, 2, 3, 4, 5
+LOC_HOME_LOW, LOC_HOME_HIGH = 32.0, 224.0
+LOC_SD = 24.0
 
 
 @dataclass(frozen=True)
@@ -185,6 +192,47 @@ def query_image(w: Workload, j: int, n: int) -> np.ndarray:
     out = np.empty((n, D), dtype=np.uint8)
     _descriptors(class_prototypes(w.seed, j % w.n_classes), n, _rng(w.seed, _QUERY, j), out)
     return out
+
+
+@lru_cache(maxsize=4096)
+def prototype_homes(seed: int, c: int) -> np.ndarray:
+    """Home positions (float32 [16, 2]) of class ``c``'s prototypes."""
+    return _rng(seed, _LOC, c).uniform(LOC_HOME_LOW, LOC_HOME_HIGH, size=(PROTOS_PER_CLASS, 2)).astype(np.float32)
+
+
+def _locations(seed: int, c: int, pick_rng: np.random.Generator, n: int, rng: np.random.Generator) -> np.ndarray:
+    # the first draw of a descriptor stream is its prototype pick (see _descriptors)
+    pick = pick_rng.integers(0, PROTOS_PER_CLASS, size=n)
+    xy = prototype_homes(seed, c)[pick] + rng.standard_normal((n, 2), dtype=np.float32) * np.float32(LOC_SD)
+    return np.rint(np.clip(xy, 0.0, 255.0)).astype(np.uint8)
+
+
+def reference_locations(w: Workload) -> np.ndarray:
+    """(x, y) of every reference descriptor (uint8 [N, 2]), row-aligned with ``reference_set``."""
+    per_img = w.ref_desc_per_img
+    out = np.empty((w.n_classes * w.ref_imgs_per_class * per_img, 2), dtype=np.uint8)
+    for g in range(w.n_classes * w.ref_imgs_per_class):
+        c, m = divmod(g, w.ref_imgs_per_class)
+        out[g * per_img:(g + 1) * per_img] = _locations(w.seed, c, _rng(w.seed, _REF, c, m), per_img,
+                                                        _rng(w.seed, _LOC, 1, c, m))
+    return out
+
+
+def query_locations(w: Workload, counts: np.ndarray | None = None) -> np.ndarray:
+    """(x, y) of every query descriptor (uint8 [M, 2]), row-aligned with ``query_set``."""
+    counts = query_counts(w) if counts is None else np.asarray(counts, dtype=np.int64)
+    out = np.empty((int(counts.sum()), 2), dtype=np.uint8)
+    at = 0
+    for j, n in enumerate(counts):
+        out[at:at + n] = _locations(w.seed, j % w.n_classes, _rng(w.seed, _QUERY, j), int(n),
+                                    _rng(w.seed, _LOC, 2, j))
+        at += n
+    return out
+
+
+def located(desc: np.ndarray, loc: np.ndarray) -> np.ndarray:
+    """130-byte rows: the 128 appearance bytes, then (x, y)."""
+    return np.ascontiguousarray(np.concatenate([desc, loc], axis=1), dtype=np.uint8)
 
 
 def workload(name: str) -> Workload:
