@@ -289,30 +289,83 @@ struct ScanOut {
   int32_t C;
   const int64_t* class_off;  // NBNN: class c owns sorted rows [class_off[c], class_off[c+1])
   const uint32_t* gate;      // null, or a word the producer waits to see nonzero before loading
+  int32_t* row_thr;          // kNN: per query row, a shared bound (below), or null
 };
 
 // kNN epilogue: the K1 smallest (distance, row) keys of the columns one
 // thread sees (Alg. 2's NN(d, k+1) restricted to a slice of the references).
+//
+// Register lists share a bound per query row with the other lists of that row
+// (the other column half, the other reference splits): row_thr[row] holds the
+// bit pattern of a distance at or below which some list already holds K1
+// entries, so a column farther than it cannot be among the row's K1 nearest
+// and is not offered (a column at exactly the bound still is: it may win on
+// its row).  A full list publishes its K1-th distance with an atomic minimum
+// after each tile that improved it, and reads the word once per tile (the
+// read issued at the end of one tile is taken in at the end of the next).  Which columns a
+// list drops depends on timing; the K1 nearest of the row never are, so the
+// merged result does not.
 template <int KMAX>
 struct KnnEpilogue {
   static constexpr int kWarpsPerQuarter = KMAX == kTcWideRegListMax ? 1 : 2;
   static constexpr uint32_t kListBytes = 0;
   RegList<KMAX> L;
   TopK top;
-  int32_t thr;
+  int32_t thr;      // bit pattern of this list's K1-th distance (INT32_MAX's while not full)
+  int32_t shared;   // the row's shared bound as last read (bit pattern)
+  int32_t pending;  // the read in flight for the next tile
+  int32_t* rthr;    // the row's shared bound, or null
   bool active;
   int K1;
   uint64_t* out;
   __device__ __forceinline__ KnnEpilogue(const ScanOut& o, int list, int64_t row, bool act, int64_t, uint8_t*, int)
       : top(o.lists + ((int64_t)list * o.stride + (act ? row : 0)) * o.K1, o.K1),
         thr(thr_bits(INT32_MAX)),
+        shared(kNoBound),
+        pending(kNoBound),
+        rthr(KMAX > 0 && act && o.row_thr ? o.row_thr + row : nullptr),
         active(act),
         K1(o.K1),
         out(o.lists + ((int64_t)list * o.stride + (act ? row : 0)) * o.K1) {
     L.init(K1);
   }
+  static constexpr int32_t kNoBound = 0x7F7F7F7F;  // the word's initial value: above every distance
   __device__ __forceinline__ void group(const uint32_t (&v)[32], uint32_t mn, int64_t col0) {
-    scan_group<KMAX>(L, top, thr, active, v, mn, col0);
+    if constexpr (KMAX > 0) {
+      int32_t lim = min(thr, shared + 1);  // strictly below: own K1-th, at or below: the shared bound
+      const bool hit = active && (int32_t)mn < lim;
+      if (__any_sync(0xffffffffu, hit)) {
+        if (hit) {
+          for (uint32_t mask = hit_mask(v, lim); mask; mask &= mask - 1) {
+            const int j = __ffs(mask) - 1;
+            const int32_t bits = select32(v, j);
+            if (bits < lim) {
+              L.insert(__float2int_rn(__int_as_float(bits)), (uint32_t)(col0 + j));
+              thr = thr_bits(L.worst());
+              lim = min(thr, shared + 1);
+            }
+          }
+        }
+        __syncwarp();
+      }
+    } else {
+      scan_group<KMAX>(L, top, thr, active, v, mn, col0);
+    }
+  }
+  // After each tile: publish an improved K1-th distance of a full list, take
+  // in the bound read a tile ago (its latency hidden behind a whole tile), and
+  // start the next read.
+  __device__ __forceinline__ void tile_end() {
+    if constexpr (KMAX > 0) {
+      if (rthr) {
+        if (L.worst() != INT32_MAX && thr < shared) {
+          atomicMin(rthr, thr);
+          shared = thr;
+        }
+        shared = min(shared, pending);
+        pending = __ldcg(rthr);
+      }
+    }
   }
   __device__ __forceinline__ void finish() {
     if (!active) return;
@@ -340,6 +393,7 @@ struct KnnSmemEpilogue {
   static constexpr int kWarpsPerQuarter = 1;
   static constexpr int kPerLane = KM / 32;  // list entries each lane computes in an insert
   static constexpr uint32_t kListBytes = 4 * kWarpsPerQuarter * 32 * KM * 8;
+  __device__ __forceinline__ void tile_end() {}
   static constexpr int32_t kInf = 0x7F800000;  // bits of +inf, above every distance
   static_assert(KM % 32 == 0 && KM <= 64, "entries i and i + 32 per lane");
   uint32_t* D;  // this warp's lists: D[list * KM + i] bit patterns, R[list * KM + i] rows
@@ -452,6 +506,7 @@ struct KnnSmemEpilogue {
 struct NbnnEpilogue {
   static constexpr int kWarpsPerQuarter = 2;
   static constexpr uint32_t kListBytes = 0;
+  __device__ __forceinline__ void tile_end() {}
   int32_t* dst;          // mins + row * C
   const int64_t* class_off;
   int64_t n_ref;
@@ -704,6 +759,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
         epi.group(v0, mn0, col0 + 64 * r);
         epi.group(v1, mn1, col0 + 64 * r + 32);
       }
+      epi.tile_end();
     }
     epi.finish();
   }
@@ -832,10 +888,11 @@ cudaError_t prepare_tc_kernels() {
 
 cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf,
                           const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
-                          int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
-                          unsigned long long* stats, const uint32_t* gate, cudaStream_t s) {
+                          int64_t split_len, int K1, uint64_t* lists, int64_t stride, int32_t* row_thr,
+                          uint32_t* dev_err, unsigned long long* stats, const uint32_t* gate, cudaStream_t s) {
   ScanOut out{};
   out.gate = gate;
+  out.row_thr = row_thr;
   out.lists = lists;
   out.stride = stride;
   out.K1 = K1;
@@ -864,10 +921,11 @@ cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv
 
 cudaError_t launch_coarse_tc(const TcTensorMaps& maps, const uint8_t* qf8, const __nv_bfloat16* qext, int64_t m,
                              int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int K1, uint64_t* lists,
-                             int64_t stride, uint32_t* dev_err, unsigned long long* stats, const uint32_t* gate,
-                             cudaStream_t s) {
+                             int64_t stride, int32_t* row_thr, uint32_t* dev_err, unsigned long long* stats,
+                             const uint32_t* gate, cudaStream_t s) {
   ScanOut out{};
   out.gate = gate;
+  out.row_thr = row_thr;
   out.lists = lists;
   out.stride = stride;
   out.K1 = K1;

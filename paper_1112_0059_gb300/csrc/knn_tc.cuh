@@ -103,18 +103,22 @@ bool make_tc_tensor_maps_e4m3(const uint8_t* ref_f8, const __nv_bfloat16* ref_f8
 // [s * split_len, min((s+1) * split_len, n_ref)) and writes L =
 // tc_lists_per_split(K1) sorted lists per query row i, list w at lists[((s * L + w) *
 // stride + i) * K1]; the K1 smallest keys of their union are the split's answer.
+// row_thr (null, or [m_pad] int32 filled with the bytes 0x7F beforehand) is
+// the per-row bound the lists of a row share: each list may leave out columns
+// that cannot be among the row's K1 nearest over all lists, so only the union
+// of a row's lists (merged) is the answer, not each list by itself.
 cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf,
                           const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
-                          int64_t split_len, int K1, uint64_t* lists, int64_t stride, uint32_t* dev_err,
-                          unsigned long long* stats, const uint32_t* gate, cudaStream_t s);
+                          int64_t split_len, int K1, uint64_t* lists, int64_t stride, int32_t* row_thr,
+                          uint32_t* dev_err, unsigned long long* stats, const uint32_t* gate, cudaStream_t s);
 // Coarse pass of the FP8 shortlist search: the same scan over the E4M3
 // operands (qf8 [m_pad, 128] bytes of -2 E4M3(q - 64), qext its extension),
 // keeping the K1 smallest (coarse + 2^21, row) keys per list in the same
 // layout as launch_knn_tc.
 cudaError_t launch_coarse_tc(const TcTensorMaps& maps, const uint8_t* qf8, const __nv_bfloat16* qext, int64_t m,
                              int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int K1, uint64_t* lists,
-                             int64_t stride, uint32_t* dev_err, unsigned long long* stats, const uint32_t* gate,
-                             cudaStream_t s);
+                             int64_t stride, int32_t* row_thr, uint32_t* dev_err, unsigned long long* stats,
+                             const uint32_t* gate, cudaStream_t s);
 // Original NBNN on the same tensor-core scan over the class-sorted copy:
 // mins [m_pad, C] (int32, filled with INT32_MAX-like values beforehand) gets
 // atomicMin(mins[i][c], ||q_i - r||^2) over every reference r of class c that

@@ -225,7 +225,7 @@ struct KnnPlan {
   int lists;  // sorted lists per query row the search writes (merged when > 1)
   int64_t split_len;
   int K1;
-  size_t off_qnorm, off_qbf, off_qext, off_lists, off_merged, bytes;
+  size_t off_qnorm, off_qbf, off_qext, off_lists, off_merged, off_rowthr, bytes;
 };
 
 // splits = 0: the modelled best; otherwise that many (an upper bound after
@@ -244,6 +244,7 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, int splits = 0, int64
   p.lists = p.splits * tc_lists_per_split(K1);
   p.off_lists = c.take<uint64_t>((size_t)p.lists * p.m_pad * K1);
   p.off_merged = c.take<uint64_t>((size_t)p.m_pad * K1);  // apart from the lists even for one list (rerank)
+  p.off_rowthr = c.take<int32_t>(p.m_pad);                // the bound a row's lists share
   p.bytes = c.off;
   return p;
 }
@@ -310,12 +311,14 @@ lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_
   __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(ws + p.off_qext);
   uint64_t* part = reinterpret_cast<uint64_t*>(ws + p.off_lists);
   uint64_t* merged = reinterpret_cast<uint64_t*>(ws + p.off_merged);
+  int32_t* row_thr = reinterpret_cast<int32_t*>(ws + p.off_rowthr);
   Range range("lnbnn: exact k+1 search");
   CK(launch_prep_query(q, m, p.m_pad, ix->row_bytes, ix->loc_w, qnorm, qbf, qext, s));
+  CK(cudaMemsetAsync(row_thr, 0x7F, sizeof(int32_t) * (size_t)p.m_pad, s));
   prof.launched(1);
   prof.mark(1);
   CK(launch_knn_tc(ix->tc, /*sorted_copy=*/false, qbf, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, K1, part,
-                   p.m_pad, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, ix->gate, s));
+                   p.m_pad, p.splits > 1 ? row_thr : nullptr, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, ix->gate, s));
   prof.launched(1, true);
   prof.mark(2);
   if (p.lists > 1) {
@@ -339,12 +342,14 @@ lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, in
   __nv_bfloat16* qext = reinterpret_cast<__nv_bfloat16*>(ws + p.off_qext);
   uint64_t* part = reinterpret_cast<uint64_t*>(ws + p.off_lists);
   uint64_t* merged = reinterpret_cast<uint64_t*>(ws + p.off_merged);
+  int32_t* row_thr = reinterpret_cast<int32_t*>(ws + p.off_rowthr);
   Range range("lnbnn: FP8 shortlist search");
   CK(launch_prep_query_e4m3(q, m, p.m_pad, qf8, qext, s));
+  CK(cudaMemsetAsync(row_thr, 0x7F, sizeof(int32_t) * (size_t)p.m_pad, s));
   prof.launched(1);
   prof.mark(1);
   CK(launch_coarse_tc(ix->tc, qf8, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, M1, part, p.m_pad,
-                      ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, ix->gate, s));
+                      p.splits > 1 ? row_thr : nullptr, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, ix->gate, s));
   prof.launched(1, true);
   prof.mark(2);
   // the shortlist is the merged lists (or the one list); the reranked lists

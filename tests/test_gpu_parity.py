@@ -106,6 +106,26 @@ def test_many_splits_small_batch(lnbnn):
         check_classify(ix, ref, labels, 5, q, off, 10)
 
 
+def test_shared_row_bound_with_ties(lnbnn):
+    # one query tile against 90k references: many splits, so the lists of a row
+    # share a bound and leave out columns beyond it; coordinates in {0..2} on
+    # a few dims put many columns exactly at the bound, where the lower row
+    # must still win (exact and FP8 shortlist, 16- and 32-entry lists)
+    for hi, dims in ((3, 5), (256, 128)):
+        ref, labels, q, off = random_case(5, 90000, 100, 6, hi=hi, dims=dims)
+        with make_index(lnbnn, ref, labels, 6) as ix:
+            assert ix.plan_splits(len(q)) > 8
+            for k in (1, 15, 31):
+                check_knn(ix, ref, q, k)
+            check_classify(ix, ref, labels, 6, q, off, 10)
+            ix.prepare_fp8()
+            for m in (16, 32):
+                idx, dist = ix.knn_search(dev(q), 11, shortlist=m)
+                ix.sync()
+                od, oj = oracle.knn_coarse(ref, q, 11, m)
+                assert np.array_equal(idx.cpu().numpy(), oj) and np.array_equal(dist.cpu().numpy(), od), (hi, m)
+
+
 # ------------------------------------------------------------------ adversarial ties
 
 def test_ties_small_values(lnbnn):
