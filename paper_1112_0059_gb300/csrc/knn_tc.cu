@@ -295,7 +295,7 @@ struct ScanOut {
 // kNN epilogue: the K1 smallest (distance, row) keys of the columns one
 // thread sees (Alg. 2's NN(d, k+1) restricted to a slice of the references).
 //
-// Register lists share a bound per query row with the other lists of that row
+// The lists (here and in KnnSmemEpilogue) share a bound per query row with the other lists of that row
 // (the other column half, the other reference splits): row_thr[row] holds the
 // bit pattern of a distance at or below which some list already holds K1
 // entries, so a column farther than it cannot be among the row's K1 nearest
@@ -393,12 +393,15 @@ struct KnnSmemEpilogue {
   static constexpr int kWarpsPerQuarter = 1;
   static constexpr int kPerLane = KM / 32;  // list entries each lane computes in an insert
   static constexpr uint32_t kListBytes = 4 * kWarpsPerQuarter * 32 * KM * 8;
-  __device__ __forceinline__ void tile_end() {}
   static constexpr int32_t kInf = 0x7F800000;  // bits of +inf, above every distance
+  static constexpr int32_t kNoBound = 0x7F7F7F7F;  // the shared bound's initial value
   static_assert(KM % 32 == 0 && KM <= 64, "entries i and i + 32 per lane");
   uint32_t* D;  // this warp's lists: D[list * KM + i] bit patterns, R[list * KM + i] rows
   uint32_t* R;
-  int32_t thr;  // bit pattern of this lane's list's K1-th entry
+  int32_t thr;      // bit pattern of this lane's list's K1-th entry
+  int32_t shared;   // the row's shared bound as last read (as in KnnEpilogue)
+  int32_t pending;  // the read in flight
+  int32_t* rthr;    // the row's shared bound, or null
   bool active;
   int K1;
   int lane;
@@ -408,6 +411,9 @@ struct KnnSmemEpilogue {
       : D(reinterpret_cast<uint32_t*>(smem_list) + (size_t)epi_warp * 32 * KM * 2),
         R(D + 32 * KM),
         thr(kInf),
+        shared(kNoBound),
+        pending(kNoBound),
+        rthr(act && o.row_thr ? o.row_thr + row : nullptr),
         active(act),
         K1(o.K1),
         lane((int)(threadIdx.x & 31)),
@@ -471,9 +477,10 @@ struct KnnSmemEpilogue {
     __syncwarp();
   }
   __device__ __forceinline__ void group(const uint32_t (&v)[32], uint32_t mn, int64_t col0) {
-    const bool hit = active && (int32_t)mn < thr;
+    // strictly below the list's K1-th entry, at or below the row's shared bound
+    const bool hit = active && (int32_t)mn < min(thr, shared + 1);
     if (!__any_sync(0xffffffffu, hit)) return;
-    uint32_t mask = hit ? hit_mask(v, thr) : 0u;
+    uint32_t mask = hit ? hit_mask(v, min(thr, shared + 1)) : 0u;
     for (;;) {
       const uint32_t who = __ballot_sync(0xffffffffu, mask != 0u);
       if (who == 0u) break;
@@ -481,9 +488,21 @@ struct KnnSmemEpilogue {
       const int j = mask ? __ffs(mask) - 1 : 0;
       const int32_t x = __shfl_sync(0xffffffffu, select32(v, j), L);
       const int jl = __shfl_sync(0xffffffffu, j, L);
-      const int32_t tl = __shfl_sync(0xffffffffu, thr, L);
+      const int32_t tl = __shfl_sync(0xffffffffu, min(thr, shared + 1), L);
       if (lane == L) mask &= mask - 1;
       if (x < tl) insert(L, x, (uint32_t)(col0 + jl));  // warp-uniform
+    }
+  }
+  // As in KnnEpilogue: publish a full list's improved K1-th entry, take in the
+  // read from a tile ago, start the next one.
+  __device__ __forceinline__ void tile_end() {
+    if (rthr) {
+      if (thr != kInf && thr < shared) {
+        atomicMin(rthr, thr);
+        shared = thr;
+      }
+      shared = min(shared, pending);
+      pending = __ldcg(rthr);
     }
   }
   __device__ __forceinline__ void finish() {

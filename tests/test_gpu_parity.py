@@ -126,6 +126,29 @@ def test_shared_row_bound_with_ties(lnbnn):
                 assert np.array_equal(idx.cpu().numpy(), oj) and np.array_equal(dist.cpu().numpy(), od), (hi, m)
 
 
+def test_randomized_shapes_against_oracle(lnbnn):
+    # random sizes (one query tile or a few, up to many reference splits), value
+    # ranges from heavy ties to full range, k across the 16- and 32-entry lists;
+    # every result bit-exact with the oracle, and the same when searched again
+    rng = np.random.default_rng(77)
+    for case in range(16):
+        N = int(rng.integers(300, 40000))
+        M = int(rng.integers(1, 400))
+        hi = int(rng.choice([2, 3, 8, 256]))
+        dims = int(rng.choice([3, 16, 128]))
+        C = int(rng.integers(1, 9))
+        k = int(rng.integers(1, min(31, N - 1) + 1))
+        ref, labels, q, off = random_case(1000 + case, N, M, C, hi=hi, dims=dims)
+        with make_index(lnbnn, ref, labels, C) as ix:
+            check_knn(ix, ref, q, k)
+            a = ix.knn_search(dev(q), k)
+            b = ix.knn_search(dev(q), k)
+            ix.sync()
+            assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), case
+            if k + 1 <= N:
+                check_classify(ix, ref, labels, C, q, off, k)
+
+
 # ------------------------------------------------------------------ adversarial ties
 
 def test_ties_small_values(lnbnn):
