@@ -231,53 +231,10 @@ __device__ __forceinline__ uint32_t hit_mask(const uint32_t (&v)[32], int32_t th
   return mask;
 }
 
-// Rare path: offer the columns of one 32-column group whose distance is below
-// the list's current largest, in column order (the threshold tightens as
-// entries are inserted, so each candidate is checked again).  v holds float
-// bit patterns of exact distances.
-template <int KMAX>
-__device__ __forceinline__ void offer_group(RegList<KMAX>& L, TopK&, int32_t& thr, const uint32_t (&v)[32],
-                                            int64_t col0) {
-  for (uint32_t mask = hit_mask(v, thr); mask; mask &= mask - 1) {
-    const int j = __ffs(mask) - 1;
-    const int32_t bits = select32(v, j);
-    if (bits < thr) {
-      L.insert(__float2int_rn(__int_as_float(bits)), (uint32_t)(col0 + j));
-      thr = thr_bits(L.worst());
-    }
-  }
-}
-
 template <>
 struct RegList<0> {
   __device__ __forceinline__ void init(int) {}
 };
-
-template <>
-__device__ __forceinline__ void offer_group<0>(RegList<0>&, TopK& top, int32_t& thr, const uint32_t (&v)[32],
-                                               int64_t col0) {
-  for (uint32_t mask = hit_mask(v, thr); mask; mask &= mask - 1) {
-    const int j = __ffs(mask) - 1;
-    const int32_t bits = select32(v, j);
-    if (bits < thr) {
-      top.push(make_key((uint32_t)__float2int_rn(__int_as_float(bits)), (uint32_t)(col0 + j)));
-      thr = thr_bits(top.threshold);
-    }
-  }
-}
-
-// One 32-column group: one compare of the group's minimum bit pattern (mn,
-// from the reducing TMEM load).  A column at exactly the threshold distance
-// cannot enter: its row is higher than every kept row's.
-template <int KMAX>
-__device__ __forceinline__ void scan_group(RegList<KMAX>& L, TopK& top, int32_t& thr, bool active,
-                                           const uint32_t (&v)[32], uint32_t mn, int64_t col0) {
-  const bool hit = active && (int32_t)mn < thr;
-  if (__any_sync(0xffffffffu, hit)) {
-    if (hit) offer_group<KMAX>(L, top, thr, v, col0);
-    __syncwarp();
-  }
-}
 
 // KMAX > 0: per-row lists in registers (K1 <= KMAX); KMAX = 0: heaps in global memory.
 // What the epilogue writes (see the two epilogues below).
@@ -323,48 +280,60 @@ struct KnnEpilogue {
         thr(thr_bits(INT32_MAX)),
         shared(kNoBound),
         pending(kNoBound),
-        rthr(KMAX > 0 && act && o.row_thr ? o.row_thr + row : nullptr),
+        rthr(act && o.row_thr ? o.row_thr + row : nullptr),
         active(act),
         K1(o.K1),
         out(o.lists + ((int64_t)list * o.stride + (act ? row : 0)) * o.K1) {
     L.init(K1);
   }
   static constexpr int32_t kNoBound = 0x7F7F7F7F;  // the word's initial value: above every distance
+  // One 32-column group: one compare of the group's minimum bit pattern (mn,
+  // from the reducing TMEM load); on a hit, the columns below the limit are
+  // offered in column order, each checked again as the limit tightens.  A
+  // column at exactly the list's K1-th distance cannot enter: its row is
+  // higher than every kept row's.
   __device__ __forceinline__ void group(const uint32_t (&v)[32], uint32_t mn, int64_t col0) {
-    if constexpr (KMAX > 0) {
-      int32_t lim = min(thr, shared + 1);  // strictly below: own K1-th, at or below: the shared bound
-      const bool hit = active && (int32_t)mn < lim;
-      if (__any_sync(0xffffffffu, hit)) {
-        if (hit) {
-          for (uint32_t mask = hit_mask(v, lim); mask; mask &= mask - 1) {
-            const int j = __ffs(mask) - 1;
-            const int32_t bits = select32(v, j);
-            if (bits < lim) {
-              L.insert(__float2int_rn(__int_as_float(bits)), (uint32_t)(col0 + j));
+    int32_t lim = min(thr, shared + 1);  // strictly below: own K1-th, at or below: the shared bound
+    const bool hit = active && (int32_t)mn < lim;
+    if (__any_sync(0xffffffffu, hit)) {
+      if (hit) {
+        for (uint32_t mask = hit_mask(v, lim); mask; mask &= mask - 1) {
+          const int j = __ffs(mask) - 1;
+          const int32_t bits = select32(v, j);
+          if (bits < lim) {
+            const int32_t d = __float2int_rn(__int_as_float(bits));
+            if constexpr (KMAX > 0) {
+              L.insert(d, (uint32_t)(col0 + j));
               thr = thr_bits(L.worst());
-              lim = min(thr, shared + 1);
+            } else {
+              top.push(make_key((uint32_t)d, (uint32_t)(col0 + j)));
+              thr = thr_bits(top.threshold);
             }
+            lim = min(thr, shared + 1);
           }
         }
-        __syncwarp();
       }
+      __syncwarp();
+    }
+  }
+  __device__ __forceinline__ bool full() const {
+    if constexpr (KMAX > 0) {
+      return L.worst() != INT32_MAX;
     } else {
-      scan_group<KMAX>(L, top, thr, active, v, mn, col0);
+      return top.size == top.cap;
     }
   }
   // After each tile: publish an improved K1-th distance of a full list, take
   // in the bound read a tile ago (its latency hidden behind a whole tile), and
   // start the next read.
   __device__ __forceinline__ void tile_end() {
-    if constexpr (KMAX > 0) {
-      if (rthr) {
-        if (L.worst() != INT32_MAX && thr < shared) {
-          atomicMin(rthr, thr);
-          shared = thr;
-        }
-        shared = min(shared, pending);
-        pending = __ldcg(rthr);
+    if (rthr) {
+      if (full() && thr < shared) {
+        atomicMin(rthr, thr);
+        shared = thr;
       }
+      shared = min(shared, pending);
+      pending = __ldcg(rthr);
     }
   }
   __device__ __forceinline__ void finish() {
