@@ -33,7 +33,7 @@ class Request:
     """One query image: its descriptors and the time it arrived (seconds)."""
 
     rid: int
-    descriptors: np.ndarray  # uint8 [n, 128]
+    descriptors: np.ndarray  # uint8 [n, row bytes of the index: 128, or 130 with a location]
     arrival: float
     totals: np.ndarray | None = None
     cls: int | None = None

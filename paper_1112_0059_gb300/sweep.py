@@ -1,6 +1,6 @@
 """Measurement sweeps on the synthetic workloads (GPU, CUDA events).
 
-    python -m paper_1112_0059_gb300.sweep [--parts kc,fp8,logodds,uneven] [--query-images Q] [--reps R]
+    python -m paper_1112_0059_gb300.sweep [--parts kc,fp8,logodds,single,uneven] [--query-images Q] [--reps R]
 
 kc      Local NBNN (Alg. 2) run time against k, on the first C classes of the
         256-class index (N = C x 45,000 references), with original NBNN
@@ -13,6 +13,9 @@ logodds NBNN as a sum of log-odds increments (Section 3.1) on the 256-class
         time outside the scan, the average number of increments added per
         descriptor (all, or only the positive ones: Table 1's measure) and the
         agreement of the chosen classes with NBNN's (Alg. 1).
+single  one query image of 100 / 632 / 1,000 / 4,000 descriptors at a time (the serving
+        regime: few query tiles, many reference splits) for k = 10, 50, 100, exact and
+        with the FP8 shortlist (m = 32, 64, 128): device time per call.
 uneven  1,024 query images with uniform [200, 3000] descriptors, flattened
         with offsets, one classify call, exact and FP8, before and after the
         split-schedule autotuner.
@@ -133,6 +136,22 @@ def part_logodds(ref, labels, betas, q_imgs, reps, rows):
                              "agreement_with_nbnn": float((c.cpu().numpy() == c_nbnn).mean())})
 
 
+def part_single(ref, labels, sizes, ks, reps, rows):
+    import torch
+    w = synth.workload("caltech256-like")
+    with lnbnn.Index(torch.from_numpy(ref).cuda(), torch.from_numpy(labels).cuda(), w.n_classes) as ix:
+        ix.prepare_fp8()
+        for n in sizes:
+            qd = torch.from_numpy(synth.query_image(w, 7, n)).cuda()
+            for k in ks:
+                m = {10: 32, 50: 64, 100: 128}.get(k, 2 * (k + 1))
+                for form, sl in (("exact", None), ("fp8", m)):
+                    t = _timed(lambda: ix.knn_search(qd, k + 1, shortlist=sl), reps)
+                    ix.sync()
+                    _emit(rows, {"part": "single", "descriptors": n, "k": k, "form": form, "shortlist": sl,
+                                 "splits": ix.plan_splits(n), "ms": t * 1e3})
+
+
 def part_uneven(ref, labels, k, m, reps, sample, rows):
     import torch
     w = synth.workload("batched-uneven")
@@ -176,6 +195,15 @@ def tables(rows) -> str:
             out.append(f"| {r['beta']:g} | {'positive' if r['positive_only'] else 'all'} | {r['desc_per_s']:,.0f} "
                        f"| {r['other_share']:.3f} | {r['increments_per_desc']:.1f} of {r['classes']} "
                        f"| {r['agreement_with_nbnn']:.3f} |")
+    si = [r for r in rows if r["part"] == "single"]
+    if si:
+        out.append("\n| descriptors | splits | k | exact ms | FP8 ms (m) |\n|---|---|---|---|---|")
+        for r in si:
+            if r["form"] == "exact":
+                f = next((x for x in si if x["form"] == "fp8" and x["descriptors"] == r["descriptors"]
+                          and x["k"] == r["k"]), None)
+                out.append(f"| {r['descriptors']:,} | {r['splits']} | {r['k']} | {r['ms']:.2f} "
+                           f"| {f['ms']:.2f} ({f['shortlist']}) |" if f else "")
     un = [r for r in rows if r["part"] == "uneven"]
     if un:
         out.append("\n| form | autotuned | splits | desc/s | images/s |\n|---|---|---|---|---|")
@@ -187,7 +215,7 @@ def tables(rows) -> str:
 
 def main():
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    p.add_argument("--parts", default="kc,fp8,logodds,uneven")
+    p.add_argument("--parts", default="kc,fp8,logodds,single,uneven")
     p.add_argument("--classes", default="32,64,128,256")
     p.add_argument("--ks", default="1,2,5,10,20,50,100")
     p.add_argument("--shortlists", default="16,32,64,128")
@@ -209,6 +237,8 @@ def main():
                  a.recall_sample, rows)
     if "logodds" in parts:
         part_logodds(ref, labels, [float(b) for b in a.betas.split(",")], a.query_images, a.reps, rows)
+    if "single" in parts:
+        part_single(ref, labels, [100, 632, 1000, 4000], [10, 50, 100], a.reps, rows)
     if "uneven" in parts:
         part_uneven(ref, labels, a.k, 32, a.reps, a.recall_sample, rows)
     print(tables(rows), flush=True)

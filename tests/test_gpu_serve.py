@@ -79,3 +79,26 @@ def test_rejects_request_larger_than_a_slot(setup):
     with serve.Server(ix, k=10, slots=1, max_batch_queries=4096) as srv:
         with pytest.raises(ValueError):
             srv.run([big])
+
+
+def test_serves_location_weighted_rows(lnbnn):
+    """A location-weighted index (130-byte rows) behind the server: batched,
+    graph-captured service gives every image the oracle's answer."""
+    from paper_1112_0059_gb300 import serve, synth
+    w = dataclasses.replace(synth.workload("serving"), n_classes=5, ref_imgs_per_class=3, ref_desc_per_img=400)
+    ref, labels = synth.reference_set(w)
+    ref = synth.located(ref, synth.reference_locations(w))
+    plain = serve.poisson_requests(w, 1e6, 12, seed=3)
+    rng = np.random.default_rng(4)
+    reqs = [dataclasses.replace(r, descriptors=synth.located(
+        r.descriptors, rng.integers(0, 256, size=(len(r.descriptors), 2)).astype(np.uint8))) for r in plain]
+    q = np.concatenate([r.descriptors for r in reqs])
+    off = np.concatenate([[0], np.cumsum([len(r.descriptors) for r in reqs])]).astype(np.int64)
+    with lnbnn.Index(torch.from_numpy(ref).cuda(), torch.from_numpy(labels).cuda(), w.n_classes,
+                     location_weight=6) as ix:
+        with serve.Server(ix, k=10, slots=2, max_batch_queries=6144, max_batch_images=6, graphs=True) as srv:
+            done = srv.run(reqs)
+    ot, oc = oracle.local_nbnn(ref, labels, w.n_classes, q, off, 10, location_weight=6)
+    by_id = {r.rid: r for r in done}
+    for i, r in enumerate(reqs):
+        assert np.array_equal(by_id[r.rid].totals, ot[i]) and by_id[r.rid].cls == oc[i], i
