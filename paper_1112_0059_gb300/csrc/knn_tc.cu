@@ -118,14 +118,19 @@ struct FmtBf16 {  // exact search: 128 BF16 coordinates, two chunks
     mma_bf16(d, a, b, kIdesc, acc);
   }
 };
-struct FmtE4m3 {  // coarse pass: 128 E4M3 coordinates, one chunk
+struct FmtE4m3Base {  // coarse pass: 128 E4M3 coordinates, one chunk
   static constexpr int kChunks = 1;
-  static constexpr int kCluster = kTcCoarseCluster;
   static constexpr bool kExtFirst = true;
   static constexpr uint32_t kIdesc = idesc_e4m3_f32(kBM, kBN);
   static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
     mma_f8(d, a, b, kIdesc, acc);
   }
+};
+struct FmtE4m3 : FmtE4m3Base {  // pairs of CTAs sharing each reference tile
+  static constexpr int kCluster = kTcCoarseCluster;
+};
+struct FmtE4m3Solo : FmtE4m3Base {  // single CTAs (small batches: query rows padded to one tile only)
+  static constexpr int kCluster = 1;
 };
 
 template <int kStages>
@@ -821,9 +826,11 @@ bool make_tc_tensor_maps(const __nv_bfloat16* ref_bf, const __nv_bfloat16* sref_
 
 bool make_tc_tensor_maps_e4m3(const uint8_t* ref_f8, const __nv_bfloat16* ref_f8_ext, int64_t n_pad,
                               TcTensorMaps* out) {
-  constexpr uint32_t rows = kBN / FmtE4m3::kCluster;
+  constexpr uint32_t rows = kBN / FmtE4m3::kCluster;  // the rows of a tile one CTA of a pair loads
   return encode_e4m3(&out->f8, ref_f8, (uint64_t)n_pad, rows) &&
-         encode_bf16(&out->f8_ext, ref_f8_ext, (uint64_t)n_pad, kExt, kExt, rows, CU_TENSOR_MAP_SWIZZLE_32B);
+         encode_bf16(&out->f8_ext, ref_f8_ext, (uint64_t)n_pad, kExt, kExt, rows, CU_TENSOR_MAP_SWIZZLE_32B) &&
+         encode_e4m3(&out->f8_solo, ref_f8, (uint64_t)n_pad, kBN) &&
+         encode_bf16(&out->f8_solo_ext, ref_f8_ext, (uint64_t)n_pad, kExt, kExt, kBN, CU_TENSOR_MAP_SWIZZLE_32B);
 }
 
 namespace {
@@ -871,6 +878,10 @@ cudaError_t prepare_tc_kernels() {
   if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<kTcCoarseRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnSmemEpilogue<kTcWideRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<0>>();
+  if (e == cudaSuccess) e = prepare_one<FmtE4m3Solo, KnnEpilogue<kTcRegListMax>>();
+  if (e == cudaSuccess) e = prepare_one<FmtE4m3Solo, KnnEpilogue<kTcCoarseRegListMax>>();
+  if (e == cudaSuccess) e = prepare_one<FmtE4m3Solo, KnnSmemEpilogue<kTcWideRegListMax>>();
+  if (e == cudaSuccess) e = prepare_one<FmtE4m3Solo, KnnEpilogue<0>>();
   return e;
 }
 
@@ -907,27 +918,43 @@ cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv
                                               stats, s);
 }
 
-cudaError_t launch_coarse_tc(const TcTensorMaps& maps, const uint8_t* qf8, const __nv_bfloat16* qext, int64_t m,
-                             int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int K1, uint64_t* lists,
-                             int64_t stride, int32_t* row_thr, uint32_t* dev_err, unsigned long long* stats,
-                             const uint32_t* gate, cudaStream_t s) {
+namespace {
+
+template <class Fmt>
+cudaError_t launch_coarse_fmt(const CUtensorMap& tr, const CUtensorMap& tre, const uint8_t* qf8,
+                              const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
+                              int64_t split_len, int K1, const ScanOut& out, uint32_t* dev_err,
+                              unsigned long long* stats, cudaStream_t s) {
+  if (K1 <= kTcRegListMax)
+    return launch_scan<Fmt, KnnEpilogue<kTcRegListMax>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits, split_len, out,
+                                                        dev_err, stats, s);
+  if (K1 <= kTcCoarseRegListMax)
+    return launch_scan<Fmt, KnnEpilogue<kTcCoarseRegListMax>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits, split_len,
+                                                              out, dev_err, stats, s);
+  if (K1 <= kTcWideRegListMax)
+    return launch_scan<Fmt, KnnSmemEpilogue<kTcWideRegListMax>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits,
+                                                                split_len, out, dev_err, stats, s);
+  return launch_scan<Fmt, KnnEpilogue<0>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits, split_len, out, dev_err, stats,
+                                          s);
+}
+
+}  // namespace
+
+cudaError_t launch_coarse_tc(const TcTensorMaps& maps, bool solo, const uint8_t* qf8, const __nv_bfloat16* qext,
+                             int64_t m, int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int K1,
+                             uint64_t* lists, int64_t stride, int32_t* row_thr, uint32_t* dev_err,
+                             unsigned long long* stats, const uint32_t* gate, cudaStream_t s) {
   ScanOut out{};
   out.gate = gate;
   out.row_thr = row_thr;
   out.lists = lists;
   out.stride = stride;
   out.K1 = K1;
-  if (K1 <= kTcRegListMax)
-    return launch_scan<FmtE4m3, KnnEpilogue<kTcRegListMax>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref, splits,
-                                                            split_len, out, dev_err, stats, s);
-  if (K1 <= kTcCoarseRegListMax)
-    return launch_scan<FmtE4m3, KnnEpilogue<kTcCoarseRegListMax>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref,
-                                                                  splits, split_len, out, dev_err, stats, s);
-  if (K1 <= kTcWideRegListMax)
-    return launch_scan<FmtE4m3, KnnSmemEpilogue<kTcWideRegListMax>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad,
-                                                                    n_ref, splits, split_len, out, dev_err, stats, s);
-  return launch_scan<FmtE4m3, KnnEpilogue<0>>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref, splits, split_len,
-                                              out, dev_err, stats, s);
+  if (solo)
+    return launch_coarse_fmt<FmtE4m3Solo>(maps.f8_solo, maps.f8_solo_ext, qf8, qext, m, m_pad, n_ref, splits,
+                                          split_len, K1, out, dev_err, stats, s);
+  return launch_coarse_fmt<FmtE4m3>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref, splits, split_len, K1, out,
+                                    dev_err, stats, s);
 }
 
 cudaError_t launch_nbnn_tc(const TcTensorMaps& maps, const __nv_bfloat16* qbf, const __nv_bfloat16* qext, int64_t m,

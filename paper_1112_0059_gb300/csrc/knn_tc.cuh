@@ -20,9 +20,14 @@ constexpr int kTcQueryTile = 128;
 constexpr int kTcCluster = 1;
 constexpr int kTcCoarseCluster = 2;
 static_assert(kQueryPad % (kTcQueryTile * kTcCluster) == 0, "query padding must cover whole clusters");
-// Query rows of the FP8 coarse pass are padded to whole clusters.
+// Query rows of the FP8 coarse pass are padded to whole clusters, except for
+// batches of at most kCoarseSoloMaxRows rows, which run single CTAs (one
+// query tile each: a lone image of 100 descriptors would otherwise do a
+// pair's 256 rows of work) and are padded to kQueryPad.
 constexpr int kCoarseQueryPad = kTcQueryTile * kTcCoarseCluster > kQueryPad ? kTcQueryTile * kTcCoarseCluster
                                                                              : kQueryPad;
+constexpr int64_t kCoarseSoloMaxRows = 1024;
+inline bool coarse_solo(int64_t m) { return m <= kCoarseSoloMaxRows; }
 // Lists of the k+1 (or shortlist) nearest per query row: up to 16 entries a
 // 16-entry register list (the fewest registers), up to 32 a 32-entry one, up
 // to 64 a 64-entry list in shared memory with warp-cooperative inserts (in
@@ -44,7 +49,8 @@ inline int tc_lists_per_split(int K1) { return K1 > kTcCoarseRegListMax && K1 <=
 struct TcTensorMaps {
   CUtensorMap ref, ref_ext;    // BF16 [n_pad,128] (128-byte swizzle) and norm digits [n_pad,16] (32-byte swizzle)
   CUtensorMap sref, sref_ext;  // the same over the class-sorted copy
-  CUtensorMap f8, f8_ext;      // E4M3 coarse operand [n_pad,128] and its extension [n_pad,16]
+  CUtensorMap f8, f8_ext;      // E4M3 coarse operand [n_pad,128] and its extension [n_pad,16] (pairs' boxes)
+  CUtensorMap f8_solo, f8_solo_ext;  // the same with whole-tile boxes, for single CTAs
 };
 
 // Split-N schedule of one scan launch over T query tiles: s reference splits
@@ -115,10 +121,12 @@ cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv
 // operands (qf8 [m_pad, 128] bytes of -2 E4M3(q - 64), qext its extension),
 // keeping the K1 smallest (coarse + 2^21, row) keys per list in the same
 // layout as launch_knn_tc.
-cudaError_t launch_coarse_tc(const TcTensorMaps& maps, const uint8_t* qf8, const __nv_bfloat16* qext, int64_t m,
-                             int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int K1, uint64_t* lists,
-                             int64_t stride, int32_t* row_thr, uint32_t* dev_err, unsigned long long* stats,
-                             const uint32_t* gate, cudaStream_t s);
+// solo: single CTAs (m_pad a multiple of the query tile); otherwise pairs
+// (m_pad a multiple of two tiles).
+cudaError_t launch_coarse_tc(const TcTensorMaps& maps, bool solo, const uint8_t* qf8, const __nv_bfloat16* qext,
+                             int64_t m, int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int K1,
+                             uint64_t* lists, int64_t stride, int32_t* row_thr, uint32_t* dev_err,
+                             unsigned long long* stats, const uint32_t* gate, cudaStream_t s);
 // Original NBNN on the same tensor-core scan over the class-sorted copy:
 // mins [m_pad, C] (int32, filled with INT32_MAX-like values beforehand) gets
 // atomicMin(mins[i][c], ||q_i - r||^2) over every reference r of class c that

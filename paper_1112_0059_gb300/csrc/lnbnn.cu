@@ -333,7 +333,8 @@ lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_
 // merge, exact rerank; *lists receives m sorted lists of K1 exact keys.
 lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_t m, int K1, int M1,
                          cudaStream_t s, const uint64_t** lists, CallProfile& prof) {
-  KnnPlan p = plan_knn(ix, m, M1, 0, kCoarseQueryPad);
+  const bool solo = coarse_solo(m);
+  KnnPlan p = plan_knn(ix, m, M1, 0, solo ? kQueryPad : kCoarseQueryPad);
   char* ws = nullptr;
   lnbnn_status st = scratch.get(p.bytes, &ws);
   if (st != LNBNN_OK) return st;
@@ -348,7 +349,7 @@ lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, in
   CK(cudaMemsetAsync(row_thr, 0x7F, sizeof(int32_t) * (size_t)p.m_pad, s));
   prof.launched(1);
   prof.mark(1);
-  CK(launch_coarse_tc(ix->tc, qf8, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, M1, part, p.m_pad,
+  CK(launch_coarse_tc(ix->tc, solo, qf8, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, M1, part, p.m_pad,
                       p.splits > 1 ? row_thr : nullptr, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, ix->gate, s));
   prof.launched(1, true);
   prof.mark(2);
