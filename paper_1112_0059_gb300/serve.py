@@ -253,8 +253,8 @@ class Server:
                 if not slot.batch and self.pending:
                     self._launch(slot, clock() - t0)
                     progressed = True
-            if not progressed:
-                time.sleep(50e-6)
+            if not progressed and not any(slot.batch for slot in self.slots):
+                time.sleep(50e-6)  # nothing on the GPU: wait for arrivals; with a batch in flight, poll
         self.index.sync()
         return finished
 
