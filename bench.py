@@ -482,7 +482,7 @@ def run_serving(index, rates, seconds, k, shortlist, classes_out: dict | None = 
     return {"form": form, "k": k, "workload": "256-class index; Poisson arrivals; log-uniform [100, 4000] "
             "descriptors per image; latency = arrival to totals and class on the host", **cfg,
             "graph_buckets": f"{len(serve.graph_buckets(cfg['max_batch_queries']))} query-count buckets, "
-                             "multiples of 128 about 25% apart", "runs": runs}
+                             "every multiple of 128 up to 4,096, then about 25% apart", "runs": runs}
 
 
 def main():

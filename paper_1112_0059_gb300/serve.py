@@ -11,8 +11,8 @@ stream.  Batches on different slots overlap on the GPU, and requests that
 arrive while batches are in flight are admitted as soon as a slot frees up.
 
 With ``graphs=True`` each slot captures, per query-count bucket (multiples
-of 128 descriptors, about 25% apart), one CUDA graph holding the copies and
-the classify call; a batch is padded up to its bucket with zero descriptors
+of 128 descriptors: every one up to 4,096, then about 25% apart), one CUDA
+graph holding the copies and the classify call; a batch is padded up to its bucket with zero descriptors
 that form one extra image, whose scores are dropped.  The padding changes no real image's result: Alg. 2 scores every
 descriptor on its own, and a descriptor counts only toward its own image.
 
@@ -57,14 +57,16 @@ def take_batch(pending: collections.deque, max_queries: int, max_images: int) ->
     return batch
 
 
-def graph_buckets(max_queries: int, granule: int = 128, ratio: float = 1.25) -> list[int]:
-    """Query counts the server captures graphs for: multiples of ``granule``
-    growing by about ``ratio`` (padding a batch to its bucket wastes at most
-    that fraction of the search), ending at ``max_queries``."""
+def graph_buckets(max_queries: int, granule: int = 128, ratio: float = 1.25, fine_upto: int = 4096) -> list[int]:
+    """Query counts the server captures graphs for: every multiple of
+    ``granule`` up to ``fine_upto`` (a lone image pads to its next query tile
+    only), then multiples of ``granule`` growing by about ``ratio`` (padding a
+    batch to its bucket wastes at most that fraction of the search), ending at
+    ``max_queries``."""
     out, b = [], granule
     while b < max_queries:
         out.append(b)
-        b = max(b + granule, -(-int(b * ratio) // granule) * granule)
+        b = b + granule if b < fine_upto else max(b + granule, -(-int(b * ratio) // granule) * granule)
     out.append(max_queries)
     return out
 

@@ -38,7 +38,8 @@ def test_graph_buckets():
     b = serve.graph_buckets(16384)
     assert b[0] == 128 and b[-1] == 16384 and b == sorted(set(b))
     assert all(x % 128 == 0 for x in b)
-    # consecutive buckets at most ~25% (or one query tile) apart
+    # every query tile up to 4,096, then consecutive buckets at most ~25% (or one tile) apart
+    assert [x for x in b if x <= 4096] == list(range(128, 4097, 128))
     assert all(y <= max(x + 128, 1.25 * x + 128) for x, y in zip(b, b[1:]))
     assert serve.bucket_of(1, b) == 128 and serve.bucket_of(128, b) == 128 and serve.bucket_of(129, b) == 256
     assert serve.bucket_of(16384, b) == 16384
