@@ -49,3 +49,28 @@ def test_max_over_ranks_single_process():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks(3.25) == 3.25
+
+
+def _run_bench(env_extra, *args):
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **env_extra)
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), *args], env=env, cwd=root,
+                         capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    return [json.loads(l) for l in out.stdout.splitlines() if l.startswith("{")]
+
+
+def test_reference_arm_rank_zero_only():
+    """The reference arm (the CPU oracle, timed) prints one line on rank 0 and
+    nothing on the other ranks, which exit 0 without work."""
+    args = ("--impl", "reference", "--workload", "tiny", "--steps", "1", "--warmup", "3")
+    assert _run_bench({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"}, *args) == []
+    lines = _run_bench({"RANK": "0", "LOCAL_RANK": "0", "WORLD_SIZE": "1"}, *args)
+    assert len(lines) == 1
+    line = lines[0]
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 3
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
