@@ -89,6 +89,25 @@ def test_k_range(lnbnn, k):
             check_classify(ix, ref, labels, 7, q, off, k)
 
 
+@pytest.mark.parametrize("K1", [15, 16, 17, 32, 33, 64, 65])
+def test_list_kind_boundaries_many_splits(lnbnn, K1):
+    # k+1 at the edges of the list kinds (16- / 32-entry register lists,
+    # 64-entry shared-memory lists, heaps), a small batch over many reference
+    # splits (so the lists of a row share a bound) and coordinates with ties;
+    # exact search and FP8 shortlists of exactly K1 and of 2 K1
+    ref, labels, q, off = random_case(6 + K1, 50000, 150, 5, hi=4, dims=6)
+    with make_index(lnbnn, ref, labels, 5) as ix:
+        assert ix.plan_splits(len(q)) > 8
+        check_knn(ix, ref, q, K1)
+        check_classify(ix, ref, labels, 5, q, off, K1 - 1)
+        ix.prepare_fp8()
+        for m in (K1, 2 * K1):
+            idx, dist = ix.knn_search(dev(q), K1, shortlist=m)
+            ix.sync()
+            od, oj = oracle.knn_coarse(ref, q, K1, m)
+            assert np.array_equal(idx.cpu().numpy(), oj) and np.array_equal(dist.cpu().numpy(), od), m
+
+
 @pytest.mark.parametrize("N,M", [(1, 1), (2, 3), (255, 129), (256, 128), (257, 127), (1000, 1), (4099, 1030)])
 def test_ragged_shapes(lnbnn, N, M):
     ref, labels, q, off = random_case(2, N, M, 1 if N < 3 else 3, n_img=2)
