@@ -24,8 +24,10 @@ def fnv1a64(data: bytes) -> int:
     return h
 
 
-def index_file(ref: np.ndarray, labels: np.ndarray, n_classes: int, magic=b"LNBNNIX1", version=1, dim=128) -> bytes:
-    body = magic + struct.pack("<IIqiI", version, dim, len(ref), n_classes, 0)
+def index_file(ref: np.ndarray, labels: np.ndarray, n_classes: int, magic=b"LNBNNIX1", version=1, dim=None,
+               weight=0) -> bytes:
+    dim = ref.shape[1] if dim is None else dim
+    body = magic + struct.pack("<IIqiI", version, dim, len(ref), n_classes, weight)
     body += np.ascontiguousarray(ref, np.uint8).tobytes() + np.ascontiguousarray(labels, "<i4").tobytes()
     return body + struct.pack("<Q", fnv1a64(body))
 
@@ -53,6 +55,11 @@ def test_rejected_files(lib, tmp_path):
         "truncated": good[:-9],
         "trailing": good + b"\0",
         "hash": good[:100] + bytes([good[100] ^ 1]) + good[101:],  # one flipped descriptor bit
+        # the row layout: 128 bytes without a location weight, 130 with one of at most 48
+        "weight on 128-byte rows": index_file(ref, labels, 3, weight=5),
+        "129-byte rows": index_file(np.zeros((40, 129), np.uint8), labels, 3),
+        "location weight 49": index_file(np.zeros((40, 130), np.uint8), labels, 3, weight=49),
+        "130 bytes declared, 128 stored": index_file(ref, labels, 3, dim=130, weight=2),
     }
     for name, data in cases.items():
         (tmp_path / name).write_bytes(data)
