@@ -110,33 +110,61 @@ __device__ __forceinline__ int64_t image_of(const int64_t* __restrict__ offsets,
 // (distance, row): dist_B = distance of the (k+1)-th; every class found among
 // the first k is updated once with dist_C - dist_B, where dist_C is the
 // distance of its first (hence nearest) occurrence in the sorted list.
-__global__ void lnbnn_score_kernel(const uint64_t* __restrict__ lists, int64_t m, int K1, int k,
-                                   const int32_t* __restrict__ labels, int64_t n_ref,
-                                   const int64_t* __restrict__ offsets, int64_t n_img, int32_t C,
-                                   int64_t* __restrict__ totals, uint32_t* __restrict__ dev_err) {
+// Thread per row; the adds are aggregated per warp: at each neighbour rank
+// the lanes that update the same (image, class) are grouped, and one of them
+// adds the group's sum (int64 addition, exact in any order).
+constexpr int kScoreThreads = 128;
+__global__ void __launch_bounds__(kScoreThreads)
+    lnbnn_score_kernel(const uint64_t* __restrict__ lists, int64_t m, int K1, int k,
+                       const int32_t* __restrict__ labels, int64_t n_ref, const int64_t* __restrict__ offsets,
+                       int64_t n_img, int32_t C, int64_t* __restrict__ totals, uint32_t* __restrict__ dev_err) {
+  __shared__ int64_t part[kScoreThreads];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  const int64_t img = image_of(offsets, n_img, i);
-  if (i < offsets[img] || i >= offsets[img + 1]) {  // only with invalid offsets
-    atomicOr(dev_err, kDevErrOffsets);
-    return;
+  const int lane = threadIdx.x & 31;
+  int64_t* wpart = part + (threadIdx.x & ~31);
+  bool ok = i < m;
+  int64_t img = 0;
+  if (ok) {
+    img = image_of(offsets, n_img, i);
+    if (i < offsets[img] || i >= offsets[img + 1]) {  // only with invalid offsets
+      atomicOr(dev_err, kDevErrOffsets);
+      ok = false;
+    }
   }
-  const uint64_t* L = lists + i * K1;
+  const uint64_t* L = lists + (ok ? i : 0) * K1;
   // A complete list holds k+1 real rows.  Only a search that gave up (a
   // timeout, reported by lnbnn_sync) leaves empty keys: skip such a row
   // rather than gather labels[] at an empty key's row.
-  for (int a = 0; a <= k; ++a)
-    if ((int64_t)key_row(L[a]) >= n_ref) return;
-  const int64_t dist_B = (int64_t)key_dist(L[k]);
-  unsigned long long* t = reinterpret_cast<unsigned long long*>(totals + img * C);
-  for (int a = 0; a < k; ++a) {
-    const uint64_t ka = L[a];
-    const int32_t c = labels[key_row(ka)];
-    bool seen = false;
-    for (int b = 0; b < a && !seen; ++b) seen = labels[key_row(L[b])] == c;
-    if (seen) continue;
-    const int64_t delta = (int64_t)key_dist(ka) - dist_B;  // <= 0
-    if (delta != 0) atomicAdd(t + c, (unsigned long long)delta);
+  if (ok)
+    for (int a = 0; a <= k; ++a)
+      if ((int64_t)key_row(L[a]) >= n_ref) ok = false;
+  const int64_t dist_B = ok ? (int64_t)key_dist(L[k]) : 0;
+  unsigned long long* t = reinterpret_cast<unsigned long long*>(totals);
+  for (int a = 0; a < k; ++a) {  // every lane of the warp takes every step
+    long long slot = -1;          // img * C + class of this lane's update, or none
+    int64_t delta = 0;
+    if (ok) {
+      const uint64_t ka = L[a];
+      const int32_t c = labels[key_row(ka)];
+      bool seen = false;
+      for (int b = 0; b < a && !seen; ++b) seen = labels[key_row(L[b])] == c;
+      if (!seen) {
+        delta = (int64_t)key_dist(ka) - dist_B;  // <= 0
+        if (delta != 0) slot = img * C + c;
+      }
+    }
+    const unsigned act = __ballot_sync(0xffffffffu, slot >= 0);
+    if (slot >= 0) {
+      const unsigned grp = __match_any_sync(act, (unsigned long long)slot);
+      wpart[lane] = delta;
+      __syncwarp(act);
+      if (lane == __ffs(grp) - 1) {
+        int64_t sum = 0;
+        for (unsigned g = grp; g; g &= g - 1) sum += wpart[__ffs(g) - 1];
+        atomicAdd(t + slot, (unsigned long long)sum);
+      }
+      __syncwarp(act);  // the leaders have read the slots before the next step writes them
+    }
   }
 }
 
@@ -220,8 +248,8 @@ cudaError_t launch_lnbnn_score(const uint64_t* lists, int64_t m, int K1, int k, 
                                const int64_t* offsets, int64_t n_img, int32_t C, int64_t* totals, uint32_t* dev_err,
                                cudaStream_t s) {
   if (m == 0 || n_img == 0) return cudaSuccess;
-  lnbnn_score_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(lists, m, K1, k, labels, n_ref, offsets, n_img, C,
-                                                                  totals, dev_err);
+  lnbnn_score_kernel<<<(unsigned)((m + kScoreThreads - 1) / kScoreThreads), kScoreThreads, 0, s>>>(
+      lists, m, K1, k, labels, n_ref, offsets, n_img, C, totals, dev_err);
   return cudaGetLastError();
 }
 
