@@ -463,7 +463,7 @@ def run_serving(index, rates, seconds, k, shortlist, classes_out: dict | None = 
     served image."""
     from paper_1112_0059_gb300 import serve
     w = synth.workload("serving")
-    cfg = {"slots": 3, "max_batch_queries": 16384, "max_batch_images": 256, "graphs": True}
+    cfg = {"slots": 2, "max_batch_queries": 16384, "max_batch_images": 256, "graphs": True}
     runs, first = [], 0
     with serve.Server(index, k=k, method="local", shortlist=shortlist, **cfg) as srv:
         srv.run(serve.poisson_requests(w, 1000.0, 8, seed=99, first_image=100000))  # warm-up

@@ -109,7 +109,7 @@ class Server:
     bucket, see ``graph_buckets``) instead of launching each call.
     """
 
-    def __init__(self, index, k: int = 10, method: str = "local", slots: int = 3, max_batch_queries: int = 16384,
+    def __init__(self, index, k: int = 10, method: str = "local", slots: int = 2, max_batch_queries: int = 16384,
                  max_batch_images: int = 256, graphs: bool = False, shortlist: int | None = None):
         import torch
 
