@@ -7,6 +7,17 @@ fallback: without the built library every call raises.
 
 Method: McCann & Lowe, "Local Naive Bayes Nearest Neighbor for Image
 Classification" -- Alg. 1 (NBNN) and Alg. 2 (LocalNBNN).
+
+``Index``        the merged reference index (128-byte rows, or 130-byte rows
+                 with a location weight); ``knn_search``, ``lnbnn_classify``
+                 (exact, or ``shortlist=m`` for the FP8 shortlist form),
+                 ``nbnn_classify``, ``nbnn_logodds_classify`` (Section 3.1),
+                 ``classify_host`` (host buffers), ``save`` / ``load``,
+                 ``autotune`` / ``plan_splits``, ``prepare_fp8``,
+                 ``profile_enable`` / ``profile_read``, ``sync``
+``Workspace``    device scratch of one in-flight call (allocation-free calls,
+                 several streams, CUDA graph capture)
+``knn_search_noalloc``, ``debug_fail_allocations``, ``LnbnnError``
 """
 from __future__ import annotations
 
