@@ -302,6 +302,38 @@ LNBNN_API lnbnn_status lnbnn_autotune(lnbnn_index *index, void *stream, lnbnn_tu
 LNBNN_API lnbnn_status lnbnn_plan_splits(const lnbnn_index *index, int64_t n_queries, int32_t *splits);
 
 /*
+ * lnbnn_plan_search reports how a search of the k1 nearest references of each
+ * of n_queries query descriptors would be launched on this index (the search
+ * step of Alg. 2, NN(d, k+1)): the exact scan (fp8 == 0; knn_search with
+ * k = k1, or a Local NBNN classify call with k + 1 = k1) or the coarse pass
+ * of the FP8 shortlist search (fp8 != 0; k1 = the shortlist length).  Nothing
+ * is launched.  Fields: the reference splits of the launch and references per
+ * split; the sorted lists per query row the scan writes (merged afterwards
+ * when more than one); where each list lives (list_storage 0: registers, 1:
+ * shared memory, 2: a heap in global memory) and how many entries it holds
+ * (16, 32 or 64; k1 for a heap); the tile of query rows x references one CTA
+ * computes per step; persistent = 1 when a fixed grid of CTAs takes
+ * (query tile, split) work items from a queue instead of one CTA per item.
+ * Errors: INVALID_ARG (null pointers, n_queries < 1), K_RANGE (k1 outside
+ * [1, LNBNN_MAX_K + 1] or above n_ref), NO_FP8 (fp8 != 0 on an index without
+ * the FP8 operand).
+ */
+typedef struct lnbnn_search_plan {
+  int32_t splits;
+  int32_t lists_per_row;
+  int64_t split_len;
+  int32_t list_storage;
+  int32_t list_capacity;
+  int32_t tile_m;
+  int32_t tile_n;
+  int32_t persistent;
+  int32_t reserved;
+} lnbnn_search_plan;
+
+LNBNN_API lnbnn_status lnbnn_plan_search(const lnbnn_index *index, int64_t n_queries, int32_t k1, int32_t fp8,
+                                         lnbnn_search_plan *out);
+
+/*
  * Host-buffer forms of the classifiers: queries, offsets, totals and
  * classes are HOST pointers.  The call copies the inputs to the device
  * (into the index's device staging buffer), classifies, copies the
@@ -361,21 +393,27 @@ LNBNN_API lnbnn_status lnbnn_profile_read(lnbnn_index *index, lnbnn_profile *out
  *
  * No index is needed: ref and queries are the caller's device uint8 arrays
  * ([n_ref * 128] and [n_queries * 128]), idx and dist its device int32 outputs
- * ([n_queries * k], as knn_search).  Every intermediate (BF16 operand copies,
- * squared norms, per-row neighbour lists, the error word) lives in one
- * fixed-size array in device global memory that the library defines at file
- * scope: LNBNN_NOALLOC_SCRATCH_BYTES (64 MiB) on every GPU that loads the
- * library, held until the process exits.  The call makes no cudaMalloc,
- * cudaFree or other allocating call.  A problem whose intermediates do not
- * fit (roughly n_ref + n_queries above about 200,000 rows at k = 10) is
- * rejected with LNBNN_ERR_SCRATCH_LIMIT before any work is issued.
+ * ([n_queries * k], as knn_search); all four must be memory of the current
+ * device (INVALID_ARG otherwise).  Every intermediate (BF16 operand copies,
+ * squared norms, per-row neighbour lists and their shared bounds, the error
+ * word) lives in one fixed-size array in device global memory that the
+ * library defines at file scope: LNBNN_NOALLOC_SCRATCH_BYTES (64 MiB),
+ * reserved on a device once the library's device code is loaded there (at
+ * the latest by the first call there) and held until the process exits.  The
+ * call makes no cudaMalloc, cudaFree or other allocating call.  n_ref or
+ * n_queries above 262,144 (the rows whose BF16 copy alone fills the array),
+ * or a problem whose intermediates do not fit (roughly n_ref + n_queries
+ * above about 200,000 rows at k = 10), is rejected with
+ * LNBNN_ERR_SCRATCH_LIMIT before any work is issued.
  *
  * The first call on each device looks up that device's address of the array
  * (once, with the device current); make that first call before any stream
- * capture begins.  All calls share the one array and find the previous call's
- * contents in it; two calls whose work overlaps on the GPU (different
- * streams, or threads without ordering) race and corrupt each other.  The
- * call waits for `stream` before returning, to report device-side errors.
+ * capture begins.  That set-up belongs to the device's primary context: after
+ * cudaDeviceReset the entry point must not be used again in the process.  All
+ * calls share the one array and find the previous call's contents in it; two
+ * calls whose work overlaps on the GPU (different streams, or threads without
+ * ordering) race and corrupt each other.  The call waits for `stream` before
+ * returning, to report device-side errors.
  * Errors: INVALID_ARG, K_RANGE, SCRATCH_LIMIT, UNSUPPORTED, CUDA, TIMEOUT.
  */
 #define LNBNN_NOALLOC_SCRATCH_BYTES (64ull << 20)

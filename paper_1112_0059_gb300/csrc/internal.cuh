@@ -21,7 +21,7 @@ constexpr float kPadNorm = 33554432.0f;  // 2^25
 // Reference rows are padded to a multiple of this (the widest reference tile).
 constexpr int kRefPad = 256;
 // Query rows are padded to a multiple of this (the 128-row query tile of the
-// tensor-core search, times its cluster size).
+// tensor-core search).
 constexpr int kQueryPad = 128;
 
 // Width of the K-extension that carries ||r||^2 into the tensor-core

@@ -14,14 +14,6 @@
 // row's current (k+1)-th distance, and keeps the k+1 smallest (distance, row)
 // pairs.  The distance matrix never leaves the SM.
 //
-// With a cluster size above 1 (per operand format: kTcCluster for the exact
-// scan, kTcCoarseCluster for the FP8 coarse pass), the CTAs of a cluster
-// (consecutive query tiles, same reference split) share every reference tile:
-// each loads its share of each K-chunk and multicasts it into all of them, and
-// a stage is refilled only after every CTA's MMAs have consumed it.  That
-// divides the reference traffic per SM by the cluster size but couples the
-// CTAs, each stage waiting for the slowest.
-//
 // The same scan runs the coarse pass of the FP8 shortlist search: operands
 // are the E4M3 roundings of the coordinates shifted by -64 (queries scaled by
 // -2, exact in E4M3), one 128-byte K-chunk per tile and four kind::f8f6f4
@@ -71,9 +63,6 @@ constexpr uint32_t kAExtBytes = kBM * kExt * 2;      // 4 KB
 constexpr uint32_t kBChunkBytes = kBN * kBK * 2;     // 32 KB
 constexpr uint32_t kBExtBytes = kBN * kExt * 2;      // 8 KB
 constexpr uint32_t kStageBytes = kBChunkBytes + kBExtBytes;
-// Longest reference split for which the exact scan keeps 33..64-entry lists
-// in shared memory rather than registers.
-constexpr int64_t kSmemListMaxRefs = int64_t(8) << 20;
 
 // Threads of a CTA whose epilogue has `epq` warps per TMEM lane quarter: the
 // producer warp, the MMA warp and 4 * epq epilogue warps.
@@ -111,26 +100,19 @@ struct Layout {
 // per operand row and one MMA consumes 32 bytes of it.
 struct FmtBf16 {  // exact search: 128 BF16 coordinates, two chunks
   static constexpr int kChunks = 2;
-  static constexpr int kCluster = kTcCluster;  // CTAs sharing each reference tile by multicast
   static constexpr bool kExtFirst = false;
   static constexpr uint32_t kIdesc = idesc_bf16_f32(kBM, kBN);
   static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
     mma_bf16(d, a, b, kIdesc, acc);
   }
 };
-struct FmtE4m3Base {  // coarse pass: 128 E4M3 coordinates, one chunk
+struct FmtE4m3 {  // coarse pass: 128 E4M3 coordinates, one chunk
   static constexpr int kChunks = 1;
   static constexpr bool kExtFirst = true;
   static constexpr uint32_t kIdesc = idesc_e4m3_f32(kBM, kBN);
   static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
     mma_f8(d, a, b, kIdesc, acc);
   }
-};
-struct FmtE4m3 : FmtE4m3Base {  // pairs of CTAs sharing each reference tile
-  static constexpr int kCluster = kTcCoarseCluster;
-};
-struct FmtE4m3Solo : FmtE4m3Base {  // single CTAs (small batches: query rows padded to one tile only)
-  static constexpr int kCluster = 1;
 };
 
 template <int kStages>
@@ -546,7 +528,7 @@ struct NbnnEpilogue {
 };
 
 template <class Fmt, class Epilogue>
-__global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __cluster_dims__(Fmt::kCluster, 1, 1)
+__global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1)
     tc_scan_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_qe,
                    const __grid_constant__ CUtensorMap tmap_r, const __grid_constant__ CUtensorMap tmap_re, int64_t m,
                    int64_t n_ref, int64_t split_len, ScanOut out, uint32_t* __restrict__ dev_err,
@@ -558,10 +540,6 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
   constexpr int kEpiWarps = 4 * kEpiPerQuarter;
   constexpr int kEpiCols = kBN / kEpiPerQuarter;  // columns of a tile per epilogue warp
   constexpr int kRounds = kEpiCols / 64;          // rounds of two 32-column loads per tile
-  constexpr int kCluster = Fmt::kCluster;
-  constexpr int kBRowsPerCta = kBN / kCluster;                 // rows of each tile one CTA loads
-  constexpr uint32_t kBChunkPart = kBChunkBytes / kCluster;   // its share of a chunk
-  constexpr uint32_t kBExtPart = kBExtBytes / kCluster;       // its share of the extension
   static_assert(KC <= kKChunks, "the query tile fits the chunks shared memory is laid out for");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -576,16 +554,14 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
   const int64_t j_begin = (int64_t)blockIdx.y * split_len;
   const int64_t j_end = min(j_begin + split_len, n_ref);
   // A timeout reported earlier and not yet collected by lnbnn_sync: scan no
-  // tiles (but keep the cluster protocol, so the partner CTA is not stranded).
+  // tiles.
   const bool stale_timeout = (*reinterpret_cast<volatile uint32_t*>(dev_err) & kDevErrTimeout) != 0;
   const int ntiles = stale_timeout ? 0 : (int)((j_end - j_begin + kBN - 1) / kBN);
-  const uint32_t rank = cluster_ctarank();
-  constexpr uint16_t kAllCtas = (uint16_t)((1u << kCluster) - 1);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(bars.full(s), 1);
-      mbar_init(bars.empty(s), kCluster);  // one MMA completion from each CTA of the cluster
+      mbar_init(bars.empty(s), 1);  // the MMA completion that frees the stage
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(bars.tfull(b), 1);
@@ -598,7 +574,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
   }
   if (warp == 1) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
   tc_fence_before();
-  cluster_sync();  // the partner's barriers exist before any multicast reaches them
+  __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -634,18 +610,9 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
           }
           const uint32_t dst = sbase + L::kOffB + s * kStageBytes;
           const bool last = kc == KC - 1;
-          // the whole chunk lands here: this CTA's half and the partner's
           mbar_arrive_expect_tx(bars.full(s), kBChunkBytes + (last ? kBExtBytes : 0u));
-          if constexpr (kCluster == 1) {
-            tma_load_2d(dst, &tmap_r, kc * kBK, row, bars.full(s));
-            if (last) tma_load_2d(dst + kBChunkBytes, &tmap_re, 0, row, bars.full(s));
-          } else {
-            const int32_t my_row = row + (int32_t)(rank * kBRowsPerCta);
-            tma_load_2d_multicast(dst + rank * kBChunkPart, &tmap_r, kc * kBK, my_row, bars.full(s), kAllCtas);
-            if (last)
-              tma_load_2d_multicast(dst + kBChunkBytes + rank * kBExtPart, &tmap_re, 0, my_row, bars.full(s),
-                                    kAllCtas);
-          }
+          tma_load_2d(dst, &tmap_r, kc * kBK, row, bars.full(s));
+          if (last) tma_load_2d(dst + kBChunkBytes, &tmap_re, 0, row, bars.full(s));
         }
       }
       // every load issued must land before the CTA may exit
@@ -697,11 +664,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
           if (!Fmt::kExtFirst && last)
             mma_bf16(d_tmem, sw32_kmajor_desc(sbase + L::kOffAExt), sw32_kmajor_desc(b_base + kBChunkBytes),
                      FmtBf16::kIdesc, 1u);
-          if constexpr (kCluster == 1) {
-            mma_commit(bars.empty(s));
-          } else {
-            mma_commit_multicast(bars.empty(s), kAllCtas);  // every CTA's producer refills this stage
-          }
+          mma_commit(bars.empty(s));  // the producer may refill this stage
         }
         if (ok) mma_commit(bars.tfull(b));
       }
@@ -758,8 +721,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1) __
   }
 
   tc_fence_before();
-  // no CTA leaves while its partner may still signal its barriers
-  cluster_sync();
+  __syncthreads();
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem_base, kTmemCols);
@@ -819,18 +781,14 @@ bool encode_operand(CUtensorMap* main, CUtensorMap* ext, const void* bf, const v
 
 bool make_tc_tensor_maps(const __nv_bfloat16* ref_bf, const __nv_bfloat16* sref_bf, const __nv_bfloat16* ref_ext,
                          const __nv_bfloat16* sref_ext, int64_t n_pad, TcTensorMaps* out) {
-  constexpr uint32_t rows = kBN / FmtBf16::kCluster;  // the rows of a tile one CTA of a cluster loads
-  return encode_operand(&out->ref, &out->ref_ext, ref_bf, ref_ext, (uint64_t)n_pad, rows) &&
-         encode_operand(&out->sref, &out->sref_ext, sref_bf, sref_ext, (uint64_t)n_pad, rows);
+  return encode_operand(&out->ref, &out->ref_ext, ref_bf, ref_ext, (uint64_t)n_pad, kBN) &&
+         encode_operand(&out->sref, &out->sref_ext, sref_bf, sref_ext, (uint64_t)n_pad, kBN);
 }
 
 bool make_tc_tensor_maps_e4m3(const uint8_t* ref_f8, const __nv_bfloat16* ref_f8_ext, int64_t n_pad,
                               TcTensorMaps* out) {
-  constexpr uint32_t rows = kBN / FmtE4m3::kCluster;  // the rows of a tile one CTA of a pair loads
-  return encode_e4m3(&out->f8, ref_f8, (uint64_t)n_pad, rows) &&
-         encode_bf16(&out->f8_ext, ref_f8_ext, (uint64_t)n_pad, kExt, kExt, rows, CU_TENSOR_MAP_SWIZZLE_32B) &&
-         encode_e4m3(&out->f8_solo, ref_f8, (uint64_t)n_pad, kBN) &&
-         encode_bf16(&out->f8_solo_ext, ref_f8_ext, (uint64_t)n_pad, kExt, kExt, kBN, CU_TENSOR_MAP_SWIZZLE_32B);
+  return encode_e4m3(&out->f8, ref_f8, (uint64_t)n_pad, kBN) &&
+         encode_bf16(&out->f8_ext, ref_f8_ext, (uint64_t)n_pad, kExt, kExt, kBN, CU_TENSOR_MAP_SWIZZLE_32B);
 }
 
 namespace {
@@ -841,7 +799,7 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const voi
                         int64_t split_len, const ScanOut& out, uint32_t* dev_err, unsigned long long* stats,
                         cudaStream_t s) {
   if (m == 0) return cudaSuccess;
-  if (m_pad % (kBM * Fmt::kCluster) != 0 || split_len % kBN != 0) return cudaErrorInvalidValue;
+  if (m_pad % kBM != 0 || split_len % kBN != 0) return cudaErrorInvalidValue;
   CUtensorMap tq, tqe;
   const bool ok = Fmt::kChunks == 1
                       ? encode_e4m3(&tq, qop, (uint64_t)m_pad, kBM) &&
@@ -878,10 +836,6 @@ cudaError_t prepare_tc_kernels() {
   if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<kTcCoarseRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnSmemEpilogue<kTcWideRegListMax>>();
   if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<0>>();
-  if (e == cudaSuccess) e = prepare_one<FmtE4m3Solo, KnnEpilogue<kTcRegListMax>>();
-  if (e == cudaSuccess) e = prepare_one<FmtE4m3Solo, KnnEpilogue<kTcCoarseRegListMax>>();
-  if (e == cudaSuccess) e = prepare_one<FmtE4m3Solo, KnnSmemEpilogue<kTcWideRegListMax>>();
-  if (e == cudaSuccess) e = prepare_one<FmtE4m3Solo, KnnEpilogue<0>>();
   return e;
 }
 
@@ -897,22 +851,21 @@ cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv
   out.K1 = K1;
   const CUtensorMap& tr = sorted_copy ? maps.sref : maps.ref;
   const CUtensorMap& tre = sorted_copy ? maps.sref_ext : maps.ref_ext;
-  if (K1 <= kTcRegListMax)
-    return launch_scan<FmtBf16, KnnEpilogue<kTcRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len,
-                                                            out, dev_err, stats, s);
-  if (K1 <= kTcCoarseRegListMax)
-    return launch_scan<FmtBf16, KnnEpilogue<kTcCoarseRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
-                                                                  split_len, out, dev_err, stats, s);
-  if (K1 <= kTcWideRegListMax) {
-    // Lists in shared memory make inserts cheap but leave room for only a
-    // two-stage ring; register lists keep four stages.  Measured on the
-    // 256-class data (k = 50): shared memory is faster while a split holds up
-    // to 5.76M references (26% at 2.88M, 8% at 5.76M), registers at 11.52M (16%).
-    if (split_len <= kSmemListMaxRefs)
+  switch (tc_list_kind(K1, split_len, false)) {
+    case ListKind::Reg16:
+      return launch_scan<FmtBf16, KnnEpilogue<kTcRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len,
+                                                              out, dev_err, stats, s);
+    case ListKind::Reg32:
+      return launch_scan<FmtBf16, KnnEpilogue<kTcCoarseRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
+                                                                    split_len, out, dev_err, stats, s);
+    case ListKind::Smem64:
       return launch_scan<FmtBf16, KnnSmemEpilogue<kTcWideRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
                                                                       split_len, out, dev_err, stats, s);
-    return launch_scan<FmtBf16, KnnEpilogue<kTcWideRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
-                                                                split_len, out, dev_err, stats, s);
+    case ListKind::Reg64:
+      return launch_scan<FmtBf16, KnnEpilogue<kTcWideRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
+                                                                  split_len, out, dev_err, stats, s);
+    case ListKind::Heap:
+      break;
   }
   return launch_scan<FmtBf16, KnnEpilogue<0>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len, out, dev_err,
                                               stats, s);
@@ -925,22 +878,27 @@ cudaError_t launch_coarse_fmt(const CUtensorMap& tr, const CUtensorMap& tre, con
                               const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
                               int64_t split_len, int K1, const ScanOut& out, uint32_t* dev_err,
                               unsigned long long* stats, cudaStream_t s) {
-  if (K1 <= kTcRegListMax)
-    return launch_scan<Fmt, KnnEpilogue<kTcRegListMax>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits, split_len, out,
-                                                        dev_err, stats, s);
-  if (K1 <= kTcCoarseRegListMax)
-    return launch_scan<Fmt, KnnEpilogue<kTcCoarseRegListMax>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits, split_len,
-                                                              out, dev_err, stats, s);
-  if (K1 <= kTcWideRegListMax)
-    return launch_scan<Fmt, KnnSmemEpilogue<kTcWideRegListMax>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits,
+  switch (tc_list_kind(K1, split_len, true)) {
+    case ListKind::Reg16:
+      return launch_scan<Fmt, KnnEpilogue<kTcRegListMax>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits, split_len,
+                                                          out, dev_err, stats, s);
+    case ListKind::Reg32:
+      return launch_scan<Fmt, KnnEpilogue<kTcCoarseRegListMax>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits,
                                                                 split_len, out, dev_err, stats, s);
+    case ListKind::Smem64:
+    case ListKind::Reg64:
+      return launch_scan<Fmt, KnnSmemEpilogue<kTcWideRegListMax>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits,
+                                                                  split_len, out, dev_err, stats, s);
+    case ListKind::Heap:
+      break;
+  }
   return launch_scan<Fmt, KnnEpilogue<0>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits, split_len, out, dev_err, stats,
                                           s);
 }
 
 }  // namespace
 
-cudaError_t launch_coarse_tc(const TcTensorMaps& maps, bool solo, const uint8_t* qf8, const __nv_bfloat16* qext,
+cudaError_t launch_coarse_tc(const TcTensorMaps& maps, const uint8_t* qf8, const __nv_bfloat16* qext,
                              int64_t m, int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int K1,
                              uint64_t* lists, int64_t stride, int32_t* row_thr, uint32_t* dev_err,
                              unsigned long long* stats, const uint32_t* gate, cudaStream_t s) {
@@ -950,9 +908,6 @@ cudaError_t launch_coarse_tc(const TcTensorMaps& maps, bool solo, const uint8_t*
   out.lists = lists;
   out.stride = stride;
   out.K1 = K1;
-  if (solo)
-    return launch_coarse_fmt<FmtE4m3Solo>(maps.f8_solo, maps.f8_solo_ext, qf8, qext, m, m_pad, n_ref, splits,
-                                          split_len, K1, out, dev_err, stats, s);
   return launch_coarse_fmt<FmtE4m3>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref, splits, split_len, K1, out,
                                     dev_err, stats, s);
 }

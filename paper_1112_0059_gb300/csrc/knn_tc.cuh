@@ -11,23 +11,11 @@ namespace lnbnn {
 
 // References per tile of the tensor-core kernels (the MMA N extent).
 constexpr int kTcRefTile = 256;
-// Query rows per CTA (the MMA M extent) and CTAs per cluster; the query
-// operand must be padded to kTcQueryTile * kTcCluster rows.
+// Query rows per CTA (the MMA M extent); the query operand is padded to
+// whole tiles.  Every kernel runs single CTAs: each loads its own reference
+// tiles, and concurrently running CTAs share them through L2.
 constexpr int kTcQueryTile = 128;
-// Exact scan: single CTAs (pairs measured ~5% slower: it is tensor-bound).
-// FP8 coarse pass: pairs (measured 4.5% faster on the 256-class workload:
-// half the reference traffic, less DRAM power, a higher SM clock).
-constexpr int kTcCluster = 1;
-constexpr int kTcCoarseCluster = 2;
-static_assert(kQueryPad % (kTcQueryTile * kTcCluster) == 0, "query padding must cover whole clusters");
-// Query rows of the FP8 coarse pass are padded to whole clusters, except for
-// batches of at most kCoarseSoloMaxRows rows, which run single CTAs (one
-// query tile each: a lone image of 100 descriptors would otherwise do a
-// pair's 256 rows of work) and are padded to kQueryPad.
-constexpr int kCoarseQueryPad = kTcQueryTile * kTcCoarseCluster > kQueryPad ? kTcQueryTile * kTcCoarseCluster
-                                                                             : kQueryPad;
-constexpr int64_t kCoarseSoloMaxRows = 1024;
-inline bool coarse_solo(int64_t m) { return m <= kCoarseSoloMaxRows; }
+static_assert(kQueryPad % kTcQueryTile == 0, "query padding must cover whole tiles");
 // Lists of the k+1 (or shortlist) nearest per query row: up to 16 entries a
 // 16-entry register list (the fewest registers), up to 32 a 32-entry one, up
 // to 64 a 64-entry list in shared memory with warp-cooperative inserts (in
@@ -44,13 +32,28 @@ constexpr int kTcWideRegListMax = 64;
 constexpr int kTcListsPerSplit = 2;
 inline int tc_lists_per_split(int K1) { return K1 > kTcCoarseRegListMax && K1 <= kTcWideRegListMax ? 1 : 2; }
 
+// Longest reference split for which the exact scan keeps 33..64-entry lists
+// in shared memory rather than registers (shared-memory lists leave room for
+// a two-stage ring only; measured on the 256-class data at k = 50, shared
+// memory is faster while a split holds up to 5.76M references, registers at
+// 11.52M).
+constexpr int64_t kSmemListMaxRefs = int64_t(8) << 20;
+
+// Where a scan keeps its per-row lists of K1 keys.
+enum class ListKind { Reg16, Reg32, Smem64, Reg64, Heap };
+inline ListKind tc_list_kind(int K1, int64_t split_len, bool coarse) {
+  if (K1 <= kTcRegListMax) return ListKind::Reg16;
+  if (K1 <= kTcCoarseRegListMax) return ListKind::Reg32;
+  if (K1 <= kTcWideRegListMax) return coarse || split_len <= kSmemListMaxRefs ? ListKind::Smem64 : ListKind::Reg64;
+  return ListKind::Heap;
+}
+
 // TMA descriptors over an index's BF16 reference operands (caller's row order
 // and class-sorted order).  Encoded once at index creation.
 struct TcTensorMaps {
   CUtensorMap ref, ref_ext;    // BF16 [n_pad,128] (128-byte swizzle) and norm digits [n_pad,16] (32-byte swizzle)
   CUtensorMap sref, sref_ext;  // the same over the class-sorted copy
-  CUtensorMap f8, f8_ext;      // E4M3 coarse operand [n_pad,128] and its extension [n_pad,16] (pairs' boxes)
-  CUtensorMap f8_solo, f8_solo_ext;  // the same with whole-tile boxes, for single CTAs
+  CUtensorMap f8, f8_ext;      // E4M3 coarse operand [n_pad,128] and its extension [n_pad,16]
 };
 
 // Split-N schedule of one scan launch over T query tiles: s reference splits
@@ -121,9 +124,7 @@ cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv
 // operands (qf8 [m_pad, 128] bytes of -2 E4M3(q - 64), qext its extension),
 // keeping the K1 smallest (coarse + 2^21, row) keys per list in the same
 // layout as launch_knn_tc.
-// solo: single CTAs (m_pad a multiple of the query tile); otherwise pairs
-// (m_pad a multiple of two tiles).
-cudaError_t launch_coarse_tc(const TcTensorMaps& maps, bool solo, const uint8_t* qf8, const __nv_bfloat16* qext,
+cudaError_t launch_coarse_tc(const TcTensorMaps& maps, const uint8_t* qf8, const __nv_bfloat16* qext,
                              int64_t m, int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int K1,
                              uint64_t* lists, int64_t stride, int32_t* row_thr, uint32_t* dev_err,
                              unsigned long long* stats, const uint32_t* gate, cudaStream_t s);

@@ -230,9 +230,9 @@ struct KnnPlan {
 
 // splits = 0: the modelled best; otherwise that many (an upper bound after
 // rounding the split length to whole tiles).
-KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, int splits = 0, int64_t pad = kQueryPad) {
+KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, int splits = 0) {
   KnnPlan p{};
-  p.m_pad = round_up(m, pad);
+  p.m_pad = round_up(m, kQueryPad);
   p.K1 = K1;
   p.splits = splits > 0 ? splits : choose_splits(ix, p.m_pad);
   p.split_len = round_up((ix->n_ref + p.splits - 1) / p.splits, kTcRefTile);
@@ -293,7 +293,6 @@ size_t scratch_bound(const lnbnn_index* ix, int64_t max_q, int K1) {
     const int64_t mm = std::min(m, max_q);
     const int64_t hi = max_splits_for(round_up(mm, kQueryPad) / kTcQueryTile, ix->n_ref, ix->sm_count, max_splits(ix));
     b = std::max(b, plan_knn(ix, mm, K1, (int)hi).bytes);
-    b = std::max(b, plan_knn(ix, mm, K1, (int)hi, kCoarseQueryPad).bytes);
     b = std::max(b, plan_nbnn(ix, mm).bytes);
   }
   return b;
@@ -333,8 +332,7 @@ lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_
 // merge, exact rerank; *lists receives m sorted lists of K1 exact keys.
 lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_t m, int K1, int M1,
                          cudaStream_t s, const uint64_t** lists, CallProfile& prof) {
-  const bool solo = coarse_solo(m);
-  KnnPlan p = plan_knn(ix, m, M1, 0, solo ? kQueryPad : kCoarseQueryPad);
+  KnnPlan p = plan_knn(ix, m, M1);
   char* ws = nullptr;
   lnbnn_status st = scratch.get(p.bytes, &ws);
   if (st != LNBNN_OK) return st;
@@ -349,7 +347,7 @@ lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, in
   CK(cudaMemsetAsync(row_thr, 0x7F, sizeof(int32_t) * (size_t)p.m_pad, s));
   prof.launched(1);
   prof.mark(1);
-  CK(launch_coarse_tc(ix->tc, solo, qf8, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, M1, part, p.m_pad,
+  CK(launch_coarse_tc(ix->tc, qf8, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, M1, part, p.m_pad,
                       p.splits > 1 ? row_thr : nullptr, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, ix->gate, s));
   prof.launched(1, true);
   prof.mark(2);
@@ -667,6 +665,30 @@ lnbnn_status lnbnn_set_start_gate(lnbnn_index* index, const uint32_t* gate) {
 lnbnn_status lnbnn_plan_splits(const lnbnn_index* index, int64_t n_queries, int32_t* splits) {
   if (!index || !splits || n_queries < 1) return LNBNN_ERR_INVALID_ARG;
   *splits = plan_knn(index, n_queries, 1).splits;
+  return LNBNN_OK;
+}
+
+lnbnn_status lnbnn_plan_search(const lnbnn_index* index, int64_t n_queries, int32_t k1, int32_t fp8,
+                               lnbnn_search_plan* out) {
+  if (!index || !out || n_queries < 1) return LNBNN_ERR_INVALID_ARG;
+  if (k1 < 1 || k1 > LNBNN_MAX_K + 1 || (int64_t)k1 > index->n_ref) return LNBNN_ERR_K_RANGE;
+  if (fp8 && !index->fp8) return LNBNN_ERR_NO_FP8;
+  const KnnPlan p = plan_knn(index, n_queries, k1);
+  lnbnn_search_plan r{};
+  r.splits = p.splits;
+  r.lists_per_row = p.lists;
+  r.split_len = p.split_len;
+  switch (tc_list_kind(k1, p.split_len, fp8 != 0)) {
+    case ListKind::Reg16: r.list_storage = 0; r.list_capacity = kTcRegListMax; break;
+    case ListKind::Reg32: r.list_storage = 0; r.list_capacity = kTcCoarseRegListMax; break;
+    case ListKind::Smem64: r.list_storage = 1; r.list_capacity = kTcWideRegListMax; break;
+    case ListKind::Reg64: r.list_storage = 0; r.list_capacity = kTcWideRegListMax; break;
+    case ListKind::Heap: r.list_storage = 2; r.list_capacity = k1; break;
+  }
+  r.tile_m = kTcQueryTile;
+  r.tile_n = kTcRefTile;
+  r.persistent = 0;
+  *out = r;
   return LNBNN_OK;
 }
 

@@ -13,7 +13,7 @@ Classification" -- Alg. 1 (NBNN) and Alg. 2 (LocalNBNN).
                  (exact, or ``shortlist=m`` for the FP8 shortlist form),
                  ``nbnn_classify``, ``nbnn_logodds_classify`` (Section 3.1),
                  ``classify_host`` (host buffers), ``save`` / ``load``,
-                 ``autotune`` / ``plan_splits``, ``prepare_fp8``,
+                 ``autotune`` / ``plan_splits`` / ``plan_search``, ``prepare_fp8``,
                  ``profile_enable`` / ``profile_read``, ``sync``
 ``Workspace``    device scratch of one in-flight call (allocation-free calls,
                  several streams, CUDA graph capture)
@@ -53,6 +53,7 @@ EXPORTS = ["lnbnn_index_create", "lnbnn_index_destroy", "lnbnn_index_info", "knn
            "lnbnn_workspace_destroy", "knn_search_ws", "lnbnn_classify_ws", "nbnn_classify_ws",
            "lnbnn_index_prepare_fp8", "knn_search_fp8", "lnbnn_classify_fp8", "knn_search_fp8_ws",
            "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host", "lnbnn_autotune", "lnbnn_plan_splits",
+           "lnbnn_plan_search",
            "lnbnn_debug_fail_allocations", "lnbnn_set_start_gate", "lnbnn_index_save", "lnbnn_index_load",
            "nbnn_logodds_classify", "nbnn_logodds_classify_ws", "lnbnn_index_create_located", "lnbnn_index_layout"]
 
@@ -74,6 +75,20 @@ class Tuning(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SearchPlan(ctypes.Structure):
+    """Mirror of ``lnbnn_search_plan`` (include/lnbnn.h)."""
+    _fields_ = [("splits", ctypes.c_int32), ("lists_per_row", ctypes.c_int32), ("split_len", ctypes.c_int64),
+                ("list_storage", ctypes.c_int32), ("list_capacity", ctypes.c_int32), ("tile_m", ctypes.c_int32),
+                ("tile_n", ctypes.c_int32), ("persistent", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    STORAGE = {0: "registers", 1: "shared memory", 2: "global-memory heap"}
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d["list_storage"] = self.STORAGE.get(self.list_storage, self.list_storage)
+        return d
 
 
 class LnbnnError(RuntimeError):
@@ -122,6 +137,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.lnbnn_classify_fp8_host.argtypes = [P, P, I64, P, I64, I32, I32, P, P, P]
         lib.lnbnn_autotune.argtypes = [P, P, ctypes.POINTER(Tuning)]
         lib.lnbnn_plan_splits.argtypes = [P, I64, ctypes.POINTER(I32)]
+        lib.lnbnn_plan_search.argtypes = [P, I64, I32, I32, ctypes.POINTER(SearchPlan)]
+        lib.lnbnn_plan_search.restype = ctypes.c_int
         lib.lnbnn_debug_fail_allocations.argtypes = [I32]
         lib.lnbnn_debug_fail_allocations.restype = None
         lib.lnbnn_set_start_gate.argtypes = [P, P]
@@ -266,6 +283,14 @@ class Index:
         out = ctypes.c_int32()
         _check(self._lib.lnbnn_plan_splits(self.handle, int(n_queries), ctypes.byref(out)), "lnbnn_plan_splits")
         return out.value
+
+    def plan_search(self, n_queries: int, k1: int, fp8: bool = False) -> dict:
+        """How a search keeping the k1 nearest of n_queries descriptors would be
+        launched (exact scan, or the FP8 coarse pass with k1 = shortlist)."""
+        out = SearchPlan()
+        _check(self._lib.lnbnn_plan_search(self.handle, int(n_queries), int(k1), int(bool(fp8)), ctypes.byref(out)),
+               "lnbnn_plan_search")
+        return out.as_dict()
 
     def set_start_gate(self, gate=None) -> None:
         """Test hook: search kernels wait (at most 1 s) for the uint32/int32 device
@@ -462,10 +487,16 @@ def knn_search_noalloc(ref, queries, k: int, stream=None):
         lib.knn_search_noalloc.argtypes = [P, I64, P, I64, I32, P, P, P]
         lib.knn_search_noalloc.restype = ctypes.c_int
         lib.knn_search_noalloc._declared = True
+    for name, t in (("ref", ref), ("queries", queries)):
+        if not isinstance(t, torch.Tensor) or t.dim() != 2 or t.shape[1] != 128:
+            raise ValueError(f"{name} must be a uint8 [N, 128] tensor")
+    if ref.device != queries.device:
+        raise ValueError("ref and queries must be on the same CUDA device")
     m = int(queries.shape[0])
-    idx = torch.empty((m, k), dtype=torch.int32, device=queries.device)
-    dist = torch.empty((m, k), dtype=torch.int32, device=queries.device)
-    _check(lib.knn_search_noalloc(_dev(ref, torch.uint8, "ref"), int(ref.shape[0]),
-                                  _dev(queries, torch.uint8, "queries"), m, k, _dev(idx, torch.int32, "idx"),
-                                  _dev(dist, torch.int32, "dist"), _stream_ptr(stream)), "knn_search_noalloc")
+    with torch.cuda.device(queries.device):
+        idx = torch.empty((m, k), dtype=torch.int32, device=queries.device)
+        dist = torch.empty((m, k), dtype=torch.int32, device=queries.device)
+        _check(lib.knn_search_noalloc(_dev(ref, torch.uint8, "ref"), int(ref.shape[0]),
+                                      _dev(queries, torch.uint8, "queries"), m, k, _dev(idx, torch.int32, "idx"),
+                                      _dev(dist, torch.int32, "dist"), _stream_ptr(stream)), "knn_search_noalloc")
     return idx, dist

@@ -80,3 +80,15 @@ def test_product_path_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "lnbnn_oracle" not in text, f
+
+
+def test_noalloc_binding_checks_shapes_before_any_call(lib):
+    # rows of 64 bytes would make the kernels read past the end of the buffers:
+    # the binding refuses them before the C entry point is reached
+    torch = pytest.importorskip("torch")
+    from paper_1112_0059_gb300 import lnbnn
+    good = torch.zeros((10, 128), dtype=torch.uint8)
+    bad = torch.zeros((10, 64), dtype=torch.uint8)
+    for ref, q in ((bad, good), (good, bad), (good.reshape(-1), good)):
+        with pytest.raises(ValueError):
+            lnbnn.knn_search_noalloc(ref, q, 3)

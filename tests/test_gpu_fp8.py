@@ -156,23 +156,6 @@ def _sample_rows(M, n, seed):
     return np.unique(np.concatenate([[0, M - 1], rng.integers(0, M, size=n)]))
 
 
-def test_fp8_caltech256_full_size_sampled(lnbnn):
-    """The bench's launch configuration (all 750k query rows in one call, one
-    reference split, clusters of two CTAs) against the oracle on sampled rows."""
-    from paper_1112_0059_gb300 import synth
-    w = synth.workload("caltech256-like")
-    ref, labels = synth.reference_set(w)
-    q, off, _ = synth.query_set(w)
-    rows = _sample_rows(len(q), 14, 21)
-    with lnbnn.Index(dev(ref), dev(labels), w.n_classes) as ix:
-        ix.prepare_fp8()
-        idx, dist = ix.knn_search(dev(q), 11, shortlist=32)
-        ix.sync()
-    od, oj = oracle.knn_coarse(ref, q[rows], 11, 32)
-    assert np.array_equal(idx.cpu().numpy()[rows], oj.astype(np.int32))
-    assert np.array_equal(dist.cpu().numpy()[rows], od.astype(np.int32))
-
-
 def test_fp8_caltech101_full_size(lnbnn):
     from paper_1112_0059_gb300 import synth
     w = synth.workload("caltech101-like")

@@ -300,19 +300,6 @@ def test_caltech101_like_full_size(lnbnn):
         assert (lt.cpu().numpy() <= 0).all() and (nt.cpu().numpy() >= 0).all()
 
 
-def test_caltech256_like_full_size_sampled(lnbnn):
-    w = synth.workload("caltech256-like")
-    ref, labels = synth.reference_set(w)
-    q, off, _ = synth.query_set(w)
-    rows = _sample_rows(len(q), 14, 11)
-    with make_index(lnbnn, ref, labels, w.n_classes) as ix:
-        idx, dist = ix.knn_search(dev(q), 11)
-        ix.sync()
-        od, oj = oracle.knn(ref, q[rows], 11)
-        assert np.array_equal(dist.cpu().numpy()[rows], od.astype(np.int32))
-        assert np.array_equal(idx.cpu().numpy()[rows], oj.astype(np.int32))
-
-
 def test_repeated_searches_with_heavy_ties(lnbnn):
     # Coordinates in {0..2} on 6 dims: most distances tie, and the lists must
     # follow the exact (distance, row) order on every call.

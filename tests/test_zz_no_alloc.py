@@ -1,4 +1,4 @@
-"""knn_search_noalloc against knn_search.
+"""knn_search_noalloc against knn_search and against the oracle.
 
 knn_search_noalloc serves callers that must not allocate device memory (a
 host framework that owns every allocation, or code that cannot afford the
@@ -49,8 +49,10 @@ def lib():
 
 
 def test_noalloc_matches_knn_search_on_two_calls(lib):
+    import oracle
     from paper_1112_0059_gb300 import lnbnn
-    # a larger call, then a smaller one that finds the first call's data in the scratch
+    # a larger call (several reference splits sharing the rows' bounds), then
+    # smaller ones that find the earlier calls' data in the scratch
     for seed, n_ref, n_q, k in ((0, 20000 + 77, 3000 + 5, 10), (1, 5000 + 3, 700, 25), (2, 6000 + 11, 500, 50)):
         ref, q = _case(seed, n_ref, n_q)
         ref_d, q_d = torch.from_numpy(ref).cuda(), torch.from_numpy(q).cuda()
@@ -59,8 +61,12 @@ def test_noalloc_matches_knn_search_on_two_calls(lib):
         with lnbnn.Index(ref_d, torch.zeros(n_ref, dtype=torch.int32, device="cuda"), 1) as ix:
             want_idx, want_dist = ix.knn_search(q_d, k)
             ix.sync()
-        # integer work: bit-exact agreement
+        # integer work: bit-exact agreement, with the existing entry point and
+        # with the oracle's (distance, lowest row) order
         assert torch.equal(idx, want_idx) and torch.equal(dist, want_dist)
+        od, oj = oracle.knn(ref, q, k)
+        assert np.array_equal(dist.cpu().numpy(), od.astype(np.int32))
+        assert np.array_equal(idx.cpu().numpy(), oj.astype(np.int32))
         assert int(dist[0, 0]) == 0 and int(idx[0, 0]) == 3
 
 
@@ -69,3 +75,19 @@ def test_noalloc_rejects_sizes_beyond_the_scratch(lib):
     q_d = torch.zeros((10, 128), dtype=torch.uint8, device="cuda")
     code, _, _ = _noalloc(lib, ref_d, q_d, 10)
     assert code == 10  # LNBNN_ERR_SCRATCH_LIMIT, before any work is issued
+    # within the per-operand bound but not in the scratch as a whole
+    ref_d = torch.zeros((200000, 128), dtype=torch.uint8, device="cuda")
+    q_d = torch.zeros((60000, 128), dtype=torch.uint8, device="cuda")
+    code, _, _ = _noalloc(lib, ref_d, q_d, 10)
+    assert code == 10
+
+
+def test_noalloc_rejects_host_memory(lib):
+    ref = torch.zeros((1000, 128), dtype=torch.uint8)  # host memory: not reachable as device memory
+    q_d = torch.zeros((10, 128), dtype=torch.uint8, device="cuda")
+    idx = torch.empty((10, 5), dtype=torch.int32, device="cuda")
+    dist = torch.empty((10, 5), dtype=torch.int32, device="cuda")
+    code = lib.knn_search_noalloc(ctypes.c_void_p(ref.data_ptr()), 1000, ctypes.c_void_p(q_d.data_ptr()), 10, 5,
+                                  ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(dist.data_ptr()),
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert code == 1  # LNBNN_ERR_INVALID_ARG
