@@ -36,6 +36,20 @@ KERNEL_SOURCES = ["paper_1112_0059_gb300/csrc/knn_tc.cu", "paper_1112_0059_gb300
                   "paper_1112_0059_gb300/csrc/topk.cuh", "paper_1112_0059_gb300/csrc/knn_tc.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "knn_tc_traffic.json")
 
+# Measurements reported beside the headline, each a block of the JSON line.
+SECTIONS = {
+    "uneven": "1,024 query images of U{200..3000} descriptors in one call on the 256-class index: exact and the "
+              "FP8 shortlist at m = 32, 64, 128, with recall, score error and class agreement",
+    "kc": "Local NBNN at k = 1, 10, 50, 100 and original NBNN on the first 32 and all 256 classes "
+          "(100 query images): run time against k and class count",
+    "caltech101": "the 101-class index (1.515M references, 200 images x 1,000 descriptors): Local NBNN at "
+                  "k = 1, 10, 50 against original NBNN",
+    "serve": "the continuous-batching server: Poisson arrivals, p50/p99 latency, exact and FP8",
+    "single": "one query image of 100 / 632 / 1,000 / 4,000 descriptors at a time, k = 10, 50, 100, exact and FP8",
+    "logodds": "NBNN as a sum of log-odds increments (all or only the positive ones) for several beta",
+}
+DEFAULT_SECTIONS = "uneven,kc,caltech101,serve"
+
 
 def parse_args():
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
@@ -59,6 +73,13 @@ def parse_args():
     p.add_argument("--serve-rates", default="100,300,1000",
                    help="Poisson arrival rates (images/s) of the serving runs; empty to skip them")
     p.add_argument("--serve-seconds", type=float, default=2.5, help="arrival window of each serving run")
+    p.add_argument("--sections", default=DEFAULT_SECTIONS,
+                   help="measurements reported beside the headline (comma-separated; empty for none): "
+                        + ", ".join(f"{k} ({v})" for k, v in SECTIONS.items()))
+    p.add_argument("--recall-rows", type=int, default=8192,
+                   help="seeded random query rows (all images) of the FP8 recall against the exact search")
+    p.add_argument("--oracle-recall-rows", type=int, default=256,
+                   help="seeded random query rows of the FP8 recall against the CPU oracle (0: skip)")
     return p.parse_args()
 
 
@@ -371,23 +392,13 @@ def run_ours(args, w):
                          "gpu_launches": int(prof8["kernel_launches"])}
             fp8_block["roofline"]["traffic"] = traffic_per_launch(fp8_block["roofline"]["kernel"], M)
         index.sync()
-        sample = min(M, 8192)
-        i_x, _ = index.knn_search(q_d[:sample], k + 1)
-        i_f, _ = index.knn_search(q_d[:sample], k + 1, shortlist=m_short)
-        index.sync()
-        ix_, if_ = i_x.cpu().numpy(), i_f.cpu().numpy()
-        recall = float(np.mean([len(set(ix_[r]) & set(if_[r])) for r in range(sample)]) / (k + 1))
-        tx, tf = t_x.cpu().numpy(), t_f.cpu().numpy()
-        fp8_block.update({
-            "knn_recall": recall, "recall_sample": f"first {sample} query descriptors, the k+1 = {k + 1} neighbours",
-            "class_agreement": float((c_x.cpu().numpy() == c_f.cpu().numpy()).mean()),
-            "score_rel_error": float(np.abs(tf - tx).sum() / max(1, np.abs(tx).sum())),
-            "score_max_abs_error": int(np.abs(tf - tx).max()),
-            "reference": "the exact tensor-core search (bit-exact with the oracle in the parity tests)"})
+        fp8_block.update(fp8_accuracy(index, q_d, q, ref, k, m_short, t_x, c_x, t_f, c_f, args.recall_rows,
+                                      args.oracle_recall_rows if rank == 0 and world == 1 else 0))
 
+    sections = [x for x in args.sections.split(",") if x.strip()]
     serve_block = None
     rates = [float(r) for r in args.serve_rates.split(",") if r.strip()]
-    if rates and local and w.n_classes == synth.workload("serving").n_classes:
+    if "serve" in sections and rates and local and w.n_classes == synth.workload("serving").n_classes:
         cls_x, cls_f = {}, {}
         serve_block = {"exact": run_serving(index, rates, args.serve_seconds, k, None, cls_x)}
         if fp8_m or shortlist:
@@ -400,6 +411,10 @@ def run_ours(args, w):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(args.method, ref, labels, w.n_classes, q, k, args.cpu_seconds, int(off[1]))
+
+    extra = {}
+    if rank == 0 and world == 1 and w.name == "caltech256-like" and local:
+        extra = run_sections(sections, index, ref, labels, k, args.fp8_shortlist or 32)
 
     if rank == 0:
         cfg = workload_config(w, k, args.method)
@@ -416,6 +431,7 @@ def run_ours(args, w):
             "cpu_baseline": cpu,
             "fp8": fp8_block,
             "serve": serve_block,
+            **extra,
             "gpu_launches": int(prof["kernel_launches"]),
             "clocks": clk,
             "profile": {"search_ms_total": prof["search_ms"], "other_ms_total": prof["other_ms"],
@@ -428,6 +444,207 @@ def run_ours(args, w):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _sample(M: int, n: int, seed: int) -> np.ndarray:
+    """n distinct seeded random rows of [0, M) (all rows if n >= M), sorted."""
+    if n >= M:
+        return np.arange(M)
+    return np.sort(np.random.default_rng(seed).choice(M, size=n, replace=False))
+
+
+def fp8_accuracy(index, q_d, q, ref, k, m, t_x, c_x, t_f, c_f, recall_rows, oracle_rows) -> dict:
+    """Recall of the k+1 neighbours of the FP8 shortlist search on seeded
+    random rows of all images, against the exact tensor-core search and (on
+    fewer rows) against the CPU oracle directly; int64 score error and class
+    agreement of the classify calls against the exact ones."""
+    import torch
+    M = int(q_d.shape[0])
+    rows = _sample(M, recall_rows, 7)
+    rd = torch.from_numpy(rows).to(q_d.device)
+    qs = q_d.index_select(0, rd)
+    i_x, _ = index.knn_search(qs, k + 1)
+    i_f, _ = index.knn_search(qs, k + 1, shortlist=m)
+    index.sync()
+    ix_, if_ = i_x.cpu().numpy(), i_f.cpu().numpy()
+    out = {"knn_recall": float(np.mean([len(set(a) & set(b)) for a, b in zip(ix_, if_)]) / (k + 1)),
+           "recall_sample": f"{len(rows)} seeded random query rows of all images, the k+1 = {k + 1} neighbours, "
+                            "against the exact tensor-core search"}
+    if oracle_rows:
+        import oracle
+        orows = _sample(M, oracle_rows, 8)
+        _, oj = oracle.knn(ref, q[orows], k + 1)
+        od = torch.from_numpy(orows).to(q_d.device)
+        j_f, _ = index.knn_search(q_d.index_select(0, od), k + 1, shortlist=m)
+        index.sync()
+        jf = j_f.cpu().numpy()
+        out["knn_recall_vs_oracle"] = float(np.mean([len(set(a) & set(b)) for a, b in zip(oj, jf)]) / (k + 1))
+        out["oracle_recall_sample"] = f"{len(orows)} seeded random query rows, against the CPU oracle's exact kNN"
+    if t_x is not None:
+        tx, tf = t_x.cpu().numpy(), t_f.cpu().numpy()
+        out.update({"class_agreement": float((c_x.cpu().numpy() == c_f.cpu().numpy()).mean()),
+                    "score_rel_error": float(np.abs(tf - tx).sum() / max(1, np.abs(tx).sum())),
+                    "score_max_abs_error": int(np.abs(tf - tx).max()),
+                    "reference": "the exact tensor-core search (bit-exact with the oracle in the parity tests)"})
+    return out
+
+
+def _timed(fn, reps: int, warm: int = 1) -> float:
+    """Median device time (s) of reps calls after warm calls (CUDA events on
+    the current stream, the queries already on the device)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return statistics.median(times)
+
+
+def section_uneven(index, ref, k, shortlists=(32, 64, 128)) -> dict:
+    """The batched uneven workload: 1,024 images of U{200..3000} descriptors,
+    flattened with offsets, one classify call per form."""
+    import torch
+    w = synth.workload("batched-uneven")
+    q, off, _ = synth.query_set(w)
+    qd, od = torch.from_numpy(q).cuda(), torch.from_numpy(off).cuda()
+    M, n_img = len(q), len(off) - 1
+    res = {"workload": f"{w.name}: {w.notes}; {M:,} descriptors", "k": k, "runs": []}
+    index.prepare_fp8()
+    outs = {}
+    for m in (None, *shortlists):
+        tot = torch.empty((n_img, w.n_classes), dtype=torch.int64, device="cuda")
+        cls = torch.empty((n_img,), dtype=torch.int32, device="cuda")
+        t = _timed(lambda: index.lnbnn_classify(qd, od, k, out=(tot, cls), shortlist=m), 1)
+        index.sync()
+        outs[m] = (tot, cls)
+        plan = index.plan_search(M, m if m else k + 1, fp8=m is not None)
+        rec = {"form": "exact" if m is None else "fp8", "shortlist": m, "seconds": t, "desc_per_s": M / t,
+               "images_per_s": n_img / t, "plan": plan}
+        if m is not None:
+            tx, cx = outs[None]
+            rec.update(fp8_accuracy(index, qd, q, ref, k, m, tx, cx, tot, cls, 8192, 256 if m == shortlists[0] else 0))
+        res["runs"].append(rec)
+    return res
+
+
+def section_kc(ref, labels, index, ks=(1, 10, 50, 100), classes=(32, 256), q_imgs=100) -> dict:
+    """Run time against k and class count: the first C classes of the
+    256-class index (N = C x 45,000), 100 query images."""
+    import torch
+    from paper_1112_0059_gb300 import lnbnn
+    res = {"query_images": q_imgs, "runs": []}
+    for C in classes:
+        w = synth.workload("caltech256-like").with_classes(C).with_query_imgs(q_imgs)
+        n = w.n_ref
+        q, off, _ = synth.query_set(w)
+        qd, od = torch.from_numpy(q).cuda(), torch.from_numpy(off).cuda()
+        own = None
+        if n == index.n_ref:
+            ix = index
+        else:
+            own = ix = lnbnn.Index(torch.from_numpy(ref[:n]).cuda(), torch.from_numpy(labels[:n]).cuda(), C)
+        try:
+            for k in ks:
+                t = _timed(lambda: ix.lnbnn_classify(qd, od, k), 2)
+                res["runs"].append({"C": C, "n_ref": n, "method": "local", "k": k, "seconds": t,
+                                    "desc_per_s": len(q) / t, "tflops": 2 * 128 * n * len(q) / t / 1e12})
+            t = _timed(lambda: ix.nbnn_classify(qd, od), 2)
+            res["runs"].append({"C": C, "n_ref": n, "method": "nbnn", "k": None, "seconds": t,
+                                "desc_per_s": len(q) / t, "tflops": 2 * 128 * n * len(q) / t / 1e12})
+            ix.sync()
+        finally:
+            if own is not None:
+                own.close()
+    return res
+
+
+def section_caltech101(ks=(1, 10, 50)) -> dict:
+    """The 101-class index: Local NBNN at several k against original NBNN."""
+    import torch
+    from paper_1112_0059_gb300 import lnbnn
+    w = synth.workload("caltech101-like")
+    ref, labels = synth.reference_set(w)
+    q, off, _ = synth.query_set(w)
+    qd, od = torch.from_numpy(q).cuda(), torch.from_numpy(off).cuda()
+    res = {"workload": f"{w.name}: {w.notes}", "runs": []}
+    with lnbnn.Index(torch.from_numpy(ref).cuda(), torch.from_numpy(labels).cuda(), w.n_classes) as ix:
+        for k in ks:
+            t = _timed(lambda: ix.lnbnn_classify(qd, od, k), 3)
+            res["runs"].append({"method": "local", "k": k, "seconds": t, "desc_per_s": len(q) / t,
+                                "images_per_s": (len(off) - 1) / t, "tflops": 2 * 128 * w.n_ref * len(q) / t / 1e12,
+                                "plan": ix.plan_search(len(q), k + 1)})
+        t = _timed(lambda: ix.nbnn_classify(qd, od), 3)
+        res["runs"].append({"method": "nbnn", "k": None, "seconds": t, "desc_per_s": len(q) / t,
+                            "images_per_s": (len(off) - 1) / t, "tflops": 2 * 128 * w.n_ref * len(q) / t / 1e12})
+        ix.sync()
+    return res
+
+
+def section_single(index, sizes=(100, 632, 1000, 4000), ks=(10, 50, 100)) -> dict:
+    """One query image at a time (few query tiles, many reference splits)."""
+    import torch
+    w = synth.workload("caltech256-like")
+    res = {"runs": []}
+    for n in sizes:
+        qd = torch.from_numpy(synth.query_image(w, 7, n)).cuda()
+        for k in ks:
+            m = {10: 32, 50: 64, 100: 128}.get(k, 2 * (k + 1))
+            for form, sl in (("exact", None), ("fp8", m)):
+                t = _timed(lambda: index.knn_search(qd, k + 1, shortlist=sl), 5)
+                res["runs"].append({"descriptors": n, "k": k, "form": form, "shortlist": sl, "ms": t * 1e3,
+                                    "plan": index.plan_search(n, sl or k + 1, fp8=sl is not None)})
+    index.sync()
+    return res
+
+
+def section_logodds(index, betas=(1e-6, 1e-5, 1e-4, 1e-3), q_imgs=100) -> dict:
+    """NBNN as a sum of log-odds increments (Section 3.1), all or positive only."""
+    import torch
+    w = synth.workload("caltech256-like").with_query_imgs(q_imgs)
+    q, off, _ = synth.query_set(w)
+    qd, od = torch.from_numpy(q).cuda(), torch.from_numpy(off).cuda()
+    _, c_nbnn = index.nbnn_classify(qd, od)
+    c_nbnn = c_nbnn.cpu().numpy()
+    res = {"query_images": q_imgs, "runs": []}
+    for beta in betas:
+        for pos in (False, True):
+            t = _timed(lambda: index.nbnn_logodds_classify(qd, od, beta, pos), 2)
+            _, c, n = index.nbnn_logodds_classify(qd, od, beta, pos)
+            index.sync()
+            res["runs"].append({"beta": beta, "positive_only": pos, "seconds": t, "desc_per_s": len(q) / t,
+                                "increments_per_desc": float(n.cpu().numpy().sum()) / len(q),
+                                "agreement_with_nbnn": float((c.cpu().numpy() == c_nbnn).mean())})
+    return res
+
+
+def run_sections(sections, index, ref, labels, k, m) -> dict:
+    """The requested sections (serving runs elsewhere), each timed outside the
+    headline's timed region."""
+    out = {}
+    for name in sections:
+        t0 = time.perf_counter()
+        if name == "uneven":
+            out[name] = section_uneven(index, ref, k)
+        elif name == "kc":
+            out[name] = section_kc(ref, labels, index)
+        elif name == "caltech101":
+            out[name] = section_caltech101()
+        elif name == "single":
+            out[name] = section_single(index)
+        elif name == "logodds":
+            out[name] = section_logodds(index)
+        else:
+            continue
+        out[name]["about"] = SECTIONS[name]
+        out[name]["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 def list_kind(K1: int) -> int:
@@ -451,9 +668,24 @@ def scan_roofline(prof, n_ref, M, peaks, peak_src, local, shortlist, k: int = 10
         src = f"bf16_tflops_sustained ({peak_src})"
         kernel = ("tc_scan_kernel<FmtBf16, KnnEpilogue<%d>>" % list_kind(k + 1) if local
                   else "tc_scan_kernel<FmtBf16, NbnnEpilogue>")
-    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": kernel, "peak_source": src, "flops_per_launch": flops,
-            "avg_launch_ms": search_ms}
+    out = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": None, "kernel": kernel, "peak_source": src, "flops_per_launch": flops,
+           "avg_launch_ms": search_ms}
+    clk = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
+    if clk:
+        out["peak_sm_mhz"] = clk  # the SM clock the peak was measured at
+    cpt = prof.get("search_cycles_per_tile") or 0.0
+    if cpt > 0:
+        # Clock-free view: SM cycles per 128 x 256 tile against the MMA floor
+        # (BF16: 8 MMAs of K = 16 plus the K-extension, 9 x 128 cycles; E4M3:
+        # 4 MMAs of K = 32 plus the BF16 extension, 5 x 128), and the share of
+        # that floor which is algorithmic work (the extension's 16 of 144, or
+        # 1 of 5 MMAs, is not).
+        floor, algo = (5 * 128, 4 / 5) if shortlist else (9 * 128, 128 / 144)
+        out.update({"kernel_sm_ghz": prof.get("search_sm_clock_ghz"), "cycles_per_tile": cpt,
+                    "mma_floor_cycles_per_tile": floor, "tensor_pipe_frac_at_kernel_clock": floor / cpt,
+                    "algorithmic_frac_at_kernel_clock": floor / cpt * algo})
+    return out
 
 
 def run_serving(index, rates, seconds, k, shortlist, classes_out: dict | None = None) -> dict:

@@ -312,8 +312,12 @@ LNBNN_API lnbnn_status lnbnn_plan_splits(const lnbnn_index *index, int64_t n_que
  * when more than one); where each list lives (list_storage 0: registers, 1:
  * shared memory, 2: a heap in global memory) and how many entries it holds
  * (16, 32 or 64; k1 for a heap); the tile of query rows x references one CTA
- * computes per step; persistent = 1 when a fixed grid of CTAs takes
- * (query tile, split) work items from a queue instead of one CTA per item.
+ * computes per step (tile_m query rows x tile_n references); persistent = 1
+ * when a fixed grid of CTAs takes (query tiles, split) work items from a
+ * queue instead of one CTA per item; bound_per_tile: how the lists of a row
+ * share their bound when there are several splits (1: every tile, as the
+ * splits of a row run at the same time; 0: read when a list starts and
+ * published when it ends, as they run one after another; -1: one split).
  * Errors: INVALID_ARG (null pointers, n_queries < 1), K_RANGE (k1 outside
  * [1, LNBNN_MAX_K + 1] or above n_ref), NO_FP8 (fp8 != 0 on an index without
  * the FP8 operand).
@@ -327,11 +331,35 @@ typedef struct lnbnn_search_plan {
   int32_t tile_m;
   int32_t tile_n;
   int32_t persistent;
-  int32_t reserved;
+  int32_t bound_per_tile;
 } lnbnn_search_plan;
 
 LNBNN_API lnbnn_status lnbnn_plan_search(const lnbnn_index *index, int64_t n_queries, int32_t k1, int32_t fp8,
                                          lnbnn_search_plan *out);
+
+/*
+ * lnbnn_set_schedule fixes parts of the launch schedule of this index's
+ * search scans (every later call; NULL restores the automatic choice of
+ * everything).  It changes speed only, never a result: every schedule gives
+ * bit-identical output.  Fields: splits > 0 fixes the reference split count
+ * (rounded to whole 256-row tiles; 0: automatic); query_tiles 1 or 2 fixes the
+ * tile shape (128 x 256 or 256 x 128 query rows x references per step; 2 is
+ * taken only where the list kind allows it, i.e. not for lists of 33..64
+ * entries; 0: automatic); persistent 1 / 0 a persistent grid with a work
+ * queue / one CTA per work item (-1: automatic); bound_per_tile 1 / 0 how
+ * the lists of a row share their bound (-1: automatic).  A fixed split count
+ * above the automatic range may need more scratch than a workspace made
+ * earlier holds (those calls then return SCRATCH_LIMIT).  Meant for tuning
+ * and tests.  Errors: INVALID_ARG (null index, a field out of range).
+ */
+typedef struct lnbnn_schedule {
+  int32_t splits;
+  int32_t query_tiles;
+  int32_t persistent;
+  int32_t bound_per_tile;
+} lnbnn_schedule;
+
+LNBNN_API lnbnn_status lnbnn_set_schedule(lnbnn_index *index, const lnbnn_schedule *schedule);
 
 /*
  * Host-buffer forms of the classifiers: queries, offsets, totals and

@@ -53,16 +53,27 @@ namespace {
 
 using namespace sm103;
 
-constexpr int kBM = kTcQueryTile;         // query rows per CTA (MMA M)
-constexpr int kBN = kTcRefTile;           // reference rows per tile (MMA N)
+constexpr int kBM = kTcQueryTile;         // query rows per query tile (MMA M)
 constexpr int kBK = 64;                   // BF16 K elements per 128-byte swizzle row
 constexpr int kKChunks = kDim / kBK;      // K-chunks of the BF16 operand (shared memory is laid out for these)
 constexpr int kMmaPerChunk = 4;           // 32-byte K-steps per 128-byte chunk (16 BF16 or 32 E4M3)
 constexpr uint32_t kAChunkBytes = kBM * kBK * 2;     // 16 KB
 constexpr uint32_t kAExtBytes = kBM * kExt * 2;      // 4 KB
-constexpr uint32_t kBChunkBytes = kBN * kBK * 2;     // 32 KB
-constexpr uint32_t kBExtBytes = kBN * kExt * 2;      // 8 KB
-constexpr uint32_t kStageBytes = kBChunkBytes + kBExtBytes;
+
+// Tile shapes: a CTA computes QT query tiles (128 rows each) against a tile
+// of 256 / QT references per step, so every step is 128 x 256 query-reference
+// pairs and its FP32 accumulator takes 256 TMEM columns (QT = 2: the two
+// query tiles' 128 x 128 blocks side by side).  QT = 2 loads each reference
+// tile once for 256 query rows: half the reference bytes per pair.
+template <int QT>
+struct Shape {
+  static_assert(QT == 1 || QT == 2, "one or two query tiles per CTA");
+  static constexpr int kQT = QT;
+  static constexpr int kTileN = kTcRefTile / QT;                 // references per tile (MMA N)
+  static constexpr uint32_t kBChunkBytes = kTileN * kBK * 2;     // 32 or 16 KB
+  static constexpr uint32_t kBExtBytes = kTileN * kExt * 2;      // 8 or 4 KB
+  static constexpr uint32_t kStageBytes = kBChunkBytes + kBExtBytes;
+};
 
 // Threads of a CTA whose epilogue has `epq` warps per TMEM lane quarter: the
 // producer warp, the MMA warp and 4 * epq epilogue warps.
@@ -72,25 +83,28 @@ constexpr int threads_for(int epq) { return 64 + 32 * 4 * epq; }
 constexpr int max_regs_for(int epq) {
   return (16384 / (32 * ((2 + 4 * epq + 3) / 4))) / 8 * 8 > 255 ? 255 : (16384 / (32 * ((2 + 4 * epq + 3) / 4))) / 8 * 8;
 }
-constexpr uint32_t kAccCols = kBN;        // FP32 columns per accumulator
+constexpr uint32_t kAccCols = kTcRefTile;  // FP32 columns per accumulator (one step)
 constexpr uint32_t kTmemCols = 2 * kAccCols;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
 
-// Shared-memory layout of one CTA: the query tile (AChunks 128-byte-swizzle
-// chunks + the 32-byte-swizzle extension), the reference ring (Stages stages,
-// each room for one K-chunk and the extension), the mbarriers, the TMEM
-// address and abort flag, and ListBytes for an epilogue that keeps its lists
-// in shared memory.
-template <int AChunks, int Stages, uint32_t ListBytes>
+// Shared-memory layout of one CTA: QT query tiles (each AChunks
+// 128-byte-swizzle chunks + the 32-byte-swizzle extension), the reference
+// ring (Stages stages, each room for one K-chunk of a reference tile and its
+// extension), the mbarriers, the TMEM address, abort flag and work-item
+// slots, and ListBytes for an epilogue that keeps its lists in shared memory.
+template <int AChunks, int Stages, uint32_t ListBytes, int QT>
 struct Layout {
+  using S = Shape<QT>;
   static constexpr int kStages = Stages;
-  static constexpr uint32_t kOffA = 0;
-  static constexpr uint32_t kOffAExt = kOffA + AChunks * kAChunkBytes;
-  static constexpr uint32_t kOffB = kOffAExt + 1024 * ((kAExtBytes + 1023) / 1024);
-  static constexpr uint32_t kOffBar = kOffB + Stages * kStageBytes;
-  static constexpr int kNumBars = 2 * Stages + 2 + 2 + 2;  // full, empty, tmem full, tmem empty, A, drain
-  static constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;  // TMEM address, abort flag
-  static constexpr uint32_t kOffList = (kOffMisc + 16 + 1023) / 1024 * 1024;
+  static constexpr uint32_t kAQueryBytes = AChunks * kAChunkBytes + 1024 * ((kAExtBytes + 1023) / 1024);
+  static constexpr uint32_t kOffA = 0;  // query tile q at kOffA + q * kAQueryBytes; its extension after its chunks
+  static constexpr uint32_t kOffB = QT * kAQueryBytes;
+  static constexpr uint32_t kOffBar = kOffB + Stages * S::kStageBytes;
+  // full, empty per stage; tmem full, tmem empty per accumulator; A full, A
+  // empty, drain; item full, item empty per item slot
+  static constexpr int kNumBars = 2 * Stages + 2 + 2 + 3 + 2 + 2;
+  static constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;  // TMEM address, abort flag, 2 item slots
+  static constexpr uint32_t kOffList = (kOffMisc + 32 + 1023) / 1024 * 1024;
   static constexpr uint32_t kSmemBytes = kOffList + ListBytes + 1024;  // + alignment slack
   static_assert(Stages % AChunks == 0, "a tile's chunks map to fixed stage parities");
   static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
@@ -101,17 +115,17 @@ struct Layout {
 struct FmtBf16 {  // exact search: 128 BF16 coordinates, two chunks
   static constexpr int kChunks = 2;
   static constexpr bool kExtFirst = false;
-  static constexpr uint32_t kIdesc = idesc_bf16_f32(kBM, kBN);
+  template <int N>
   static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-    mma_bf16(d, a, b, kIdesc, acc);
+    mma_bf16(d, a, b, idesc_bf16_f32(kBM, N), acc);
   }
 };
 struct FmtE4m3 {  // coarse pass: 128 E4M3 coordinates, one chunk
   static constexpr int kChunks = 1;
   static constexpr bool kExtFirst = true;
-  static constexpr uint32_t kIdesc = idesc_e4m3_f32(kBM, kBN);
+  template <int N>
   static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-    mma_f8(d, a, b, kIdesc, acc);
+    mma_f8(d, a, b, idesc_e4m3_f32(kBM, N), acc);
   }
 };
 
@@ -123,13 +137,22 @@ struct Bars {
   __device__ uint32_t tfull(int b) const { return base + 8 * (2 * kStages + b); }
   __device__ uint32_t tempty(int b) const { return base + 8 * (2 * kStages + 2 + b); }
   __device__ uint32_t afull() const { return base + 8 * (2 * kStages + 4); }
-  __device__ uint32_t drain() const { return base + 8 * (2 * kStages + 5); }
+  __device__ uint32_t aempty() const { return base + 8 * (2 * kStages + 5); }
+  __device__ uint32_t drain() const { return base + 8 * (2 * kStages + 6); }
+  __device__ uint32_t ifull(int i) const { return base + 8 * (2 * kStages + 7 + i); }
+  __device__ uint32_t iempty(int i) const { return base + 8 * (2 * kStages + 9 + i); }
 };
 
-// The layout of a kernel instantiation: the format's query chunks; four ring
-// stages, or three when the epilogue's lists take shared memory.
-template <class Fmt, class Epilogue>
-using LayoutOf = Layout<Fmt::kChunks, Epilogue::kListBytes ? (Fmt::kChunks == 2 ? 2 : 3) : 4, Epilogue::kListBytes>;
+// The layout of a kernel instantiation: the format's query chunks; ring
+// stages for two tiles of 256 references (BF16: four chunks, E4M3: two), as
+// many as fit when the epilogue's lists take shared memory (BF16 two, E4M3
+// three), and three or four times as many tiles of 128 references for QT = 2
+// (BF16 six stages, E4M3 eight).
+template <class Fmt, class Epilogue, int QT>
+using LayoutOf = Layout<Fmt::kChunks,
+                        QT == 2 ? (Fmt::kChunks == 2 ? 6 : 8)
+                                : (Epilogue::kListBytes ? (Fmt::kChunks == 2 ? 2 : 3) : 4),
+                        Epilogue::kListBytes, QT>;
 
 __device__ __forceinline__ void flag_timeout(volatile uint32_t* abort_flag, uint32_t* dev_err) {
   *abort_flag = 1u;
@@ -234,6 +257,7 @@ struct ScanOut {
   const int64_t* class_off;  // NBNN: class c owns sorted rows [class_off[c], class_off[c+1])
   const uint32_t* gate;      // null, or a word the producer waits to see nonzero before loading
   int32_t* row_thr;          // kNN: per query row, a shared bound (below), or null
+  bool bound_per_tile;       // row_thr read and published every tile, or at a work item's start and end
 };
 
 // kNN epilogue: the K1 smallest (distance, row) keys of the columns one
@@ -244,11 +268,14 @@ struct ScanOut {
 // bit pattern of a distance at or below which some list already holds K1
 // entries, so a column farther than it cannot be among the row's K1 nearest
 // and is not offered (a column at exactly the bound still is: it may win on
-// its row).  A full list publishes its K1-th distance with an atomic minimum
-// after each tile that improved it, and reads the word once per tile (the
-// read issued at the end of one tile is taken in at the end of the next).  Which columns a
-// list drops depends on timing; the K1 nearest of the row never are, so the
-// merged result does not.
+// its row).  When the lists of a row run at the same time (few query tiles,
+// many splits), a full list publishes its K1-th distance with an atomic
+// minimum after each tile that improved it, and reads the word once per tile
+// (the read issued at the end of one tile is taken in at the end of the
+// next).  When they run one after another (many query tiles: the splits of a
+// row are work items far apart), a list reads the word once when it starts
+// and publishes once when it ends.  Which columns a list drops depends on
+// timing; the K1 nearest of the row never are, so the merged result does not.
 template <int KMAX>
 struct KnnEpilogue {
   static constexpr int kWarpsPerQuarter = KMAX == kTcWideRegListMax ? 1 : 2;
@@ -259,6 +286,7 @@ struct KnnEpilogue {
   int32_t shared;   // the row's shared bound as last read (bit pattern)
   int32_t pending;  // the read in flight for the next tile
   int32_t* rthr;    // the row's shared bound, or null
+  bool per_tile;    // share the bound every tile (else at start and end)
   bool active;
   int K1;
   uint64_t* out;
@@ -268,10 +296,12 @@ struct KnnEpilogue {
         shared(kNoBound),
         pending(kNoBound),
         rthr(act && o.row_thr ? o.row_thr + row : nullptr),
+        per_tile(o.bound_per_tile),
         active(act),
         K1(o.K1),
         out(o.lists + ((int64_t)list * o.stride + (act ? row : 0)) * o.K1) {
     L.init(K1);
+    if (rthr && !per_tile) shared = __ldcg(rthr);
   }
   static constexpr int32_t kNoBound = 0x7F7F7F7F;  // the word's initial value: above every distance
   // One 32-column group: one compare of the group's minimum bit pattern (mn,
@@ -314,7 +344,7 @@ struct KnnEpilogue {
   // in the bound read a tile ago (its latency hidden behind a whole tile), and
   // start the next read.
   __device__ __forceinline__ void tile_end() {
-    if (rthr) {
+    if (rthr && per_tile) {
       if (full() && thr < shared) {
         atomicMin(rthr, thr);
         shared = thr;
@@ -325,6 +355,7 @@ struct KnnEpilogue {
   }
   __device__ __forceinline__ void finish() {
     if (!active) return;
+    if (rthr && !per_tile && full() && thr < shared) atomicMin(rthr, thr);
     if constexpr (KMAX > 0) {
       L.store(out, K1);
     } else {
@@ -358,6 +389,7 @@ struct KnnSmemEpilogue {
   int32_t shared;   // the row's shared bound as last read (as in KnnEpilogue)
   int32_t pending;  // the read in flight
   int32_t* rthr;    // the row's shared bound, or null
+  bool per_tile;    // share the bound every tile (else at start and end)
   bool active;
   int K1;
   int lane;
@@ -370,10 +402,13 @@ struct KnnSmemEpilogue {
         shared(kNoBound),
         pending(kNoBound),
         rthr(act && o.row_thr ? o.row_thr + row : nullptr),
+        per_tile(o.bound_per_tile),
         active(act),
         K1(o.K1),
         lane((int)(threadIdx.x & 31)),
         out(o.lists + ((int64_t)list * o.stride + (act ? row : 0)) * o.K1) {
+    if (rthr && !per_tile) shared = __ldcg(rthr);
+    __syncwarp();  // the previous work item's lists have been read out
     for (int l = 0; l < 32; ++l)
 #pragma unroll
       for (int e = 0; e < kPerLane; ++e) {
@@ -452,7 +487,7 @@ struct KnnSmemEpilogue {
   // As in KnnEpilogue: publish a full list's improved K1-th entry, take in the
   // read from a tile ago, start the next one.
   __device__ __forceinline__ void tile_end() {
-    if (rthr) {
+    if (rthr && per_tile) {
       if (thr != kInf && thr < shared) {
         atomicMin(rthr, thr);
         shared = thr;
@@ -464,6 +499,7 @@ struct KnnSmemEpilogue {
   __device__ __forceinline__ void finish() {
     __syncwarp();
     if (!active) return;
+    if (rthr && !per_tile && thr != kInf && thr < shared) atomicMin(rthr, thr);
     for (int i = 0; i < K1; ++i) {
       const uint32_t bits = D[lane * KM + i];
       out[i] = (int32_t)bits == kInf ? kEmptyKey
@@ -527,19 +563,37 @@ struct NbnnEpilogue {
   __device__ __forceinline__ void finish() { flush(); }
 };
 
-template <class Fmt, class Epilogue>
+// The work of one launch: T query-tile groups (QT query tiles each) x S
+// reference splits = n_items items; item w is group w % T of split w / T
+// (split-major, so the CTAs that run at the same time scan the same split and
+// L2 serves its tiles to all of them).  queue == null: one CTA per item,
+// item = blockIdx.x.  Otherwise a persistent grid: each CTA's producer takes
+// the next item from *queue (zero at launch) with an atomic add and hands it
+// to the CTA's other roles through a two-slot ring in shared memory; no CTA
+// ever waits for another.
+struct Work {
+  int64_t T;
+  int64_t n_items;
+  int64_t split_len;
+  uint32_t* queue;
+};
+
+template <class Fmt, class Epilogue, int QT>
 __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1)
     tc_scan_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_qe,
                    const __grid_constant__ CUtensorMap tmap_r, const __grid_constant__ CUtensorMap tmap_re, int64_t m,
-                   int64_t n_ref, int64_t split_len, ScanOut out, uint32_t* __restrict__ dev_err,
+                   int64_t n_ref, Work work, ScanOut out, uint32_t* __restrict__ dev_err,
                    unsigned long long* __restrict__ stats) {
+  using Sh = Shape<QT>;
   constexpr int KC = Fmt::kChunks;
-  using L = LayoutOf<Fmt, Epilogue>;
+  constexpr int kTileN = Sh::kTileN;
+  using L = LayoutOf<Fmt, Epilogue, QT>;
   constexpr int kStages = L::kStages;
   constexpr int kEpiPerQuarter = Epilogue::kWarpsPerQuarter;  // epilogue warps per TMEM lane quarter
   constexpr int kEpiWarps = 4 * kEpiPerQuarter;
-  constexpr int kEpiCols = kBN / kEpiPerQuarter;  // columns of a tile per epilogue warp
-  constexpr int kRounds = kEpiCols / 64;          // rounds of two 32-column loads per tile
+  constexpr int kEpiCols = kAccCols / kEpiPerQuarter;  // accumulator columns per epilogue warp
+  constexpr int kRounds = kEpiCols / 64;               // rounds of two 32-column loads per tile
+  static_assert(QT == 1 || kEpiPerQuarter == 2, "two query tiles need one epilogue warp per tile and quarter");
   static_assert(KC <= kKChunks, "the query tile fits the chunks shared memory is laid out for");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -547,16 +601,14 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1)
   const Bars<kStages> bars{sbase + L::kOffBar};
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kOffMisc);
   volatile uint32_t* abort_flag = tmem_slot + 1;
+  volatile int64_t* item_slot = reinterpret_cast<volatile int64_t*>(smem + L::kOffMisc + 16);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * kBM;
-  const int64_t j_begin = (int64_t)blockIdx.y * split_len;
-  const int64_t j_end = min(j_begin + split_len, n_ref);
+  const bool persistent = work.queue != nullptr;
   // A timeout reported earlier and not yet collected by lnbnn_sync: scan no
-  // tiles.
+  // tiles (every item's lists are still written, empty).
   const bool stale_timeout = (*reinterpret_cast<volatile uint32_t*>(dev_err) & kDevErrTimeout) != 0;
-  const int ntiles = stale_timeout ? 0 : (int)((j_end - j_begin + kBN - 1) / kBN);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -566,8 +618,11 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(bars.tfull(b), 1);
       mbar_init(bars.tempty(b), 32 * kEpiWarps);
+      mbar_init(bars.ifull(b), 1);
+      mbar_init(bars.iempty(b), 1 + kEpiWarps);  // the MMA thread and each epilogue warp
     }
     mbar_init(bars.afull(), 1);
+    mbar_init(bars.aempty(), 1);
     mbar_init(bars.drain(), 1);
     *abort_flag = 0u;
     fence_barrier_init();
@@ -578,46 +633,96 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
+  // Item i of this CTA for the MMA and epilogue roles (the producer publishes
+  // it in the persistent form); n_items means no more work.
+  auto consume_item = [&](int i, int64_t* w) -> bool {
+    if (!persistent) {
+      *w = i == 0 ? (int64_t)blockIdx.x : work.n_items;
+      return true;
+    }
+    const int slot = i & 1;
+    if (!mbar_wait(bars.ifull(slot), (uint32_t)((i >> 1) & 1), kWaitLimitNs, abort_flag)) return false;
+    *w = item_slot[slot];
+    return true;
+  };
+  auto item_tiles = [&](int64_t w, int64_t* m0, int64_t* j_begin) -> int {
+    const int64_t x = w % work.T, y = w / work.T;
+    *m0 = x * (int64_t)(kBM * QT);
+    *j_begin = y * work.split_len;
+    const int64_t j_end = min(*j_begin + work.split_len, n_ref);
+    return stale_timeout ? 0 : (int)((j_end - *j_begin + kTileN - 1) / kTileN);
+  };
+
   if (warp == 0) {
     if (lane == 0) {
       // ------------------------------------------------------------ producer
       // an optional start gate; with nothing loaded the other roles' waits
       // run out on the abort flag
       bool go = true;
-      if (out.gate != nullptr && ntiles > 0 && !wait_gate(out.gate, kWaitLimitNs, abort_flag)) {
+      if (out.gate != nullptr && !stale_timeout && !wait_gate(out.gate, kWaitLimitNs, abort_flag)) {
         flag_timeout(abort_flag, dev_err);
         go = false;
       }
-      if (go) {
-        prefetch_tmap(&tmap_q);
-        prefetch_tmap(&tmap_qe);
-        prefetch_tmap(&tmap_r);
-        prefetch_tmap(&tmap_re);
-        mbar_arrive_expect_tx(bars.afull(), KC * kAChunkBytes + kAExtBytes);
-        for (int kc = 0; kc < KC; ++kc)
-          tma_load_2d(sbase + L::kOffA + kc * kAChunkBytes, &tmap_q, kc * kBK, (int32_t)m0, bars.afull());
-        tma_load_2d(sbase + L::kOffAExt, &tmap_qe, 0, (int32_t)m0, bars.afull());
-      }
-      int it = 0;
-      for (int t = 0; go && t < ntiles && !*abort_flag; ++t) {
-        const int32_t row = (int32_t)(j_begin + (int64_t)t * kBN);
-        for (int kc = 0; kc < KC; ++kc, ++it) {
-          const int s = it % kStages;
-          const uint32_t round = (uint32_t)(it / kStages);
-          if (!mbar_wait(bars.empty(s), (round & 1u) ^ 1u, kWaitLimitNs, abort_flag)) {
+      prefetch_tmap(&tmap_q);
+      prefetch_tmap(&tmap_qe);
+      prefetch_tmap(&tmap_r);
+      prefetch_tmap(&tmap_re);
+      int it = 0;       // reference K-chunks issued
+      int a_loads = 0;  // query tiles issued
+      for (int i = 0; go; ++i) {
+        int64_t w;
+        if (persistent) {
+          const int slot = i & 1;
+          if (i >= 2 && !mbar_wait(bars.iempty(slot), (uint32_t)(((i >> 1) - 1) & 1), kWaitLimitNs, abort_flag)) {
             flag_timeout(abort_flag, dev_err);
             break;
           }
-          const uint32_t dst = sbase + L::kOffB + s * kStageBytes;
-          const bool last = kc == KC - 1;
-          mbar_arrive_expect_tx(bars.full(s), kBChunkBytes + (last ? kBExtBytes : 0u));
-          tma_load_2d(dst, &tmap_r, kc * kBK, row, bars.full(s));
-          if (last) tma_load_2d(dst + kBChunkBytes, &tmap_re, 0, row, bars.full(s));
+          w = *abort_flag ? work.n_items : (int64_t)atomicAdd(work.queue, 1u);
+          if (w > work.n_items) w = work.n_items;
+          item_slot[slot] = w;
+          mbar_arrive(bars.ifull(slot));
+        } else {
+          w = i == 0 ? (int64_t)blockIdx.x : work.n_items;
         }
+        if (w >= work.n_items) break;
+        int64_t m0, j_begin;
+        const int ntiles = item_tiles(w, &m0, &j_begin);
+        // the query tiles: once the previous item's MMAs have read theirs
+        if (a_loads > 0 && !mbar_wait(bars.aempty(), (uint32_t)((a_loads - 1) & 1), kWaitLimitNs, abort_flag)) {
+          flag_timeout(abort_flag, dev_err);
+          break;
+        }
+        mbar_arrive_expect_tx(bars.afull(), QT * (KC * kAChunkBytes + kAExtBytes));
+        for (int q = 0; q < QT; ++q) {
+          const uint32_t a = sbase + L::kOffA + q * L::kAQueryBytes;
+          const int32_t qrow = (int32_t)(m0 + q * kBM);
+          for (int kc = 0; kc < KC; ++kc) tma_load_2d(a + kc * kAChunkBytes, &tmap_q, kc * kBK, qrow, bars.afull());
+          tma_load_2d(a + KC * kAChunkBytes, &tmap_qe, 0, qrow, bars.afull());
+        }
+        ++a_loads;
+        bool ok = true;
+        for (int t = 0; ok && t < ntiles && !*abort_flag; ++t) {
+          const int32_t row = (int32_t)(j_begin + (int64_t)t * kTileN);
+          for (int kc = 0; kc < KC; ++kc, ++it) {
+            const int s = it % kStages;
+            const uint32_t round = (uint32_t)(it / kStages);
+            if (!mbar_wait(bars.empty(s), (round & 1u) ^ 1u, kWaitLimitNs, abort_flag)) {
+              flag_timeout(abort_flag, dev_err);
+              ok = false;
+              break;
+            }
+            const uint32_t dst = sbase + L::kOffB + s * Sh::kStageBytes;
+            const bool last = kc == KC - 1;
+            mbar_arrive_expect_tx(bars.full(s), Sh::kBChunkBytes + (last ? Sh::kBExtBytes : 0u));
+            tma_load_2d(dst, &tmap_r, kc * kBK, row, bars.full(s));
+            if (last) tma_load_2d(dst + Sh::kBChunkBytes, &tmap_re, 0, row, bars.full(s));
+          }
+        }
+        if (!ok || *abort_flag) break;
       }
       // every load issued must land before the CTA may exit
       const uint32_t never = 0;
-      if (go) mbar_wait(bars.afull(), 0, kWaitLimitNs, &never);
+      if (a_loads > 0) mbar_wait(bars.afull(), (uint32_t)((a_loads - 1) & 1), kWaitLimitNs, &never);
       for (int s = 0; s < kStages; ++s) {
         const int issued = it / kStages + (s < it % kStages ? 1 : 0);
         if (issued > 0) mbar_wait(bars.full(s), (uint32_t)((issued - 1) & 1), kWaitLimitNs, &never);
@@ -628,45 +733,69 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1)
       // ---------------------------------------------------------- MMA issuer
       const long long clk0 = clock64();
       const uint64_t ns0 = globaltimer_ns();
-      bool ok = mbar_wait(bars.afull(), 0, kWaitLimitNs, abort_flag);
-      if (!ok) flag_timeout(abort_flag, dev_err);
-      tc_fence_after();
-      int it = 0;
-      for (int t = 0; ok && t < ntiles && !*abort_flag; ++t) {
-        const int b = t & 1;
-        const uint32_t use = (uint32_t)(t >> 1);
-        if (!mbar_wait(bars.tempty(b), (use & 1u) ^ 1u, kWaitLimitNs, abort_flag)) {
+      int it = 0;       // reference K-chunks consumed
+      int tg = 0;       // tiles over all items (accumulator use)
+      int64_t tiles_done = 0;
+      bool ok = true;
+      for (int i = 0; ok; ++i) {
+        int64_t w;
+        if (!consume_item(i, &w)) {
+          flag_timeout(abort_flag, dev_err);
+          break;
+        }
+        if (w >= work.n_items) break;
+        int64_t m0, j_begin;
+        const int ntiles = item_tiles(w, &m0, &j_begin);
+        if (!mbar_wait(bars.afull(), (uint32_t)(i & 1), kWaitLimitNs, abort_flag)) {
           flag_timeout(abort_flag, dev_err);
           break;
         }
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + b * kAccCols;
-        for (int kc = 0; kc < KC; ++kc, ++it) {
-          const int s = it % kStages;
-          const uint32_t round = (uint32_t)(it / kStages);
-          if (!mbar_wait(bars.full(s), round & 1u, kWaitLimitNs, abort_flag)) {
+        for (int t = 0; ok && t < ntiles && !*abort_flag; ++t, ++tg) {
+          const int b = tg & 1;
+          const uint32_t use = (uint32_t)(tg >> 1);
+          if (!mbar_wait(bars.tempty(b), (use & 1u) ^ 1u, kWaitLimitNs, abort_flag)) {
             flag_timeout(abort_flag, dev_err);
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a_base = sbase + L::kOffA + kc * kAChunkBytes;
-          const uint32_t b_base = sbase + L::kOffB + s * kStageBytes;
-          const bool last = kc == KC - 1;  // the norms' K-extension rides with the last chunk
-          if (Fmt::kExtFirst && last)
-            mma_bf16(d_tmem, sw32_kmajor_desc(sbase + L::kOffAExt), sw32_kmajor_desc(b_base + kBChunkBytes),
-                     FmtBf16::kIdesc, kc != 0 ? 1u : 0u);
+          const uint32_t d_tmem = tmem_base + b * kAccCols;
+          for (int kc = 0; kc < KC; ++kc, ++it) {
+            const int s = it % kStages;
+            const uint32_t round = (uint32_t)(it / kStages);
+            if (!mbar_wait(bars.full(s), round & 1u, kWaitLimitNs, abort_flag)) {
+              flag_timeout(abort_flag, dev_err);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t b_base = sbase + L::kOffB + s * Sh::kStageBytes;
+            const bool last = kc == KC - 1;  // the norms' K-extension rides with the last chunk
 #pragma unroll
-          for (int kk = 0; kk < kMmaPerChunk; ++kk) {
-            Fmt::mma(d_tmem, sw128_kmajor_desc(a_base + kk * 32), sw128_kmajor_desc(b_base + kk * 32),
-                     (kc | kk) != 0 || (Fmt::kExtFirst && last) ? 1u : 0u);
+            for (int q = 0; q < QT; ++q) {
+              const uint32_t a_q = sbase + L::kOffA + q * L::kAQueryBytes;
+              const uint32_t d_q = d_tmem + q * kTileN;
+              if (Fmt::kExtFirst && last)
+                mma_bf16(d_q, sw32_kmajor_desc(a_q + KC * kAChunkBytes), sw32_kmajor_desc(b_base + Sh::kBChunkBytes),
+                         idesc_bf16_f32(kBM, kTileN), kc != 0 ? 1u : 0u);
+#pragma unroll
+              for (int kk = 0; kk < kMmaPerChunk; ++kk) {
+                Fmt::template mma<kTileN>(d_q, sw128_kmajor_desc(a_q + kc * kAChunkBytes + kk * 32),
+                                          sw128_kmajor_desc(b_base + kk * 32),
+                                          (kc | kk) != 0 || (Fmt::kExtFirst && last) ? 1u : 0u);
+              }
+              if (!Fmt::kExtFirst && last)
+                mma_bf16(d_q, sw32_kmajor_desc(a_q + KC * kAChunkBytes), sw32_kmajor_desc(b_base + Sh::kBChunkBytes),
+                         idesc_bf16_f32(kBM, kTileN), 1u);
+            }
+            mma_commit(bars.empty(s));  // the producer may refill this stage
           }
-          if (!Fmt::kExtFirst && last)
-            mma_bf16(d_tmem, sw32_kmajor_desc(sbase + L::kOffAExt), sw32_kmajor_desc(b_base + kBChunkBytes),
-                     FmtBf16::kIdesc, 1u);
-          mma_commit(bars.empty(s));  // the producer may refill this stage
+          if (ok) mma_commit(bars.tfull(b));
         }
-        if (ok) mma_commit(bars.tfull(b));
+        tiles_done += ntiles;
+        mma_commit(bars.aempty());  // the query tiles may be replaced once these MMAs are done
+        if (persistent) mbar_arrive(bars.iempty(i & 1));
       }
       // all MMAs issued by this thread must finish before TMEM is released
       const uint32_t never = 0;
@@ -675,49 +804,69 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1)
       if (stats) {
         atomicAdd(stats + 0, (unsigned long long)(clock64() - clk0));
         atomicAdd(stats + 1, (unsigned long long)(globaltimer_ns() - ns0));
-        atomicAdd(stats + 2, (unsigned long long)ntiles);
+        atomicAdd(stats + 2, (unsigned long long)tiles_done);
         atomicAdd(stats + 3, 1ull);
       }
     }
   } else {
     // ------------------------------------------------------------- epilogue
     const int quarter = warp & 3;          // this warp may read TMEM lanes [32*quarter, 32*quarter+32)
-    const int half = (warp - 2) >> 2;      // its column slice of every tile
-    const int64_t row = m0 + quarter * 32 + lane;
-    const bool active = row < m;
-    Epilogue epi(out, (int)blockIdx.y * kEpiPerQuarter + half, row, active, j_begin + half * kEpiCols,
-                 smem + L::kOffList, warp - 2);
+    const int half = (warp - 2) >> 2;      // QT = 1: its column half of every tile; QT = 2: its query tile
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-    for (int t = 0; t < ntiles; ++t) {
-      const int b = t & 1;
-      const uint32_t use = (uint32_t)(t >> 1);
-      if (!mbar_wait(bars.tfull(b), use & 1u, kWaitLimitNs, abort_flag)) {
+    int tg = 0;
+    for (int i = 0;; ++i) {
+      int64_t w;
+      if (!consume_item(i, &w)) {
         flag_timeout(abort_flag, dev_err);
         break;
       }
-      tc_fence_after();
-      // rounds of 64 columns; the accumulator goes back as soon as the last
-      // round is in registers
-      const uint32_t taddr = tmem_base + lane_addr + b * kAccCols + half * kEpiCols;
-      const int64_t col0 = j_begin + (int64_t)t * kBN + half * kEpiCols;
-#pragma unroll
-      for (int r = 0; r < kRounds; ++r) {
-        uint32_t v0[32], v1[32], mn0, mn1;
-        tmem_ld_min_32x32b_x32(taddr + 64 * r, v0, mn0);
-        tmem_ld_min_32x32b_x32(taddr + 64 * r + 32, v1, mn1);
-        tmem_ld_wait(v0, mn0);
-        reg_fence(v1);
-        asm volatile("" : "+r"(mn1));
-        if (r == kRounds - 1) {
-          tc_fence_before();
-          mbar_arrive(bars.tempty(b));
+      if (w >= work.n_items) break;
+      int64_t m0, j_begin;
+      const int ntiles = item_tiles(w, &m0, &j_begin);
+      const int64_t y = w / work.T;
+      const int64_t row = m0 + (QT == 2 ? half * kBM : 0) + quarter * 32 + lane;
+      const int64_t c_off = QT == 2 ? 0 : half * kEpiCols;  // this warp's first column within a tile
+      const int list = QT == 2 ? (int)y : (int)y * kEpiPerQuarter + half;
+      const bool active = row < m;
+      Epilogue epi(out, list, row, active, j_begin + c_off, smem + L::kOffList, warp - 2);
+      bool ok = true;
+      for (int t = 0; t < ntiles; ++t, ++tg) {
+        const int b = tg & 1;
+        const uint32_t use = (uint32_t)(tg >> 1);
+        if (!mbar_wait(bars.tfull(b), use & 1u, kWaitLimitNs, abort_flag)) {
+          flag_timeout(abort_flag, dev_err);
+          ok = false;
+          break;
         }
-        epi.group(v0, mn0, col0 + 64 * r);
-        epi.group(v1, mn1, col0 + 64 * r + 32);
+        tc_fence_after();
+        // rounds of 64 columns; the accumulator goes back as soon as the last
+        // round is in registers
+        const uint32_t taddr = tmem_base + lane_addr + b * kAccCols + half * kEpiCols;
+        const int64_t col0 = j_begin + (int64_t)t * kTileN + c_off;
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+          uint32_t v0[32], v1[32], mn0, mn1;
+          tmem_ld_min_32x32b_x32(taddr + 64 * r, v0, mn0);
+          tmem_ld_min_32x32b_x32(taddr + 64 * r + 32, v1, mn1);
+          tmem_ld_wait(v0, mn0);
+          reg_fence(v1);
+          asm volatile("" : "+r"(mn1));
+          if (r == kRounds - 1) {
+            tc_fence_before();
+            mbar_arrive(bars.tempty(b));
+          }
+          epi.group(v0, mn0, col0 + 64 * r);
+          epi.group(v1, mn1, col0 + 64 * r + 32);
+        }
+        epi.tile_end();
       }
-      epi.tile_end();
+      epi.finish();
+      if (!ok) break;
+      if (persistent) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bars.iempty(i & 1));
+      }
     }
-    epi.finish();
   }
 
   tc_fence_before();
@@ -781,148 +930,178 @@ bool encode_operand(CUtensorMap* main, CUtensorMap* ext, const void* bf, const v
 
 bool make_tc_tensor_maps(const __nv_bfloat16* ref_bf, const __nv_bfloat16* sref_bf, const __nv_bfloat16* ref_ext,
                          const __nv_bfloat16* sref_ext, int64_t n_pad, TcTensorMaps* out) {
-  return encode_operand(&out->ref, &out->ref_ext, ref_bf, ref_ext, (uint64_t)n_pad, kBN) &&
-         encode_operand(&out->sref, &out->sref_ext, sref_bf, sref_ext, (uint64_t)n_pad, kBN);
+  return encode_operand(&out->ref, &out->ref_ext, ref_bf, ref_ext, (uint64_t)n_pad, Shape<1>::kTileN) &&
+         encode_operand(&out->sref, &out->sref_ext, sref_bf, sref_ext, (uint64_t)n_pad, Shape<1>::kTileN) &&
+         encode_operand(&out->ref_h, &out->ref_ext_h, ref_bf, ref_ext, (uint64_t)n_pad, Shape<2>::kTileN) &&
+         encode_operand(&out->sref_h, &out->sref_ext_h, sref_bf, sref_ext, (uint64_t)n_pad, Shape<2>::kTileN);
 }
 
 bool make_tc_tensor_maps_e4m3(const uint8_t* ref_f8, const __nv_bfloat16* ref_f8_ext, int64_t n_pad,
                               TcTensorMaps* out) {
-  return encode_e4m3(&out->f8, ref_f8, (uint64_t)n_pad, kBN) &&
-         encode_bf16(&out->f8_ext, ref_f8_ext, (uint64_t)n_pad, kExt, kExt, kBN, CU_TENSOR_MAP_SWIZZLE_32B);
+  return encode_e4m3(&out->f8, ref_f8, (uint64_t)n_pad, Shape<1>::kTileN) &&
+         encode_bf16(&out->f8_ext, ref_f8_ext, (uint64_t)n_pad, kExt, kExt, Shape<1>::kTileN,
+                     CU_TENSOR_MAP_SWIZZLE_32B) &&
+         encode_e4m3(&out->f8_h, ref_f8, (uint64_t)n_pad, Shape<2>::kTileN) &&
+         encode_bf16(&out->f8_ext_h, ref_f8_ext, (uint64_t)n_pad, kExt, kExt, Shape<2>::kTileN,
+                     CU_TENSOR_MAP_SWIZZLE_32B);
 }
 
 namespace {
 
-template <class Fmt, class Epilogue>
+template <class Fmt, class Epilogue, int QT>
 cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const void* qop,
                         const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
                         int64_t split_len, const ScanOut& out, uint32_t* dev_err, unsigned long long* stats,
-                        cudaStream_t s) {
+                        const TcSched& sched, cudaStream_t s) {
   if (m == 0) return cudaSuccess;
-  if (m_pad % kBM != 0 || split_len % kBN != 0) return cudaErrorInvalidValue;
+  if (m_pad % kBM != 0 || split_len % kTcRefTile != 0 || splits < 1) return cudaErrorInvalidValue;
+  if (sched.persistent_ctas > 0 && sched.queue == nullptr) return cudaErrorInvalidValue;
   CUtensorMap tq, tqe;
   const bool ok = Fmt::kChunks == 1
                       ? encode_e4m3(&tq, qop, (uint64_t)m_pad, kBM) &&
                             encode_bf16(&tqe, qext, (uint64_t)m_pad, kExt, kExt, kBM, CU_TENSOR_MAP_SWIZZLE_32B)
                       : encode_operand(&tq, &tqe, qop, qext, (uint64_t)m_pad, kBM);
   if (!ok) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)(m_pad / kBM), (unsigned)splits);
-  tc_scan_kernel<Fmt, Epilogue><<<grid, threads_for(Epilogue::kWarpsPerQuarter), LayoutOf<Fmt, Epilogue>::kSmemBytes, s>>>(
-      tq, tqe, tr, tre, m, n_ref, split_len, out,
-                                                                   dev_err, stats);
+  Work work;
+  work.T = (m_pad + kBM * QT - 1) / (kBM * QT);
+  work.n_items = work.T * splits;
+  work.split_len = split_len;
+  work.queue = sched.persistent_ctas > 0 ? sched.queue : nullptr;
+  if (work.n_items > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
+  const int64_t grid = work.queue ? std::min<int64_t>(work.n_items, sched.persistent_ctas) : work.n_items;
+  tc_scan_kernel<Fmt, Epilogue, QT>
+      <<<(unsigned)grid, threads_for(Epilogue::kWarpsPerQuarter), LayoutOf<Fmt, Epilogue, QT>::kSmemBytes, s>>>(
+          tq, tqe, tr, tre, m, n_ref, work, out, dev_err, stats);
   return cudaGetLastError();
 }
 
-template <class Fmt, class Epilogue>
+template <class Fmt, class Epilogue, int QT>
 cudaError_t prepare_one() {
   cudaFuncAttributes a;
-  cudaError_t e = cudaFuncGetAttributes(&a, tc_scan_kernel<Fmt, Epilogue>);
+  cudaError_t e = cudaFuncGetAttributes(&a, tc_scan_kernel<Fmt, Epilogue, QT>);
   if (e != cudaSuccess) return e;
   if (a.numRegs > max_regs_for(Epilogue::kWarpsPerQuarter)) return cudaErrorInvalidKernelImage;
-  return cudaFuncSetAttribute(tc_scan_kernel<Fmt, Epilogue>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)LayoutOf<Fmt, Epilogue>::kSmemBytes);
+  return cudaFuncSetAttribute(tc_scan_kernel<Fmt, Epilogue, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)LayoutOf<Fmt, Epilogue, QT>::kSmemBytes);
+}
+
+// One list kind's kernel for the tile shape the schedule asks for (two query
+// tiles per CTA only where the epilogue has two warps per lane quarter).
+template <class Fmt, class Epilogue>
+cudaError_t launch_shape(const TcTensorMaps& maps, bool sorted_copy, const void* qop, const __nv_bfloat16* qext,
+                         int64_t m, int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, const ScanOut& out,
+                         uint32_t* dev_err, unsigned long long* stats, const TcSched& sched, cudaStream_t s) {
+  constexpr bool coarse = Fmt::kChunks == 1;
+  if constexpr (Epilogue::kWarpsPerQuarter == 2) {
+    if (sched.qt == 2) {
+      const CUtensorMap& tr = coarse ? maps.f8_h : (sorted_copy ? maps.sref_h : maps.ref_h);
+      const CUtensorMap& tre = coarse ? maps.f8_ext_h : (sorted_copy ? maps.sref_ext_h : maps.ref_ext_h);
+      return launch_scan<Fmt, Epilogue, 2>(tr, tre, qop, qext, m, m_pad, n_ref, splits, split_len, out, dev_err,
+                                           stats, sched, s);
+    }
+  }
+  if (sched.qt != 1) return cudaErrorInvalidValue;
+  const CUtensorMap& tr = coarse ? maps.f8 : (sorted_copy ? maps.sref : maps.ref);
+  const CUtensorMap& tre = coarse ? maps.f8_ext : (sorted_copy ? maps.sref_ext : maps.ref_ext);
+  return launch_scan<Fmt, Epilogue, 1>(tr, tre, qop, qext, m, m_pad, n_ref, splits, split_len, out, dev_err, stats,
+                                       sched, s);
+}
+
+template <class Fmt, class Epilogue>
+cudaError_t prepare_both() {
+  cudaError_t e = prepare_one<Fmt, Epilogue, 1>();
+  if constexpr (Epilogue::kWarpsPerQuarter == 2) {
+    if (e == cudaSuccess) e = prepare_one<Fmt, Epilogue, 2>();
+  }
+  return e;
+}
+
+// The kNN scan with the list kind for K1 and the split length.
+template <class Fmt>
+cudaError_t launch_lists(const TcTensorMaps& maps, bool sorted_copy, const void* qop, const __nv_bfloat16* qext,
+                         int64_t m, int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int K1,
+                         const ScanOut& out, uint32_t* dev_err, unsigned long long* stats, const TcSched& sched,
+                         cudaStream_t s) {
+  switch (tc_list_kind(K1, split_len, Fmt::kChunks == 1)) {
+    case ListKind::Reg16:
+      return launch_shape<Fmt, KnnEpilogue<kTcRegListMax>>(maps, sorted_copy, qop, qext, m, m_pad, n_ref, splits,
+                                                           split_len, out, dev_err, stats, sched, s);
+    case ListKind::Reg32:
+      return launch_shape<Fmt, KnnEpilogue<kTcCoarseRegListMax>>(maps, sorted_copy, qop, qext, m, m_pad, n_ref,
+                                                                 splits, split_len, out, dev_err, stats, sched, s);
+    case ListKind::Smem64:
+      return launch_shape<Fmt, KnnSmemEpilogue<kTcWideRegListMax>>(maps, sorted_copy, qop, qext, m, m_pad, n_ref,
+                                                                   splits, split_len, out, dev_err, stats, sched, s);
+    case ListKind::Reg64:
+      if constexpr (Fmt::kChunks == 2)
+        return launch_shape<Fmt, KnnEpilogue<kTcWideRegListMax>>(maps, sorted_copy, qop, qext, m, m_pad, n_ref,
+                                                                 splits, split_len, out, dev_err, stats, sched, s);
+      return cudaErrorInvalidValue;
+    case ListKind::Heap:
+      break;
+  }
+  return launch_shape<Fmt, KnnEpilogue<0>>(maps, sorted_copy, qop, qext, m, m_pad, n_ref, splits, split_len, out,
+                                           dev_err, stats, sched, s);
 }
 
 }  // namespace
 
 cudaError_t prepare_tc_kernels() {
-  cudaError_t e = prepare_one<FmtBf16, KnnEpilogue<kTcRegListMax>>();
-  if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnEpilogue<kTcCoarseRegListMax>>();
-  if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnSmemEpilogue<kTcWideRegListMax>>();
-  if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnEpilogue<kTcWideRegListMax>>();
-  if (e == cudaSuccess) e = prepare_one<FmtBf16, KnnEpilogue<0>>();
-  if (e == cudaSuccess) e = prepare_one<FmtBf16, NbnnEpilogue>();
-  if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<kTcRegListMax>>();
-  if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<kTcCoarseRegListMax>>();
-  if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnSmemEpilogue<kTcWideRegListMax>>();
-  if (e == cudaSuccess) e = prepare_one<FmtE4m3, KnnEpilogue<0>>();
+  cudaError_t e = prepare_both<FmtBf16, KnnEpilogue<kTcRegListMax>>();
+  if (e == cudaSuccess) e = prepare_both<FmtBf16, KnnEpilogue<kTcCoarseRegListMax>>();
+  if (e == cudaSuccess) e = prepare_both<FmtBf16, KnnSmemEpilogue<kTcWideRegListMax>>();
+  if (e == cudaSuccess) e = prepare_both<FmtBf16, KnnEpilogue<kTcWideRegListMax>>();
+  if (e == cudaSuccess) e = prepare_both<FmtBf16, KnnEpilogue<0>>();
+  if (e == cudaSuccess) e = prepare_both<FmtBf16, NbnnEpilogue>();
+  if (e == cudaSuccess) e = prepare_both<FmtE4m3, KnnEpilogue<kTcRegListMax>>();
+  if (e == cudaSuccess) e = prepare_both<FmtE4m3, KnnEpilogue<kTcCoarseRegListMax>>();
+  if (e == cudaSuccess) e = prepare_both<FmtE4m3, KnnSmemEpilogue<kTcWideRegListMax>>();
+  if (e == cudaSuccess) e = prepare_both<FmtE4m3, KnnEpilogue<0>>();
   return e;
 }
 
 cudaError_t launch_knn_tc(const TcTensorMaps& maps, bool sorted_copy, const __nv_bfloat16* qbf,
                           const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
                           int64_t split_len, int K1, uint64_t* lists, int64_t stride, int32_t* row_thr,
-                          uint32_t* dev_err, unsigned long long* stats, const uint32_t* gate, cudaStream_t s) {
+                          uint32_t* dev_err, unsigned long long* stats, const uint32_t* gate, const TcSched& sched,
+                          cudaStream_t s) {
   ScanOut out{};
   out.gate = gate;
   out.row_thr = row_thr;
+  out.bound_per_tile = sched.bound_per_tile;
   out.lists = lists;
   out.stride = stride;
   out.K1 = K1;
-  const CUtensorMap& tr = sorted_copy ? maps.sref : maps.ref;
-  const CUtensorMap& tre = sorted_copy ? maps.sref_ext : maps.ref_ext;
-  switch (tc_list_kind(K1, split_len, false)) {
-    case ListKind::Reg16:
-      return launch_scan<FmtBf16, KnnEpilogue<kTcRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len,
-                                                              out, dev_err, stats, s);
-    case ListKind::Reg32:
-      return launch_scan<FmtBf16, KnnEpilogue<kTcCoarseRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
-                                                                    split_len, out, dev_err, stats, s);
-    case ListKind::Smem64:
-      return launch_scan<FmtBf16, KnnSmemEpilogue<kTcWideRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
-                                                                      split_len, out, dev_err, stats, s);
-    case ListKind::Reg64:
-      return launch_scan<FmtBf16, KnnEpilogue<kTcWideRegListMax>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits,
-                                                                  split_len, out, dev_err, stats, s);
-    case ListKind::Heap:
-      break;
-  }
-  return launch_scan<FmtBf16, KnnEpilogue<0>>(tr, tre, qbf, qext, m, m_pad, n_ref, splits, split_len, out, dev_err,
-                                              stats, s);
+  return launch_lists<FmtBf16>(maps, sorted_copy, qbf, qext, m, m_pad, n_ref, splits, split_len, K1, out, dev_err,
+                               stats, sched, s);
 }
-
-namespace {
-
-template <class Fmt>
-cudaError_t launch_coarse_fmt(const CUtensorMap& tr, const CUtensorMap& tre, const uint8_t* qf8,
-                              const __nv_bfloat16* qext, int64_t m, int64_t m_pad, int64_t n_ref, int splits,
-                              int64_t split_len, int K1, const ScanOut& out, uint32_t* dev_err,
-                              unsigned long long* stats, cudaStream_t s) {
-  switch (tc_list_kind(K1, split_len, true)) {
-    case ListKind::Reg16:
-      return launch_scan<Fmt, KnnEpilogue<kTcRegListMax>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits, split_len,
-                                                          out, dev_err, stats, s);
-    case ListKind::Reg32:
-      return launch_scan<Fmt, KnnEpilogue<kTcCoarseRegListMax>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits,
-                                                                split_len, out, dev_err, stats, s);
-    case ListKind::Smem64:
-    case ListKind::Reg64:
-      return launch_scan<Fmt, KnnSmemEpilogue<kTcWideRegListMax>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits,
-                                                                  split_len, out, dev_err, stats, s);
-    case ListKind::Heap:
-      break;
-  }
-  return launch_scan<Fmt, KnnEpilogue<0>>(tr, tre, qf8, qext, m, m_pad, n_ref, splits, split_len, out, dev_err, stats,
-                                          s);
-}
-
-}  // namespace
 
 cudaError_t launch_coarse_tc(const TcTensorMaps& maps, const uint8_t* qf8, const __nv_bfloat16* qext,
                              int64_t m, int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int K1,
                              uint64_t* lists, int64_t stride, int32_t* row_thr, uint32_t* dev_err,
-                             unsigned long long* stats, const uint32_t* gate, cudaStream_t s) {
+                             unsigned long long* stats, const uint32_t* gate, const TcSched& sched, cudaStream_t s) {
   ScanOut out{};
   out.gate = gate;
   out.row_thr = row_thr;
+  out.bound_per_tile = sched.bound_per_tile;
   out.lists = lists;
   out.stride = stride;
   out.K1 = K1;
-  return launch_coarse_fmt<FmtE4m3>(maps.f8, maps.f8_ext, qf8, qext, m, m_pad, n_ref, splits, split_len, K1, out,
-                                    dev_err, stats, s);
+  return launch_lists<FmtE4m3>(maps, false, qf8, qext, m, m_pad, n_ref, splits, split_len, K1, out, dev_err, stats,
+                               sched, s);
 }
 
 cudaError_t launch_nbnn_tc(const TcTensorMaps& maps, const __nv_bfloat16* qbf, const __nv_bfloat16* qext, int64_t m,
                            int64_t m_pad, int64_t n_ref, int splits, int64_t split_len, int32_t* mins, int32_t C,
                            const int64_t* class_off, uint32_t* dev_err, unsigned long long* stats,
-                           const uint32_t* gate, cudaStream_t s) {
+                           const uint32_t* gate, const TcSched& sched, cudaStream_t s) {
   ScanOut out{};
   out.gate = gate;
   out.mins = mins;
   out.C = C;
   out.class_off = class_off;
-  return launch_scan<FmtBf16, NbnnEpilogue>(maps.sref, maps.sref_ext, qbf, qext, m, m_pad, n_ref, splits, split_len,
-                                            out, dev_err, stats, s);
+  return launch_shape<FmtBf16, NbnnEpilogue>(maps, true, qbf, qext, m, m_pad, n_ref, splits, split_len, out, dev_err,
+                                             stats, sched, s);
 }
 
 }  // namespace lnbnn

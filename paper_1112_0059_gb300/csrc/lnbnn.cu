@@ -50,6 +50,7 @@ struct lnbnn_index {
   bool fp8 = false;
   TcTensorMaps tc;  // tensor maps over ref_bf / sref_bf (and ref_f8) for the tensor-core kernels
   SplitModel split_model;  // split-N schedule (defaults, or fitted by lnbnn_autotune)
+  lnbnn_schedule sched{0, 0, -1, -1};  // lnbnn_set_schedule: fixed choices (0 / -1: automatic)
   const uint32_t* gate = nullptr;  // lnbnn_set_start_gate: search kernels wait for *gate != 0
   // optional device-time profile (lnbnn_profile_enable)
   struct CallEvents {
@@ -215,8 +216,40 @@ int64_t max_splits(const lnbnn_index* ix) {
   return std::min<int64_t>(2 * (int64_t)ix->sm_count, 32 * kMaxListsPerLane / 2);
 }
 
-int choose_splits(const lnbnn_index* ix, int64_t m_pad) {
-  return choose_splits_model(ix->split_model, m_pad / kTcQueryTile, ix->n_ref, ix->sm_count, max_splits(ix));
+// What a scan computes: kNN lists over the exact BF16 operand, kNN lists over
+// the E4M3 coarse operand, or NBNN's class minima.
+enum class ScanKind { Exact, Coarse, Nbnn };
+
+// Reference operand bytes a scan streams per reference row.
+int64_t op_row_bytes(ScanKind k) { return k == ScanKind::Coarse ? kDim + 2 * kExt : 2 * (kDim + kExt); }
+
+// Reference bytes one split may stream for the CTAs running at the same time
+// to find every tile in L2 (129 MB), with room for the next split and the
+// other traffic.
+constexpr int64_t kL2SplitBytes = int64_t(48) << 20;
+
+// Schedule rules (measured on the 256-class data; see the schedule
+// measurements in the design notes).  A launch with at least a full wave of
+// query-tile groups streams its references in splits of at most
+// kL2SplitBytes for the coarse pass, which otherwise re-reads most of its
+// operand from DRAM once per wave.
+bool l2_splits_for(ScanKind k) { return k == ScanKind::Coarse; }
+// Query tiles per CTA chosen automatically for a scan kind: one (measured on
+// the 256-class data, 750k query rows: exact 1,350 vs 1,766 cycles per step,
+// FP8 shortlist 1,112 vs 1,109 ms); lnbnn_set_schedule selects two.
+int auto_query_tiles(const lnbnn_index*, ScanKind) { return 1; }
+
+int64_t l2_splits(const lnbnn_index* ix, ScanKind k) {
+  const int64_t bytes = ix->n_ref * op_row_bytes(k);
+  return std::min<int64_t>(max_splits(ix), std::max<int64_t>(1, (bytes + kL2SplitBytes - 1) / kL2SplitBytes));
+}
+
+// Largest split count a launch over T query-tile groups may use (workspaces
+// are sized for it).
+int64_t splits_bound(const lnbnn_index* ix, int64_t T, ScanKind k) {
+  int64_t hi = max_splits_for(T, ix->n_ref, ix->sm_count, max_splits(ix));
+  if (T >= ix->sm_count) hi = std::max(hi, l2_splits(ix, k));
+  return hi;
 }
 
 struct KnnPlan {
@@ -225,26 +258,53 @@ struct KnnPlan {
   int lists;  // sorted lists per query row the search writes (merged when > 1)
   int64_t split_len;
   int K1;
-  size_t off_qnorm, off_qbf, off_qext, off_lists, off_merged, off_rowthr, bytes;
+  int qt;               // 128-row query tiles per CTA
+  bool persistent;      // a persistent grid taking items from a queue
+  bool bound_per_tile;  // with several splits: the row bound shared every tile (else at item start/end)
+  size_t off_qnorm, off_qbf, off_qext, off_lists, off_merged, off_rowthr, off_queue, bytes;
+  TcSched sched(char* ws, int sm_count) const {
+    TcSched t;
+    t.qt = qt;
+    t.persistent_ctas = persistent ? sm_count : 0;
+    t.queue = reinterpret_cast<uint32_t*>(ws + off_queue);
+    t.bound_per_tile = bound_per_tile;
+    return t;
+  }
 };
 
-// splits = 0: the modelled best; otherwise that many (an upper bound after
-// rounding the split length to whole tiles).
-KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, int splits = 0) {
+// The launch schedule of a scan over m queries keeping K1 keys per row:
+// tile shape, split count, bound mode and grid form, each from the index's
+// fixed choices (lnbnn_set_schedule) or else the rules and split model above.
+// splits > 0 fixes the split count (an upper bound after rounding the split
+// length to whole tiles).
+KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, ScanKind kind, int splits = 0) {
   KnnPlan p{};
+  const lnbnn_schedule& o = ix->sched;
+  const int P = ix->sm_count;
   p.m_pad = round_up(m, kQueryPad);
   p.K1 = K1;
-  p.splits = splits > 0 ? splits : choose_splits(ix, p.m_pad);
-  p.split_len = round_up((ix->n_ref + p.splits - 1) / p.splits, kTcRefTile);
+  const int64_t T1 = p.m_pad / kTcQueryTile;
+  const bool qt2_ok = kind == ScanKind::Nbnn || K1 <= kTcCoarseRegListMax || K1 > kTcWideRegListMax;
+  p.qt = qt2_ok && (o.query_tiles == 2 || (o.query_tiles == 0 && auto_query_tiles(ix, kind) == 2)) ? 2 : 1;
+  const int64_t T = (T1 + p.qt - 1) / p.qt;
+  if (splits <= 0) splits = o.splits;
+  if (splits <= 0) {
+    splits = choose_splits_model(ix->split_model, T, ix->n_ref, P, max_splits(ix), p.qt);
+    if (T >= P && l2_splits_for(kind)) splits = (int)std::max<int64_t>(splits, l2_splits(ix, kind));
+  }
+  p.split_len = round_up((ix->n_ref + splits - 1) / splits, kTcRefTile);
   p.splits = (int)((ix->n_ref + p.split_len - 1) / p.split_len);
+  p.persistent = o.persistent == 1;
+  p.bound_per_tile = o.bound_per_tile >= 0 ? o.bound_per_tile == 1 : T < P;
   Carve c;
   p.off_qnorm = c.take<int32_t>(p.m_pad);
   p.off_qbf = c.take<__nv_bfloat16>(p.m_pad * kDim);
   p.off_qext = c.take<__nv_bfloat16>(p.m_pad * kExt);
-  p.lists = p.splits * tc_lists_per_split(K1);
-  p.off_lists = c.take<uint64_t>((size_t)p.lists * p.m_pad * K1);
-  p.off_merged = c.take<uint64_t>((size_t)p.m_pad * K1);  // apart from the lists even for one list (rerank)
+  p.lists = p.splits * tc_lists_per_split(K1, p.qt);
+  p.off_lists = c.take<uint64_t>(kind == ScanKind::Nbnn ? 0 : (size_t)p.lists * p.m_pad * K1);
+  p.off_merged = c.take<uint64_t>(kind == ScanKind::Nbnn ? 0 : (size_t)p.m_pad * K1);  // apart from the lists (rerank)
   p.off_rowthr = c.take<int32_t>(p.m_pad);                // the bound a row's lists share
+  p.off_queue = c.take<uint32_t>(1);                      // the work counter of a persistent launch
   p.bytes = c.off;
   return p;
 }
@@ -268,32 +328,40 @@ struct Scratch {
 
 struct NbnnPlan {
   KnnPlan k;
-  size_t off_qnorm, off_qbf, off_qext, off_mins, off_rowstat, bytes;
+  size_t off_qnorm, off_qbf, off_qext, off_mins, off_rowstat, off_queue, bytes;
 };
 
-NbnnPlan plan_nbnn(const lnbnn_index* ix, int64_t m) {
+NbnnPlan plan_nbnn(const lnbnn_index* ix, int64_t m, int splits = 0) {
   NbnnPlan p{};
-  p.k = plan_knn(ix, m, 1);
+  p.k = plan_knn(ix, m, 1, ScanKind::Nbnn, splits);
   Carve c;
   p.off_qnorm = c.take<int32_t>(p.k.m_pad);
   p.off_qbf = c.take<__nv_bfloat16>(p.k.m_pad * kDim);
   p.off_qext = c.take<__nv_bfloat16>(p.k.m_pad * kExt);
   p.off_mins = c.take<int32_t>((size_t)p.k.m_pad * ix->n_classes);
   p.off_rowstat = c.take<char>((size_t)p.k.m_pad * kLogoddsRowStatBytes);  // log-odds rule only
+  p.off_queue = c.take<uint32_t>(1);
+  p.k.off_queue = p.off_queue;
   p.bytes = c.off;
   return p;
 }
 
 // Largest scratch any call with at most max_q queries and lists of K1 needs.
 // The lists grow with the split count, so the bound takes the largest count
-// the schedule may choose, whatever model lnbnn_autotune fits later.
+// the schedule may choose (for either tile shape), whatever model
+// lnbnn_autotune fits later.
 size_t scratch_bound(const lnbnn_index* ix, int64_t max_q, int K1) {
   size_t b = 0;
   for (int64_t m = kQueryPad; m < max_q + kQueryPad; m += kQueryPad) {
     const int64_t mm = std::min(m, max_q);
-    const int64_t hi = max_splits_for(round_up(mm, kQueryPad) / kTcQueryTile, ix->n_ref, ix->sm_count, max_splits(ix));
-    b = std::max(b, plan_knn(ix, mm, K1, (int)hi).bytes);
-    b = std::max(b, plan_nbnn(ix, mm).bytes);
+    const int64_t T1 = round_up(mm, kQueryPad) / kTcQueryTile;
+    for (ScanKind k : {ScanKind::Exact, ScanKind::Coarse, ScanKind::Nbnn}) {
+      const int64_t hi = std::max(splits_bound(ix, T1, k), splits_bound(ix, (T1 + 1) / 2, k));
+      if (k == ScanKind::Nbnn)
+        b = std::max(b, plan_nbnn(ix, mm, (int)hi).bytes);
+      else
+        b = std::max(b, plan_knn(ix, mm, K1, k, (int)hi).bytes);
+    }
   }
   return b;
 }
@@ -301,7 +369,7 @@ size_t scratch_bound(const lnbnn_index* ix, int64_t max_q, int K1) {
 // Runs the exact search; *lists receives m sorted lists of K1 keys.
 lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_t m, int K1, cudaStream_t s,
                      const uint64_t** lists, CallProfile& prof, int force_splits = 0) {
-  KnnPlan p = plan_knn(ix, m, K1, force_splits);
+  KnnPlan p = plan_knn(ix, m, K1, ScanKind::Exact, force_splits);
   char* ws = nullptr;
   lnbnn_status st = scratch.get(p.bytes, &ws);
   if (st != LNBNN_OK) return st;
@@ -314,10 +382,13 @@ lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_
   Range range("lnbnn: exact k+1 search");
   CK(launch_prep_query(q, m, p.m_pad, ix->row_bytes, ix->loc_w, qnorm, qbf, qext, s));
   CK(cudaMemsetAsync(row_thr, 0x7F, sizeof(int32_t) * (size_t)p.m_pad, s));
+  const TcSched sched = p.sched(ws, ix->sm_count);
+  if (p.persistent) CK(cudaMemsetAsync(sched.queue, 0, sizeof(uint32_t), s));
   prof.launched(1);
   prof.mark(1);
   CK(launch_knn_tc(ix->tc, /*sorted_copy=*/false, qbf, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, K1, part,
-                   p.m_pad, p.splits > 1 ? row_thr : nullptr, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, ix->gate, s));
+                   p.m_pad, p.splits > 1 ? row_thr : nullptr, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr,
+                   ix->gate, sched, s));
   prof.launched(1, true);
   prof.mark(2);
   if (p.lists > 1) {
@@ -332,7 +403,7 @@ lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_
 // merge, exact rerank; *lists receives m sorted lists of K1 exact keys.
 lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_t m, int K1, int M1,
                          cudaStream_t s, const uint64_t** lists, CallProfile& prof) {
-  KnnPlan p = plan_knn(ix, m, M1);
+  KnnPlan p = plan_knn(ix, m, M1, ScanKind::Coarse);
   char* ws = nullptr;
   lnbnn_status st = scratch.get(p.bytes, &ws);
   if (st != LNBNN_OK) return st;
@@ -345,10 +416,13 @@ lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, in
   Range range("lnbnn: FP8 shortlist search");
   CK(launch_prep_query_e4m3(q, m, p.m_pad, qf8, qext, s));
   CK(cudaMemsetAsync(row_thr, 0x7F, sizeof(int32_t) * (size_t)p.m_pad, s));
+  const TcSched sched = p.sched(ws, ix->sm_count);
+  if (p.persistent) CK(cudaMemsetAsync(sched.queue, 0, sizeof(uint32_t), s));
   prof.launched(1);
   prof.mark(1);
   CK(launch_coarse_tc(ix->tc, qf8, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, M1, part, p.m_pad,
-                      p.splits > 1 ? row_thr : nullptr, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr, ix->gate, s));
+                      p.splits > 1 ? row_thr : nullptr, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr,
+                      ix->gate, sched, s));
   prof.launched(1, true);
   prof.mark(2);
   // the shortlist is the merged lists (or the one list); the reranked lists
@@ -664,7 +738,21 @@ lnbnn_status lnbnn_set_start_gate(lnbnn_index* index, const uint32_t* gate) {
 
 lnbnn_status lnbnn_plan_splits(const lnbnn_index* index, int64_t n_queries, int32_t* splits) {
   if (!index || !splits || n_queries < 1) return LNBNN_ERR_INVALID_ARG;
-  *splits = plan_knn(index, n_queries, 1).splits;
+  *splits = plan_knn(index, n_queries, 1, ScanKind::Exact).splits;
+  return LNBNN_OK;
+}
+
+lnbnn_status lnbnn_set_schedule(lnbnn_index* index, const lnbnn_schedule* schedule) {
+  if (!index) return LNBNN_ERR_INVALID_ARG;
+  if (!schedule) {
+    index->sched = lnbnn_schedule{0, 0, -1, -1};
+    return LNBNN_OK;
+  }
+  const lnbnn_schedule& o = *schedule;
+  if (o.splits < 0 || o.splits > max_splits(index) || o.query_tiles < 0 || o.query_tiles > 2 ||
+      o.persistent < -1 || o.persistent > 1 || o.bound_per_tile < -1 || o.bound_per_tile > 1)
+    return LNBNN_ERR_INVALID_ARG;
+  index->sched = o;
   return LNBNN_OK;
 }
 
@@ -673,7 +761,7 @@ lnbnn_status lnbnn_plan_search(const lnbnn_index* index, int64_t n_queries, int3
   if (!index || !out || n_queries < 1) return LNBNN_ERR_INVALID_ARG;
   if (k1 < 1 || k1 > LNBNN_MAX_K + 1 || (int64_t)k1 > index->n_ref) return LNBNN_ERR_K_RANGE;
   if (fp8 && !index->fp8) return LNBNN_ERR_NO_FP8;
-  const KnnPlan p = plan_knn(index, n_queries, k1);
+  const KnnPlan p = plan_knn(index, n_queries, k1, fp8 ? ScanKind::Coarse : ScanKind::Exact);
   lnbnn_search_plan r{};
   r.splits = p.splits;
   r.lists_per_row = p.lists;
@@ -685,9 +773,10 @@ lnbnn_status lnbnn_plan_search(const lnbnn_index* index, int64_t n_queries, int3
     case ListKind::Reg64: r.list_storage = 0; r.list_capacity = kTcWideRegListMax; break;
     case ListKind::Heap: r.list_storage = 2; r.list_capacity = k1; break;
   }
-  r.tile_m = kTcQueryTile;
-  r.tile_n = kTcRefTile;
-  r.persistent = 0;
+  r.tile_m = kTcQueryTile * p.qt;
+  r.tile_n = kTcRefTile / p.qt;
+  r.persistent = p.persistent ? 1 : 0;
+  r.bound_per_tile = p.splits > 1 ? (p.bound_per_tile ? 1 : 0) : -1;
   *out = r;
   return LNBNN_OK;
 }
@@ -722,7 +811,8 @@ lnbnn_status lnbnn_autotune(lnbnn_index* index, void* stream, lnbnn_tuning* out)
   const int K1 = 11;
   const int64_t m_max = t_max * kTcQueryTile;
   size_t need = 0;
-  for (const Run& r : runs) need = std::max(need, plan_knn(index, r.T * kTcQueryTile, K1, (int)r.splits).bytes);
+  for (const Run& r : runs)
+    need = std::max(need, plan_knn(index, r.T * kTcQueryTile, K1, ScanKind::Exact, (int)r.splits).bytes);
   lnbnn_workspace w;
   w.index = index;
   w.bytes = need;
@@ -972,11 +1062,13 @@ static lnbnn_status scan_class_minima(lnbnn_index* index, lnbnn_workspace* w, co
   if (rowstat) *rowstat = ws + np.off_rowstat;
   CK(launch_prep_query(queries, n_queries, p.m_pad, index->row_bytes, index->loc_w, qnorm, qbf, qext, s));
   CK(cudaMemsetAsync(*mins, 0x7F, sizeof(int32_t) * (size_t)p.m_pad * index->n_classes, s));  // > any distance
+  const TcSched sched = p.sched(ws, index->sm_count);
+  if (p.persistent) CK(cudaMemsetAsync(sched.queue, 0, sizeof(uint32_t), s));
   prof.launched(1);
   prof.mark(1);
   CK(launch_nbnn_tc(index->tc, qbf, qext, n_queries, p.m_pad, index->n_ref, p.splits, p.split_len, *mins,
                     index->n_classes, index->class_off_d, index->dev_err,
-                    index->prof_on ? index->prof_stats : nullptr, index->gate, s));
+                    index->prof_on ? index->prof_stats : nullptr, index->gate, sched, s));
   prof.launched(1, true);
   prof.mark(2);
   return LNBNN_OK;

@@ -162,7 +162,7 @@ extern "C" LNBNN_API lnbnn_status knn_search_noalloc(const uint8_t* ref, int64_t
   if (e == cudaSuccess) e = launch_prep_query(queries, n_queries, m_pad, kDim, 0, qnorm, qbf, qext, s);
   if (e == cudaSuccess)
     e = launch_knn_tc(maps, false, qbf, qext, n_queries, m_pad, n_ref, (int)splits, split_len, k, lists, m_pad,
-                      splits > 1 ? row_thr : nullptr, err, nullptr, nullptr, s);
+                      splits > 1 ? row_thr : nullptr, err, nullptr, nullptr, TcSched{}, s);
   if (e == cudaSuccess && n_lists > 1) e = launch_merge_lists(lists, (int)n_lists, n_queries, m_pad, k, merged, s);
   if (e == cudaSuccess) e = launch_extract_knn(merged, n_queries, k, k, idx, dist, s);
   uint32_t herr = 0;

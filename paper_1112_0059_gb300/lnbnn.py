@@ -53,7 +53,7 @@ EXPORTS = ["lnbnn_index_create", "lnbnn_index_destroy", "lnbnn_index_info", "knn
            "lnbnn_workspace_destroy", "knn_search_ws", "lnbnn_classify_ws", "nbnn_classify_ws",
            "lnbnn_index_prepare_fp8", "knn_search_fp8", "lnbnn_classify_fp8", "knn_search_fp8_ws",
            "lnbnn_classify_fp8_ws", "lnbnn_classify_fp8_host", "lnbnn_autotune", "lnbnn_plan_splits",
-           "lnbnn_plan_search",
+           "lnbnn_plan_search", "lnbnn_set_schedule",
            "lnbnn_debug_fail_allocations", "lnbnn_set_start_gate", "lnbnn_index_save", "lnbnn_index_load",
            "nbnn_logodds_classify", "nbnn_logodds_classify_ws", "lnbnn_index_create_located", "lnbnn_index_layout"]
 
@@ -81,14 +81,20 @@ class SearchPlan(ctypes.Structure):
     """Mirror of ``lnbnn_search_plan`` (include/lnbnn.h)."""
     _fields_ = [("splits", ctypes.c_int32), ("lists_per_row", ctypes.c_int32), ("split_len", ctypes.c_int64),
                 ("list_storage", ctypes.c_int32), ("list_capacity", ctypes.c_int32), ("tile_m", ctypes.c_int32),
-                ("tile_n", ctypes.c_int32), ("persistent", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tile_n", ctypes.c_int32), ("persistent", ctypes.c_int32), ("bound_per_tile", ctypes.c_int32)]
 
     STORAGE = {0: "registers", 1: "shared memory", 2: "global-memory heap"}
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d = {f: getattr(self, f) for f, _ in self._fields_}
         d["list_storage"] = self.STORAGE.get(self.list_storage, self.list_storage)
         return d
+
+
+class Schedule(ctypes.Structure):
+    """Mirror of ``lnbnn_schedule`` (include/lnbnn.h)."""
+    _fields_ = [("splits", ctypes.c_int32), ("query_tiles", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("bound_per_tile", ctypes.c_int32)]
 
 
 class LnbnnError(RuntimeError):
@@ -139,6 +145,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.lnbnn_plan_splits.argtypes = [P, I64, ctypes.POINTER(I32)]
         lib.lnbnn_plan_search.argtypes = [P, I64, I32, I32, ctypes.POINTER(SearchPlan)]
         lib.lnbnn_plan_search.restype = ctypes.c_int
+        lib.lnbnn_set_schedule.argtypes = [P, ctypes.POINTER(Schedule)]
+        lib.lnbnn_set_schedule.restype = ctypes.c_int
         lib.lnbnn_debug_fail_allocations.argtypes = [I32]
         lib.lnbnn_debug_fail_allocations.restype = None
         lib.lnbnn_set_start_gate.argtypes = [P, P]
@@ -291,6 +299,13 @@ class Index:
         _check(self._lib.lnbnn_plan_search(self.handle, int(n_queries), int(k1), int(bool(fp8)), ctypes.byref(out)),
                "lnbnn_plan_search")
         return out.as_dict()
+
+    def set_schedule(self, splits: int = 0, query_tiles: int = 0, persistent: int = -1,
+                     bound_per_tile: int = -1, automatic: bool = False) -> None:
+        """Fix parts of the scans' launch schedule (0 / -1: automatic); speed
+        only, never results.  ``automatic=True`` restores every choice."""
+        sch = None if automatic else ctypes.byref(Schedule(splits, query_tiles, persistent, bound_per_tile))
+        _check(self._lib.lnbnn_set_schedule(self.handle, sch), "lnbnn_set_schedule")
 
     def set_start_gate(self, gate=None) -> None:
         """Test hook: search kernels wait (at most 1 s) for the uint32/int32 device

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 import bench  # noqa: E402
-from paper_1112_0059_gb300 import sweep, synth  # noqa: E402
+from paper_1112_0059_gb300 import synth  # noqa: E402
 
 
 def test_scan_roofline_arithmetic():
@@ -54,15 +54,21 @@ def test_measured_peaks_and_workload_config():
     assert bench.workload_config(synth.workload("tiny"), 10, "nbnn")["k"] is None
 
 
-def test_sweep_tables():
-    rows = [{"part": "kc", "method": "local", "C": 32, "n_ref": 1440000, "k": 10, "desc_per_s": 4e6, "tflops": 1500.0},
-            {"part": "kc", "method": "nbnn", "C": 32, "n_ref": 1440000, "k": None, "desc_per_s": 4.5e6,
-             "tflops": 1700.0},
-            {"part": "fp8", "form": "fp8", "shortlist": 32, "desc_per_s": 7e5, "knn_recall": 1.0,
-             "class_agreement": 1.0, "score_rel_error": 0.0},
-            {"part": "uneven", "form": "exact", "autotuned": False, "splits": 1, "desc_per_s": 5e5,
-             "images_per_s": 300.0}]
-    t = sweep.tables(rows)
-    assert "| 32 | 1,440,000 | 10 | 4,000,000 | 1500 |" in t
-    assert "| 32 | 1,440,000 | NBNN |" in t
-    assert "| fp8 | 32 | 700,000 |" in t and "| exact | False | 1 | 500,000 | 300.0 |" in t
+def test_roofline_clock_normalised():
+    prof = {"search_ms": 1000.0, "search_launches": 1, "search_cycles_per_tile": 1280.0, "search_sm_clock_ghz": 1.9}
+    peaks = {"bf16_tflops_sustained": 1000.0, "clocks_under_load": {"sm_mhz_median": 1470.0}}
+    r = bench.scan_roofline(prof, 10, 10, peaks, "measured", True, None)
+    assert r["mma_floor_cycles_per_tile"] == 1152 and r["tensor_pipe_frac_at_kernel_clock"] == 1152 / 1280
+    assert abs(r["algorithmic_frac_at_kernel_clock"] - 0.8) < 1e-12 and r["peak_sm_mhz"] == 1470.0
+    f = bench.scan_roofline(prof, 10, 10, peaks, "measured", True, 32)
+    assert f["mma_floor_cycles_per_tile"] == 640 and abs(f["algorithmic_frac_at_kernel_clock"] - 0.4) < 1e-12
+    assert "cycles_per_tile" not in bench.scan_roofline({"search_ms": 1.0, "search_launches": 1}, 10, 10, peaks,
+                                                        "measured", True, None)
+
+
+def test_sections_and_row_samples():
+    assert set(bench.DEFAULT_SECTIONS.split(",")) <= set(bench.SECTIONS)
+    r = bench._sample(1000, 100, 7)
+    assert len(r) == 100 and len(set(r.tolist())) == 100 and (r[1:] > r[:-1]).all() and r.max() < 1000
+    assert bench._sample(50, 100, 7).tolist() == list(range(50))
+    assert bench._sample(1000, 100, 7).tolist() == r.tolist()  # seeded

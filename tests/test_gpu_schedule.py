@@ -64,3 +64,76 @@ def test_autotune_on_a_tiny_index(lnbnn):
         ix.sync()
         od, oj = oracle.knn(ref, q, 5)
         assert np.array_equal(i.cpu().numpy(), oj) and np.array_equal(d.cpu().numpy(), od)
+
+
+def _case(seed, N, M, C, hi=256):
+    rng = np.random.default_rng(seed)
+    ref = rng.integers(0, hi, size=(N, 128), dtype=np.uint8)
+    ref[50:60] = ref[5]  # exact ties across reference tiles
+    q = rng.integers(0, hi, size=(M, 128), dtype=np.uint8)
+    q[:3] = ref[5]
+    labels = (rng.integers(0, C, size=N)).astype(np.int32)
+    labels[:C] = np.arange(C)
+    cuts = np.sort(rng.integers(0, M + 1, size=6))
+    offsets = np.concatenate([[0], cuts, [M]]).astype(np.int64)
+    return ref, labels, q, offsets
+
+
+SCHEDULES = [dict(splits=s, query_tiles=qt, persistent=p, bound_per_tile=b)
+             for s in (1, 3, 8) for qt in (1, 2) for p in (0, 1) for b in (0, 1)]
+
+
+def test_every_schedule_is_bit_identical(lnbnn):
+    """Tile shape (one or two query tiles per CTA), grid form (one CTA per work
+    item or a persistent grid with a work queue), row-bound mode and split
+    count change speed only: kNN lists of every list kind, Local NBNN, NBNN
+    and the FP8 shortlist all equal the oracle under each schedule."""
+    N, M, C = 60_000 + 77, 3_000 + 13, 7  # 24 query tiles (an odd count of pairs is padded), ragged tails
+    ref, labels, q, off = _case(90, N, M, C)
+    ks = (10, 40, 100)  # register lists, 64-entry lists (one query tile per CTA only), heaps
+    want = {k1: oracle.knn(ref, q, k1) for k1 in ks}
+    wl = oracle.local_nbnn(ref, labels, C, q, off, 10)
+    wn = oracle.nbnn(ref, labels, C, q, off)
+    wf = oracle.knn_coarse(ref, q, 11, 32)
+    with lnbnn.Index(dev(ref), dev(labels), C) as ix:
+        ix.prepare_fp8()
+        qd, od = dev(q), dev(off)
+        seen = set()
+        for sch in SCHEDULES:
+            ix.set_schedule(**sch)
+            for k1 in ks:
+                plan = ix.plan_search(M, k1)
+                seen.add((plan["tile_m"], plan["persistent"], plan["bound_per_tile"], k1 > 32 and k1 <= 64))
+                i, d = ix.knn_search(qd, k1)
+                ix.sync()
+                assert np.array_equal(d.cpu().numpy(), want[k1][0]), (sch, k1)
+                assert np.array_equal(i.cpu().numpy(), want[k1][1]), (sch, k1)
+            t, c = ix.lnbnn_classify(qd, od, 10)
+            nt, nc = ix.nbnn_classify(qd, od)
+            fi, fd = ix.knn_search(qd, 11, shortlist=32)
+            ix.sync()
+            assert np.array_equal(t.cpu().numpy(), wl[0]) and np.array_equal(c.cpu().numpy(), wl[1]), sch
+            assert np.array_equal(nt.cpu().numpy(), wn[0]) and np.array_equal(nc.cpu().numpy(), wn[1]), sch
+            assert np.array_equal(fd.cpu().numpy(), wf[0]) and np.array_equal(fi.cpu().numpy(), wf[1]), sch
+        ix.set_schedule(automatic=True)
+    # both tile shapes, both grid forms and both bound modes were exercised
+    assert {s[0] for s in seen} == {128, 256} and {s[1] for s in seen} == {0, 1}
+    assert {s[2] for s in seen} >= {0, 1}
+
+
+def test_schedule_arguments_are_checked(lnbnn):
+    rng = np.random.default_rng(91)
+    ref = rng.integers(0, 256, size=(5000, 128), dtype=np.uint8)
+    with lnbnn.Index(dev(ref), dev(np.zeros(5000, np.int32)), 1) as ix:
+        for bad in (dict(splits=-1), dict(query_tiles=3), dict(persistent=2), dict(bound_per_tile=-2),
+                    dict(splits=100000)):
+            with pytest.raises(lnbnn.LnbnnError):
+                ix.set_schedule(**bad)
+        ix.set_schedule(query_tiles=2, persistent=1)
+        p = ix.plan_search(40_000, 11)
+        assert p["tile_m"] == 256 and p["tile_n"] == 128 and p["persistent"] == 1
+        p = ix.plan_search(40_000, 50)  # 64-entry lists: one query tile per CTA whatever is asked
+        assert p["tile_m"] == 128 and p["tile_n"] == 256
+        ix.set_schedule(automatic=True)
+        p = ix.plan_search(100, 11)
+        assert p["tile_m"] == 128 and p["persistent"] == 0
