@@ -713,6 +713,9 @@ def run_serving(index, rates, seconds, k, shortlist, classes_out: dict | None = 
     form = "exact" if shortlist is None else f"FP8 E4M3 shortlist m = {shortlist} + exact rerank"
     return {"form": form, "k": k, "workload": "256-class index; Poisson arrivals; log-uniform [100, 4000] "
             "descriptors per image; latency = arrival to totals and class on the host", **cfg,
+            "admission": f"arrival order into the next free slot while its batch stays within "
+                         f"{cfg['max_batch_queries']:,} descriptors and {cfg['max_batch_images']} images; a request "
+                         f"of more than {cfg['max_batch_queries']:,} descriptors is refused (ValueError)",
             "graph_buckets": f"{len(serve.graph_buckets(cfg['max_batch_queries']))} query-count buckets, "
                              "every multiple of 128 up to 4,096, then about 25% apart", "runs": runs}
 
