@@ -39,7 +39,7 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "knn_tc_traffic.json")
 # Measurements reported beside the headline, each a block of the JSON line.
 SECTIONS = {
     "uneven": "1,024 query images of U{200..3000} descriptors in one call on the 256-class index: exact and the "
-              "FP8 shortlist at m = 32, 64, 128, with recall, score error and class agreement",
+              "FP8 shortlist at m = 24, 32, 64, 128, with recall, score error and class agreement",
     "kc": "Local NBNN at k = 1, 10, 50, 100 and original NBNN on the first 32 and all 256 classes "
           "(100 query images): run time against k and class count",
     "caltech101": "the 101-class index (1.515M references, 200 images x 1,000 descriptors): Local NBNN at "
@@ -68,7 +68,7 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--shortlist", type=int, default=None,
                    help="time the FP8 E4M3 shortlist search (shortlist length m) instead of the exact one")
-    p.add_argument("--fp8-shortlist", type=int, default=32,
+    p.add_argument("--fp8-shortlist", type=int, default=24,
                    help="shortlist of the FP8 block and FP8 serving runs reported beside the exact form (0: skip)")
     p.add_argument("--serve-rates", default="100,300,1000",
                    help="Poisson arrival rates (images/s) of the serving runs; empty to skip them")
@@ -76,6 +76,9 @@ def parse_args():
     p.add_argument("--sections", default=DEFAULT_SECTIONS,
                    help="measurements reported beside the headline (comma-separated; empty for none): "
                         + ", ".join(f"{k} ({v})" for k, v in SECTIONS.items()))
+    p.add_argument("--schedule", default="",
+                   help="fixed launch schedule of the scans, e.g. 'query_tiles=2,persistent=1,splits=19' "
+                        "(lnbnn_set_schedule; results never change); empty: automatic")
     p.add_argument("--recall-rows", type=int, default=8192,
                    help="seeded random query rows (all images) of the FP8 recall against the exact search")
     p.add_argument("--oracle-recall-rows", type=int, default=256,
@@ -294,6 +297,8 @@ def run_ours(args, w):
     off_d = torch.from_numpy(off).to(dev)
     index = lnbnn.Index(ref_d, lab_d, w.n_classes)
     del ref_d, lab_d
+    if args.schedule:
+        index.set_schedule(**{k.strip(): int(v) for k, v in (kv.split("=") for kv in args.schedule.split(","))})
     if shortlist or fp8_m:
         index.prepare_fp8()
     totals = torch.empty((n_img, w.n_classes), dtype=torch.int64, device=dev)
@@ -347,7 +352,10 @@ def run_ours(args, w):
 
     value = M * args.steps * world / elapsed
     peaks, peak_src = measured_peaks()
-    roofline = scan_roofline(prof, w.n_ref, M, peaks, peak_src, local, shortlist, k)
+    plan = index.plan_search(M, (shortlist or k + 1) if local else 1, fp8=bool(shortlist)) if local else None
+    roofline = scan_roofline(prof, w.n_ref, M, peaks, peak_src, local, shortlist, k, plan)
+    if plan:
+        roofline["schedule"] = plan
     roofline["traffic"] = traffic_per_launch(roofline["kernel"], M)
 
     e2e = None
@@ -388,7 +396,8 @@ def run_ours(args, w):
             el8, prof8 = timed(fp8_step, args.steps)
             fp8_block = {"shortlist": m_short, "value": M * args.steps * world / el8, "unit": UNIT,
                          "images_per_s": n_img * args.steps * world / el8, "ms_per_step": el8 / args.steps * 1e3,
-                         "roofline": scan_roofline(prof8, w.n_ref, M, peaks, peak_src, True, m_short, k),
+                         "roofline": scan_roofline(prof8, w.n_ref, M, peaks, peak_src, True, m_short, k,
+                                                   index.plan_search(M, m_short, fp8=True)),
                          "gpu_launches": int(prof8["kernel_launches"])}
             fp8_block["roofline"]["traffic"] = traffic_per_launch(fp8_block["roofline"]["kernel"], M)
         index.sync()
@@ -507,7 +516,7 @@ def _timed(fn, reps: int, warm: int = 1) -> float:
     return statistics.median(times)
 
 
-def section_uneven(index, ref, k, shortlists=(32, 64, 128)) -> dict:
+def section_uneven(index, ref, k, shortlists=(24, 32, 64, 128)) -> dict:
     """The batched uneven workload: 1,024 images of U{200..3000} descriptors,
     flattened with offsets, one classify call per form."""
     import torch
@@ -649,10 +658,25 @@ def run_sections(sections, index, ref, labels, k, m) -> dict:
 
 def list_kind(K1: int) -> int:
     """Register-list size the search kernel uses for lists of K1 (0: heap)."""
-    return 16 if K1 <= 16 else 32 if K1 <= 32 else 64 if K1 <= 64 else 0
+    return 16 if K1 <= 16 else 24 if K1 <= 24 else 32 if K1 <= 32 else 64 if K1 <= 64 else 0
 
 
-def scan_roofline(prof, n_ref, M, peaks, peak_src, local, shortlist, k: int = 10) -> dict:
+def kernel_name(local: bool, shortlist, k: int, plan: dict | None = None) -> str:
+    """The search kernel a launch runs: operand format, epilogue (list kind)
+    and query tiles per CTA, as in the profiler's kernel names."""
+    qt = (plan or {}).get("tile_m", 128) // 128
+    if not local:
+        return f"tc_scan_kernel<FmtBf16, NbnnEpilogue, {qt}>"
+    K1 = shortlist or k + 1
+    fmt = "FmtE4m3" if shortlist else "FmtBf16"
+    if plan and plan.get("list_storage") == "shared memory":
+        epi = "KnnSmemEpilogue<64>"
+    else:
+        epi = f"KnnEpilogue<{list_kind(K1)}>"
+    return f"tc_scan_kernel<{fmt}, {epi}, {qt}>"
+
+
+def scan_roofline(prof, n_ref, M, peaks, peak_src, local, shortlist, k: int = 10, plan: dict | None = None) -> dict:
     """Roofline of the search kernel from the call profile: algorithmic
     2 * 128 flops per (query, reference) pair over its mean launch time."""
     search_ms = prof["search_ms"] / max(prof["search_launches"], 1)
@@ -662,12 +686,10 @@ def scan_roofline(prof, n_ref, M, peaks, peak_src, local, shortlist, k: int = 10
         # E4M3 contraction: twice the BF16 rate (nominal dense 4.5 vs 2.25 PFLOP/s)
         peak = 2.0 * float(peaks["bf16_tflops_sustained"])
         src = f"2 x bf16_tflops_sustained ({peak_src}), the nominal fp8/bf16 ratio"
-        kernel = "tc_scan_kernel<FmtE4m3, KnnEpilogue<%d>>" % list_kind(shortlist)
     else:
         peak = float(peaks["bf16_tflops_sustained"])
         src = f"bf16_tflops_sustained ({peak_src})"
-        kernel = ("tc_scan_kernel<FmtBf16, KnnEpilogue<%d>>" % list_kind(k + 1) if local
-                  else "tc_scan_kernel<FmtBf16, NbnnEpilogue>")
+    kernel = kernel_name(local, shortlist, k, plan)
     out = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
            "traffic": None, "kernel": kernel, "peak_source": src, "flops_per_launch": flops,
            "avg_launch_ms": search_ms}

@@ -273,22 +273,36 @@ LNBNN_API lnbnn_status lnbnn_classify_fp8_ws(lnbnn_index *index, lnbnn_workspace
                                              int32_t *classes, void *stream);
 
 /*
- * Split-N schedule.  Each search launch runs ceil(n_queries / 128) query tiles
- * x `splits` reference ranges as CTAs, one per SM, and merges the splits'
- * lists; the split count is chosen per call by a device-time model
- *   waves(tiles * splits) * (a * tiles_per_CTA + b) + c * tiles * splits.
- * lnbnn_autotune times a dozen search launches of 1 to 64 query tiles (query
- * rows copied from the index's own references) with several split counts on
- * `stream`, fits a, b, c by least squares and keeps them in the index; it
- * synchronises `stream`, allocates and frees its own scratch, and changes no
- * result (every schedule gives bit-identical output), only speed.  Call it
- * outside stream capture.  out (may be NULL) receives the fitted milliseconds
- * per tile, per wave and per (query tile, split), the number of timed runs and
- * the largest relative error of the fit (tile_ms = 0: no fit, the model is
- * unchanged).  lnbnn_plan_splits reports the
- * split count a call with n_queries query descriptors would use.
- * Workspaces are sized for the largest split count any model may choose, so
- * they stay valid after tuning.
+ * Search schedule.  Each search launch runs ceil(n_queries / (128 qt)) groups
+ * of qt query tiles (qt = 1 or 2) x `splits` reference ranges as work items,
+ * one CTA per item or a persistent grid that takes items from a queue, and
+ * merges the splits' lists; the split count is chosen per call by a
+ * device-time model
+ *   waves(groups * splits) * (a * qt * tiles_per_item + b + e * k1)
+ *     + c * groups * splits,
+ * where the term e * k1 (k1 = list length) is the cost of filling one item's
+ * lists, so longer lists favour fewer splits.  lnbnn_autotune times about
+ * thirty search launches of 1 to 64 query tiles (query rows copied from the
+ * index's own references) with several split counts and two list lengths
+ * (k1 = 11 and 51) on `stream` and fits a, b, c, e by least squares; then, on
+ * indexes with enough references for two waves of query tiles, it times the
+ * four large-batch forms of the exact scan (k1 = 11) and, when the index has
+ * its FP8 operand, of the coarse pass (k1 = 32): one or two query tiles per
+ * CTA, one CTA per item or persistent; the fastest form of each is then used
+ * for launches of at least a full wave of query tiles.  It keeps all of this
+ * in the index; it synchronises `stream`, allocates and frees its own
+ * scratch, and changes no result (every schedule gives bit-identical output),
+ * only speed.  Call it outside stream capture.  out (may be NULL) receives
+ * the fitted milliseconds per 128 x 256 step, per wave, per (query-tile
+ * group, split) and per list entry and wave, the number of timed split-model
+ * runs and the largest relative error of that fit (tile_ms = 0: no fit, the
+ * model is unchanged), the chosen large-batch forms (query tiles per CTA 1 or
+ * 2, persistent 0 or 1; 0 and -1 when not timed) and the timed milliseconds
+ * of the candidates, [0..3] exact and [4..7] coarse, in the order (1, grid),
+ * (1, persistent), (2, grid), (2, persistent) (0 when not timed).
+ * lnbnn_plan_splits reports the split count a call with n_queries query
+ * descriptors would use.  Workspaces are sized for the largest split count
+ * any model may choose, so they stay valid after tuning.
  */
 typedef struct lnbnn_tuning {
   double tile_ms;
@@ -296,6 +310,13 @@ typedef struct lnbnn_tuning {
   double list_ms;
   double max_rel_error;
   int32_t runs;
+  int32_t exact_query_tiles;
+  double entry_ms;
+  int32_t exact_persistent;
+  int32_t coarse_query_tiles;
+  int32_t coarse_persistent;
+  int32_t form_runs;
+  double form_ms[8];
 } lnbnn_tuning;
 
 LNBNN_API lnbnn_status lnbnn_autotune(lnbnn_index *index, void *stream, lnbnn_tuning *out);

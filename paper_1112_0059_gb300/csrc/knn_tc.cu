@@ -68,20 +68,23 @@ constexpr uint32_t kAExtBytes = kBM * kExt * 2;      // 4 KB
 template <int QT>
 struct Shape {
   static_assert(QT == 1 || QT == 2, "one or two query tiles per CTA");
-  static constexpr int kQT = QT;
   static constexpr int kTileN = kTcRefTile / QT;                 // references per tile (MMA N)
   static constexpr uint32_t kBChunkBytes = kTileN * kBK * 2;     // 32 or 16 KB
   static constexpr uint32_t kBExtBytes = kTileN * kExt * 2;      // 8 or 4 KB
   static constexpr uint32_t kStageBytes = kBChunkBytes + kBExtBytes;
 };
 
-// Threads of a CTA whose epilogue has `epq` warps per TMEM lane quarter: the
-// producer warp, the MMA warp and 4 * epq epilogue warps.
-constexpr int threads_for(int epq) { return 64 + 32 * 4 * epq; }
+// Threads of a CTA whose epilogue has `epq` warps per TMEM lane quarter and
+// which computes `qt` query tiles: the producer warp, one MMA warp per query
+// tile (the second after the epilogue warps) and 4 * epq epilogue warps.
+constexpr int warps_for(int epq, int qt) { return 1 + qt + 4 * epq; }
+constexpr int threads_for(int epq, int qt) { return 32 * warps_for(epq, qt); }
 // Registers per thread above which the CTA's warps cannot share one SM (the
 // sub-partition holding the most warps has 16,384 registers).
-constexpr int max_regs_for(int epq) {
-  return (16384 / (32 * ((2 + 4 * epq + 3) / 4))) / 8 * 8 > 255 ? 255 : (16384 / (32 * ((2 + 4 * epq + 3) / 4))) / 8 * 8;
+constexpr int max_regs_for(int epq, int qt) {
+  return (16384 / (32 * ((warps_for(epq, qt) + 3) / 4))) / 8 * 8 > 255
+             ? 255
+             : (16384 / (32 * ((warps_for(epq, qt) + 3) / 4))) / 8 * 8;
 }
 constexpr uint32_t kAccCols = kTcRefTile;  // FP32 columns per accumulator (one step)
 constexpr uint32_t kTmemCols = 2 * kAccCols;
@@ -579,7 +582,7 @@ struct Work {
 };
 
 template <class Fmt, class Epilogue, int QT>
-__global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1)
+__global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1)
     tc_scan_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_qe,
                    const __grid_constant__ CUtensorMap tmap_r, const __grid_constant__ CUtensorMap tmap_re, int64_t m,
                    int64_t n_ref, Work work, ScanOut out, uint32_t* __restrict__ dev_err,
@@ -606,6 +609,12 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1)
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const bool persistent = work.queue != nullptr;
+  // MMA issuers: one thread per query tile (warp 1, and for QT = 2 the warp
+  // after the epilogue warps), each issuing its tile's MMAs into its half of
+  // the accumulator, so that no single thread issues all of a step's MMAs.
+  constexpr int kIssuers = QT;
+  constexpr int kSecondIssuerWarp = 2 + kEpiWarps;
+  const bool issuer = warp == 1 || (kIssuers == 2 && warp == kSecondIssuerWarp);
   // A timeout reported earlier and not yet collected by lnbnn_sync: scan no
   // tiles (every item's lists are still written, empty).
   const bool stale_timeout = (*reinterpret_cast<volatile uint32_t*>(dev_err) & kDevErrTimeout) != 0;
@@ -613,17 +622,17 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(bars.full(s), 1);
-      mbar_init(bars.empty(s), 1);  // the MMA completion that frees the stage
+      mbar_init(bars.empty(s), kIssuers);  // the MMA completions that free the stage
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(bars.tfull(b), 1);
+      mbar_init(bars.tfull(b), kIssuers);
       mbar_init(bars.tempty(b), 32 * kEpiWarps);
       mbar_init(bars.ifull(b), 1);
-      mbar_init(bars.iempty(b), 1 + kEpiWarps);  // the MMA thread and each epilogue warp
+      mbar_init(bars.iempty(b), kIssuers + kEpiWarps);  // the MMA threads and each epilogue warp
     }
     mbar_init(bars.afull(), 1);
-    mbar_init(bars.aempty(), 1);
-    mbar_init(bars.drain(), 1);
+    mbar_init(bars.aempty(), kIssuers);
+    mbar_init(bars.drain(), kIssuers);
     *abort_flag = 0u;
     fence_barrier_init();
   }
@@ -728,9 +737,11 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1)
         if (issued > 0) mbar_wait(bars.full(s), (uint32_t)((issued - 1) & 1), kWaitLimitNs, &never);
       }
     }
-  } else if (warp == 1) {
+  } else if (issuer) {
     if (lane == 0) {
-      // ---------------------------------------------------------- MMA issuer
+      // --------------------------------------------------------- MMA issuers
+      const int q_first = kIssuers == QT ? (warp == 1 ? 0 : 1) : 0;  // this thread's query tiles
+      const int q_last = kIssuers == QT ? q_first + 1 : QT;
       const long long clk0 = clock64();
       const uint64_t ns0 = globaltimer_ns();
       int it = 0;       // reference K-chunks consumed
@@ -772,8 +783,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1)
             tc_fence_after();
             const uint32_t b_base = sbase + L::kOffB + s * Sh::kStageBytes;
             const bool last = kc == KC - 1;  // the norms' K-extension rides with the last chunk
-#pragma unroll
-            for (int q = 0; q < QT; ++q) {
+            for (int q = q_first; q < q_last; ++q) {
               const uint32_t a_q = sbase + L::kOffA + q * L::kAQueryBytes;
               const uint32_t d_q = d_tmem + q * kTileN;
               if (Fmt::kExtFirst && last)
@@ -801,7 +811,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter), 1)
       const uint32_t never = 0;
       mma_commit(bars.drain());
       mbar_wait(bars.drain(), 0, kWaitLimitNs, &never);
-      if (stats) {
+      if (stats && warp == 1) {
         atomicAdd(stats + 0, (unsigned long long)(clock64() - clk0));
         atomicAdd(stats + 1, (unsigned long long)(globaltimer_ns() - ns0));
         atomicAdd(stats + 2, (unsigned long long)tiles_done);
@@ -970,7 +980,7 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const voi
   if (work.n_items > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
   const int64_t grid = work.queue ? std::min<int64_t>(work.n_items, sched.persistent_ctas) : work.n_items;
   tc_scan_kernel<Fmt, Epilogue, QT>
-      <<<(unsigned)grid, threads_for(Epilogue::kWarpsPerQuarter), LayoutOf<Fmt, Epilogue, QT>::kSmemBytes, s>>>(
+      <<<(unsigned)grid, threads_for(Epilogue::kWarpsPerQuarter, QT), LayoutOf<Fmt, Epilogue, QT>::kSmemBytes, s>>>(
           tq, tqe, tr, tre, m, n_ref, work, out, dev_err, stats);
   return cudaGetLastError();
 }
@@ -980,7 +990,7 @@ cudaError_t prepare_one() {
   cudaFuncAttributes a;
   cudaError_t e = cudaFuncGetAttributes(&a, tc_scan_kernel<Fmt, Epilogue, QT>);
   if (e != cudaSuccess) return e;
-  if (a.numRegs > max_regs_for(Epilogue::kWarpsPerQuarter)) return cudaErrorInvalidKernelImage;
+  if (a.numRegs > max_regs_for(Epilogue::kWarpsPerQuarter, QT)) return cudaErrorInvalidKernelImage;
   return cudaFuncSetAttribute(tc_scan_kernel<Fmt, Epilogue, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)LayoutOf<Fmt, Epilogue, QT>::kSmemBytes);
 }
@@ -1026,6 +1036,9 @@ cudaError_t launch_lists(const TcTensorMaps& maps, bool sorted_copy, const void*
     case ListKind::Reg16:
       return launch_shape<Fmt, KnnEpilogue<kTcRegListMax>>(maps, sorted_copy, qop, qext, m, m_pad, n_ref, splits,
                                                            split_len, out, dev_err, stats, sched, s);
+    case ListKind::Reg24:
+      return launch_shape<Fmt, KnnEpilogue<kTcMidRegListMax>>(maps, sorted_copy, qop, qext, m, m_pad, n_ref, splits,
+                                                              split_len, out, dev_err, stats, sched, s);
     case ListKind::Reg32:
       return launch_shape<Fmt, KnnEpilogue<kTcCoarseRegListMax>>(maps, sorted_copy, qop, qext, m, m_pad, n_ref,
                                                                  splits, split_len, out, dev_err, stats, sched, s);
@@ -1048,6 +1061,8 @@ cudaError_t launch_lists(const TcTensorMaps& maps, bool sorted_copy, const void*
 
 cudaError_t prepare_tc_kernels() {
   cudaError_t e = prepare_both<FmtBf16, KnnEpilogue<kTcRegListMax>>();
+  if (e == cudaSuccess) e = prepare_both<FmtBf16, KnnEpilogue<kTcMidRegListMax>>();
+  if (e == cudaSuccess) e = prepare_both<FmtE4m3, KnnEpilogue<kTcMidRegListMax>>();
   if (e == cudaSuccess) e = prepare_both<FmtBf16, KnnEpilogue<kTcCoarseRegListMax>>();
   if (e == cudaSuccess) e = prepare_both<FmtBf16, KnnSmemEpilogue<kTcWideRegListMax>>();
   if (e == cudaSuccess) e = prepare_both<FmtBf16, KnnEpilogue<kTcWideRegListMax>>();

@@ -17,11 +17,13 @@ constexpr int kTcRefTile = 256;
 constexpr int kTcQueryTile = 128;
 static_assert(kQueryPad % kTcQueryTile == 0, "query padding must cover whole tiles");
 // Lists of the k+1 (or shortlist) nearest per query row: up to 16 entries a
-// 16-entry register list (the fewest registers), up to 32 a 32-entry one, up
+// 16-entry register list (the fewest registers), up to 24 a 24-entry one (a
+// narrower insertion network than 32), up to 32 a 32-entry one, up
 // to 64 a 64-entry list in shared memory with warp-cooperative inserts (in
 // registers for an exact scan of long splits), longer ones a heap in global
 // memory.
 constexpr int kTcRegListMax = 16;
+constexpr int kTcMidRegListMax = 24;
 constexpr int kTcCoarseRegListMax = 32;
 constexpr int kTcWideRegListMax = 64;
 // Epilogue warps per TMEM lane quarter.  Each owns a column slice of every
@@ -43,9 +45,10 @@ inline int tc_lists_per_split(int K1, int qt = 1) {
 constexpr int64_t kSmemListMaxRefs = int64_t(8) << 20;
 
 // Where a scan keeps its per-row lists of K1 keys.
-enum class ListKind { Reg16, Reg32, Smem64, Reg64, Heap };
+enum class ListKind { Reg16, Reg24, Reg32, Smem64, Reg64, Heap };
 inline ListKind tc_list_kind(int K1, int64_t split_len, bool coarse) {
   if (K1 <= kTcRegListMax) return ListKind::Reg16;
+  if (K1 <= kTcMidRegListMax) return ListKind::Reg24;
   if (K1 <= kTcCoarseRegListMax) return ListKind::Reg32;
   if (K1 <= kTcWideRegListMax) return coarse || split_len <= kSmemListMaxRefs ? ListKind::Smem64 : ListKind::Reg64;
   return ListKind::Heap;
@@ -71,16 +74,19 @@ struct TcSched {
 };
 
 // Split-N schedule of one scan launch over T query-tile groups (qt 128-row
-// query tiles per CTA): s reference splits make T * s CTAs, run one per SM in
-// waves of sm_count.  Modelled device time:
-//   ceil(T * s / sm_count) * (a * qt * tiles_per_cta(s) + b) + c * T * s,
-// tiles_per_cta(s) = ceil(ceil(n_ref / s) / kTcRefTile): a is the time of one
-// step of 128 x 256 query-reference pairs, b the fixed time of a wave (CTA
-// start, drain, epilogue store), c the merge time per (query-tile group,
-// split).  lnbnn_autotune fits a, b, c on the device; these defaults are in
-// step units.
+// query tiles per CTA) keeping lists of K1 keys: s reference splits make
+// T * s work items, run one per SM in waves of sm_count.  Modelled device
+// time:
+//   ceil(T * s / sm_count) * (a * qt * tiles_per_item(s) + b + e * K1) + c * T * s,
+// tiles_per_item(s) = ceil(ceil(n_ref / s) / kTcRefTile): a is the time of one
+// step of 128 x 256 query-reference pairs, b the fixed time of a wave (start,
+// drain, epilogue store), e the time per list entry of filling an item's lists
+// (a list of K1 takes about K1 (1 + ln(n / K1)) inserts, most of them at the
+// start of the item), c the merge time per (query-tile group, split).
+// lnbnn_autotune fits a, b, c, e on the device; these defaults are in step
+// units.
 struct SplitModel {
-  double a = 1.0, b = 64.0, c = 0.02;
+  double a = 1.0, b = 64.0, c = 0.02, e = 0.5;
 };
 
 // Largest split count considered for T query-tile groups: at most four waves
@@ -92,20 +98,21 @@ inline int64_t max_splits_for(int64_t T, int64_t n_ref, int sm_count, int64_t ma
   return std::max<int64_t>(1, std::min<int64_t>(hi, max_splits));
 }
 
-inline double split_cost(const SplitModel& md, int64_t T, int64_t s, int64_t n_ref, int sm_count, int qt = 1) {
+inline double split_cost(const SplitModel& md, int64_t T, int64_t s, int64_t n_ref, int sm_count, int qt = 1,
+                         int K1 = 0) {
   const int64_t tiles = ((n_ref + s - 1) / s + kTcRefTile - 1) / kTcRefTile;
   const int64_t waves = (T * s + sm_count - 1) / sm_count;
-  return (double)waves * (md.a * (double)(qt * tiles) + md.b) + md.c * (double)(T * s);
+  return (double)waves * (md.a * (double)(qt * tiles) + md.b + md.e * (double)K1) + md.c * (double)(T * s);
 }
 
 // The split count of least modelled time (the smaller one on ties).
 inline int choose_splits_model(const SplitModel& md, int64_t T, int64_t n_ref, int sm_count, int64_t max_splits,
-                               int qt = 1) {
+                               int qt = 1, int K1 = 0) {
   const int64_t hi = max_splits_for(T, n_ref, sm_count, max_splits);
   int64_t best = 1;
-  double best_cost = split_cost(md, T, 1, n_ref, sm_count, qt);
+  double best_cost = split_cost(md, T, 1, n_ref, sm_count, qt, K1);
   for (int64_t s = 2; s <= hi; ++s) {
-    const double c = split_cost(md, T, s, n_ref, sm_count, qt);
+    const double c = split_cost(md, T, s, n_ref, sm_count, qt, K1);
     if (c < best_cost * (1.0 - 1e-9)) {
       best_cost = c;
       best = s;

@@ -51,6 +51,9 @@ struct lnbnn_index {
   TcTensorMaps tc;  // tensor maps over ref_bf / sref_bf (and ref_f8) for the tensor-core kernels
   SplitModel split_model;  // split-N schedule (defaults, or fitted by lnbnn_autotune)
   lnbnn_schedule sched{0, 0, -1, -1};  // lnbnn_set_schedule: fixed choices (0 / -1: automatic)
+  // large-batch forms per scan kind (exact, coarse, NBNN), chosen by lnbnn_autotune
+  int auto_qt[3] = {1, 2, 1};
+  int auto_persistent[3] = {0, 0, 0};
   const uint32_t* gate = nullptr;  // lnbnn_set_start_gate: search kernels wait for *gate != 0
   // optional device-time profile (lnbnn_profile_enable)
   struct CallEvents {
@@ -234,10 +237,20 @@ constexpr int64_t kL2SplitBytes = int64_t(48) << 20;
 // kL2SplitBytes for the coarse pass, which otherwise re-reads most of its
 // operand from DRAM once per wave.
 bool l2_splits_for(ScanKind k) { return k == ScanKind::Coarse; }
-// Query tiles per CTA chosen automatically for a scan kind: one (measured on
-// the 256-class data, 750k query rows: exact 1,350 vs 1,766 cycles per step,
-// FP8 shortlist 1,112 vs 1,109 ms); lnbnn_set_schedule selects two.
-int auto_query_tiles(const lnbnn_index*, ScanKind) { return 1; }
+// The large-batch form of a scan kind (query tiles per CTA, persistent grid)
+// for launches of at least a full wave of query tiles, unless lnbnn_autotune
+// measured another form faster on this index.  Defaults, measured on the
+// 256-class data (750k query rows): the exact and NBNN scans one query tile
+// per CTA (exact 1,356 cycles per step against 1,511 with two; NBNN 1,369
+// against 1,526), the FP8 coarse pass two (shortlist 32: 1,013 against
+// 1,119 ms; 24: 960 against 989 ms); one CTA per work item (persistent grids
+// within 0.2%).
+int auto_query_tiles(const lnbnn_index* ix, ScanKind k, int64_t T1) {
+  return T1 >= ix->sm_count ? ix->auto_qt[(int)k] : 1;
+}
+bool auto_persistent(const lnbnn_index* ix, ScanKind k, int64_t T1) {
+  return T1 >= ix->sm_count && ix->auto_persistent[(int)k] == 1;
+}
 
 int64_t l2_splits(const lnbnn_index* ix, ScanKind k) {
   const int64_t bytes = ix->n_ref * op_row_bytes(k);
@@ -285,16 +298,16 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, ScanKind kind, int sp
   p.K1 = K1;
   const int64_t T1 = p.m_pad / kTcQueryTile;
   const bool qt2_ok = kind == ScanKind::Nbnn || K1 <= kTcCoarseRegListMax || K1 > kTcWideRegListMax;
-  p.qt = qt2_ok && (o.query_tiles == 2 || (o.query_tiles == 0 && auto_query_tiles(ix, kind) == 2)) ? 2 : 1;
+  p.qt = qt2_ok && (o.query_tiles == 2 || (o.query_tiles == 0 && auto_query_tiles(ix, kind, T1) == 2)) ? 2 : 1;
   const int64_t T = (T1 + p.qt - 1) / p.qt;
   if (splits <= 0) splits = o.splits;
   if (splits <= 0) {
-    splits = choose_splits_model(ix->split_model, T, ix->n_ref, P, max_splits(ix), p.qt);
+    splits = choose_splits_model(ix->split_model, T, ix->n_ref, P, max_splits(ix), p.qt, K1);
     if (T >= P && l2_splits_for(kind)) splits = (int)std::max<int64_t>(splits, l2_splits(ix, kind));
   }
   p.split_len = round_up((ix->n_ref + splits - 1) / splits, kTcRefTile);
   p.splits = (int)((ix->n_ref + p.split_len - 1) / p.split_len);
-  p.persistent = o.persistent == 1;
+  p.persistent = o.persistent == 1 || (o.persistent == -1 && auto_persistent(ix, kind, T1));
   p.bound_per_tile = o.bound_per_tile >= 0 ? o.bound_per_tile == 1 : T < P;
   Carve c;
   p.off_qnorm = c.take<int32_t>(p.m_pad);
@@ -768,6 +781,7 @@ lnbnn_status lnbnn_plan_search(const lnbnn_index* index, int64_t n_queries, int3
   r.split_len = p.split_len;
   switch (tc_list_kind(k1, p.split_len, fp8 != 0)) {
     case ListKind::Reg16: r.list_storage = 0; r.list_capacity = kTcRegListMax; break;
+    case ListKind::Reg24: r.list_storage = 0; r.list_capacity = kTcMidRegListMax; break;
     case ListKind::Reg32: r.list_storage = 0; r.list_capacity = kTcCoarseRegListMax; break;
     case ListKind::Smem64: r.list_storage = 1; r.list_capacity = kTcWideRegListMax; break;
     case ListKind::Reg64: r.list_storage = 0; r.list_capacity = kTcWideRegListMax; break;
@@ -787,43 +801,76 @@ lnbnn_status lnbnn_autotune(lnbnn_index* index, void* stream, lnbnn_tuning* out)
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int P = index->sm_count;
   const int64_t n_ref = index->n_ref;
+  lnbnn_tuning res{};
+  res.exact_persistent = res.coarse_persistent = -1;
   // query tiles up to 64 (a few waves of CTAs with few splits), copied from
   // reference rows spread over the set, so their neighbour structure is real
   const int64_t t_max = std::min<int64_t>(64, n_ref / kTcQueryTile);
   if (t_max < 1) {  // too few references for a whole query tile: keep the defaults
-    if (out) *out = lnbnn_tuning{};
+    if (out) *out = res;
     return LNBNN_OK;
   }
   struct Run {
     int64_t T, splits;
+    int K1;
     double ms;
   };
   std::vector<Run> runs;
-  for (int64_t T = 1; T <= t_max; T *= 2) {
-    const int64_t hi = max_splits_for(T, n_ref, P, max_splits(index));
-    int64_t last = 0;
-    for (int64_t w : {1, 2, 4}) {
-      const int64_t sp = std::min<int64_t>(hi, std::max<int64_t>(1, w * P / T));
-      if (sp != last) runs.push_back({T, sp, 0.0});
-      last = sp;
+  for (int K1 : {11, 51}) {
+    if (K1 > n_ref) continue;
+    for (int64_t T = 1; T <= t_max; T *= (K1 == 11 ? 2 : 4)) {
+      const int64_t hi = max_splits_for(T, n_ref, P, max_splits(index));
+      int64_t last = 0;
+      for (int64_t w : {1, 2, 4}) {
+        const int64_t sp = std::min<int64_t>(hi, std::max<int64_t>(1, w * P / T));
+        if (sp != last) runs.push_back({T, sp, K1, 0.0});
+        last = sp;
+      }
     }
   }
-  const int K1 = 11;
-  const int64_t m_max = t_max * kTcQueryTile;
+  // large-batch forms: two waves of query tiles, when the references hold that many rows
+  const int64_t t_big = (int64_t)2 * P;
+  const bool forms = n_ref >= t_big * kTcQueryTile;
+  struct Form {
+    ScanKind kind;
+    int qt, persistent;
+    double ms;
+  };
+  std::vector<Form> cand;
+  if (forms)
+    for (ScanKind k : {ScanKind::Exact, ScanKind::Coarse}) {
+      if (k == ScanKind::Coarse && !index->fp8) continue;
+      for (int qt : {1, 2})
+        for (int pe : {0, 1}) cand.push_back({k, qt, pe, 0.0});
+    }
+  const int64_t m_max = std::max(t_max, forms ? t_big : int64_t(0)) * kTcQueryTile;
+  const lnbnn_schedule saved = index->sched;
   size_t need = 0;
+  index->sched = lnbnn_schedule{0, 0, 0, -1};
   for (const Run& r : runs)
-    need = std::max(need, plan_knn(index, r.T * kTcQueryTile, K1, ScanKind::Exact, (int)r.splits).bytes);
+    need = std::max(need, plan_knn(index, r.T * kTcQueryTile, r.K1, ScanKind::Exact, (int)r.splits).bytes);
+  for (const Form& f : cand) {
+    index->sched = lnbnn_schedule{0, f.qt, f.persistent, -1};
+    need = std::max(need, plan_knn(index, t_big * kTcQueryTile, f.kind == ScanKind::Coarse ? 32 : 11, f.kind).bytes);
+  }
+  index->sched = saved;
   lnbnn_workspace w;
   w.index = index;
   w.bytes = need;
   uint8_t* q = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   lnbnn_status st = LNBNN_OK;
-  auto cleanup = [&]() {
+  const bool prof_was_on = index->prof_on;
+  auto cleanup = [&]() {  // idempotent
+    index->sched = saved;
+    index->prof_on = prof_was_on;
     cudaFree(q);
     cudaFree(w.base);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    q = nullptr;
+    w.base = nullptr;
+    e0 = e1 = nullptr;
   };
 #define CKA(call)                         \
   do {                                    \
@@ -841,92 +888,142 @@ lnbnn_status lnbnn_autotune(lnbnn_index* index, void* stream, lnbnn_tuning* out)
   CKA(cudaEventCreate(&e1));
   const int64_t step = n_ref / m_max;  // >= 1
   CKA(cudaMemcpy2DAsync(q, rb, index->ref_u8, (size_t)step * rb, rb, (size_t)m_max, cudaMemcpyDeviceToDevice, s));
-  const bool prof_was_on = index->prof_on;
   index->prof_on = false;
-  for (Run& r : runs) {
+  // the best of two timed calls after a warm-up
+  auto time_call = [&](auto&& call, double* ms_out) -> lnbnn_status {
     float best = 0.f;
-    for (int rep = 0; rep < 3; ++rep) {  // the first is a warm-up
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaError_t e = cudaEventRecord(e0, s);
+      if (e != cudaSuccess) return status_of(e);
+      const lnbnn_status cs = call();
+      if (cs != LNBNN_OK) return cs;
+      e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) return status_of(e);
+      if (rep == 1 || (rep > 1 && ms < best)) best = ms;
+    }
+    *ms_out = best;
+    return LNBNN_OK;
+  };
+  // split-model runs: one query tile per CTA, one CTA per item
+  index->sched = lnbnn_schedule{0, 1, 0, -1};
+  for (Run& r : runs) {
+    st = time_call([&]() {
       Scratch scratch{index, &w};
       CallProfile prof(index, s);
       const uint64_t* lists = nullptr;
-      CKA(cudaEventRecord(e0, s));
-      st = run_knn(index, scratch, q, r.T * kTcQueryTile, K1, s, &lists, prof, (int)r.splits);
-      if (st != LNBNN_OK) {
-        index->prof_on = prof_was_on;
-        cleanup();
-        return st;
-      }
-      CKA(cudaEventRecord(e1, s));
-      CKA(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CKA(cudaEventElapsedTime(&ms, e0, e1));
-      if (rep == 1 || (rep > 1 && ms < best)) best = ms;
+      return run_knn(index, scratch, q, r.T * kTcQueryTile, r.K1, s, &lists, prof, (int)r.splits);
+    }, &r.ms);
+    if (st != LNBNN_OK) {
+      cleanup();
+      return st;
     }
-    r.ms = best;
   }
-  index->prof_on = prof_was_on;
+  // large-batch forms at the automatic split count of each
+  for (Form& f : cand) {
+    index->sched = lnbnn_schedule{0, f.qt, f.persistent, -1};
+    st = time_call([&]() {
+      Scratch scratch{index, &w};
+      CallProfile prof(index, s);
+      const uint64_t* lists = nullptr;
+      return f.kind == ScanKind::Coarse
+                 ? run_knn_fp8(index, scratch, q, t_big * kTcQueryTile, 11, 32, s, &lists, prof)
+                 : run_knn(index, scratch, q, t_big * kTcQueryTile, 11, s, &lists, prof);
+    }, &f.ms);
+    if (st != LNBNN_OK) {
+      cleanup();
+      return st;
+    }
+  }
   cleanup();
 #undef CKA
-  // least squares for ms = a * waves * tiles + b * waves + c * T * splits + d,
+  // the fastest form of each kind (the first, one query tile per CTA and one
+  // CTA per item, unless another is faster by more than 2%)
+  for (ScanKind k : {ScanKind::Exact, ScanKind::Coarse}) {
+    const Form* best = nullptr;
+    for (const Form& f : cand)
+      if (f.kind == k && (!best || f.ms < best->ms * 0.98)) best = &f;
+    if (!best) continue;
+    index->auto_qt[(int)k] = best->qt;
+    index->auto_persistent[(int)k] = best->persistent;
+    (k == ScanKind::Exact ? res.exact_query_tiles : res.coarse_query_tiles) = best->qt;
+    (k == ScanKind::Exact ? res.exact_persistent : res.coarse_persistent) = best->persistent;
+  }
+  for (size_t i = 0; i < cand.size() && i < 8; ++i) {
+    const int slot = (cand[i].kind == ScanKind::Coarse ? 4 : 0) + 2 * (cand[i].qt - 1) + cand[i].persistent;
+    res.form_ms[slot] = cand[i].ms;
+  }
+  res.form_runs = (int32_t)cand.size();
+  // least squares for ms = a * waves * tiles + b * waves + c * T * splits + e * waves * K1 + d,
   // dropping a term whose coefficient comes out negative
-  bool use[4] = {true, true, true, true};
-  double coef[4] = {0, 0, 0, 0};
+  constexpr int NF = 5;
+  bool use[NF] = {true, true, true, true, true};
+  double coef[NF] = {0, 0, 0, 0, 0};
   auto feat = [&](const Run& r, int j) {
     const int64_t split_len = round_up((n_ref + r.splits - 1) / r.splits, kTcRefTile);
     const int64_t sp = (n_ref + split_len - 1) / split_len;
     const double waves = (double)((r.T * sp + P - 1) / P);
     const double tiles = (double)(split_len / kTcRefTile);
-    return j == 0 ? waves * tiles : j == 1 ? waves : j == 2 ? (double)(r.T * sp) : 1.0;
+    switch (j) {
+      case 0: return waves * tiles;
+      case 1: return waves;
+      case 2: return (double)(r.T * sp);
+      case 3: return waves * (double)r.K1;
+      default: return 1.0;
+    }
   };
-  for (int pass = 0; pass < 4; ++pass) {
-    double A[4][5] = {};
+  for (int pass = 0; pass < NF; ++pass) {
+    double A[NF][NF + 1] = {};
     for (const Run& r : runs)
-      for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) A[i][j] += use[i] && use[j] ? feat(r, i) * feat(r, j) : 0.0;
+      for (int i = 0; i < NF; ++i)
+        for (int j = 0; j < NF; ++j) A[i][j] += use[i] && use[j] ? feat(r, i) * feat(r, j) : 0.0;
     for (const Run& r : runs)
-      for (int i = 0; i < 4; ++i) A[i][4] += use[i] ? feat(r, i) * r.ms : 0.0;
-    for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < NF; ++i) A[i][NF] += use[i] ? feat(r, i) * r.ms : 0.0;
+    for (int i = 0; i < NF; ++i)
       if (!use[i]) A[i][i] = 1.0;
     // Gaussian elimination with partial pivoting
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < NF; ++c) {
       int piv = c;
-      for (int r = c + 1; r < 4; ++r)
+      for (int r = c + 1; r < NF; ++r)
         if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
-      for (int j = 0; j < 5; ++j) std::swap(A[c][j], A[piv][j]);
+      for (int j = 0; j <= NF; ++j) std::swap(A[c][j], A[piv][j]);
       if (std::fabs(A[c][c]) < 1e-300) continue;
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < NF; ++r) {
         if (r == c) continue;
         const double f = A[r][c] / A[c][c];
-        for (int j = c; j < 5; ++j) A[r][j] -= f * A[c][j];
+        for (int j = c; j <= NF; ++j) A[r][j] -= f * A[c][j];
       }
     }
-    for (int i = 0; i < 4; ++i) coef[i] = use[i] && std::fabs(A[i][i]) > 1e-300 ? A[i][4] / A[i][i] : 0.0;
+    for (int i = 0; i < NF; ++i) coef[i] = use[i] && std::fabs(A[i][i]) > 1e-300 ? A[i][NF] / A[i][i] : 0.0;
     int worst = -1;
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < NF - 1; ++i)
       if (use[i] && coef[i] < 0 && (worst < 0 || coef[i] < coef[worst])) worst = i;
     if (worst < 0) break;
     use[worst] = false;
   }
+  res.runs = (int32_t)runs.size();
   if (coef[0] <= 0) {  // measurements no schedule model explains: keep the current model
-    if (out) *out = lnbnn_tuning{0.0, 0.0, 0.0, 0.0, (int32_t)runs.size()};
+    if (out) *out = res;
     return LNBNN_OK;
   }
   index->split_model.a = coef[0];
   index->split_model.b = std::max(0.0, coef[1]);
   index->split_model.c = std::max(0.0, coef[2]);
-  if (out) {
-    out->tile_ms = coef[0];
-    out->wave_ms = index->split_model.b;
-    out->list_ms = index->split_model.c;
-    out->runs = (int32_t)runs.size();
-    double worst = 0;
-    for (const Run& r : runs) {
-      double pred = coef[3];
-      for (int j = 0; j < 3; ++j) pred += (j == 0 ? coef[0] : j == 1 ? index->split_model.b : index->split_model.c) * feat(r, j);
-      worst = std::max(worst, std::fabs(pred - r.ms) / r.ms);
-    }
-    out->max_rel_error = worst;
+  index->split_model.e = std::max(0.0, coef[3]);
+  res.tile_ms = coef[0];
+  res.wave_ms = index->split_model.b;
+  res.list_ms = index->split_model.c;
+  res.entry_ms = index->split_model.e;
+  double worst = 0;
+  for (const Run& r : runs) {
+    const double pred = coef[4] + coef[0] * feat(r, 0) + index->split_model.b * feat(r, 1) +
+                        index->split_model.c * feat(r, 2) + index->split_model.e * feat(r, 3);
+    worst = std::max(worst, std::fabs(pred - r.ms) / r.ms);
   }
+  res.max_rel_error = worst;
+  if (out) *out = res;
   return LNBNN_OK;
 }
 

@@ -71,10 +71,15 @@ class Profile(ctypes.Structure):
 class Tuning(ctypes.Structure):
     """Mirror of ``lnbnn_tuning`` (include/lnbnn.h)."""
     _fields_ = [("tile_ms", ctypes.c_double), ("wave_ms", ctypes.c_double), ("list_ms", ctypes.c_double),
-                ("max_rel_error", ctypes.c_double), ("runs", ctypes.c_int32)]
+                ("max_rel_error", ctypes.c_double), ("runs", ctypes.c_int32), ("exact_query_tiles", ctypes.c_int32),
+                ("entry_ms", ctypes.c_double), ("exact_persistent", ctypes.c_int32),
+                ("coarse_query_tiles", ctypes.c_int32), ("coarse_persistent", ctypes.c_int32),
+                ("form_runs", ctypes.c_int32), ("form_ms", ctypes.c_double * 8)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["form_ms"] = list(self.form_ms)
+        return d
 
 
 class SearchPlan(ctypes.Structure):

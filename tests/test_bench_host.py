@@ -22,20 +22,22 @@ def test_scan_roofline_arithmetic():
     assert abs(r["achieved"] - flops / 1.0 / 1e12) < 1e-9
     assert abs(r["frac"] - r["achieved"] / 1000.0) < 1e-12
     assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
-    assert r["kernel"] == "tc_scan_kernel<FmtBf16, KnnEpilogue<16>>"
-    f = bench.scan_roofline(prof, 1_000_000, 500_000, peaks, "measured", True, 32)
-    assert f["peak"] == 2000.0 and f["kernel"] == "tc_scan_kernel<FmtE4m3, KnnEpilogue<32>>"
-    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 64)["kernel"].endswith("KnnEpilogue<64>>")
-    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 128)["kernel"].endswith("KnnEpilogue<0>>")
-    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, None, 20)["kernel"].endswith("<FmtBf16, KnnEpilogue<32>>")
-    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, None, 100)["kernel"].endswith("<FmtBf16, KnnEpilogue<0>>")
-    assert bench.scan_roofline(prof, 10, 10, peaks, "x", False, None)["kernel"].endswith("NbnnEpilogue>")
+    assert r["kernel"] == "tc_scan_kernel<FmtBf16, KnnEpilogue<16>, 1>"
+    f = bench.scan_roofline(prof, 1_000_000, 500_000, peaks, "measured", True, 32, plan={"tile_m": 256})
+    assert f["peak"] == 2000.0 and f["kernel"] == "tc_scan_kernel<FmtE4m3, KnnEpilogue<32>, 2>"
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 24)["kernel"].endswith("KnnEpilogue<24>, 1>")
+    smem = {"tile_m": 128, "list_storage": "shared memory"}
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 64, plan=smem)["kernel"].endswith("KnnSmemEpilogue<64>, 1>")
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 128)["kernel"].endswith("KnnEpilogue<0>, 1>")
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, None, 20)["kernel"].endswith("<FmtBf16, KnnEpilogue<24>, 1>")
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, None, 100)["kernel"].endswith("<FmtBf16, KnnEpilogue<0>, 1>")
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", False, None)["kernel"].endswith("NbnnEpilogue, 1>")
 
 
 def test_traffic_lookup_matches_committed_capture():
     with open(bench.TRAFFIC_FILE) as f:
         t = json.load(f)
-    name = "tc_scan_kernel<FmtBf16, KnnEpilogue<16>>"
+    name = "tc_scan_kernel<FmtBf16, KnnEpilogue<16>, 1>"
     got = bench.traffic_per_launch(name, 750000)
     if t["kernel_hash"] == bench.kernel_hash():
         assert got == pytest.approx(t["kernels"][name]["dram_bytes_per_launch"])

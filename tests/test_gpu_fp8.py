@@ -45,7 +45,7 @@ def sift_case(classes=12, ref_imgs=4, ref_desc=400, q_imgs=6):
     return ref, labels, q, off, classes
 
 
-@pytest.mark.parametrize("shortlist", [16, 32, 64])
+@pytest.mark.parametrize("shortlist", [16, 24, 32, 64])
 @pytest.mark.parametrize("data", ["uniform", "sift"])
 def test_knn_fp8_matches_oracle(lnbnn, shortlist, data):
     # ragged: N not a multiple of the 256-row tile, M not a multiple of 128

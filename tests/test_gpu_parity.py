@@ -89,9 +89,9 @@ def test_k_range(lnbnn, k):
             check_classify(ix, ref, labels, 7, q, off, k)
 
 
-@pytest.mark.parametrize("K1", [15, 16, 17, 32, 33, 64, 65])
+@pytest.mark.parametrize("K1", [15, 16, 17, 24, 25, 32, 33, 64, 65])
 def test_list_kind_boundaries_many_splits(lnbnn, K1):
-    # k+1 at the edges of the list kinds (16- / 32-entry register lists,
+    # k+1 at the edges of the list kinds (16- / 24- / 32-entry register lists,
     # 64-entry shared-memory lists, heaps), a small batch over many reference
     # splits (so the lists of a row share a bound) and coordinates with ties;
     # exact search and FP8 shortlists of exactly K1 and of 2 K1

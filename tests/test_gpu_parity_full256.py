@@ -117,13 +117,14 @@ def test_fp8_shortlist_sampled_and_one_image(full):
     oracle's coarse form (bit-exact) and its recall against the exact oracle."""
     ix, q, off, w = full["ix"], full["q"], full["off"], full["w"]
     ix.prepare_fp8()
-    plan = ix.plan_search(len(q), 32, fp8=True)
-    assert plan["splits"] >= 1 and plan["list_capacity"] == 32
+    m = 24  # the benchmark's shortlist
+    plan = ix.plan_search(len(q), m, fp8=True)
+    assert plan["splits"] >= 1 and plan["list_capacity"] == 24
     rows = _sample_rows(len(q), 30, 21)
-    idx, dist = ix.knn_search(full["qd"], 11, shortlist=32)
-    t, c = ix.lnbnn_classify(full["qd"], full["offd"], 10, shortlist=32)
+    idx, dist = ix.knn_search(full["qd"], 11, shortlist=m)
+    t, c = ix.lnbnn_classify(full["qd"], full["offd"], 10, shortlist=m)
     ix.sync()
-    od, oj = oracle.knn_coarse(full["ref"], q[rows], 11, 32)
+    od, oj = oracle.knn_coarse(full["ref"], q[rows], 11, m)
     assert np.array_equal(idx.cpu().numpy()[rows], oj.astype(np.int32))
     assert np.array_equal(dist.cpu().numpy()[rows], od.astype(np.int32))
     ed, ej = oracle.knn(full["ref"], q[rows], 11)
@@ -131,5 +132,5 @@ def test_fp8_shortlist_sampled_and_one_image(full):
     assert recall >= 0.99
     img = 123
     qi = q[off[img]:off[img + 1]]
-    ot, oc = oracle.local_nbnn_coarse(full["ref"], full["labels"], w.n_classes, qi, np.array([0, len(qi)]), 10, 32)
+    ot, oc = oracle.local_nbnn_coarse(full["ref"], full["labels"], w.n_classes, qi, np.array([0, len(qi)]), 10, m)
     assert np.array_equal(t.cpu().numpy()[img], ot[0]) and c.cpu().numpy()[img] == oc[0]

@@ -38,7 +38,13 @@ def test_many_splits_and_autotune(lnbnn):
         od, oj = oracle.knn(ref, q_small, 11)
         assert np.array_equal(before[0][0].cpu().numpy(), oj) and np.array_equal(before[0][1].cpu().numpy(), od)
         tuned = ix.autotune()
-        assert tuned["runs"] >= 10 and tuned["tile_ms"] > 0, tuned
+        assert tuned["runs"] >= 20 and tuned["tile_ms"] > 0, tuned
+        # the large-batch forms of the exact scan were timed (no FP8 operand here)
+        assert tuned["form_runs"] == 4 and all(x > 0 for x in tuned["form_ms"][:4]), tuned
+        assert tuned["exact_query_tiles"] in (1, 2) and tuned["exact_persistent"] in (0, 1), tuned
+        assert tuned["coarse_persistent"] == -1 and not any(tuned["form_ms"][4:]), tuned
+        big = ix.plan_search(100_000, 11)
+        assert (big["tile_m"], big["persistent"]) == (128 * tuned["exact_query_tiles"], tuned["exact_persistent"])
         for n in (1, 100, 1000, 20000, 200000):
             s = ix.plan_splits(n)
             assert 1 <= s <= 2 * torch.cuda.get_device_properties(0).multi_processor_count
