@@ -104,8 +104,8 @@ struct Layout {
   static constexpr uint32_t kOffB = QT * kAQueryBytes;
   static constexpr uint32_t kOffBar = kOffB + Stages * S::kStageBytes;
   // full, empty per stage; tmem full, tmem empty per accumulator; A full, A
-  // empty, drain; item full, item empty per item slot
-  static constexpr int kNumBars = 2 * Stages + 2 + 2 + 3 + 2 + 2;
+  // empty, drain; item full, item empty per item slot; lists written
+  static constexpr int kNumBars = 2 * Stages + 2 + 2 + 3 + 2 + 2 + 1;
   static constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;  // TMEM address, abort flag, 2 item slots
   static constexpr uint32_t kOffList = (kOffMisc + 32 + 1023) / 1024 * 1024;
   static constexpr uint32_t kSmemBytes = kOffList + ListBytes + 1024;  // + alignment slack
@@ -144,6 +144,7 @@ struct Bars {
   __device__ uint32_t drain() const { return base + 8 * (2 * kStages + 6); }
   __device__ uint32_t ifull(int i) const { return base + 8 * (2 * kStages + 7 + i); }
   __device__ uint32_t iempty(int i) const { return base + 8 * (2 * kStages + 9 + i); }
+  __device__ uint32_t lists_done() const { return base + 8 * (2 * kStages + 11); }
 };
 
 // The layout of a kernel instantiation: the format's query chunks; ring
@@ -194,6 +195,19 @@ struct RegList {
     }
   }
   __device__ __forceinline__ int32_t worst() const { return d[KMAX - 1]; }
+  // Start from a finished list of K1 ascending keys (kEmptyKey: no entry).
+  __device__ __forceinline__ void seed(const uint64_t* src, int K1) {
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+      if (i >= KMAX - K1) {
+        const uint64_t k = __ldcg(src + (i - (KMAX - K1)));
+        d[i] = k == kEmptyKey ? INT32_MAX : (int32_t)key_dist(k);
+        r[i] = key_row(k);
+      }
+      // at most four keys in flight: the list itself holds the registers
+      if ((i & 3) == 3) asm volatile("" ::: "memory");
+    }
+  }
   // new[i] = old[i-1] if x sorts before it, else min(x, old[i]); requires x < worst().
   __device__ __forceinline__ void insert(int32_t x, uint32_t row) {
 #pragma unroll
@@ -261,6 +275,10 @@ struct ScanOut {
   const uint32_t* gate;      // null, or a word the producer waits to see nonzero before loading
   int32_t* row_thr;          // kNN: per query row, a shared bound (below), or null
   bool bound_per_tile;       // row_thr read and published every tile, or at a work item's start and end
+  uint32_t* done;            // kNN with splits run one after another: per work item, 1 once its lists are
+                             // written (zero before the launch), or null
+  int64_t T;                 // query-tile groups of the launch (work item w - T is the same rows' previous split)
+  int lists_per_split;
 };
 
 // kNN epilogue: the K1 smallest (distance, row) keys of the columns one
@@ -282,6 +300,7 @@ struct ScanOut {
 template <int KMAX>
 struct KnnEpilogue {
   static constexpr int kWarpsPerQuarter = KMAX == kTcWideRegListMax ? 1 : 2;
+  static constexpr bool kSeeds = true;  // can start from the previous split's list of its rows
   static constexpr uint32_t kListBytes = 0;
   RegList<KMAX> L;
   TopK top;
@@ -336,6 +355,23 @@ struct KnnEpilogue {
       __syncwarp();
     }
   }
+  // Start from the same rows' finished list of the previous split (K1
+  // ascending keys of lower reference rows than any column to come, so the
+  // strict distance tests keep exact (distance, row) order): the list then
+  // holds the best keys so far and offers only columns that improve on them.
+  __device__ __forceinline__ void seed(const uint64_t* src) {
+    if (!active) return;
+    if constexpr (KMAX > 0) {
+      L.seed(src, K1);
+      thr = thr_bits(L.worst());
+    } else {
+      for (int i = 0; i < K1; ++i) {
+        const uint64_t k = __ldcg(src + i);
+        if (k != kEmptyKey) top.push(k);
+      }
+      thr = thr_bits(top.threshold);
+    }
+  }
   __device__ __forceinline__ bool full() const {
     if constexpr (KMAX > 0) {
       return L.worst() != INT32_MAX;
@@ -381,11 +417,13 @@ struct KnnEpilogue {
 template <int KM>
 struct KnnSmemEpilogue {
   static constexpr int kWarpsPerQuarter = 1;
+  static constexpr bool kSeeds = false;
   static constexpr int kPerLane = KM / 32;  // list entries each lane computes in an insert
   static constexpr uint32_t kListBytes = 4 * kWarpsPerQuarter * 32 * KM * 8;
   static constexpr int32_t kInf = 0x7F800000;  // bits of +inf, above every distance
   static constexpr int32_t kNoBound = 0x7F7F7F7F;  // the shared bound's initial value
   static_assert(KM % 32 == 0 && KM <= 64, "entries i and i + 32 per lane");
+  __device__ __forceinline__ void seed(const uint64_t*) {}
   uint32_t* D;  // this warp's lists: D[list * KM + i] bit patterns, R[list * KM + i] rows
   uint32_t* R;
   int32_t thr;      // bit pattern of this lane's list's K1-th entry
@@ -519,6 +557,8 @@ struct KnnSmemEpilogue {
 // is uniform across the warp.
 struct NbnnEpilogue {
   static constexpr int kWarpsPerQuarter = 2;
+  static constexpr bool kSeeds = false;
+  __device__ __forceinline__ void seed(const uint64_t*) {}
   static constexpr uint32_t kListBytes = 0;
   __device__ __forceinline__ void tile_end() {}
   int32_t* dst;          // mins + row * C
@@ -633,6 +673,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
     mbar_init(bars.afull(), 1);
     mbar_init(bars.aempty(), kIssuers);
     mbar_init(bars.drain(), kIssuers);
+    mbar_init(bars.lists_done(), kEpiWarps);
     *abort_flag = 0u;
     fence_barrier_init();
   }
@@ -839,6 +880,10 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
       const int list = QT == 2 ? (int)y : (int)y * kEpiPerQuarter + half;
       const bool active = row < m;
       Epilogue epi(out, list, row, active, j_begin + c_off, smem + L::kOffList, warp - 2);
+      // the previous split of these rows, if it has finished: start from its list
+      if (Epilogue::kSeeds && out.done != nullptr && y > 0 && ntiles > 0 &&
+          ld_acquire_gpu(out.done + (w - out.T)) != 0u)
+        epi.seed(out.lists + ((int64_t)(list - out.lists_per_split) * out.stride + (active ? row : 0)) * out.K1);
       bool ok = true;
       for (int t = 0; t < ntiles; ++t, ++tg) {
         const int b = tg & 1;
@@ -871,6 +916,22 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
         epi.tile_end();
       }
       epi.finish();
+      if (Epilogue::kSeeds && out.done != nullptr) {
+        // this item's lists are complete once every epilogue warp has written
+        // its rows' lists; one thread then marks the item done (if the wait
+        // runs out nothing is marked and a later split simply starts empty)
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bars.lists_done());
+        if (warp == 2 && lane == 0 && ok &&
+            mbar_wait(bars.lists_done(), (uint32_t)(i & 1), kWaitLimitNs, abort_flag)) {
+          // the item index again (from its slot, which the producer refills
+          // only after this warp's release below), not kept live across the tiles
+          const int64_t wd = persistent ? item_slot[i & 1] : (int64_t)blockIdx.x;
+          __threadfence();
+          st_release_gpu(out.done + wd, 1u);
+        }
+      }
       if (!ok) break;
       if (persistent) {
         __syncwarp();
@@ -978,10 +1039,14 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const voi
   work.split_len = split_len;
   work.queue = sched.persistent_ctas > 0 ? sched.queue : nullptr;
   if (work.n_items > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
+  ScanOut o = out;
+  o.done = splits > 1 ? sched.done : nullptr;
+  o.T = work.T;
+  o.lists_per_split = QT == 2 ? 1 : Epilogue::kWarpsPerQuarter;
   const int64_t grid = work.queue ? std::min<int64_t>(work.n_items, sched.persistent_ctas) : work.n_items;
   tc_scan_kernel<Fmt, Epilogue, QT>
       <<<(unsigned)grid, threads_for(Epilogue::kWarpsPerQuarter, QT), LayoutOf<Fmt, Epilogue, QT>::kSmemBytes, s>>>(
-          tq, tqe, tr, tre, m, n_ref, work, out, dev_err, stats);
+          tq, tqe, tr, tre, m, n_ref, work, o, dev_err, stats);
   return cudaGetLastError();
 }
 

@@ -71,6 +71,12 @@ struct TcSched {
   int persistent_ctas = 0;     // > 0: a persistent grid of that many CTAs taking work items from *queue
   uint32_t* queue = nullptr;   // the item counter of a persistent launch, zeroed before it
   bool bound_per_tile = true;  // with row_thr: share the row bound every tile, or at item start and end
+  // kNN lists with several splits run one after another: per work item a
+  // flag (zeroed before the launch) set once its lists are written; the
+  // same rows' next split, if it finds the flag set when it starts, begins
+  // from those lists (so a row's lists carry its best keys across splits and
+  // the merge drops the duplicates).  Null: every item starts empty.
+  uint32_t* done = nullptr;
 };
 
 // Split-N schedule of one scan launch over T query-tile groups (qt 128-row

@@ -52,7 +52,7 @@ struct lnbnn_index {
   SplitModel split_model;  // split-N schedule (defaults, or fitted by lnbnn_autotune)
   lnbnn_schedule sched{0, 0, -1, -1};  // lnbnn_set_schedule: fixed choices (0 / -1: automatic)
   // large-batch forms per scan kind (exact, coarse, NBNN), chosen by lnbnn_autotune
-  int auto_qt[3] = {1, 2, 1};
+  int auto_qt[3] = {1, 1, 1};
   int auto_persistent[3] = {0, 0, 0};
   const uint32_t* gate = nullptr;  // lnbnn_set_start_gate: search kernels wait for *gate != 0
   // optional device-time profile (lnbnn_profile_enable)
@@ -240,11 +240,11 @@ bool l2_splits_for(ScanKind k) { return k == ScanKind::Coarse; }
 // The large-batch form of a scan kind (query tiles per CTA, persistent grid)
 // for launches of at least a full wave of query tiles, unless lnbnn_autotune
 // measured another form faster on this index.  Defaults, measured on the
-// 256-class data (750k query rows): the exact and NBNN scans one query tile
-// per CTA (exact 1,356 cycles per step against 1,511 with two; NBNN 1,369
-// against 1,526), the FP8 coarse pass two (shortlist 32: 1,013 against
-// 1,119 ms; 24: 960 against 989 ms); one CTA per work item (persistent grids
-// within 0.2%).
+// 256-class data (750k query rows): one query tile per CTA for every scan
+// (exact 1,356 cycles per step against 1,511 with two; NBNN 1,369 against
+// 1,526; FP8 shortlist 24 with its lists carried across the 37 L2-sized
+// splits 934 against 945 ms with two query tiles and 19 splits); one CTA per
+// work item (persistent grids within 0.2%).
 int auto_query_tiles(const lnbnn_index* ix, ScanKind k, int64_t T1) {
   return T1 >= ix->sm_count ? ix->auto_qt[(int)k] : 1;
 }
@@ -274,14 +274,25 @@ struct KnnPlan {
   int qt;               // 128-row query tiles per CTA
   bool persistent;      // a persistent grid taking items from a queue
   bool bound_per_tile;  // with several splits: the row bound shared every tile (else at item start/end)
-  size_t off_qnorm, off_qbf, off_qext, off_lists, off_merged, off_rowthr, off_queue, bytes;
+  bool seeded;          // each split's lists may start from the same rows' previous split's lists
+  int64_t items;        // work items of the launch (query-tile groups x splits)
+  size_t off_qnorm, off_qbf, off_qext, off_lists, off_merged, off_rowthr, off_queue, off_done, bytes;
   TcSched sched(char* ws, int sm_count) const {
     TcSched t;
     t.qt = qt;
     t.persistent_ctas = persistent ? sm_count : 0;
     t.queue = reinterpret_cast<uint32_t*>(ws + off_queue);
     t.bound_per_tile = bound_per_tile;
+    t.done = seeded ? reinterpret_cast<uint32_t*>(ws + off_done) : nullptr;
     return t;
+  }
+  // Clears what a launch needs zeroed: the work counter of a persistent
+  // launch, the per-item flags of a seeded one.
+  cudaError_t clear(char* ws, cudaStream_t s) const {
+    cudaError_t e = cudaSuccess;
+    if (persistent) e = cudaMemsetAsync(ws + off_queue, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess && seeded) e = cudaMemsetAsync(ws + off_done, 0, sizeof(uint32_t) * (size_t)items, s);
+    return e;
   }
 };
 
@@ -309,6 +320,8 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, ScanKind kind, int sp
   p.splits = (int)((ix->n_ref + p.split_len - 1) / p.split_len);
   p.persistent = o.persistent == 1 || (o.persistent == -1 && auto_persistent(ix, kind, T1));
   p.bound_per_tile = o.bound_per_tile >= 0 ? o.bound_per_tile == 1 : T < P;
+  p.items = T * p.splits;
+  p.seeded = kind != ScanKind::Nbnn && p.splits > 1 && !p.bound_per_tile;
   Carve c;
   p.off_qnorm = c.take<int32_t>(p.m_pad);
   p.off_qbf = c.take<__nv_bfloat16>(p.m_pad * kDim);
@@ -318,6 +331,7 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, ScanKind kind, int sp
   p.off_merged = c.take<uint64_t>(kind == ScanKind::Nbnn ? 0 : (size_t)p.m_pad * K1);  // apart from the lists (rerank)
   p.off_rowthr = c.take<int32_t>(p.m_pad);                // the bound a row's lists share
   p.off_queue = c.take<uint32_t>(1);                      // the work counter of a persistent launch
+  p.off_done = c.take<uint32_t>((size_t)p.items);        // per-item "lists written" flags
   p.bytes = c.off;
   return p;
 }
@@ -355,6 +369,7 @@ NbnnPlan plan_nbnn(const lnbnn_index* ix, int64_t m, int splits = 0) {
   p.off_rowstat = c.take<char>((size_t)p.k.m_pad * kLogoddsRowStatBytes);  // log-odds rule only
   p.off_queue = c.take<uint32_t>(1);
   p.k.off_queue = p.off_queue;
+  p.k.seeded = false;
   p.bytes = c.off;
   return p;
 }
@@ -396,7 +411,7 @@ lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_
   CK(launch_prep_query(q, m, p.m_pad, ix->row_bytes, ix->loc_w, qnorm, qbf, qext, s));
   CK(cudaMemsetAsync(row_thr, 0x7F, sizeof(int32_t) * (size_t)p.m_pad, s));
   const TcSched sched = p.sched(ws, ix->sm_count);
-  if (p.persistent) CK(cudaMemsetAsync(sched.queue, 0, sizeof(uint32_t), s));
+  CK(p.clear(ws, s));
   prof.launched(1);
   prof.mark(1);
   CK(launch_knn_tc(ix->tc, /*sorted_copy=*/false, qbf, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, K1, part,
@@ -430,7 +445,7 @@ lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, in
   CK(launch_prep_query_e4m3(q, m, p.m_pad, qf8, qext, s));
   CK(cudaMemsetAsync(row_thr, 0x7F, sizeof(int32_t) * (size_t)p.m_pad, s));
   const TcSched sched = p.sched(ws, ix->sm_count);
-  if (p.persistent) CK(cudaMemsetAsync(sched.queue, 0, sizeof(uint32_t), s));
+  CK(p.clear(ws, s));
   prof.launched(1);
   prof.mark(1);
   CK(launch_coarse_tc(ix->tc, qf8, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, M1, part, p.m_pad,
@@ -1160,7 +1175,7 @@ static lnbnn_status scan_class_minima(lnbnn_index* index, lnbnn_workspace* w, co
   CK(launch_prep_query(queries, n_queries, p.m_pad, index->row_bytes, index->loc_w, qnorm, qbf, qext, s));
   CK(cudaMemsetAsync(*mins, 0x7F, sizeof(int32_t) * (size_t)p.m_pad * index->n_classes, s));  // > any distance
   const TcSched sched = p.sched(ws, index->sm_count);
-  if (p.persistent) CK(cudaMemsetAsync(sched.queue, 0, sizeof(uint32_t), s));
+  CK(p.clear(ws, s));
   prof.launched(1);
   prof.mark(1);
   CK(launch_nbnn_tc(index->tc, qbf, qext, n_queries, p.m_pad, index->n_ref, p.splits, p.split_len, *mins,

@@ -8,8 +8,10 @@ namespace {
 // Row i's `n_lists` partial lists live at lists[(l * stride + i) * K1]; each is
 // sorted ascending.  One warp per row writes the K1 smallest keys of their
 // union, ascending: lane j holds the heads of lists j, j + 32, ...; each round
-// the warp minimum is written and the list that held it advances.  Keys are
-// unique (each holds a distinct reference row), except the empty key.
+// the warp minimum is written and the list that held it advances.  A key
+// names one reference row; it can sit in several lists of a row when a split
+// started from the previous split's list, and is written once (a key equal to
+// the last one written only advances its lists).
 constexpr int kMergeWarps = 4;
 // Up to this many lists a thread merges a row on its own (few lists: the
 // warp form would leave most lanes idle).
@@ -26,7 +28,8 @@ __global__ void merge_lists_thread_kernel(const uint64_t* __restrict__ lists, in
     pos[l] = 0;
     head[l] = l < n_lists ? lists[((int64_t)l * stride + i) * K1] : kEmptyKey;
   }
-  for (int t = 0; t < K1; ++t) {
+  uint64_t last = kEmptyKey;
+  for (int t = 0; t < K1;) {
     uint64_t best = head[0];
     int bl = 0;
 #pragma unroll
@@ -35,7 +38,12 @@ __global__ void merge_lists_thread_kernel(const uint64_t* __restrict__ lists, in
         best = head[l];
         bl = l;
       }
-    out[i * K1 + t] = best;
+    const bool dup = best != kEmptyKey && best == last;
+    if (!dup) {
+      out[i * K1 + t] = best;
+      ++t;
+      last = best;
+    }
     if (best == kEmptyKey) continue;
 #pragma unroll
     for (int l = 0; l < kThreadMergeLists; ++l)
@@ -60,7 +68,8 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
     pos[c] = 0;
     head[c] = l < n_lists ? lists[((int64_t)l * stride + i) * K1] : kEmptyKey;
   }
-  for (int t = 0; t < K1; ++t) {
+  uint64_t last = kEmptyKey;
+  for (int t = 0; t < K1;) {
     uint64_t best = kEmptyKey;
     int bc = 0;
 #pragma unroll
@@ -72,7 +81,12 @@ __global__ void __launch_bounds__(32 * kMergeWarps)
     uint64_t wmin = best;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) wmin = min(wmin, __shfl_xor_sync(0xffffffffu, wmin, off));
-    if (lane == 0) out[i * K1 + t] = wmin;
+    const bool dup = wmin != kEmptyKey && wmin == last;  // warp-uniform
+    if (!dup) {
+      if (lane == 0) out[i * K1 + t] = wmin;
+      ++t;
+      last = wmin;
+    }
     if (wmin != kEmptyKey && best == wmin) {
 #pragma unroll
       for (int c = 0; c < kMaxListsPerLane; ++c)

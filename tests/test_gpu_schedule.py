@@ -143,3 +143,33 @@ def test_schedule_arguments_are_checked(lnbnn):
         ix.set_schedule(automatic=True)
         p = ix.plan_search(100, 11)
         assert p["tile_m"] == 128 and p["persistent"] == 0
+
+
+def test_lists_seeded_from_earlier_splits(lnbnn):
+    """More query tiles than SMs and several splits run one after another: a
+    split's lists start from the same rows' finished lists of the previous
+    split (duplicates merged away).  Every list kind, Local NBNN and the FP8
+    shortlist equal the oracle, with one CTA per item and persistent."""
+    N, M, C = 30_000 + 5, 160 * 128 + 77, 6  # 161 query tiles
+    ref, labels, q, off = _case(93, N, M, C)
+    rows = np.random.default_rng(94).choice(M, size=1500, replace=False)
+    with lnbnn.Index(dev(ref), dev(labels), C) as ix:
+        ix.prepare_fp8()
+        qd, od = dev(q), dev(off)
+        for persistent in (0, 1):
+            ix.set_schedule(splits=5, query_tiles=1, persistent=persistent, bound_per_tile=0)
+            for k1 in (11, 24, 32, 101):
+                i, d = ix.knn_search(qd, k1)
+                ix.sync()
+                od_, oj = oracle.knn(ref, q[rows], k1)
+                assert np.array_equal(d.cpu().numpy()[rows], od_) and np.array_equal(i.cpu().numpy()[rows], oj), k1
+            t, c = ix.lnbnn_classify(qd, od, 10)
+            ix.sync()
+            wt, wc = oracle.local_nbnn(ref, labels, C, q, off, 10)
+            assert np.array_equal(t.cpu().numpy(), wt) and np.array_equal(c.cpu().numpy(), wc)
+            ix.set_schedule(splits=5, query_tiles=2, persistent=persistent, bound_per_tile=0)
+            fi, fd = ix.knn_search(qd, 11, shortlist=24)
+            ix.sync()
+            cd, cj = oracle.knn_coarse(ref, q[rows], 11, 24)
+            assert np.array_equal(fd.cpu().numpy()[rows], cd) and np.array_equal(fi.cpu().numpy()[rows], cj)
+        ix.set_schedule(automatic=True)
