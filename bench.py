@@ -206,10 +206,11 @@ def measured_peaks() -> tuple[dict, str]:
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def traffic_per_launch(kernel: str, n_query_rows: int) -> float | None:
-    """DRAM bytes per launch of a search kernel from a committed ncu capture,
-    scaled to this launch by query rows; None if the kernel changed since or
-    was not captured."""
+def traffic_per_launch(kernel: str, n_query_rows: int, n_ref: int) -> float | None:
+    """DRAM bytes of one launch of a search kernel from a committed ncu capture
+    of a smaller case, scaled by query rows x references (an upper bound: a
+    larger launch reuses L2 more); None if the kernel changed since or was not
+    captured."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     with open(TRAFFIC_FILE) as f:
@@ -217,7 +218,7 @@ def traffic_per_launch(kernel: str, n_query_rows: int) -> float | None:
     if t.get("kernel_hash") != kernel_hash() or kernel not in t.get("kernels", {}):
         return None
     k = t["kernels"][kernel]
-    return k["dram_bytes_per_launch"] * n_query_rows / k["query_rows"]
+    return k["dram_bytes"] * (n_query_rows * n_ref) / (k["query_rows"] * k["n_ref"])
 
 
 def max_over_ranks(x: float, device=None) -> float:
@@ -356,7 +357,9 @@ def run_ours(args, w):
     roofline = scan_roofline(prof, w.n_ref, M, peaks, peak_src, local, shortlist, k, plan)
     if plan:
         roofline["schedule"] = plan
-    roofline["traffic"] = traffic_per_launch(roofline["kernel"], M)
+    roofline["traffic"] = traffic_per_launch(roofline["kernel"], M, w.n_ref)
+    roofline["traffic_note"] = ("ncu DRAM bytes of a 101-class, 20-image launch scaled by query rows x references "
+                                "(an upper bound; profiles/knn_tc_traffic.json)")
 
     e2e = None
     if not args.no_e2e:
@@ -399,7 +402,7 @@ def run_ours(args, w):
                          "roofline": scan_roofline(prof8, w.n_ref, M, peaks, peak_src, True, m_short, k,
                                                    index.plan_search(M, m_short, fp8=True)),
                          "gpu_launches": int(prof8["kernel_launches"])}
-            fp8_block["roofline"]["traffic"] = traffic_per_launch(fp8_block["roofline"]["kernel"], M)
+            fp8_block["roofline"]["traffic"] = traffic_per_launch(fp8_block["roofline"]["kernel"], M, w.n_ref)
         index.sync()
         fp8_block.update(fp8_accuracy(index, q_d, q, ref, k, m_short, t_x, c_x, t_f, c_f, args.recall_rows,
                                       args.oracle_recall_rows if rank == 0 and world == 1 else 0))

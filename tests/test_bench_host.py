@@ -38,13 +38,15 @@ def test_traffic_lookup_matches_committed_capture():
     with open(bench.TRAFFIC_FILE) as f:
         t = json.load(f)
     name = "tc_scan_kernel<FmtBf16, KnnEpilogue<16>, 1>"
-    got = bench.traffic_per_launch(name, 750000)
+    k = t["kernels"][name]
+    got = bench.traffic_per_launch(name, k["query_rows"], k["n_ref"])
     if t["kernel_hash"] == bench.kernel_hash():
-        assert got == pytest.approx(t["kernels"][name]["dram_bytes_per_launch"])
-        assert bench.traffic_per_launch(name, 375000) == pytest.approx(got / 2)
+        assert got == pytest.approx(k["dram_bytes"])
+        # scaled by query rows x references
+        assert bench.traffic_per_launch(name, 2 * k["query_rows"], 3 * k["n_ref"]) == pytest.approx(6 * got)
     else:  # sources changed since the capture: no stale number is reported
         assert got is None
-    assert bench.traffic_per_launch("no such kernel", 750000) is None
+    assert bench.traffic_per_launch("no such kernel", 750000, 11520000) is None
 
 
 def test_measured_peaks_and_workload_config():
