@@ -252,6 +252,21 @@ bool auto_persistent(const lnbnn_index* ix, ScanKind k, int64_t T1) {
   return T1 >= ix->sm_count && ix->auto_persistent[(int)k] == 1;
 }
 
+// Splits for the exact scan of a launch of at least a full wave whose lists
+// are dearer than the 16-entry ones: with the splits run one after another
+// and their lists carried across, the later splits insert little, and the
+// shorter reference ranges stay in L2.  Measured on the 256-class data (300k
+// query rows): k = 20 (24-entry lists) 1 / 4 splits 556 / 527 ms; k = 100
+// (heaps) 1 / 2 / 4 / 8 splits 1,493 / 1,464 / 1,437 / 1,413 ms.  The
+// 64-entry lists keep one split (at shorter splits they move to shared
+// memory, 2,660 against 2,367 cycles per step at k = 50).
+int long_list_splits(const lnbnn_index* ix, int K1) {
+  int want = 1;
+  if (K1 > kTcRegListMax && K1 <= kTcCoarseRegListMax) want = 4;
+  if (K1 > kTcWideRegListMax) want = 8;
+  return (int)std::min<int64_t>(want, std::max<int64_t>(1, ix->n_ref / (int64_t(1) << 20)));
+}
+
 int64_t l2_splits(const lnbnn_index* ix, ScanKind k) {
   const int64_t bytes = ix->n_ref * op_row_bytes(k);
   return std::min<int64_t>(max_splits(ix), std::max<int64_t>(1, (bytes + kL2SplitBytes - 1) / kL2SplitBytes));
@@ -261,7 +276,7 @@ int64_t l2_splits(const lnbnn_index* ix, ScanKind k) {
 // are sized for it).
 int64_t splits_bound(const lnbnn_index* ix, int64_t T, ScanKind k) {
   int64_t hi = max_splits_for(T, ix->n_ref, ix->sm_count, max_splits(ix));
-  if (T >= ix->sm_count) hi = std::max(hi, l2_splits(ix, k));
+  if (T >= ix->sm_count) hi = std::max<int64_t>(hi, std::max<int64_t>(l2_splits(ix, k), 8));
   return hi;
 }
 
@@ -315,6 +330,7 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, ScanKind kind, int sp
   if (splits <= 0) {
     splits = choose_splits_model(ix->split_model, T, ix->n_ref, P, max_splits(ix), p.qt, K1);
     if (T >= P && l2_splits_for(kind)) splits = (int)std::max<int64_t>(splits, l2_splits(ix, kind));
+    if (T >= P && kind == ScanKind::Exact) splits = std::max(splits, long_list_splits(ix, K1));
   }
   p.split_len = round_up((ix->n_ref + splits - 1) / splits, kTcRefTile);
   p.splits = (int)((ix->n_ref + p.split_len - 1) / p.split_len);
