@@ -281,7 +281,13 @@ LNBNN_API lnbnn_status lnbnn_classify_fp8_ws(lnbnn_index *index, lnbnn_workspace
  *   waves(groups * splits) * (a * qt * tiles_per_item + b + e * k1)
  *     + c * groups * splits,
  * where the term e * k1 (k1 = list length) is the cost of filling one item's
- * lists, so longer lists favour fewer splits.  lnbnn_autotune times about
+ * lists, so longer lists favour fewer splits.  A launch with at least one
+ * wave of query tiles also takes at least as many splits as keep each
+ * split's reference bytes in L2 for the FP8 coarse pass (48 MB a split), and
+ * 4 (lists of 17..32 entries) or 8 (heaps) for the exact scan; the splits of
+ * a row then run one after another, and each starts from the row's lists of
+ * the previous split when that split has finished (the results never depend
+ * on whether it has).  lnbnn_autotune times about
  * thirty search launches of 1 to 64 query tiles (query rows copied from the
  * index's own references) with several split counts and two list lengths
  * (k1 = 11 and 51) on `stream` and fits a, b, c, e by least squares; then, on

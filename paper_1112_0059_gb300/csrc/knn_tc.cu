@@ -25,21 +25,28 @@
 // 2 q'.r'), and with the extension issued first every partial sum stays in
 // [0, 2^24), so FP32 holds it exactly.
 //
-// Roles (one CTA = 128 query rows x one reference split):
-//   warp 0, one thread : TMA producer (query tile once; reference K-chunks
-//                        into a 4-stage ring, the K-extension riding with the
-//                        second chunk of each tile)
+// Work: a launch covers T groups of QT query tiles (128 rows each) x S
+// reference splits as T x S work items, split-major; a CTA takes one item, or
+// (persistent form) items from a queue one after another (see Work below).
+//
+// Roles (one CTA = QT query tiles x one reference split at a time):
+//   warp 0, one thread : TMA producer (the item's query tiles; reference
+//                        K-chunks into a ring, the K-extension riding with
+//                        the last chunk of each tile)
 //   warp 1, one thread : tcgen05.mma issuer (9 MMAs of 128x256x16 per tile);
-//                        warp 1 also owns the TMEM allocation
+//                        warp 1 also owns the TMEM allocation; with QT = 2 a
+//                        second issuer (the warp after the epilogue warps)
+//                        issues the second query tile's MMAs
 //   warps 2-9          : epilogue: two warps per TMEM lane quarter, each
-//                        taking a 128-column half of every tile with one
-//                        thread per query row (TMEM lane); each keeps its own
-//                        sorted list of the k+1 nearest (in registers for
-//                        k+1 <= 64, otherwise a heap in global memory; for
-//                        33..64 one warp per quarter takes all 256 columns,
-//                        to have the registers); two
-//                        256-column FP32 accumulators in flight; each
-//                        32-column load also returns the columns' minimum
+//                        taking a 128-column half of every tile (QT = 2: its
+//                        query tile's 128 x 128 block) with one thread per
+//                        query row (TMEM lane); each keeps its own sorted
+//                        list of the k+1 nearest (in registers for k+1 <= 64,
+//                        otherwise a heap in global memory; for 33..64 one
+//                        warp per quarter takes all 256 columns, to have the
+//                        registers); two 256-column FP32 accumulators in
+//                        flight; each 32-column load also returns the
+//                        columns' minimum
 // Every wait is bounded; on expiry the CTA records a timeout in the index's
 // device error word, drains what it issued and returns.
 #include <cudaTypedefs.h>

@@ -1,5 +1,5 @@
 """Host-side logic of the measurement scripts: roofline arithmetic, the
-committed ncu traffic lookup, workload descriptions and sweep tables."""
+committed ncu traffic lookup, workload descriptions, sections and row samples."""
 import json
 import os
 import sys
