@@ -829,23 +829,29 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
               break;
             }
             tc_fence_after();
+            // descriptors are built once per stage and advanced by adding the
+            // byte offset >> 4 to their start-address field (14 bits of
+            // addr >> 4; every shared address is below 256 KB, so the sum
+            // never carries out of the field): the MMA thread's issue loop is
+            // on the critical path of the N = 128 shape, which issues twice
+            // as many MMAs per step
             const uint32_t b_base = sbase + L::kOffB + s * Sh::kStageBytes;
+            const uint64_t b_desc = sw128_kmajor_desc(b_base);
+            const uint64_t b_ext = sw32_kmajor_desc(b_base + Sh::kBChunkBytes);
             const bool last = kc == KC - 1;  // the norms' K-extension rides with the last chunk
-            for (int q = q_first; q < q_last; ++q) {
-              const uint32_t a_q = sbase + L::kOffA + q * L::kAQueryBytes;
-              const uint32_t d_q = d_tmem + q * kTileN;
-              if (Fmt::kExtFirst && last)
-                mma_bf16(d_q, sw32_kmajor_desc(a_q + KC * kAChunkBytes), sw32_kmajor_desc(b_base + Sh::kBChunkBytes),
-                         idesc_bf16_f32(kBM, kTileN), kc != 0 ? 1u : 0u);
 #pragma unroll
-              for (int kk = 0; kk < kMmaPerChunk; ++kk) {
-                Fmt::template mma<kTileN>(d_q, sw128_kmajor_desc(a_q + kc * kAChunkBytes + kk * 32),
-                                          sw128_kmajor_desc(b_base + kk * 32),
+            for (int q = 0; q < QT; ++q) {
+              if (q < q_first || q >= q_last) continue;
+              const uint32_t a_q = sbase + L::kOffA + q * L::kAQueryBytes;
+              const uint64_t a_desc = sw128_kmajor_desc(a_q) + (uint64_t)((kc * kAChunkBytes) >> 4);
+              const uint64_t a_ext = sw32_kmajor_desc(a_q + KC * kAChunkBytes);
+              const uint32_t d_q = d_tmem + q * kTileN;
+              if (Fmt::kExtFirst && last) mma_bf16(d_q, a_ext, b_ext, idesc_bf16_f32(kBM, kTileN), kc != 0 ? 1u : 0u);
+#pragma unroll
+              for (int kk = 0; kk < kMmaPerChunk; ++kk)  // K-steps of 32 bytes
+                Fmt::template mma<kTileN>(d_q, a_desc + (uint64_t)(2 * kk), b_desc + (uint64_t)(2 * kk),
                                           (kc | kk) != 0 || (Fmt::kExtFirst && last) ? 1u : 0u);
-              }
-              if (!Fmt::kExtFirst && last)
-                mma_bf16(d_q, sw32_kmajor_desc(a_q + KC * kAChunkBytes), sw32_kmajor_desc(b_base + Sh::kBChunkBytes),
-                         idesc_bf16_f32(kBM, kTileN), 1u);
+              if (!Fmt::kExtFirst && last) mma_bf16(d_q, a_ext, b_ext, idesc_bf16_f32(kBM, kTileN), 1u);
             }
             mma_commit(bars.empty(s));  // the producer may refill this stage
           }
