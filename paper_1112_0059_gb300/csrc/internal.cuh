@@ -81,10 +81,18 @@ cudaError_t launch_gather_ref(const int64_t* perm, int64_t n, const __nv_bfloat1
 cudaError_t launch_fill_float(float* dst, int64_t n, float v, cudaStream_t s);
 
 // Merge `splits` sorted lists per row into one sorted list of K1 keys
-// (at most 32 * kMaxListsPerLane lists).
+// (at most 32 * kMaxListsPerLane lists).  With `chain.done` set (the scan's
+// per-work-item flags of a launch whose splits carried their lists), a row
+// whose last split reports 2 merges only that split's lists_per_split lists.
 constexpr int kMaxListsPerLane = 20;
+struct MergeChain {
+  const uint32_t* done = nullptr;
+  int64_t T = 0;              // query-tile groups: work item x + y T is split y of group x
+  int64_t rows_per_item = 0;  // query rows per group
+  int lists_per_split = 0;
+};
 cudaError_t launch_merge_lists(const uint64_t* lists, int splits, int64_t m, int64_t list_stride_rows,
-                               int K1, uint64_t* out, cudaStream_t s);
+                               int K1, uint64_t* out, cudaStream_t s, const MergeChain& chain = MergeChain{});
 // knn_search output: first k entries of each sorted list as (row, distance).
 cudaError_t launch_extract_knn(const uint64_t* lists, int64_t m, int K1, int k, int32_t* idx,
                                int32_t* dist, cudaStream_t s);

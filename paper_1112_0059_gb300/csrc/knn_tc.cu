@@ -113,8 +113,9 @@ struct Layout {
   // full, empty per stage; tmem full, tmem empty per accumulator; A full, A
   // empty, drain; item full, item empty per item slot; lists written
   static constexpr int kNumBars = 2 * Stages + 2 + 2 + 3 + 2 + 2 + 1;
-  static constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;  // TMEM address, abort flag, 2 item slots
-  static constexpr uint32_t kOffList = (kOffMisc + 32 + 1023) / 1024 * 1024;
+  // TMEM address, abort flag, 2 item slots, 2 "an earlier split was not carried" words
+  static constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;
+  static constexpr uint32_t kOffList = (kOffMisc + 48 + 1023) / 1024 * 1024;
   static constexpr uint32_t kSmemBytes = kOffList + ListBytes + 1024;  // + alignment slack
   static_assert(Stages % AChunks == 0, "a tile's chunks map to fixed stage parities");
   static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
@@ -282,8 +283,9 @@ struct ScanOut {
   const uint32_t* gate;      // null, or a word the producer waits to see nonzero before loading
   int32_t* row_thr;          // kNN: per query row, a shared bound (below), or null
   bool bound_per_tile;       // row_thr read and published every tile, or at a work item's start and end
-  uint32_t* done;            // kNN with splits run one after another: per work item, 1 once its lists are
-                             // written (zero before the launch), or null
+  uint32_t* done;            // kNN with splits run one after another: per work item, nonzero once its
+                             // lists are written, 2 if they also hold every earlier split's keys (zero
+                             // before the launch), or null
   int64_t T;                 // query-tile groups of the launch (work item w - T is the same rows' previous split)
   int lists_per_split;
 };
@@ -652,6 +654,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::kOffMisc);
   volatile uint32_t* abort_flag = tmem_slot + 1;
   volatile int64_t* item_slot = reinterpret_cast<volatile int64_t*>(smem + L::kOffMisc + 16);
+  volatile uint32_t* chain_broken = reinterpret_cast<volatile uint32_t*>(smem + L::kOffMisc + 32);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -682,6 +685,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
     mbar_init(bars.drain(), kIssuers);
     mbar_init(bars.lists_done(), kEpiWarps);
     *abort_flag = 0u;
+    chain_broken[0] = chain_broken[1] = 0u;
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
@@ -893,10 +897,17 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
       const int list = QT == 2 ? (int)y : (int)y * kEpiPerQuarter + half;
       const bool active = row < m;
       Epilogue epi(out, list, row, active, j_begin + c_off, smem + L::kOffList, warp - 2);
-      // the previous split of these rows, if it has finished: start from its list
-      if (Epilogue::kSeeds && out.done != nullptr && y > 0 && ntiles > 0 &&
-          ld_acquire_gpu(out.done + (w - out.T)) != 0u)
-        epi.seed(out.lists + ((int64_t)(list - out.lists_per_split) * out.stride + (active ? row : 0)) * out.K1);
+      // the previous split of these rows, if it has finished: start from its
+      // list.  Its flag says 2 when every earlier split of the rows was
+      // carried into it; a warp that cannot say the same of this item marks
+      // the item's slot (cleared by the thread that publishes the slot's
+      // previous item before that item's slot is released)
+      if (Epilogue::kSeeds && out.done != nullptr) {
+        const uint32_t prev = y > 0 && ntiles > 0 ? ld_acquire_gpu(out.done + (w - out.T)) : 0u;
+        if (prev != 0u)
+          epi.seed(out.lists + ((int64_t)(list - out.lists_per_split) * out.stride + (active ? row : 0)) * out.K1);
+        if (lane == 0 && y > 0 && prev != 2u) chain_broken[i & 1] = 1u;
+      }
       bool ok = true;
       for (int t = 0; t < ntiles; ++t, ++tg) {
         const int b = tg & 1;
@@ -931,8 +942,10 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
       epi.finish();
       if (Epilogue::kSeeds && out.done != nullptr) {
         // this item's lists are complete once every epilogue warp has written
-        // its rows' lists; one thread then marks the item done (if the wait
-        // runs out nothing is marked and a later split simply starts empty)
+        // its rows' lists; one thread then marks the item done: 2 if its
+        // lists hold every earlier split's keys (each split of the rows
+        // started from the one before), else 1 (if the wait runs out nothing
+        // is marked and a later split simply starts empty)
         __threadfence();
         __syncwarp();
         if (lane == 0) mbar_arrive(bars.lists_done());
@@ -941,8 +954,10 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
           // the item index again (from its slot, which the producer refills
           // only after this warp's release below), not kept live across the tiles
           const int64_t wd = persistent ? item_slot[i & 1] : (int64_t)blockIdx.x;
+          const uint32_t flag = chain_broken[i & 1] != 0u ? 1u : 2u;
+          chain_broken[i & 1] = 0u;
           __threadfence();
-          st_release_gpu(out.done + wd, 1u);
+          st_release_gpu(out.done + wd, flag);
         }
       }
       if (!ok) break;

@@ -309,6 +309,17 @@ struct KnnPlan {
     if (e == cudaSuccess && seeded) e = cudaMemsetAsync(ws + off_done, 0, sizeof(uint32_t) * (size_t)items, s);
     return e;
   }
+  // The merge's view of a seeded launch: rows whose last split holds every
+  // split's keys merge only that split's lists.
+  MergeChain chain(char* ws) const {
+    MergeChain c;
+    if (!seeded) return c;
+    c.done = reinterpret_cast<const uint32_t*>(ws + off_done);
+    c.T = items / splits;
+    c.rows_per_item = (int64_t)kTcQueryTile * qt;
+    c.lists_per_split = lists / splits;
+    return c;
+  }
 };
 
 // The launch schedule of a scan over m queries keeping K1 keys per row:
@@ -436,7 +447,7 @@ lnbnn_status run_knn(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, int64_
   prof.launched(1, true);
   prof.mark(2);
   if (p.lists > 1) {
-    CK(launch_merge_lists(part, p.lists, m, p.m_pad, K1, merged, s));
+    CK(launch_merge_lists(part, p.lists, m, p.m_pad, K1, merged, s, p.chain(ws)));
     prof.launched(1);
   }
   *lists = p.lists > 1 ? merged : part;
@@ -472,7 +483,7 @@ lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, in
   // the shortlist is the merged lists (or the one list); the reranked lists
   // go to the other buffer
   if (p.lists > 1) {
-    CK(launch_merge_lists(part, p.lists, m, p.m_pad, M1, merged, s));
+    CK(launch_merge_lists(part, p.lists, m, p.m_pad, M1, merged, s, p.chain(ws)));
     CK(launch_rerank(merged, m, M1, q, ix->ref_u8, ix->n_ref, K1, part, s));
     prof.launched(2);
     *lists = part;

@@ -17,10 +17,24 @@ constexpr int kMergeWarps = 4;
 // warp form would leave most lanes idle).
 constexpr int kThreadMergeLists = 8;
 
+// The first list of row i to merge: all of them, or only the last split's
+// when that split's work item says its lists hold every earlier split's keys
+// (the scan's done flag 2).  Work item x + y T covers query rows
+// [x rows_per_item, (x + 1) rows_per_item) of split y.
+__device__ __forceinline__ int first_list(const MergeChain& c, int64_t i, int n_lists) {
+  if (c.done == nullptr) return 0;
+  const int splits = n_lists / c.lists_per_split;
+  const int64_t w = i / c.rows_per_item + (int64_t)(splits - 1) * c.T;
+  return c.done[w] == 2u ? n_lists - c.lists_per_split : 0;
+}
+
 __global__ void merge_lists_thread_kernel(const uint64_t* __restrict__ lists, int n_lists, int64_t m, int64_t stride,
-                                          int K1, uint64_t* __restrict__ out) {
+                                          int K1, MergeChain chain, uint64_t* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
+  const int l0 = first_list(chain, i, n_lists);
+  lists += (int64_t)l0 * stride * K1;
+  n_lists -= l0;
   int pos[kThreadMergeLists];
   uint64_t head[kThreadMergeLists];
 #pragma unroll
@@ -56,10 +70,13 @@ __global__ void merge_lists_thread_kernel(const uint64_t* __restrict__ lists, in
 
 __global__ void __launch_bounds__(32 * kMergeWarps)
     merge_lists_kernel(const uint64_t* __restrict__ lists, int n_lists, int64_t m, int64_t stride, int K1,
-                       uint64_t* __restrict__ out) {
+                       MergeChain chain, uint64_t* __restrict__ out) {
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * kMergeWarps + (threadIdx.x >> 5);
   if (i >= m) return;
+  const int l0 = first_list(chain, i, n_lists);  // the same for the whole warp (one row)
+  lists += (int64_t)l0 * stride * K1;
+  n_lists -= l0;
   uint64_t head[kMaxListsPerLane];
   int pos[kMaxListsPerLane];
 #pragma unroll
@@ -238,15 +255,18 @@ __global__ void argmin_kernel(const int64_t* __restrict__ totals, int64_t n_img,
 }  // namespace
 
 cudaError_t launch_merge_lists(const uint64_t* lists, int splits, int64_t m, int64_t stride, int K1, uint64_t* out,
-                               cudaStream_t s) {
+                               cudaStream_t s, const MergeChain& chain) {
   if (m == 0) return cudaSuccess;
   if (splits < 1 || splits > 32 * kMaxListsPerLane) return cudaErrorInvalidValue;
+  if (chain.done != nullptr &&
+      (chain.lists_per_split < 1 || splits % chain.lists_per_split != 0 || chain.T < 1 || chain.rows_per_item < 1))
+    return cudaErrorInvalidValue;
   if (splits <= kThreadMergeLists) {
-    merge_lists_thread_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(lists, splits, m, stride, K1, out);
+    merge_lists_thread_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(lists, splits, m, stride, K1, chain, out);
     return cudaGetLastError();
   }
-  merge_lists_kernel<<<(unsigned)((m + kMergeWarps - 1) / kMergeWarps), 32 * kMergeWarps, 0, s>>>(lists, splits, m,
-                                                                                                stride, K1, out);
+  merge_lists_kernel<<<(unsigned)((m + kMergeWarps - 1) / kMergeWarps), 32 * kMergeWarps, 0, s>>>(
+      lists, splits, m, stride, K1, chain, out);
   return cudaGetLastError();
 }
 
