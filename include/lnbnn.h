@@ -338,17 +338,13 @@ LNBNN_API lnbnn_status lnbnn_plan_splits(const lnbnn_index *index, int64_t n_que
  * split; the sorted lists per query row the scan writes (merged afterwards
  * when more than one); where each list lives (list_storage 0: registers, 1:
  * shared memory, 2: a heap in global memory) and how many entries it holds
- * (16, 24, 32 or 64; k1 for a heap); the tile of query rows x references one CTA
+ * (16, 32 or 64; k1 for a heap); the tile of query rows x references one CTA
  * computes per step (tile_m query rows x tile_n references); persistent = 1
  * when a fixed grid of CTAs takes (query tiles, split) work items from a
  * queue instead of one CTA per item; bound_per_tile: how the lists of a row
  * share their bound when there are several splits (1: every tile, as the
  * splits of a row run at the same time; 0: read when a list starts and
- * published when it ends, as they run one after another; -1: one split);
- * interleaved = 1 when split y scans every splits-th 256-row reference tile
- * starting at tile y (several splits whose lists are not carried from one
- * split to the next: every split then sees every part of a class-sorted
- * reference set), 0 when it scans one contiguous range of split_len rows.
+ * published when it ends, as they run one after another; -1: one split).
  * Errors: INVALID_ARG (null pointers, n_queries < 1), K_RANGE (k1 outside
  * [1, LNBNN_MAX_K + 1] or above n_ref), NO_FP8 (fp8 != 0 on an index without
  * the FP8 operand).
@@ -363,7 +359,6 @@ typedef struct lnbnn_search_plan {
   int32_t tile_n;
   int32_t persistent;
   int32_t bound_per_tile;
-  int32_t interleaved;
 } lnbnn_search_plan;
 
 LNBNN_API lnbnn_status lnbnn_plan_search(const lnbnn_index *index, int64_t n_queries, int32_t k1, int32_t fp8,

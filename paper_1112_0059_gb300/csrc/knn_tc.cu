@@ -317,8 +317,6 @@ template <int KMAX>
 struct KnnEpilogue {
   static constexpr int kWarpsPerQuarter = KMAX == kTcWideRegListMax ? 1 : 2;
   static constexpr bool kSeeds = true;  // can start from the previous split's list of its rows
-  // lists take columns in any tile order, as long as each list gets them in increasing row order
-  static constexpr bool kAnyTileOrder = true;
   static constexpr uint32_t kListBytes = 0;
   RegList<KMAX> L;
   TopK top;
@@ -449,8 +447,6 @@ template <int KM>
 struct KnnSmemEpilogue {
   static constexpr int kWarpsPerQuarter = 1;
   static constexpr bool kSeeds = false;
-  // lists take columns in any tile order, as long as each list gets them in increasing row order
-  static constexpr bool kAnyTileOrder = true;
   static constexpr int kPerLane = KM / 32;  // list entries each lane computes in an insert
   static constexpr uint32_t kListBytes = 4 * kWarpsPerQuarter * 32 * KM * 8;
   static constexpr int32_t kInf = 0x7F800000;  // bits of +inf, above every distance
@@ -591,8 +587,6 @@ struct KnnSmemEpilogue {
 struct NbnnEpilogue {
   static constexpr int kWarpsPerQuarter = 2;
   static constexpr bool kSeeds = false;
-  // walks the classes of a contiguous reference range
-  static constexpr bool kAnyTileOrder = false;
   __device__ __forceinline__ void seed(const uint64_t*) {}
   static constexpr uint32_t kListBytes = 0;
   __device__ __forceinline__ void tile_end() {}
@@ -654,9 +648,6 @@ struct Work {
   int64_t n_items;
   int64_t split_len;
   uint32_t* queue;
-  int splits;
-  bool interleaved;   // split y takes reference tiles y, y + splits, ... (else rows [y split_len, (y+1) split_len))
-  int64_t tile_step;  // reference rows from one of an item's tiles to the next
 };
 
 template <class Fmt, class Epilogue, int QT>
@@ -740,11 +731,6 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
   auto item_tiles = [&](int64_t w, int64_t* m0, int64_t* j_begin) -> int {
     const int64_t x = w % work.T, y = w / work.T;
     *m0 = x * (int64_t)(kBM * QT);
-    if (work.interleaved) {
-      *j_begin = y * kTileN;
-      const int64_t n_tiles = (n_ref + kTileN - 1) / kTileN;
-      return stale_timeout || y >= n_tiles ? 0 : (int)((n_tiles - y + work.splits - 1) / work.splits);
-    }
     *j_begin = y * work.split_len;
     const int64_t j_end = min(*j_begin + work.split_len, n_ref);
     return stale_timeout ? 0 : (int)((j_end - *j_begin + kTileN - 1) / kTileN);
@@ -799,7 +785,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
         ++a_loads;
         bool ok = true;
         for (int t = 0; ok && t < ntiles && !*abort_flag; ++t) {
-          const int32_t row = (int32_t)(j_begin + (int64_t)t * work.tile_step);
+          const int32_t row = (int32_t)(j_begin + (int64_t)t * kTileN);
           for (int kc = 0; kc < KC; ++kc, ++it) {
             const int s = it % kStages;
             const uint32_t round = (uint32_t)(it / kStages);
@@ -964,7 +950,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
         // rounds of 64 columns; the accumulator goes back as soon as the last
         // round is in registers
         const uint32_t taddr = tmem_base + lane_addr + b * kAccCols + half * kEpiCols;
-        const int64_t col0 = j_begin + (int64_t)t * work.tile_step + c_off;
+        const int64_t col0 = j_begin + (int64_t)t * kTileN + c_off;
 #pragma unroll
         for (int r = 0; r < kRounds; ++r) {
           uint32_t v0[32], v1[32], mn0, mn1;
@@ -1109,15 +1095,9 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const voi
   work.n_items = work.T * splits;
   work.split_len = split_len;
   work.queue = sched.persistent_ctas > 0 ? sched.queue : nullptr;
-  work.splits = splits;
   if (work.n_items > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
   ScanOut o = out;
   o.done = splits > 1 ? sched.done : nullptr;
-  // interleaved splits: kNN lists only (the NBNN epilogue walks the classes
-  // of a contiguous range), and never with lists carried across splits
-  // (those rely on every earlier split's rows being lower)
-  work.interleaved = sched.interleave && splits > 1 && Epilogue::kAnyTileOrder && o.done == nullptr;
-  work.tile_step = work.interleaved ? (int64_t)splits * Shape<QT>::kTileN : Shape<QT>::kTileN;
   o.T = work.T;
   o.lists_per_split = QT == 2 ? 1 : Epilogue::kWarpsPerQuarter;
   const int64_t grid = work.queue ? std::min<int64_t>(work.n_items, sched.persistent_ctas) : work.n_items;

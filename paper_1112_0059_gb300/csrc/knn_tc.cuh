@@ -77,12 +77,6 @@ struct TcSched {
   // from those lists (so a row's lists carry its best keys across splits and
   // the merge drops the duplicates).  Null: every item starts empty.
   uint32_t* done = nullptr;
-  // kNN lists not carried across splits: split y scans reference tiles y,
-  // y + splits, y + 2 splits, ... instead of one contiguous range, so that
-  // every split sees every part of the reference set (a class-sorted index
-  // otherwise gives the splits holding a query's own class most of the list
-  // inserts, and those splits set the launch's time)
-  bool interleave = false;
 };
 
 // Split-N schedule of one scan launch over T query-tile groups (qt 128-row

@@ -290,7 +290,6 @@ struct KnnPlan {
   bool persistent;      // a persistent grid taking items from a queue
   bool bound_per_tile;  // with several splits: the row bound shared every tile (else at item start/end)
   bool seeded;          // each split's lists may start from the same rows' previous split's lists
-  bool interleave;      // split y scans reference tiles y, y + splits, ... (lists not carried across splits)
   int64_t items;        // work items of the launch (query-tile groups x splits)
   size_t off_qnorm, off_qbf, off_qext, off_lists, off_merged, off_rowthr, off_queue, off_done, bytes;
   TcSched sched(char* ws, int sm_count) const {
@@ -300,7 +299,6 @@ struct KnnPlan {
     t.queue = reinterpret_cast<uint32_t*>(ws + off_queue);
     t.bound_per_tile = bound_per_tile;
     t.done = seeded ? reinterpret_cast<uint32_t*>(ws + off_done) : nullptr;
-    t.interleave = interleave;
     return t;
   }
   // Clears what a launch needs zeroed: the work counter of a persistent
@@ -351,7 +349,6 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, ScanKind kind, int sp
   p.bound_per_tile = o.bound_per_tile >= 0 ? o.bound_per_tile == 1 : T < P;
   p.items = T * p.splits;
   p.seeded = kind != ScanKind::Nbnn && p.splits > 1 && !p.bound_per_tile;
-  p.interleave = kind != ScanKind::Nbnn && p.splits > 1 && !p.seeded;
   Carve c;
   p.off_qnorm = c.take<int32_t>(p.m_pad);
   p.off_qbf = c.take<__nv_bfloat16>(p.m_pad * kDim);
@@ -836,7 +833,6 @@ lnbnn_status lnbnn_plan_search(const lnbnn_index* index, int64_t n_queries, int3
   r.tile_n = kTcRefTile / p.qt;
   r.persistent = p.persistent ? 1 : 0;
   r.bound_per_tile = p.splits > 1 ? (p.bound_per_tile ? 1 : 0) : -1;
-  r.interleaved = p.interleave ? 1 : 0;
   *out = r;
   return LNBNN_OK;
 }

@@ -173,44 +173,3 @@ def test_lists_seeded_from_earlier_splits(lnbnn):
             cd, cj = oracle.knn_coarse(ref, q[rows], 11, 24)
             assert np.array_equal(fd.cpu().numpy()[rows], cd) and np.array_equal(fi.cpu().numpy()[rows], cj)
         ix.set_schedule(automatic=True)
-
-
-def test_interleaved_splits_on_a_class_sorted_index(lnbnn):
-    """A few query tiles over many splits whose lists are not carried: split y
-    takes reference tiles y, y + splits, ..., so every split sees every class
-    of a class-sorted index.  Exact duplicates sit in tiles of different
-    splits, of one split, and in the ragged last tile; every list kind and
-    the FP8 shortlist keep the oracle's (distance, row) order, and the
-    contiguous order (forced) gives the same bits."""
-    rng = np.random.default_rng(97)
-    C, per = 12, 5000
-    N = C * per + 37  # a ragged last tile
-    protos = rng.integers(0, 256, size=(C, 128))
-    labels = np.minimum(np.arange(N) // per, C - 1).astype(np.int32)
-    ref = np.clip(protos[labels] + rng.normal(0, 18, size=(N, 128)), 0, 255).astype(np.uint8)
-    ref[[300, 600, 20000, 45000, N - 1]] = ref[100]
-    q = np.clip(protos[rng.integers(0, C, 300)] + rng.normal(0, 18, size=(300, 128)), 0, 255).astype(np.uint8)
-    q[0] = ref[100]
-    with lnbnn.Index(dev(ref), dev(labels), C) as ix:
-        ix.prepare_fp8()
-        qd = dev(q)
-        plan = ix.plan_search(len(q), 11)
-        assert plan["splits"] > 1 and plan["interleaved"] == 1 and plan["bound_per_tile"] == 1, plan
-        first = None
-        for k1 in (11, 24, 32, 51, 101):
-            i, d = ix.knn_search(qd, k1)
-            ix.sync()
-            od, oj = oracle.knn(ref, q, k1)
-            assert np.array_equal(d.cpu().numpy(), od) and np.array_equal(i.cpu().numpy(), oj), k1
-            first = first or (i, d)
-        assert ix.plan_search(len(q), 24, fp8=True)["interleaved"] == 1
-        fi, fd = ix.knn_search(qd, 11, shortlist=24)
-        ix.sync()
-        cd, cj = oracle.knn_coarse(ref, q, 11, 24)
-        assert np.array_equal(fd.cpu().numpy(), cd) and np.array_equal(fi.cpu().numpy(), cj)
-        ix.set_schedule(bound_per_tile=0)  # the carried-lists mode keeps contiguous splits
-        assert ix.plan_search(len(q), 11)["interleaved"] == 0
-        i2, d2 = ix.knn_search(qd, 11)
-        ix.sync()
-        assert torch.equal(i2, first[0]) and torch.equal(d2, first[1])
-        ix.set_schedule(automatic=True)
