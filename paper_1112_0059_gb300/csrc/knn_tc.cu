@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(bars.tfull(b), kIssuers);
-      mbar_init(bars.tempty(b), 32 * kEpiWarps);
+      mbar_init(bars.tempty(b), kEpiWarps);  // one arrival per epilogue warp
       mbar_init(bars.ifull(b), 1);
       mbar_init(bars.iempty(b), kIssuers + kEpiWarps);  // the MMA threads and each epilogue warp
     }
@@ -960,8 +960,13 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
           reg_fence(v1);
           asm volatile("" : "+r"(mn1));
           if (r == kRounds - 1) {
+            // every lane's loads are complete (waited above); one arrival
+            // per warp after a warp barrier (256 single-thread arrivals on
+            // one barrier, while the MMAs read their operands from shared
+            // memory, delayed the accumulator's return by ~100 cycles a step)
             tc_fence_before();
-            mbar_arrive(bars.tempty(b));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bars.tempty(b));
           }
           epi.group(v0, mn0, col0 + 64 * r);
           epi.group(v1, mn1, col0 + 64 * r + 32);
