@@ -97,9 +97,6 @@ constexpr uint32_t kAccCols = kTcRefTile;  // FP32 columns per accumulator (one 
 constexpr uint32_t kTmemCols = 2 * kAccCols;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
 
-constexpr uint32_t kPairBytes = 2 * 2 * 128 * 4;
-constexpr int32_t kPairNoBound = 0x7F7F7F7F;  // above the bit pattern of every distance
-
 // Shared-memory layout of one CTA: QT query tiles (each AChunks
 // 128-byte-swizzle chunks + the 32-byte-swizzle extension), the reference
 // ring (Stages stages, each room for one K-chunk of a reference tile and its
@@ -118,11 +115,7 @@ struct Layout {
   static constexpr int kNumBars = 2 * Stages + 2 + 2 + 3 + 2 + 2 + 1;
   // TMEM address, abort flag, 2 item slots, 2 "an earlier split was not carried" words
   static constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;
-  // the bounds the two column-half lists of a query row exchange, int32
-  // [item parity][half][128 rows] (1024-aligned: the other half's slot is
-  // the own slot's address ^ 512)
-  static constexpr uint32_t kOffPair = (kOffMisc + 48 + 1023) / 1024 * 1024;
-  static constexpr uint32_t kOffList = kOffPair + kPairBytes;
+  static constexpr uint32_t kOffList = (kOffMisc + 48 + 1023) / 1024 * 1024;
   static constexpr uint32_t kSmemBytes = kOffList + ListBytes + 1024;  // + alignment slack
   static_assert(Stages % AChunks == 0, "a tile's chunks map to fixed stage parities");
   static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
@@ -324,19 +317,16 @@ struct KnnEpilogue {
   int32_t shared;   // the row's shared bound as last read (bit pattern)
   int32_t pending;  // the read in flight for the next tile
   int32_t* rthr;    // the row's shared bound, or null
-  uint32_t pair;    // shared address of this list's slot in the exchange with the row's other column half, or 0
   bool per_tile;    // share the bound every tile (else at start and end)
   bool active;
   int K1;
   uint64_t* out;
-  __device__ __forceinline__ KnnEpilogue(const ScanOut& o, int list, int64_t row, bool act, int64_t, uint8_t*, int,
-                                         uint32_t pair_slot)
+  __device__ __forceinline__ KnnEpilogue(const ScanOut& o, int list, int64_t row, bool act, int64_t, uint8_t*, int)
       : top(o.lists + ((int64_t)list * o.stride + (act ? row : 0)) * o.K1, o.K1),
         thr(thr_bits(INT32_MAX)),
         shared(kNoBound),
         pending(kNoBound),
         rthr(act && o.row_thr ? o.row_thr + row : nullptr),
-        pair(pair_slot),
         per_tile(o.bound_per_tile),
         active(act),
         K1(o.K1),
@@ -400,10 +390,7 @@ struct KnnEpilogue {
   }
   // After each tile: publish an improved K1-th distance of a full list, take
   // in the bound read a tile ago (its latency hidden behind a whole tile), and
-  // start the next read.  Within the CTA, the list also posts its K1-th
-  // distance (the bit pattern of a float above every distance while not
-  // full) for the row's other column half and takes in that half's: the
-  // K1-th distance of either half is a bound on the row's K1-th.
+  // start the next read.
   __device__ __forceinline__ void tile_end() {
     if (rthr && per_tile) {
       if (full() && thr < shared) {
@@ -413,15 +400,8 @@ struct KnnEpilogue {
       shared = min(shared, pending);
       pending = __ldcg(rthr);
     }
-    if (pair) {
-      st_shared_b32(pair, thr);
-      shared = min(shared, ld_shared_b32(pair ^ 512u));
-    }
   }
   __device__ __forceinline__ void finish() {
-    // the slot goes back to "no bound" for the CTA's next item of this
-    // parity; the other half reading it meanwhile only loses its bound
-    if (pair) st_shared_b32(pair, kPairNoBound);
     if (!active) return;
     if (rthr && !per_tile && full() && thr < shared) atomicMin(rthr, thr);
     if constexpr (KMAX > 0) {
@@ -465,7 +445,7 @@ struct KnnSmemEpilogue {
   int lane;
   uint64_t* out;
   __device__ __forceinline__ KnnSmemEpilogue(const ScanOut& o, int list, int64_t row, bool act, int64_t,
-                                             uint8_t* smem_list, int epi_warp, uint32_t)
+                                             uint8_t* smem_list, int epi_warp)
       : D(reinterpret_cast<uint32_t*>(smem_list) + (size_t)epi_warp * 32 * KM * 2),
         R(D + 32 * KM),
         thr(kInf),
@@ -599,7 +579,7 @@ struct NbnnEpilogue {
   int32_t run;           // float bits of the running minimum over cls
   bool active;
   __device__ __forceinline__ NbnnEpilogue(const ScanOut& o, int, int64_t row, bool act, int64_t j_begin, uint8_t*,
-                                          int, uint32_t)
+                                          int)
       : dst(o.mins + (act ? row : 0) * (int64_t)o.C), class_off(o.class_off), n_ref(o.class_off[o.C]), C(o.C),
         run(INT32_MAX), active(act) {
     // class of j_begin: the last c with class_off[c] <= j_begin
@@ -709,8 +689,6 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
-  for (uint32_t j = threadIdx.x; j < kPairBytes / 4; j += blockDim.x)
-    reinterpret_cast<int32_t*>(smem + L::kOffPair)[j] = kPairNoBound;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -918,14 +896,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
       const int64_t c_off = QT == 2 ? 0 : half * kEpiCols;  // this warp's first column within a tile
       const int list = QT == 2 ? (int)y : (int)y * kEpiPerQuarter + half;
       const bool active = row < m;
-      // one query tile: the two column-half lists of a row share their bounds
-      // through the item parity's slots (a slot is reused two items later,
-      // after every epilogue warp has released the item in between)
-      const uint32_t pair_slot = QT == 1 && kEpiPerQuarter == 2
-                                     ? sbase + L::kOffPair + (uint32_t)(i & 1) * 1024u + (uint32_t)half * 512u +
-                                           (uint32_t)(quarter * 32 + lane) * 4u
-                                     : 0u;
-      Epilogue epi(out, list, row, active, j_begin + c_off, smem + L::kOffList, warp - 2, pair_slot);
+      Epilogue epi(out, list, row, active, j_begin + c_off, smem + L::kOffList, warp - 2);
       // the previous split of these rows, if it has finished: start from its
       // list.  Its flag says 2 when every earlier split of the rows was
       // carried into it; a warp that cannot say the same of this item marks

@@ -199,17 +199,6 @@ __device__ __forceinline__ void reg_fence(uint32_t (&r)[32]) {
 // Fields: start address >> 4 (bits 0-13), leading-dimension byte offset >> 4
 // (bits 16-29, unused for this layout), stride byte offset >> 4 (bits 32-45),
 // descriptor version 1 (bits 46-47), swizzle mode 2 = 128B (bits 61-63).
-// Plain 32-bit shared-memory store and load that the compiler keeps in place
-// (words other warps of the CTA write and read without a barrier).
-__device__ __forceinline__ void st_shared_b32(uint32_t addr, int32_t v) {
-  asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v));
-}
-__device__ __forceinline__ int32_t ld_shared_b32(uint32_t addr) {
-  int32_t v;
-  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr));
-  return v;
-}
-
 __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t smem_addr) {
   uint64_t d = 0;
   d |= static_cast<uint64_t>((smem_addr >> 4) & 0x3FFFu);
