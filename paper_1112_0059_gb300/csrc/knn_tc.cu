@@ -814,42 +814,24 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
           break;
         }
         tc_fence_after();
-        // Each satisfied barrier wait and its tcgen05 fence cost the issuing
-        // thread ~100 cycles, and MMA issue runs only a little ahead of the
-        // tensor pipe: waits taken at a tile boundary left the pipe idle.  So
-        // the waits of the next chunk (its reference data and, when it starts
-        // the item's next tile, that tile's accumulator) are taken right after
-        // the first MMA of the current chunk, while the MMAs issued before
-        // are still queued.  Neither wait depends on an MMA not yet issued
-        // (the stage's previous chunk and the accumulator's previous tile were
-        // issued and committed in full).
-        bool next_full = false, next_tempty = false;  // the next chunk's / tile's waits already taken
-        auto wait_full = [&](int itx) -> bool {
-          if (mbar_wait(bars.full(itx % kStages), (uint32_t)(itx / kStages) & 1u, kWaitLimitNs, abort_flag)) return true;
-          flag_timeout(abort_flag, dev_err);
-          return false;
-        };
-        auto wait_tempty = [&](int tgx) -> bool {
-          if (mbar_wait(bars.tempty(tgx & 1), ((uint32_t)(tgx >> 1) & 1u) ^ 1u, kWaitLimitNs, abort_flag)) return true;
-          flag_timeout(abort_flag, dev_err);
-          return false;
-        };
         for (int t = 0; ok && t < ntiles && !*abort_flag; ++t, ++tg) {
           const int b = tg & 1;
-          if (!next_tempty && !wait_tempty(tg)) {
+          const uint32_t use = (uint32_t)(tg >> 1);
+          if (!mbar_wait(bars.tempty(b), (use & 1u) ^ 1u, kWaitLimitNs, abort_flag)) {
+            flag_timeout(abort_flag, dev_err);
             ok = false;
             break;
           }
-          next_tempty = false;
           tc_fence_after();
           const uint32_t d_tmem = tmem_base + b * kAccCols;
           for (int kc = 0; kc < KC; ++kc, ++it) {
             const int s = it % kStages;
-            if (!next_full && !wait_full(it)) {
+            const uint32_t round = (uint32_t)(it / kStages);
+            if (!mbar_wait(bars.full(s), round & 1u, kWaitLimitNs, abort_flag)) {
+              flag_timeout(abort_flag, dev_err);
               ok = false;
               break;
             }
-            next_full = false;
             tc_fence_after();
             // descriptors are built once per stage and advanced by adding the
             // byte offset >> 4 to their start-address field (14 bits of
@@ -861,8 +843,6 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
             const uint64_t b_desc = sw128_kmajor_desc(b_base);
             const uint64_t b_ext = sw32_kmajor_desc(b_base + Sh::kBChunkBytes);
             const bool last = kc == KC - 1;  // the norms' K-extension rides with the last chunk
-            const bool more = !last || t + 1 < ntiles;  // a next chunk in this item
-            bool pre_ok = true;
 #pragma unroll
             for (int q = 0; q < QT; ++q) {
               if (q < q_first || q >= q_last) continue;
@@ -872,23 +852,12 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
               const uint32_t d_q = d_tmem + q * kTileN;
               if (Fmt::kExtFirst && last) mma_bf16(d_q, a_ext, b_ext, idesc_bf16_f32(kBM, kTileN), kc != 0 ? 1u : 0u);
 #pragma unroll
-              for (int kk = 0; kk < kMmaPerChunk; ++kk) {  // K-steps of 32 bytes
+              for (int kk = 0; kk < kMmaPerChunk; ++kk)  // K-steps of 32 bytes
                 Fmt::template mma<kTileN>(d_q, a_desc + (uint64_t)(2 * kk), b_desc + (uint64_t)(2 * kk),
                                           (kc | kk) != 0 || (Fmt::kExtFirst && last) ? 1u : 0u);
-                if (kk == 0 && q == q_first && more) {
-                  pre_ok = wait_full(it + 1) && (!last || wait_tempty(tg + 1));
-                  next_full = true;
-                  next_tempty = last;
-                  tc_fence_after();
-                }
-              }
               if (!Fmt::kExtFirst && last) mma_bf16(d_q, a_ext, b_ext, idesc_bf16_f32(kBM, kTileN), 1u);
             }
             mma_commit(bars.empty(s));  // the producer may refill this stage
-            if (!pre_ok) {
-              ok = false;
-              break;
-            }
           }
           if (ok) mma_commit(bars.tfull(b));
         }
