@@ -814,39 +814,19 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
           break;
         }
         tc_fence_after();
-        // A satisfied barrier wait and its tcgen05 fence cost the issuing
-        // thread ~90 cycles, and MMA issue runs only a few MMAs ahead of the
-        // tensor pipe, so waits stacked at a tile boundary idle the pipe.
-        // With two K-chunks per tile the next tile's accumulator (returned by
-        // the epilogue long before: it held the tile before this one) is
-        // waited for at the start of this tile's second chunk, while the
-        // first chunk's MMAs are queued; the reference data is still waited
-        // for chunk by chunk (it lands only just in time).
-        constexpr bool kEarlyTempty = KC == 2;
-        bool tempty_taken = false;  // the next tile's accumulator wait already done
         for (int t = 0; ok && t < ntiles && !*abort_flag; ++t, ++tg) {
           const int b = tg & 1;
           const uint32_t use = (uint32_t)(tg >> 1);
-          if (!tempty_taken && !mbar_wait(bars.tempty(b), (use & 1u) ^ 1u, kWaitLimitNs, abort_flag)) {
+          if (!mbar_wait(bars.tempty(b), (use & 1u) ^ 1u, kWaitLimitNs, abort_flag)) {
             flag_timeout(abort_flag, dev_err);
             ok = false;
             break;
           }
-          tempty_taken = false;
           tc_fence_after();
           const uint32_t d_tmem = tmem_base + b * kAccCols;
           for (int kc = 0; kc < KC; ++kc, ++it) {
             const int s = it % kStages;
             const uint32_t round = (uint32_t)(it / kStages);
-            if (kEarlyTempty && kc == 1 && t + 1 < ntiles) {
-              const uint32_t use_n = (uint32_t)((tg + 1) >> 1);
-              if (!mbar_wait(bars.tempty((tg + 1) & 1), (use_n & 1u) ^ 1u, kWaitLimitNs, abort_flag)) {
-                flag_timeout(abort_flag, dev_err);
-                ok = false;
-                break;
-              }
-              tempty_taken = true;
-            }
             if (!mbar_wait(bars.full(s), round & 1u, kWaitLimitNs, abort_flag)) {
               flag_timeout(abort_flag, dev_err);
               ok = false;
