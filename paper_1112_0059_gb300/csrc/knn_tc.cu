@@ -814,7 +814,11 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
           break;
         }
         tc_fence_after();
-        for (int t = 0; ok && t < ntiles && !*abort_flag; ++t, ++tg) {
+        // no abort-flag read per tile here: shared-memory loads are slow on
+        // this thread while the MMAs stream their operands (the per-tile
+        // read cost 2% of the FP8 pass), and a role that gives up stops
+        // completing barriers, so the next wait below sees the flag
+        for (int t = 0; ok && t < ntiles; ++t, ++tg) {
           const int b = tg & 1;
           const uint32_t use = (uint32_t)(tg >> 1);
           if (!mbar_wait(bars.tempty(b), (use & 1u) ^ 1u, kWaitLimitNs, abort_flag)) {
