@@ -287,7 +287,12 @@ LNBNN_API lnbnn_status lnbnn_classify_fp8_ws(lnbnn_index *index, lnbnn_workspace
  * 4 (lists of 17..32 entries) or 8 (heaps) for the exact scan; the splits of
  * a row then run one after another, and each starts from the row's lists of
  * the previous split when that split has finished (the results never depend
- * on whether it has).  lnbnn_autotune times about
+ * on whether it has).  A launch with fewer query tiles than SMs runs the FP8
+ * coarse pass over twice the modelled split count (capped at four waves of
+ * items) on a persistent grid: on a class-sorted index the few splits that
+ * hold a query's own class do most of the shortlist inserts, and shorter
+ * items with the rest drained around them keep them from setting the
+ * launch's time.  lnbnn_autotune times about
  * thirty search launches of 1 to 64 query tiles (query rows copied from the
  * index's own references) with several split counts and two list lengths
  * (k1 = 11 and 51) on `stream` and fits a, b, c, e by least squares; then, on

@@ -338,14 +338,28 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, ScanKind kind, int sp
   p.qt = qt2_ok && (o.query_tiles == 2 || (o.query_tiles == 0 && auto_query_tiles(ix, kind, T1) == 2)) ? 2 : 1;
   const int64_t T = (T1 + p.qt - 1) / p.qt;
   if (splits <= 0) splits = o.splits;
+  bool few_coarse = false;
   if (splits <= 0) {
     splits = choose_splits_model(ix->split_model, T, ix->n_ref, P, max_splits(ix), p.qt, K1);
     if (T >= P && l2_splits_for(kind)) splits = (int)std::max<int64_t>(splits, l2_splits(ix, kind));
     if (T >= P && kind == ScanKind::Exact) splits = std::max(splits, long_list_splits(ix, K1));
+    // The coarse pass of fewer query tiles than SMs: the splits holding a
+    // query's own class (on a class-sorted index) do most of the shortlist
+    // inserts and set the launch's time, so twice the modelled split count
+    // is drained from a work queue by a persistent grid: shorter heavy items,
+    // with the light ones filling in around them.  256-class data, shortlist
+    // 24, one image of 100 / 300 / 632 / 1,000 / 2,000 descriptors: 0.68 ->
+    // 0.49, 1.12 -> 0.85, 1.53 -> 1.45, 1.97 -> 1.77, 3.26 -> 3.03 ms (the
+    // exact scan, whose inserts are few, gains at some sizes and loses at
+    // others, and keeps one CTA per item).
+    if (T < P && kind == ScanKind::Coarse) {
+      splits = (int)std::min<int64_t>(2 * (int64_t)splits, max_splits_for(T, ix->n_ref, P, max_splits(ix)));
+      few_coarse = true;
+    }
   }
   p.split_len = round_up((ix->n_ref + splits - 1) / splits, kTcRefTile);
   p.splits = (int)((ix->n_ref + p.split_len - 1) / p.split_len);
-  p.persistent = o.persistent == 1 || (o.persistent == -1 && auto_persistent(ix, kind, T1));
+  p.persistent = o.persistent == 1 || (o.persistent == -1 && (auto_persistent(ix, kind, T1) || few_coarse));
   p.bound_per_tile = o.bound_per_tile >= 0 ? o.bound_per_tile == 1 : T < P;
   p.items = T * p.splits;
   p.seeded = kind != ScanKind::Nbnn && p.splits > 1 && !p.bound_per_tile;

@@ -173,3 +173,27 @@ def test_lists_seeded_from_earlier_splits(lnbnn):
             cd, cj = oracle.knn_coarse(ref, q[rows], 11, 24)
             assert np.array_equal(fd.cpu().numpy()[rows], cd) and np.array_equal(fi.cpu().numpy()[rows], cj)
         ix.set_schedule(automatic=True)
+
+
+def test_fp8_coarse_pass_of_few_query_tiles_runs_persistent(lnbnn):
+    """Fewer query tiles than SMs: the FP8 coarse pass takes a persistent grid
+    over more splits than the exact scan's one-CTA-per-item launch, on a
+    class-sorted index whose query class sits in a few splits; results equal
+    the oracle's coarse form."""
+    rng = np.random.default_rng(101)
+    C, per = 10, 30000
+    N = C * per + 13
+    protos = rng.integers(0, 256, size=(C, 128))
+    labels = np.minimum(np.arange(N) // per, C - 1).astype(np.int32)
+    ref = np.clip(protos[labels] + rng.normal(0, 20, size=(N, 128)), 0, 255).astype(np.uint8)
+    q = np.clip(protos[3] + rng.normal(0, 20, size=(300, 128)), 0, 255).astype(np.uint8)
+    with lnbnn.Index(dev(ref), dev(labels), C) as ix:
+        ix.prepare_fp8()
+        coarse = ix.plan_search(len(q), 24, fp8=True)
+        exact = ix.plan_search(len(q), 11)
+        assert coarse["persistent"] == 1 and coarse["bound_per_tile"] == 1 and coarse["splits"] > 1, coarse
+        assert exact["persistent"] == 0, exact
+        i, d = ix.knn_search(dev(q), 11, shortlist=24)
+        ix.sync()
+        cd, cj = oracle.knn_coarse(ref, q, 11, 24)
+        assert np.array_equal(d.cpu().numpy(), cd) and np.array_equal(i.cpu().numpy(), cj)
