@@ -343,13 +343,19 @@ LNBNN_API lnbnn_status lnbnn_plan_splits(const lnbnn_index *index, int64_t n_que
  * split; the sorted lists per query row the scan writes (merged afterwards
  * when more than one); where each list lives (list_storage 0: registers, 1:
  * shared memory, 2: a heap in global memory) and how many entries it holds
- * (16, 32 or 64; k1 for a heap); the tile of query rows x references one CTA
+ * (16, 24, 32 or 64; k1 for a heap); the tile of query rows x references one CTA
  * computes per step (tile_m query rows x tile_n references); persistent = 1
  * when a fixed grid of CTAs takes (query tiles, split) work items from a
  * queue instead of one CTA per item; bound_per_tile: how the lists of a row
  * share their bound when there are several splits (1: every tile, as the
  * splits of a row run at the same time; 0: read when a list starts and
- * published when it ends, as they run one after another; -1: one split).
+ * published when it ends, as they run one after another; -1: one split);
+ * chunked = 1 for the claimed-chunk form of launches with fewer query-tile
+ * groups than SMs: `splits` CTAs per group each keep that group's lists for
+ * the whole launch and claim reference chunks of split_len rows, in
+ * increasing order, from a counter the group's CTAs share (so the reference
+ * ranges that hold a query's own class, where most list inserts fall, are
+ * shared by whichever CTAs are free).
  * Errors: INVALID_ARG (null pointers, n_queries < 1), K_RANGE (k1 outside
  * [1, LNBNN_MAX_K + 1] or above n_ref), NO_FP8 (fp8 != 0 on an index without
  * the FP8 operand).
@@ -364,6 +370,7 @@ typedef struct lnbnn_search_plan {
   int32_t tile_n;
   int32_t persistent;
   int32_t bound_per_tile;
+  int32_t chunked;
 } lnbnn_search_plan;
 
 LNBNN_API lnbnn_status lnbnn_plan_search(const lnbnn_index *index, int64_t n_queries, int32_t k1, int32_t fp8,

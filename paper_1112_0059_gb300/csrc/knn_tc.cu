@@ -310,6 +310,7 @@ template <int KMAX>
 struct KnnEpilogue {
   static constexpr int kWarpsPerQuarter = KMAX == kTcWideRegListMax ? 1 : 2;
   static constexpr bool kSeeds = true;  // can start from the previous split's list of its rows
+  static constexpr bool kClaimsChunks = true;  // can keep its lists across claimed reference chunks
   static constexpr uint32_t kListBytes = 0;
   RegList<KMAX> L;
   TopK top;
@@ -427,6 +428,7 @@ template <int KM>
 struct KnnSmemEpilogue {
   static constexpr int kWarpsPerQuarter = 1;
   static constexpr bool kSeeds = false;
+  static constexpr bool kClaimsChunks = false;
   static constexpr int kPerLane = KM / 32;  // list entries each lane computes in an insert
   static constexpr uint32_t kListBytes = 4 * kWarpsPerQuarter * 32 * KM * 8;
   static constexpr int32_t kInf = 0x7F800000;  // bits of +inf, above every distance
@@ -567,6 +569,7 @@ struct KnnSmemEpilogue {
 struct NbnnEpilogue {
   static constexpr int kWarpsPerQuarter = 2;
   static constexpr bool kSeeds = false;
+  static constexpr bool kClaimsChunks = false;
   __device__ __forceinline__ void seed(const uint64_t*) {}
   static constexpr uint32_t kListBytes = 0;
   __device__ __forceinline__ void tile_end() {}
@@ -628,6 +631,13 @@ struct Work {
   int64_t n_items;
   int64_t split_len;
   uint32_t* queue;
+  // 0: work items are (query-tile group, reference split) pairs.  > 0 (the
+  // claimed-chunk form, persistent): `group` CTAs serve each query-tile
+  // group, CTA c the group c / group; each keeps that group's query tiles
+  // and its lists for the whole launch and claims reference chunks of
+  // split_len rows, in increasing order, from the group's counter
+  // queue[c / group]; n_items is then the number of chunks.
+  int group;
 };
 
 template <class Fmt, class Epilogue, int QT>
@@ -706,8 +716,10 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
     *w = item_slot[slot];
     return true;
   };
+  const bool chunked = work.group > 0;
   auto item_tiles = [&](int64_t w, int64_t* m0, int64_t* j_begin) -> int {
-    const int64_t x = w % work.T, y = w / work.T;
+    const int64_t x = chunked ? (int64_t)blockIdx.x / work.group : w % work.T;
+    const int64_t y = chunked ? w : w / work.T;
     *m0 = x * (int64_t)(kBM * QT);
     *j_begin = y * work.split_len;
     const int64_t j_end = min(*j_begin + work.split_len, n_ref);
@@ -738,7 +750,8 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
             flag_timeout(abort_flag, dev_err);
             break;
           }
-          w = *abort_flag ? work.n_items : (int64_t)atomicAdd(work.queue, 1u);
+          w = *abort_flag ? work.n_items
+                          : (int64_t)atomicAdd(work.queue + (chunked ? blockIdx.x / work.group : 0u), 1u);
           if (w > work.n_items) w = work.n_items;
           item_slot[slot] = w;
           mbar_arrive(bars.ifull(slot));
@@ -748,19 +761,22 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
         if (w >= work.n_items) break;
         int64_t m0, j_begin;
         const int ntiles = item_tiles(w, &m0, &j_begin);
-        // the query tiles: once the previous item's MMAs have read theirs
-        if (a_loads > 0 && !mbar_wait(bars.aempty(), (uint32_t)((a_loads - 1) & 1), kWaitLimitNs, abort_flag)) {
-          flag_timeout(abort_flag, dev_err);
-          break;
+        // the query tiles: once the previous item's MMAs have read theirs (in
+        // the claimed-chunk form, once for the whole launch)
+        if (!chunked || a_loads == 0) {
+          if (a_loads > 0 && !mbar_wait(bars.aempty(), (uint32_t)((a_loads - 1) & 1), kWaitLimitNs, abort_flag)) {
+            flag_timeout(abort_flag, dev_err);
+            break;
+          }
+          mbar_arrive_expect_tx(bars.afull(), QT * (KC * kAChunkBytes + kAExtBytes));
+          for (int q = 0; q < QT; ++q) {
+            const uint32_t a = sbase + L::kOffA + q * L::kAQueryBytes;
+            const int32_t qrow = (int32_t)(m0 + q * kBM);
+            for (int kc = 0; kc < KC; ++kc) tma_load_2d(a + kc * kAChunkBytes, &tmap_q, kc * kBK, qrow, bars.afull());
+            tma_load_2d(a + KC * kAChunkBytes, &tmap_qe, 0, qrow, bars.afull());
+          }
+          ++a_loads;
         }
-        mbar_arrive_expect_tx(bars.afull(), QT * (KC * kAChunkBytes + kAExtBytes));
-        for (int q = 0; q < QT; ++q) {
-          const uint32_t a = sbase + L::kOffA + q * L::kAQueryBytes;
-          const int32_t qrow = (int32_t)(m0 + q * kBM);
-          for (int kc = 0; kc < KC; ++kc) tma_load_2d(a + kc * kAChunkBytes, &tmap_q, kc * kBK, qrow, bars.afull());
-          tma_load_2d(a + KC * kAChunkBytes, &tmap_qe, 0, qrow, bars.afull());
-        }
-        ++a_loads;
         bool ok = true;
         for (int t = 0; ok && t < ntiles && !*abort_flag; ++t) {
           const int32_t row = (int32_t)(j_begin + (int64_t)t * kTileN);
@@ -809,7 +825,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
         if (w >= work.n_items) break;
         int64_t m0, j_begin;
         const int ntiles = item_tiles(w, &m0, &j_begin);
-        if (!mbar_wait(bars.afull(), (uint32_t)(i & 1), kWaitLimitNs, abort_flag)) {
+        if ((!chunked || i == 0) && !mbar_wait(bars.afull(), (uint32_t)(i & 1), kWaitLimitNs, abort_flag)) {
           flag_timeout(abort_flag, dev_err);
           break;
         }
@@ -866,7 +882,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
           if (ok) mma_commit(bars.tfull(b));
         }
         tiles_done += ntiles;
-        mma_commit(bars.aempty());  // the query tiles may be replaced once these MMAs are done
+        if (!chunked) mma_commit(bars.aempty());  // the query tiles may be replaced once these MMAs are done
         if (persistent) mbar_arrive(bars.iempty(i & 1));
       }
       // all MMAs issued by this thread must finish before TMEM is released
@@ -886,7 +902,73 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
     const int half = (warp - 2) >> 2;      // QT = 1: its column half of every tile; QT = 2: its query tile
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     int tg = 0;
-    for (int i = 0;; ++i) {
+    // the tiles of one work item into the lists of `e`; false if a wait ran out
+    auto scan_tiles = [&](auto& e, int ntiles, int64_t col_base) -> bool {
+      for (int t = 0; t < ntiles; ++t, ++tg) {
+        const int b = tg & 1;
+        const uint32_t use = (uint32_t)(tg >> 1);
+        if (!mbar_wait(bars.tfull(b), use & 1u, kWaitLimitNs, abort_flag)) {
+          flag_timeout(abort_flag, dev_err);
+          return false;
+        }
+        tc_fence_after();
+        // rounds of 64 columns; the accumulator goes back as soon as the last
+        // round is in registers
+        const uint32_t taddr = tmem_base + lane_addr + b * kAccCols + half * kEpiCols;
+        const int64_t col0 = col_base + (int64_t)t * kTileN;
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+          uint32_t v0[32], v1[32], mn0, mn1;
+          tmem_ld_min_32x32b_x32(taddr + 64 * r, v0, mn0);
+          tmem_ld_min_32x32b_x32(taddr + 64 * r + 32, v1, mn1);
+          tmem_ld_wait(v0, mn0);
+          reg_fence(v1);
+          asm volatile("" : "+r"(mn1));
+          if (r == kRounds - 1) {
+            // every lane's loads are complete (waited above); one arrival
+            // per warp after a warp barrier (256 single-thread arrivals on
+            // one barrier, while the MMAs read their operands from shared
+            // memory, delayed the accumulator's return by ~100 cycles a step)
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bars.tempty(b));
+          }
+          e.group(v0, mn0, col0 + 64 * r);
+          e.group(v1, mn1, col0 + 64 * r + 32);
+        }
+        e.tile_end();
+      }
+      return true;
+    };
+    if constexpr (Epilogue::kClaimsChunks) {
+      if (chunked) {
+        // claimed-chunk form: one query-tile group and one set of lists for
+        // the whole launch (list = this CTA's rank in the group's CTAs x the
+        // lists per CTA), written once every claimed chunk is scanned
+        const int rank = (int)(blockIdx.x % (unsigned)work.group);
+        const int64_t row =
+            (int64_t)(blockIdx.x / (unsigned)work.group) * (kBM * QT) + (QT == 2 ? half * kBM : 0) + quarter * 32 + lane;
+        const int64_t c_off = QT == 2 ? 0 : half * kEpiCols;
+        const int list = QT == 2 ? rank : rank * kEpiPerQuarter + half;
+        const bool active = row < m;
+        Epilogue epi(out, list, row, active, c_off, smem + L::kOffList, warp - 2);
+        for (int i = 0;; ++i) {
+          int64_t w;
+          if (!consume_item(i, &w)) {
+            flag_timeout(abort_flag, dev_err);
+            break;
+          }
+          if (w >= work.n_items) break;
+          int64_t m0, j_begin;
+          const int ntiles = item_tiles(w, &m0, &j_begin);
+          if (!scan_tiles(epi, ntiles, j_begin + c_off)) break;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bars.iempty(i & 1));
+        }
+        epi.finish();
+      }
+    }
+    for (int i = 0; !chunked; ++i) {
       int64_t w;
       if (!consume_item(i, &w)) {
         flag_timeout(abort_flag, dev_err);
@@ -912,42 +994,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
           epi.seed(out.lists + ((int64_t)(list - out.lists_per_split) * out.stride + (active ? row : 0)) * out.K1);
         if (lane == 0 && y > 0 && prev != 2u) chain_broken[i & 1] = 1u;
       }
-      bool ok = true;
-      for (int t = 0; t < ntiles; ++t, ++tg) {
-        const int b = tg & 1;
-        const uint32_t use = (uint32_t)(tg >> 1);
-        if (!mbar_wait(bars.tfull(b), use & 1u, kWaitLimitNs, abort_flag)) {
-          flag_timeout(abort_flag, dev_err);
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        // rounds of 64 columns; the accumulator goes back as soon as the last
-        // round is in registers
-        const uint32_t taddr = tmem_base + lane_addr + b * kAccCols + half * kEpiCols;
-        const int64_t col0 = j_begin + (int64_t)t * kTileN + c_off;
-#pragma unroll
-        for (int r = 0; r < kRounds; ++r) {
-          uint32_t v0[32], v1[32], mn0, mn1;
-          tmem_ld_min_32x32b_x32(taddr + 64 * r, v0, mn0);
-          tmem_ld_min_32x32b_x32(taddr + 64 * r + 32, v1, mn1);
-          tmem_ld_wait(v0, mn0);
-          reg_fence(v1);
-          asm volatile("" : "+r"(mn1));
-          if (r == kRounds - 1) {
-            // every lane's loads are complete (waited above); one arrival
-            // per warp after a warp barrier (256 single-thread arrivals on
-            // one barrier, while the MMAs read their operands from shared
-            // memory, delayed the accumulator's return by ~100 cycles a step)
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bars.tempty(b));
-          }
-          epi.group(v0, mn0, col0 + 64 * r);
-          epi.group(v1, mn1, col0 + 64 * r + 32);
-        }
-        epi.tile_end();
-      }
+      const bool ok = scan_tiles(epi, ntiles, j_begin + c_off);
       epi.finish();
       if (Epilogue::kSeeds && out.done != nullptr) {
         // this item's lists are complete once every epilogue warp has written
@@ -1075,12 +1122,23 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const voi
   work.n_items = work.T * splits;
   work.split_len = split_len;
   work.queue = sched.persistent_ctas > 0 ? sched.queue : nullptr;
-  if (work.n_items > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
+  work.group = 0;
   ScanOut o = out;
   o.done = splits > 1 ? sched.done : nullptr;
   o.T = work.T;
   o.lists_per_split = QT == 2 ? 1 : Epilogue::kWarpsPerQuarter;
-  const int64_t grid = work.queue ? std::min<int64_t>(work.n_items, sched.persistent_ctas) : work.n_items;
+  int64_t grid = work.queue ? std::min<int64_t>(work.n_items, sched.persistent_ctas) : work.n_items;
+  if (sched.group > 0) {
+    // the claimed-chunk form: `splits` is the CTAs per query-tile group (the
+    // lists' "split" index is the CTA's rank), split_len the chunk length
+    if (!Epilogue::kClaimsChunks || sched.queue == nullptr || o.done != nullptr || sched.group != splits)
+      return cudaErrorInvalidValue;
+    work.group = sched.group;
+    work.queue = sched.queue;
+    work.n_items = (n_ref + split_len - 1) / split_len;
+    grid = work.T * sched.group;
+  }
+  if (work.n_items > (int64_t)INT32_MAX || grid > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
   tc_scan_kernel<Fmt, Epilogue, QT>
       <<<(unsigned)grid, threads_for(Epilogue::kWarpsPerQuarter, QT), LayoutOf<Fmt, Epilogue, QT>::kSmemBytes, s>>>(
           tq, tqe, tr, tre, m, n_ref, work, o, dev_err, stats);

@@ -77,6 +77,14 @@ struct TcSched {
   // from those lists (so a row's lists carry its best keys across splits and
   // the merge drops the duplicates).  Null: every item starts empty.
   uint32_t* done = nullptr;
+  // > 0: the claimed-chunk form for launches of few query-tile groups:
+  // `group` CTAs per group, each keeping the group's query tiles and its own
+  // lists for the whole launch and claiming reference chunks of split_len
+  // rows in increasing order from the group's counter queue[group index]
+  // (T counters zeroed before the launch); the launch writes `group` x lists
+  // per CTA lists per query row.  kNN register lists and heaps only; never
+  // with `done`.
+  int group = 0;
 };
 
 // Split-N schedule of one scan launch over T query-tile groups (qt 128-row

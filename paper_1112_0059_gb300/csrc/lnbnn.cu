@@ -290,6 +290,7 @@ struct KnnPlan {
   bool persistent;      // a persistent grid taking items from a queue
   bool bound_per_tile;  // with several splits: the row bound shared every tile (else at item start/end)
   bool seeded;          // each split's lists may start from the same rows' previous split's lists
+  int group;            // > 0: the claimed-chunk form (`splits` = CTAs per query-tile group, split_len = chunk)
   int64_t items;        // work items of the launch (query-tile groups x splits)
   size_t off_qnorm, off_qbf, off_qext, off_lists, off_merged, off_rowthr, off_queue, off_done, bytes;
   TcSched sched(char* ws, int sm_count) const {
@@ -299,13 +300,14 @@ struct KnnPlan {
     t.queue = reinterpret_cast<uint32_t*>(ws + off_queue);
     t.bound_per_tile = bound_per_tile;
     t.done = seeded ? reinterpret_cast<uint32_t*>(ws + off_done) : nullptr;
+    t.group = group;
     return t;
   }
   // Clears what a launch needs zeroed: the work counter of a persistent
   // launch, the per-item flags of a seeded one.
   cudaError_t clear(char* ws, cudaStream_t s) const {
     cudaError_t e = cudaSuccess;
-    if (persistent) e = cudaMemsetAsync(ws + off_queue, 0, sizeof(uint32_t), s);
+    if (persistent) e = cudaMemsetAsync(ws + off_queue, 0, sizeof(uint32_t) * (size_t)(group > 0 ? items / splits : 1), s);
     if (e == cudaSuccess && seeded) e = cudaMemsetAsync(ws + off_done, 0, sizeof(uint32_t) * (size_t)items, s);
     return e;
   }
@@ -338,29 +340,37 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, ScanKind kind, int sp
   p.qt = qt2_ok && (o.query_tiles == 2 || (o.query_tiles == 0 && auto_query_tiles(ix, kind, T1) == 2)) ? 2 : 1;
   const int64_t T = (T1 + p.qt - 1) / p.qt;
   if (splits <= 0) splits = o.splits;
-  bool few_coarse = false;
-  if (splits <= 0) {
-    splits = choose_splits_model(ix->split_model, T, ix->n_ref, P, max_splits(ix), p.qt, K1);
-    if (T >= P && l2_splits_for(kind)) splits = (int)std::max<int64_t>(splits, l2_splits(ix, kind));
-    if (T >= P && kind == ScanKind::Exact) splits = std::max(splits, long_list_splits(ix, K1));
-    // The coarse pass of fewer query tiles than SMs: the splits holding a
-    // query's own class (on a class-sorted index) do most of the shortlist
-    // inserts and set the launch's time, so twice the modelled split count
-    // is drained from a work queue by a persistent grid: shorter heavy items,
-    // with the light ones filling in around them.  256-class data, shortlist
-    // 24, one image of 100 / 300 / 632 / 1,000 / 2,000 descriptors: 0.68 ->
-    // 0.49, 1.12 -> 0.85, 1.53 -> 1.45, 1.97 -> 1.77, 3.26 -> 3.03 ms (the
-    // exact scan, whose inserts are few, gains at some sizes and loses at
-    // others, and keeps one CTA per item).
-    if (T < P && kind == ScanKind::Coarse) {
-      splits = (int)std::min<int64_t>(2 * (int64_t)splits, max_splits_for(T, ix->n_ref, P, max_splits(ix)));
-      few_coarse = true;
+  // The claimed-chunk form for launches of fewer query-tile groups than SMs
+  // (automatic split count; register lists or heaps): on a class-sorted
+  // index the few reference ranges that hold a query's own class carry most
+  // of the list inserts, and with fixed splits the CTAs that draw them set
+  // the launch's time.  Instead each of P / T CTAs per group keeps the
+  // group's lists for the whole launch and claims short reference chunks, in
+  // increasing order, from the group's counter: the near-class chunks are
+  // shared by whichever CTAs are free.
+  const bool claim_kind = kind != ScanKind::Nbnn && (K1 <= kTcCoarseRegListMax || K1 > kTcWideRegListMax);
+  const int64_t ref_tiles = (ix->n_ref + kTcRefTile - 1) / kTcRefTile;
+  p.group = splits <= 0 && T < P && claim_kind && o.persistent != 0 && o.bound_per_tile != 0
+                ? (int)std::max<int64_t>(1, std::min<int64_t>(P / T, ref_tiles / 4))  // chunks of >= 4 tiles each
+                : 0;
+  if (p.group > 0) {
+    const int64_t tiles = ref_tiles;
+    const int64_t chunk_tiles = std::max<int64_t>(4, (tiles + 8 * (int64_t)p.group - 1) / (8 * (int64_t)p.group));
+    p.split_len = chunk_tiles * kTcRefTile;  // about eight chunks per CTA
+    p.splits = p.group;
+    p.persistent = true;
+    p.bound_per_tile = true;
+  } else {
+    if (splits <= 0) {
+      splits = choose_splits_model(ix->split_model, T, ix->n_ref, P, max_splits(ix), p.qt, K1);
+      if (T >= P && l2_splits_for(kind)) splits = (int)std::max<int64_t>(splits, l2_splits(ix, kind));
+      if (T >= P && kind == ScanKind::Exact) splits = std::max(splits, long_list_splits(ix, K1));
     }
+    p.split_len = round_up((ix->n_ref + splits - 1) / splits, kTcRefTile);
+    p.splits = (int)((ix->n_ref + p.split_len - 1) / p.split_len);
+    p.persistent = o.persistent == 1 || (o.persistent == -1 && auto_persistent(ix, kind, T1));
+    p.bound_per_tile = o.bound_per_tile >= 0 ? o.bound_per_tile == 1 : T < P;
   }
-  p.split_len = round_up((ix->n_ref + splits - 1) / splits, kTcRefTile);
-  p.splits = (int)((ix->n_ref + p.split_len - 1) / p.split_len);
-  p.persistent = o.persistent == 1 || (o.persistent == -1 && (auto_persistent(ix, kind, T1) || few_coarse));
-  p.bound_per_tile = o.bound_per_tile >= 0 ? o.bound_per_tile == 1 : T < P;
   p.items = T * p.splits;
   p.seeded = kind != ScanKind::Nbnn && p.splits > 1 && !p.bound_per_tile;
   Carve c;
@@ -371,7 +381,7 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, ScanKind kind, int sp
   p.off_lists = c.take<uint64_t>(kind == ScanKind::Nbnn ? 0 : (size_t)p.lists * p.m_pad * K1);
   p.off_merged = c.take<uint64_t>(kind == ScanKind::Nbnn ? 0 : (size_t)p.m_pad * K1);  // apart from the lists (rerank)
   p.off_rowthr = c.take<int32_t>(p.m_pad);                // the bound a row's lists share
-  p.off_queue = c.take<uint32_t>(1);                      // the work counter of a persistent launch
+  p.off_queue = c.take<uint32_t>((size_t)T);             // the work counter(s) of a persistent launch
   p.off_done = c.take<uint32_t>((size_t)p.items);        // per-item "lists written" flags
   p.bytes = c.off;
   return p;
@@ -847,6 +857,7 @@ lnbnn_status lnbnn_plan_search(const lnbnn_index* index, int64_t n_queries, int3
   r.tile_n = kTcRefTile / p.qt;
   r.persistent = p.persistent ? 1 : 0;
   r.bound_per_tile = p.splits > 1 ? (p.bound_per_tile ? 1 : 0) : -1;
+  r.chunked = p.group > 0 ? 1 : 0;
   *out = r;
   return LNBNN_OK;
 }

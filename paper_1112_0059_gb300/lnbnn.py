@@ -86,7 +86,8 @@ class SearchPlan(ctypes.Structure):
     """Mirror of ``lnbnn_search_plan`` (include/lnbnn.h)."""
     _fields_ = [("splits", ctypes.c_int32), ("lists_per_row", ctypes.c_int32), ("split_len", ctypes.c_int64),
                 ("list_storage", ctypes.c_int32), ("list_capacity", ctypes.c_int32), ("tile_m", ctypes.c_int32),
-                ("tile_n", ctypes.c_int32), ("persistent", ctypes.c_int32), ("bound_per_tile", ctypes.c_int32)]
+                ("tile_n", ctypes.c_int32), ("persistent", ctypes.c_int32), ("bound_per_tile", ctypes.c_int32),
+                ("chunked", ctypes.c_int32)]
 
     STORAGE = {0: "registers", 1: "shared memory", 2: "global-memory heap"}
 

@@ -141,8 +141,10 @@ def test_schedule_arguments_are_checked(lnbnn):
         p = ix.plan_search(40_000, 50)  # 64-entry lists: one query tile per CTA whatever is asked
         assert p["tile_m"] == 128 and p["tile_n"] == 256
         ix.set_schedule(automatic=True)
-        p = ix.plan_search(100, 11)
-        assert p["tile_m"] == 128 and p["persistent"] == 0
+        p = ix.plan_search(100, 11)  # one query tile: the claimed-chunk form
+        assert p["tile_m"] == 128 and p["persistent"] == 1 and p["chunked"] == 1
+        assert 1 <= p["splits"] <= 5  # CTAs sharing the tile: at most one per four of the 20 reference tiles
+        assert ix.plan_search(100, 51)["chunked"] == 0  # 64-entry shared-memory lists keep their splits
 
 
 def test_lists_seeded_from_earlier_splits(lnbnn):
@@ -175,25 +177,44 @@ def test_lists_seeded_from_earlier_splits(lnbnn):
         ix.set_schedule(automatic=True)
 
 
-def test_fp8_coarse_pass_of_few_query_tiles_runs_persistent(lnbnn):
-    """Fewer query tiles than SMs: the FP8 coarse pass takes a persistent grid
-    over more splits than the exact scan's one-CTA-per-item launch, on a
-    class-sorted index whose query class sits in a few splits; results equal
-    the oracle's coarse form."""
+def test_claimed_chunks_for_few_query_tiles(lnbnn):
+    """Fewer query tiles than SMs: P / T CTAs per query tile each keep its lists
+    for the whole launch and claim short reference chunks in increasing order
+    from a shared counter.  On a class-sorted index whose query class sits in
+    one stretch of references, every list kind that takes this form (16-, 24-
+    and 32-entry register lists, heaps) and the FP8 shortlist equal the
+    oracle, and a fixed split count (the split form) gives the same bits."""
     rng = np.random.default_rng(101)
     C, per = 10, 30000
     N = C * per + 13
     protos = rng.integers(0, 256, size=(C, 128))
     labels = np.minimum(np.arange(N) // per, C - 1).astype(np.int32)
     ref = np.clip(protos[labels] + rng.normal(0, 20, size=(N, 128)), 0, 255).astype(np.uint8)
+    ref[[40, 70000, 150000, N - 1]] = ref[7]  # exact ties in different chunks
     q = np.clip(protos[3] + rng.normal(0, 20, size=(300, 128)), 0, 255).astype(np.uint8)
+    q[0] = ref[7]
     with lnbnn.Index(dev(ref), dev(labels), C) as ix:
         ix.prepare_fp8()
-        coarse = ix.plan_search(len(q), 24, fp8=True)
-        exact = ix.plan_search(len(q), 11)
-        assert coarse["persistent"] == 1 and coarse["bound_per_tile"] == 1 and coarse["splits"] > 1, coarse
-        assert exact["persistent"] == 0, exact
-        i, d = ix.knn_search(dev(q), 11, shortlist=24)
+        qd = dev(q)
+        for k1 in (11, 24, 32, 101):
+            plan = ix.plan_search(len(q), k1)
+            assert plan["chunked"] == 1 and plan["persistent"] == 1 and plan["splits"] > 1, plan
+            i, d = ix.knn_search(qd, k1)
+            ix.sync()
+            od, oj = oracle.knn(ref, q, k1)
+            assert np.array_equal(d.cpu().numpy(), od) and np.array_equal(i.cpu().numpy(), oj), k1
+            ix.set_schedule(splits=3)  # the split form
+            assert ix.plan_search(len(q), k1)["chunked"] == 0
+            i2, d2 = ix.knn_search(qd, k1)
+            ix.sync()
+            assert torch.equal(i, i2) and torch.equal(d, d2), k1
+            ix.set_schedule(automatic=True)
+        assert ix.plan_search(len(q), 24, fp8=True)["chunked"] == 1
+        fi, fd = ix.knn_search(qd, 11, shortlist=24)
         ix.sync()
         cd, cj = oracle.knn_coarse(ref, q, 11, 24)
-        assert np.array_equal(d.cpu().numpy(), cd) and np.array_equal(i.cpu().numpy(), cj)
+        assert np.array_equal(fd.cpu().numpy(), cd) and np.array_equal(fi.cpu().numpy(), cj)
+        t, c = ix.lnbnn_classify(qd, dev(np.array([0, 100, 300], dtype=np.int64)), 10)
+        ix.sync()
+        wt, wc = oracle.local_nbnn(ref, labels, C, q, np.array([0, 100, 300]), 10)
+        assert np.array_equal(t.cpu().numpy(), wt) and np.array_equal(c.cpu().numpy(), wc)
