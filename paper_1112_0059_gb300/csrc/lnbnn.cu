@@ -348,7 +348,17 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, ScanKind kind, int sp
   // group's lists for the whole launch and claims short reference chunks, in
   // increasing order, from the group's counter: the near-class chunks are
   // shared by whichever CTAs are free.
-  const bool claim_kind = kind != ScanKind::Nbnn && (K1 <= kTcCoarseRegListMax || K1 > kTcWideRegListMax);
+  // The coarse pass, whose shortlist inserts are dear, takes it while there
+  // are at least 8 CTAs per query tile (256-class data, shortlist 24, one
+  // image of 100 / 256 / 512 / 768 / 1,280 / 2,000 descriptors: 0.42-0.54 /
+  // 0.71-0.76 / 1.07-1.13 / 1.38-1.50 / 2.11-2.32 / 2.93-3.44 ms against
+  // 0.55-0.66 / 0.84-0.89 / 1.14-1.27 / 1.69-1.74 / 2.41-2.47 / 3.28-3.53
+  // with splits; 4,000: slower, 4 CTAs per tile leave SMs idle); the exact
+  // scan, whose inserts are few, for a lone query tile only (0.53 against
+  // 0.55 ms at 100 descriptors; 2 and 3 tiles were 7-30% slower, 4 to 10
+  // tiles 1-12% faster).
+  const bool claim_kind = kind != ScanKind::Nbnn && (K1 <= kTcCoarseRegListMax || K1 > kTcWideRegListMax) &&
+                          (kind == ScanKind::Coarse ? T * 8 <= P : T == 1);
   const int64_t ref_tiles = (ix->n_ref + kTcRefTile - 1) / kTcRefTile;
   p.group = splits <= 0 && T < P && claim_kind && o.persistent != 0 && o.bound_per_tile != 0
                 // chunks of >= 4 tiles each, and no more lists than the split

@@ -191,7 +191,7 @@ def test_claimed_chunks_for_few_query_tiles(lnbnn):
     labels = np.minimum(np.arange(N) // per, C - 1).astype(np.int32)
     ref = np.clip(protos[labels] + rng.normal(0, 20, size=(N, 128)), 0, 255).astype(np.uint8)
     ref[[40, 70000, 150000, N - 1]] = ref[7]  # exact ties in different chunks
-    q = np.clip(protos[3] + rng.normal(0, 20, size=(300, 128)), 0, 255).astype(np.uint8)
+    q = np.clip(protos[3] + rng.normal(0, 20, size=(120, 128)), 0, 255).astype(np.uint8)  # one query tile
     q[0] = ref[7]
     with lnbnn.Index(dev(ref), dev(labels), C) as ix:
         ix.prepare_fp8()
@@ -214,7 +214,14 @@ def test_claimed_chunks_for_few_query_tiles(lnbnn):
         ix.sync()
         cd, cj = oracle.knn_coarse(ref, q, 11, 24)
         assert np.array_equal(fd.cpu().numpy(), cd) and np.array_equal(fi.cpu().numpy(), cj)
-        t, c = ix.lnbnn_classify(qd, dev(np.array([0, 100, 300], dtype=np.int64)), 10)
+        q3 = np.concatenate([q, q[::-1], q[:60]])  # three query tiles: the FP8 pass still claims chunks
+        assert ix.plan_search(len(q3), 24, fp8=True)["chunked"] == 1
+        assert ix.plan_search(len(q3), 11)["chunked"] == 0
+        f3, d3 = ix.knn_search(dev(q3), 11, shortlist=24)
         ix.sync()
-        wt, wc = oracle.local_nbnn(ref, labels, C, q, np.array([0, 100, 300]), 10)
+        cd3, cj3 = oracle.knn_coarse(ref, q3, 11, 24)
+        assert np.array_equal(d3.cpu().numpy(), cd3) and np.array_equal(f3.cpu().numpy(), cj3)
+        t, c = ix.lnbnn_classify(qd, dev(np.array([0, 50, 120], dtype=np.int64)), 10)
+        ix.sync()
+        wt, wc = oracle.local_nbnn(ref, labels, C, q, np.array([0, 50, 120]), 10)
         assert np.array_equal(t.cpu().numpy(), wt) and np.array_equal(c.cpu().numpy(), wc)
