@@ -640,7 +640,9 @@ struct Work {
   int group;
 };
 
-template <class Fmt, class Epilogue, int QT>
+// Claim: the claimed-chunk form (Work::group > 0), a separate instantiation
+// so that the split form's kernels carry none of its code.
+template <class Fmt, class Epilogue, int QT, bool Claim>
 __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1)
     tc_scan_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_qe,
                    const __grid_constant__ CUtensorMap tmap_r, const __grid_constant__ CUtensorMap tmap_re, int64_t m,
@@ -716,7 +718,8 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
     *w = item_slot[slot];
     return true;
   };
-  const bool chunked = work.group > 0;
+  static_assert(!Claim || (QT == 1 && Epilogue::kClaimsChunks), "the claimed-chunk form: one query tile per CTA, kNN lists");
+  constexpr bool chunked = Claim;
   auto item_tiles = [&](int64_t w, int64_t* m0, int64_t* j_begin) -> int {
     const int64_t x = chunked ? (int64_t)blockIdx.x / work.group : w % work.T;
     const int64_t y = chunked ? w : w / work.T;
@@ -940,8 +943,8 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
       }
       return true;
     };
-    if constexpr (Epilogue::kClaimsChunks) {
-      if (chunked) {
+    if constexpr (Claim) {
+      {
         // claimed-chunk form: one query-tile group and one set of lists for
         // the whole launch (list = this CTA's rank in the group's CTAs x the
         // lists per CTA), written once every claimed chunk is scanned
@@ -1139,20 +1142,38 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const voi
     grid = work.T * sched.group;
   }
   if (work.n_items > (int64_t)INT32_MAX || grid > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
-  tc_scan_kernel<Fmt, Epilogue, QT>
+  if constexpr (QT == 1 && Epilogue::kClaimsChunks) {
+    if (work.group > 0) {
+      tc_scan_kernel<Fmt, Epilogue, QT, true>
+          <<<(unsigned)grid, threads_for(Epilogue::kWarpsPerQuarter, QT), LayoutOf<Fmt, Epilogue, QT>::kSmemBytes,
+             s>>>(tq, tqe, tr, tre, m, n_ref, work, o, dev_err, stats);
+      return cudaGetLastError();
+    }
+  }
+  if (work.group > 0) return cudaErrorInvalidValue;
+  tc_scan_kernel<Fmt, Epilogue, QT, false>
       <<<(unsigned)grid, threads_for(Epilogue::kWarpsPerQuarter, QT), LayoutOf<Fmt, Epilogue, QT>::kSmemBytes, s>>>(
           tq, tqe, tr, tre, m, n_ref, work, o, dev_err, stats);
   return cudaGetLastError();
 }
 
-template <class Fmt, class Epilogue, int QT>
-cudaError_t prepare_one() {
+template <class Fmt, class Epilogue, int QT, bool Claim>
+cudaError_t prepare_kernel() {
   cudaFuncAttributes a;
-  cudaError_t e = cudaFuncGetAttributes(&a, tc_scan_kernel<Fmt, Epilogue, QT>);
+  cudaError_t e = cudaFuncGetAttributes(&a, tc_scan_kernel<Fmt, Epilogue, QT, Claim>);
   if (e != cudaSuccess) return e;
   if (a.numRegs > max_regs_for(Epilogue::kWarpsPerQuarter, QT)) return cudaErrorInvalidKernelImage;
-  return cudaFuncSetAttribute(tc_scan_kernel<Fmt, Epilogue, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(tc_scan_kernel<Fmt, Epilogue, QT, Claim>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)LayoutOf<Fmt, Epilogue, QT>::kSmemBytes);
+}
+
+template <class Fmt, class Epilogue, int QT>
+cudaError_t prepare_one() {
+  cudaError_t e = prepare_kernel<Fmt, Epilogue, QT, false>();
+  if constexpr (QT == 1 && Epilogue::kClaimsChunks) {
+    if (e == cudaSuccess) e = prepare_kernel<Fmt, Epilogue, QT, true>();
+  }
+  return e;
 }
 
 // One list kind's kernel for the tile shape the schedule asks for (two query

@@ -360,7 +360,7 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, ScanKind kind, int sp
   const bool claim_kind = kind != ScanKind::Nbnn && (K1 <= kTcCoarseRegListMax || K1 > kTcWideRegListMax) &&
                           (kind == ScanKind::Coarse ? T * 8 <= P : T == 1);
   const int64_t ref_tiles = (ix->n_ref + kTcRefTile - 1) / kTcRefTile;
-  p.group = splits <= 0 && T < P && claim_kind && o.persistent != 0 && o.bound_per_tile != 0
+  p.group = splits <= 0 && T < P && p.qt == 1 && claim_kind && o.persistent != 0 && o.bound_per_tile != 0
                 // chunks of >= 4 tiles each, and no more lists than the split
                 // form may write (workspaces are sized for that)
                 ? (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(P / T, ref_tiles / 4),
