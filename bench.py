@@ -666,18 +666,20 @@ def list_kind(K1: int) -> int:
 
 
 def kernel_name(local: bool, shortlist, k: int, plan: dict | None = None) -> str:
-    """The search kernel a launch runs: operand format, epilogue (list kind)
-    and query tiles per CTA, as in the profiler's kernel names."""
+    """The search kernel a launch runs: operand format, epilogue (list kind),
+    query tiles per CTA and whether it claims reference chunks, as in the
+    profiler's kernel names."""
     qt = (plan or {}).get("tile_m", 128) // 128
+    claim = int((plan or {}).get("chunked", 0))
     if not local:
-        return f"tc_scan_kernel<FmtBf16, NbnnEpilogue, {qt}>"
+        return f"tc_scan_kernel<FmtBf16, NbnnEpilogue, {qt}, 0>"
     K1 = shortlist or k + 1
     fmt = "FmtE4m3" if shortlist else "FmtBf16"
     if plan and plan.get("list_storage") == "shared memory":
         epi = "KnnSmemEpilogue<64>"
     else:
         epi = f"KnnEpilogue<{list_kind(K1)}>"
-    return f"tc_scan_kernel<{fmt}, {epi}, {qt}>"
+    return f"tc_scan_kernel<{fmt}, {epi}, {qt}, {claim}>"
 
 
 def scan_roofline(prof, n_ref, M, peaks, peak_src, local, shortlist, k: int = 10, plan: dict | None = None) -> dict:

@@ -22,22 +22,24 @@ def test_scan_roofline_arithmetic():
     assert abs(r["achieved"] - flops / 1.0 / 1e12) < 1e-9
     assert abs(r["frac"] - r["achieved"] / 1000.0) < 1e-12
     assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
-    assert r["kernel"] == "tc_scan_kernel<FmtBf16, KnnEpilogue<16>, 1>"
+    assert r["kernel"] == "tc_scan_kernel<FmtBf16, KnnEpilogue<16>, 1, 0>"
     f = bench.scan_roofline(prof, 1_000_000, 500_000, peaks, "measured", True, 32, plan={"tile_m": 256})
-    assert f["peak"] == 2000.0 and f["kernel"] == "tc_scan_kernel<FmtE4m3, KnnEpilogue<32>, 2>"
-    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 24)["kernel"].endswith("KnnEpilogue<24>, 1>")
+    assert f["peak"] == 2000.0 and f["kernel"] == "tc_scan_kernel<FmtE4m3, KnnEpilogue<32>, 2, 0>"
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 24)["kernel"].endswith("KnnEpilogue<24>, 1, 0>")
     smem = {"tile_m": 128, "list_storage": "shared memory"}
-    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 64, plan=smem)["kernel"].endswith("KnnSmemEpilogue<64>, 1>")
-    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 128)["kernel"].endswith("KnnEpilogue<0>, 1>")
-    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, None, 20)["kernel"].endswith("<FmtBf16, KnnEpilogue<24>, 1>")
-    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, None, 100)["kernel"].endswith("<FmtBf16, KnnEpilogue<0>, 1>")
-    assert bench.scan_roofline(prof, 10, 10, peaks, "x", False, None)["kernel"].endswith("NbnnEpilogue, 1>")
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 64, plan=smem)["kernel"].endswith("KnnSmemEpilogue<64>, 1, 0>")
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 128)["kernel"].endswith("KnnEpilogue<0>, 1, 0>")
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, None, 20)["kernel"].endswith("<FmtBf16, KnnEpilogue<24>, 1, 0>")
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, None, 100)["kernel"].endswith("<FmtBf16, KnnEpilogue<0>, 1, 0>")
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", False, None)["kernel"].endswith("NbnnEpilogue, 1, 0>")
+    chunk = {"tile_m": 128, "chunked": 1}  # the claimed-chunk instantiation
+    assert bench.scan_roofline(prof, 10, 10, peaks, "x", True, 24, plan=chunk)["kernel"].endswith("KnnEpilogue<24>, 1, 1>")
 
 
 def test_traffic_lookup_matches_committed_capture():
     with open(bench.TRAFFIC_FILE) as f:
         t = json.load(f)
-    name = "tc_scan_kernel<FmtBf16, KnnEpilogue<16>, 1>"
+    name = "tc_scan_kernel<FmtBf16, KnnEpilogue<16>, 1, 0>"
     k = t["kernels"][name]
     got = bench.traffic_per_launch(name, k["query_rows"], k["n_ref"])
     if t["kernel_hash"] == bench.kernel_hash():
