@@ -333,7 +333,7 @@ struct KnnEpilogue {
         K1(o.K1),
         out(o.lists + ((int64_t)list * o.stride + (act ? row : 0)) * o.K1) {
     L.init(K1);
-    if (rthr) shared = __ldcg(rthr);  // a bound published before this list started (a probe, another split)
+    if (rthr && !per_tile) shared = __ldcg(rthr);
   }
   static constexpr int32_t kNoBound = 0x7F7F7F7F;  // the word's initial value: above every distance
   // One 32-column group: one compare of the group's minimum bit pattern (mn,
@@ -636,10 +636,8 @@ struct Work {
   // group, CTA c the group c / group; each keeps that group's query tiles
   // and its lists for the whole launch and claims reference chunks of
   // split_len rows, in increasing order, from the group's counter
-  // queue[c / group]; n_items is then the number of chunks, chunk w
-  // starting at row w * chunk_stride.
+  // queue[c / group]; n_items is then the number of chunks.
   int group;
-  int64_t chunk_stride;
 };
 
 // Claim: the claimed-chunk form (Work::group > 0), a separate instantiation
@@ -726,7 +724,7 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
     const int64_t x = chunked ? (int64_t)blockIdx.x / work.group : w % work.T;
     const int64_t y = chunked ? w : w / work.T;
     *m0 = x * (int64_t)(kBM * QT);
-    *j_begin = y * (chunked ? work.chunk_stride : work.split_len);
+    *j_begin = y * work.split_len;
     const int64_t j_end = min(*j_begin + work.split_len, n_ref);
     return stale_timeout ? 0 : (int)((j_end - *j_begin + kTileN - 1) / kTileN);
   };
@@ -1128,7 +1126,6 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const voi
   work.split_len = split_len;
   work.queue = sched.persistent_ctas > 0 ? sched.queue : nullptr;
   work.group = 0;
-  work.chunk_stride = 0;
   ScanOut o = out;
   o.done = splits > 1 ? sched.done : nullptr;
   o.T = work.T;
@@ -1141,9 +1138,7 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const voi
       return cudaErrorInvalidValue;
     work.group = sched.group;
     work.queue = sched.queue;
-    work.chunk_stride = sched.chunk_stride > 0 ? sched.chunk_stride : split_len;
-    if (work.chunk_stride % kTcRefTile != 0 || work.chunk_stride < split_len) return cudaErrorInvalidValue;
-    work.n_items = (n_ref + work.chunk_stride - 1) / work.chunk_stride;
+    work.n_items = (n_ref + split_len - 1) / split_len;
     grid = work.T * sched.group;
   }
   if (work.n_items > (int64_t)INT32_MAX || grid > (int64_t)INT32_MAX) return cudaErrorInvalidValue;

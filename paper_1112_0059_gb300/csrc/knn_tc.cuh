@@ -85,10 +85,6 @@ struct TcSched {
   // per CTA lists per query row.  kNN register lists and heaps only; never
   // with `done`.
   int group = 0;
-  // The claimed-chunk form's reference rows from one chunk's start to the
-  // next (0: chunk length, the chunks back to back).  A larger stride scans
-  // a sample: the probe that publishes every row's bound before the scan.
-  int64_t chunk_stride = 0;
 };
 
 // Split-N schedule of one scan launch over T query-tile groups (qt 128-row

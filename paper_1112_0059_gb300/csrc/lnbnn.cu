@@ -226,10 +226,6 @@ enum class ScanKind { Exact, Coarse, Nbnn };
 // Reference operand bytes a scan streams per reference row.
 int64_t op_row_bytes(ScanKind k) { return k == ScanKind::Coarse ? kDim + 2 * kExt : 2 * (kDim + kExt); }
 
-// The FP8 coarse pass's probe before a claimed-chunk scan samples one
-// reference tile in this many.
-constexpr int64_t kProbeStrideTiles = 32;
-
 // Reference bytes one split may stream for the CTAs running at the same time
 // to find every tile in L2 (129 MB), with room for the next split and the
 // other traffic.
@@ -516,23 +512,6 @@ lnbnn_status run_knn_fp8(lnbnn_index* ix, Scratch& scratch, const uint8_t* q, in
   CK(p.clear(ws, s));
   prof.launched(1);
   prof.mark(1);
-  if (p.group > 1 && (ix->n_ref + kTcRefTile - 1) / kTcRefTile >= 64 * kProbeStrideTiles) {
-    // The probe: the same claimed-chunk launch over one reference tile in
-    // kProbeStrideTiles, spread over the whole index, publishes every row's
-    // bound before the scan.  Chunks are claimed in index order, and a
-    // query whose own class lies late in a class-sorted index would
-    // otherwise scan all the far classes with a loose bound, filling
-    // shortlists from columns that cannot stay.  Any list's K1-th distance
-    // over real columns bounds the row's K1-th from above, so the sample's
-    // bound is valid; its lists land in the scan's buffer, which the scan
-    // then overwrites in full.
-    TcSched probe = sched;
-    probe.chunk_stride = kProbeStrideTiles * kTcRefTile;
-    CK(launch_coarse_tc(ix->tc, qf8, qext, m, p.m_pad, ix->n_ref, p.splits, kTcRefTile, M1, part, p.m_pad, row_thr,
-                        ix->dev_err, nullptr, nullptr, probe, s));
-    CK(p.clear(ws, s));  // the chunk counters again, for the scan
-    prof.launched(1);
-  }
   CK(launch_coarse_tc(ix->tc, qf8, qext, m, p.m_pad, ix->n_ref, p.splits, p.split_len, M1, part, p.m_pad,
                       p.splits > 1 ? row_thr : nullptr, ix->dev_err, ix->prof_on ? ix->prof_stats : nullptr,
                       ix->gate, sched, s));
