@@ -287,12 +287,16 @@ LNBNN_API lnbnn_status lnbnn_classify_fp8_ws(lnbnn_index *index, lnbnn_workspace
  * 4 (lists of 17..32 entries) or 8 (heaps) for the exact scan; the splits of
  * a row then run one after another, and each starts from the row's lists of
  * the previous split when that split has finished (the results never depend
- * on whether it has).  A launch with fewer query tiles than SMs runs the FP8
- * coarse pass over twice the modelled split count (capped at four waves of
- * items) on a persistent grid: on a class-sorted index the few splits that
- * hold a query's own class do most of the shortlist inserts, and shorter
- * items with the rest drained around them keep them from setting the
- * launch's time.  lnbnn_autotune times about
+ * on whether it has).  A launch of few query tiles with an automatic split
+ * count takes the claimed-chunk form instead of splits (the FP8 coarse pass
+ * while there are at least 8 SMs per query tile, the exact scan for a lone
+ * query tile; lists of up to 32 entries or heaps): each of P / T CTAs per
+ * query tile keeps that tile's lists for the whole launch and claims short
+ * reference chunks, in increasing order, from a counter the tile's CTAs
+ * share, so that the reference ranges holding a query's own class, where
+ * most list inserts fall on a class-sorted index, are shared by whichever
+ * CTAs are free (lnbnn_plan_search reports chunked = 1; `splits` is then the
+ * CTAs per query tile and split_len the chunk length).  lnbnn_autotune times about
  * thirty search launches of 1 to 64 query tiles (query rows copied from the
  * index's own references) with several split counts and two list lengths
  * (k1 = 11 and 51) on `stream` and fits a, b, c, e by least squares; then, on
