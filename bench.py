@@ -207,19 +207,38 @@ def measured_peaks() -> tuple[dict, str]:
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def traffic_per_launch(kernel: str, n_query_rows: int, n_ref: int) -> float | None:
-    """DRAM bytes of one launch of a search kernel from a committed ncu capture
-    of a smaller case, scaled by query rows x references (an upper bound: a
-    larger launch reuses L2 more); None if the kernel changed since or was not
-    captured."""
+def _traffic_entry(kernel: str) -> dict | None:
     if not os.path.exists(TRAFFIC_FILE):
         return None
     with open(TRAFFIC_FILE) as f:
         t = json.load(f)
     if t.get("kernel_hash") != kernel_hash() or kernel not in t.get("kernels", {}):
         return None
-    k = t["kernels"][kernel]
+    return t["kernels"][kernel]
+
+
+def traffic_per_launch(kernel: str, n_query_rows: int, n_ref: int) -> float | None:
+    """DRAM bytes of one launch of a search kernel from a committed ncu capture:
+    the capture's own figure for a launch of the same size, else scaled by
+    query rows x references (from a smaller case an upper bound: a larger
+    launch reuses L2 more); None if the kernel changed since or was not
+    captured."""
+    k = _traffic_entry(kernel)
+    if k is None:
+        return None
     return k["dram_bytes"] * (n_query_rows * n_ref) / (k["query_rows"] * k["n_ref"])
+
+
+def traffic_note(kernel: str, n_query_rows: int, n_ref: int) -> str:
+    """Where roofline.traffic comes from."""
+    k = _traffic_entry(kernel)
+    if k is None:
+        return "no ncu capture of the current kernel sources"
+    if (k["query_rows"], k["n_ref"]) == (n_query_rows, n_ref):
+        return ("ncu one-pass capture of this launch (dram__bytes_read.sum + dram__bytes_write.sum); "
+                "profiles/knn_tc_traffic.json")
+    return (f"ncu DRAM bytes of a launch of {k['query_rows']:,} query rows x {k['n_ref']:,} references scaled by "
+            "query rows x references; profiles/knn_tc_traffic.json")
 
 
 def max_over_ranks(x: float, device=None) -> float:
@@ -359,8 +378,7 @@ def run_ours(args, w):
     if plan:
         roofline["schedule"] = plan
     roofline["traffic"] = traffic_per_launch(roofline["kernel"], M, w.n_ref)
-    roofline["traffic_note"] = ("ncu DRAM bytes of a 101-class, 20-image launch scaled by query rows x references "
-                                "(an upper bound; profiles/knn_tc_traffic.json)")
+    roofline["traffic_note"] = traffic_note(roofline["kernel"], M, w.n_ref)
 
     e2e = None
     if not args.no_e2e:
@@ -404,6 +422,7 @@ def run_ours(args, w):
                                                    index.plan_search(M, m_short, fp8=True)),
                          "gpu_launches": int(prof8["kernel_launches"])}
             fp8_block["roofline"]["traffic"] = traffic_per_launch(fp8_block["roofline"]["kernel"], M, w.n_ref)
+            fp8_block["roofline"]["traffic_note"] = traffic_note(fp8_block["roofline"]["kernel"], M, w.n_ref)
         index.sync()
         fp8_block.update(fp8_accuracy(index, q_d, q, ref, k, m_short, t_x, c_x, t_f, c_f, args.recall_rows,
                                       args.oracle_recall_rows if rank == 0 and world == 1 else 0))

@@ -49,6 +49,11 @@ def test_traffic_lookup_matches_committed_capture():
     else:  # sources changed since the capture: no stale number is reported
         assert got is None
     assert bench.traffic_per_launch("no such kernel", 750000, 11520000) is None
+    assert bench.traffic_note("no such kernel", 750000, 11520000).startswith("no ncu capture")
+    if t["kernel_hash"] == bench.kernel_hash():
+        # the capture's own size: its figure as measured; another size: scaled
+        assert "this launch" in bench.traffic_note(name, k["query_rows"], k["n_ref"])
+        assert "scaled" in bench.traffic_note(name, k["query_rows"] // 2, k["n_ref"])
 
 
 def test_measured_peaks_and_workload_config():
