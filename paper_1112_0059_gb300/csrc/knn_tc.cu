@@ -51,8 +51,6 @@
 // device error word, drains what it issued and returns.
 #include <cudaTypedefs.h>
 
-#include <cmath>
-
 #include "knn_tc.cuh"
 #include "sm103.cuh"
 #include "topk.cuh"
@@ -636,19 +634,10 @@ struct Work {
   // 0: work items are (query-tile group, reference split) pairs.  > 0 (the
   // claimed-chunk form, persistent): `group` CTAs serve each query-tile
   // group, CTA c the group c / group; each keeps that group's query tiles
-  // and its lists for the whole launch and claims reference chunks, in
-  // increasing order, from the group's counter queue[c / group]; n_items is
-  // then the number of chunks.  Chunks are g_unit tiles while more than
-  // half the references remain, then shrink as the scan proceeds (guided
-  // self-scheduling) down to split_len rows, so the last chunks are short and
-  // a costly stretch of references met late is spread over many CTAs; chunk
-  // c starts at reference tile
-  //   c * g_unit                                   for c < g_cA,
-  //   g_sA + R - ceil(R gq^(c - g_cA)), R = NT - g_sA  for c < g_cA + g_jB,
-  //   g_sB + (c - g_cA - g_jB) * split_len tiles      from then on.
+  // and its lists for the whole launch and claims reference chunks of
+  // split_len rows, in increasing order, from the group's counter
+  // queue[c / group]; n_items is then the number of chunks.
   int group;
-  double gq;
-  int64_t g_unit, g_cA, g_sA, g_jB, g_sB;
 };
 
 // Claim: the claimed-chunk form (Work::group > 0), a separate instantiation
@@ -735,19 +724,6 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
     const int64_t x = chunked ? (int64_t)blockIdx.x / work.group : w % work.T;
     const int64_t y = chunked ? w : w / work.T;
     *m0 = x * (int64_t)(kBM * QT);
-    if constexpr (chunked) {
-      const int64_t nt = (n_ref + kTileN - 1) / kTileN;
-      const int64_t min_tiles = work.split_len / kTileN;
-      auto start = [&](int64_t c) -> int64_t {
-        if (c < work.g_cA) return c * work.g_unit;
-        const int64_t r = nt - work.g_sA;
-        if (c < work.g_cA + work.g_jB) return work.g_sA + r - (int64_t)ceil((double)r * pow(work.gq, (double)(c - work.g_cA)));
-        return min(nt, work.g_sB + (c - work.g_cA - work.g_jB) * min_tiles);
-      };
-      const int64_t t0 = start(y), t1 = start(y + 1);
-      *j_begin = t0 * kTileN;
-      return stale_timeout || t1 <= t0 ? 0 : (int)(t1 - t0);
-    }
     *j_begin = y * work.split_len;
     const int64_t j_end = min(*j_begin + work.split_len, n_ref);
     return stale_timeout ? 0 : (int)((j_end - *j_begin + kTileN - 1) / kTileN);
@@ -1150,8 +1126,6 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const voi
   work.split_len = split_len;
   work.queue = sched.persistent_ctas > 0 ? sched.queue : nullptr;
   work.group = 0;
-  work.gq = 0.0;
-  work.g_unit = work.g_cA = work.g_sA = work.g_jB = work.g_sB = 0;
   ScanOut o = out;
   o.done = splits > 1 ? sched.done : nullptr;
   o.T = work.T;
@@ -1164,23 +1138,7 @@ cudaError_t launch_scan(const CUtensorMap& tr, const CUtensorMap& tre, const voi
       return cudaErrorInvalidValue;
     work.group = sched.group;
     work.queue = sched.queue;
-    // chunk sizes: about an eighth of a CTA's share while more than half the
-    // references remain, then R / (4 group) tiles while R tiles remain, down
-    // to split_len rows
-    const int64_t nt = (n_ref + Shape<QT>::kTileN - 1) / Shape<QT>::kTileN;
-    const int64_t min_tiles = split_len / Shape<QT>::kTileN;
-    if (min_tiles < 1 || split_len % Shape<QT>::kTileN != 0) return cudaErrorInvalidValue;
-    const int64_t g4 = 4 * (int64_t)sched.group;
-    work.g_unit = std::max<int64_t>(min_tiles, (nt + 2 * g4 - 1) / (2 * g4));
-    work.g_cA = std::max<int64_t>(0, (nt - g4 * work.g_unit + work.g_unit - 1) / work.g_unit);
-    work.g_sA = std::min<int64_t>(nt, work.g_cA * work.g_unit);
-    const int64_t r = nt - work.g_sA;
-    work.gq = 1.0 - 1.0 / (double)g4;
-    const double r_end = (double)(g4 * min_tiles);  // where chunks reach the smallest
-    work.g_jB = (double)r > r_end ? (int64_t)std::ceil(std::log(r_end / (double)r) / std::log(work.gq)) : 0;
-    work.g_sB = work.g_sA + (work.g_jB > 0 ? r - (int64_t)std::ceil((double)r * std::pow(work.gq, (double)work.g_jB)) : 0);
-    if (work.g_sB < work.g_sA || work.g_sB > nt) return cudaErrorInvalidValue;
-    work.n_items = work.g_cA + work.g_jB + (nt - work.g_sB + min_tiles - 1) / min_tiles;
+    work.n_items = (n_ref + split_len - 1) / split_len;
     grid = work.T * sched.group;
   }
   if (work.n_items > (int64_t)INT32_MAX || grid > (int64_t)INT32_MAX) return cudaErrorInvalidValue;

@@ -367,7 +367,9 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, ScanKind kind, int sp
                                                               max_splits_for(T, ix->n_ref, P, max_splits(ix))))
                 : 0;
   if (p.group > 0) {
-    p.split_len = 4 * kTcRefTile;  // the smallest chunk: the scan's chunks shrink to it (guided sizes)
+    const int64_t tiles = ref_tiles;
+    const int64_t chunk_tiles = std::max<int64_t>(4, (tiles + 8 * (int64_t)p.group - 1) / (8 * (int64_t)p.group));
+    p.split_len = chunk_tiles * kTcRefTile;  // about eight chunks per CTA
     p.splits = p.group;
     p.persistent = true;
     p.bound_per_tile = true;
