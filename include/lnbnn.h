@@ -304,7 +304,9 @@ LNBNN_API lnbnn_status lnbnn_classify_fp8_ws(lnbnn_index *index, lnbnn_workspace
  * four large-batch forms of the exact scan (k1 = 11) and, when the index has
  * its FP8 operand, of the coarse pass (k1 = 32): one or two query tiles per
  * CTA, one CTA per item or persistent; the fastest form of each is then used
- * for launches of at least a full wave of query tiles.  It keeps all of this
+ * for launches of at least a full wave of query tiles (without tuning: one
+ * query tile per CTA for the exact and NBNN scans, two for the coarse pass,
+ * one CTA per item).  It keeps all of this
  * in the index; it synchronises `stream`, allocates and frees its own
  * scratch, and changes no result (every schedule gives bit-identical output),
  * only speed.  Call it outside stream capture.  out (may be NULL) receives

@@ -653,6 +653,13 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
   constexpr int kTileN = Sh::kTileN;
   using L = LayoutOf<Fmt, Epilogue, QT>;
   constexpr int kStages = L::kStages;
+  // The epilogue learns that a tile's MMAs are done from the commit that
+  // frees the tile's last ring stage, where that stage is not reused within
+  // two tiles (its next phase then needs this tile's accumulator back, so a
+  // parity wait cannot miss a phase); a separate accumulator-full commit per
+  // tile cost the MMA thread 2-10% of a step.  With a two-stage ring the
+  // stage comes back within a tile and the separate commit stays.
+  constexpr bool kStageSignalsTile = kStages >= 2 * KC;
   constexpr int kEpiPerQuarter = Epilogue::kWarpsPerQuarter;  // epilogue warps per TMEM lane quarter
   constexpr int kEpiWarps = 4 * kEpiPerQuarter;
   constexpr int kEpiCols = kAccCols / kEpiPerQuarter;  // accumulator columns per epilogue warp
@@ -882,7 +889,9 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
             }
             mma_commit(bars.empty(s));  // the producer may refill this stage
           }
-          if (ok) mma_commit(bars.tfull(b));
+          if constexpr (!kStageSignalsTile) {
+            if (ok) mma_commit(bars.tfull(b));
+          }
         }
         tiles_done += ntiles;
         if (!chunked) mma_commit(bars.aempty());  // the query tiles may be replaced once these MMAs are done
@@ -909,8 +918,14 @@ __global__ void __launch_bounds__(threads_for(Epilogue::kWarpsPerQuarter, QT), 1
     auto scan_tiles = [&](auto& e, int ntiles, int64_t col_base) -> bool {
       for (int t = 0; t < ntiles; ++t, ++tg) {
         const int b = tg & 1;
-        const uint32_t use = (uint32_t)(tg >> 1);
-        if (!mbar_wait(bars.tfull(b), use & 1u, kWaitLimitNs, abort_flag)) {
+        bool done;
+        if constexpr (kStageSignalsTile) {
+          const int itl = tg * KC + KC - 1;  // the tile's last K-chunk
+          done = mbar_wait(bars.empty(itl % kStages), (uint32_t)(itl / kStages) & 1u, kWaitLimitNs, abort_flag);
+        } else {
+          done = mbar_wait(bars.tfull(b), (uint32_t)(tg >> 1) & 1u, kWaitLimitNs, abort_flag);
+        }
+        if (!done) {
           flag_timeout(abort_flag, dev_err);
           return false;
         }

@@ -52,7 +52,7 @@ struct lnbnn_index {
   SplitModel split_model;  // split-N schedule (defaults, or fitted by lnbnn_autotune)
   lnbnn_schedule sched{0, 0, -1, -1};  // lnbnn_set_schedule: fixed choices (0 / -1: automatic)
   // large-batch forms per scan kind (exact, coarse, NBNN), chosen by lnbnn_autotune
-  int auto_qt[3] = {1, 1, 1};
+  int auto_qt[3] = {1, 2, 1};
   int auto_persistent[3] = {0, 0, 0};
   const uint32_t* gate = nullptr;  // lnbnn_set_start_gate: search kernels wait for *gate != 0
   // optional device-time profile (lnbnn_profile_enable)
@@ -240,11 +240,12 @@ bool l2_splits_for(ScanKind k) { return k == ScanKind::Coarse; }
 // The large-batch form of a scan kind (query tiles per CTA, persistent grid)
 // for launches of at least a full wave of query tiles, unless lnbnn_autotune
 // measured another form faster on this index.  Defaults, measured on the
-// 256-class data (750k query rows): one query tile per CTA for every scan
-// (exact 1,356 cycles per step against 1,511 with two; NBNN 1,369 against
-// 1,526; FP8 shortlist 24 with its lists carried across the 37 L2-sized
-// splits 934 against 945 ms with two query tiles and 19 splits); one CTA per
-// work item (persistent grids within 0.2%).
+// 256-class data (750k query rows): one query tile per CTA for the exact and
+// NBNN scans (exact 1,229 ms a classify call against 1,263 with two, whose
+// steps take fewer cycles, 1,305 against 1,341, at a lower SM clock); two
+// for the FP8 coarse pass (shortlist 24, lists carried across the 37
+// L2-sized splits: 860 against 899 ms); one CTA per work item (persistent
+// grids within 0.2%).
 int auto_query_tiles(const lnbnn_index* ix, ScanKind k, int64_t T1) {
   return T1 >= ix->sm_count ? ix->auto_qt[(int)k] : 1;
 }
