@@ -305,8 +305,10 @@ LNBNN_API lnbnn_status lnbnn_classify_fp8_ws(lnbnn_index *index, lnbnn_workspace
  * its FP8 operand, of the coarse pass (k1 = 32): one or two query tiles per
  * CTA, one CTA per item or persistent; the fastest form of each is then used
  * for launches of at least a full wave of query tiles (without tuning: one
- * query tile per CTA for the exact and NBNN scans, two for the coarse pass,
- * one CTA per item).  It keeps all of this
+ * query tile per CTA for the NBNN scan and the exact scan of lists of up to
+ * 16 entries, two for longer exact lists and the coarse pass, one CTA per
+ * item; longer exact lists take two query tiles after tuning too).  It keeps
+ * all of this
  * in the index; it synchronises `stream`, allocates and frees its own
  * scratch, and changes no result (every schedule gives bit-identical output),
  * only speed.  Call it outside stream capture.  out (may be NULL) receives

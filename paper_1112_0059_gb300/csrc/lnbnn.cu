@@ -246,8 +246,15 @@ bool l2_splits_for(ScanKind k) { return k == ScanKind::Coarse; }
 // for the FP8 coarse pass (shortlist 24, lists carried across the 37
 // L2-sized splits: 860 against 899 ms); one CTA per work item (persistent
 // grids within 0.2%).
-int auto_query_tiles(const lnbnn_index* ix, ScanKind k, int64_t T1) {
-  return T1 >= ix->sm_count ? ix->auto_qt[(int)k] : 1;
+// The exact scan with lists longer than 16 entries takes two query tiles
+// per CTA whatever the tuned k+1 = 11 form is: one list per row and split
+// instead of two column halves halves the list work (256-class data, 750k
+// query rows: k = 20 1,277 against 1,303 ms, k = 100 with heaps 2,225
+// against 3,571 ms).
+int auto_query_tiles(const lnbnn_index* ix, ScanKind k, int64_t T1, int K1) {
+  if (T1 < ix->sm_count) return 1;
+  if (k == ScanKind::Exact && K1 > kTcRegListMax) return 2;
+  return ix->auto_qt[(int)k];
 }
 bool auto_persistent(const lnbnn_index* ix, ScanKind k, int64_t T1) {
   return T1 >= ix->sm_count && ix->auto_persistent[(int)k] == 1;
@@ -338,7 +345,7 @@ KnnPlan plan_knn(const lnbnn_index* ix, int64_t m, int K1, ScanKind kind, int sp
   p.K1 = K1;
   const int64_t T1 = p.m_pad / kTcQueryTile;
   const bool qt2_ok = kind == ScanKind::Nbnn || K1 <= kTcCoarseRegListMax || K1 > kTcWideRegListMax;
-  p.qt = qt2_ok && (o.query_tiles == 2 || (o.query_tiles == 0 && auto_query_tiles(ix, kind, T1) == 2)) ? 2 : 1;
+  p.qt = qt2_ok && (o.query_tiles == 2 || (o.query_tiles == 0 && auto_query_tiles(ix, kind, T1, K1) == 2)) ? 2 : 1;
   const int64_t T = (T1 + p.qt - 1) / p.qt;
   if (splits <= 0) splits = o.splits;
   // The claimed-chunk form for launches of fewer query-tile groups than SMs
