@@ -6,9 +6,10 @@ k = 10).
 Each search runs over all 750,000 query rows on the GPU, so the list kind and
 schedule are the full-size ones (asserted through lnbnn_plan_search); the
 oracle then checks sampled rows (kNN) or whole images (class totals), bit for
-bit.  The survey's identity I2 (Local NBNN totals = sum over descriptors of
-min(0, NN_C - dist_B)) ties the NBNN scan, the kNN scan and the Local NBNN
-update together over 50 whole images.
+bit.  An identity of Algorithm 2's update (Local NBNN totals = sum over
+descriptors of min(0, NN_C - dist_B): a class absent from the k nearest has
+NN_C >= dist_B) ties the NBNN scan, the kNN scan and the Local NBNN update
+together over 50 whole images.
 """
 import numpy as np
 import pytest
@@ -93,7 +94,7 @@ def test_whole_images_local_and_nbnn(full):
     assert (lt <= 0).all() and (nt >= 0).all()
 
 
-def test_identity_i2_over_50_images(full):
+def test_local_update_identity_over_50_images(full):
     """Local totals == sum_i min(0, NN_C(i) - dist_B(i)) with NN_C from the NBNN
     scan (one descriptor per image) and dist_B the (k+1)-th distance of the kNN
     scan: three kernels' outputs tied together exactly, at full size."""
